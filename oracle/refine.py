@@ -1,0 +1,211 @@
+"""ORACLE (test infrastructure only): the refinement method, step by step, in
+plain numpy FP64, in the paper's literal form (explicit Y-hat, T-hat, V and
+E-tilde_L; the orthogonal H-hat is applied through its compact WY factors and
+never formed).
+
+Paper: Terao, Ozaki, Imamura, Ogita, "Iterative Refinement for a Subset of
+Eigenvectors of Symmetric Matrices via Matrix Multiplications".
+Readings of points the paper leaves open are marked READING and listed with
+their reasons in the design notes.
+"""
+import numpy as np
+
+U_FP64 = 2.0 ** -53          # unit roundoff of binary64 (Section 3.1.3, choice of delta)
+
+
+class SingularWY(np.linalg.LinAlgError):
+    """Algorithm 1 needs a nonsingular leading block Y_1 (Section 3.1.1)."""
+
+
+def compact_wy(Q):
+    """Algorithm 1, CompactWY(Q): Y = Q - I_{n,k}, T = -Y_1^{-T}.
+
+    Ensures (for Q with orthonormal columns) Q = (I - Y T Y^T) I_{n,k} and that
+    I - Y T Y^T is orthogonal.  T is obtained by an LU solve with partial
+    pivoting, not an explicit inverse.
+    """
+    n, k = Q.shape
+    Y = np.array(Q, dtype=np.float64, copy=True)
+    Y[np.arange(k), np.arange(k)] -= 1.0
+    Y1 = Y[:k, :k]
+    if not np.all(np.isfinite(Y1)) or np.linalg.cond(Y1) > 1.0 / (k * U_FP64):
+        raise SingularWY("leading k x k block of Y is singular to working precision")
+    T = -np.linalg.solve(Y1.T, np.eye(k))     # Y_1^T (-T) = I
+    return Y, T
+
+
+def sign_of(v):
+    """READING: sign(0) := +1 in Algorithm 2 (the paper leaves sign(0) open;
+    MATLAB's sign(0) = 0 would make the pivot q_jj - sigma_j zero)."""
+    return 1.0 if v >= 0 else -1.0
+
+
+def modified_lu(Q):
+    """Algorithm 2, modified_LU(Q): unpivoted LU of Q - Sigma with
+    sigma_j = -sign(q_jj) chosen at step j.  Returns (Y, U, sigma) with
+    Y unit lower trapezoidal (n x k), U upper triangular (k x k) and
+    Q - [diag(sigma); 0] = Y U."""
+    q = np.array(Q, dtype=np.float64, copy=True)
+    n, k = q.shape
+    sigma = np.empty(k)
+    for j in range(k):
+        sigma[j] = -sign_of(q[j, j])
+        q[j, j] -= sigma[j]
+        q[j + 1:, j] /= q[j, j]
+        q[j + 1:, j + 1:k] -= np.outer(q[j + 1:, j], q[j, j + 1:k])
+    U = np.triu(q[:k, :k])
+    Y = np.tril(q, -1)
+    Y[np.arange(k), np.arange(k)] = 1.0
+    return Y, U, sigma
+
+
+def compact_wy_lu(Q):
+    """Algorithm 3, CompactWY_LU(Q): [Y, U, Sigma] = modified_LU(Q),
+    T = -U Sigma Y_1^{-T}.
+
+    READING: with this T the WY matrix satisfies (I - Y T Y^T) I_{n,k} = Q Sigma
+    (the columns of Q with the signs sigma), which equals Q only when Sigma = I;
+    the orthogonality of I - Y T Y^T holds as stated.
+    """
+    Y, U, sigma = modified_lu(Q)
+    k = Q.shape[1]
+    Y1 = Y[:k, :k]
+    T = -(U * sigma[None, :]) @ np.linalg.solve(Y1.T, np.eye(k))   # -U Sigma Y_1^{-T}
+    return Y, T, sigma
+
+
+def sign_fix(X):
+    """The practical rule closing Section 3.1.1: the signs sigma of
+    Algorithm 2, applied once as X <- X Sigma, make Algorithm 1 applicable.
+
+    sigma depends only on the leading k x k block (the pivots of Algorithm 2
+    never read rows > k), so it is computed from that block alone.
+    READING: applied always, at the start of every refinement call, and undone
+    on exit.
+    """
+    k = X.shape[1]
+    _, _, sigma = modified_lu(X[:k, :k])
+    return sigma
+
+
+def apply_h(Y, T, B):
+    """H-hat B = B - Y (T (Y^T B)) (compact WY application, Section 3.1.2)."""
+    return B - Y @ (T @ (Y.T @ B))
+
+
+def apply_ht(Y, T, B):
+    """H-hat^T B = B - Y (T^T (Y^T B))."""
+    return B - Y @ (T.T @ (Y.T @ B))
+
+
+class StepInfo(dict):
+    __getattr__ = dict.__getitem__
+
+
+def refine_step(apply_b, Xh, delta, beta="cluster"):
+    """Algorithm 4: one refinement step X-tilde = X-hat + H-hat E-tilde_L.
+
+    apply_b(X) returns B X for the operator whose dominant eigenvectors are
+    refined (B = A, or the shifted A - alpha I of Section 5).
+    beta = "cluster": beta_ij = -x_i^T x_j / 2 (near-equal Rayleigh quotients),
+    beta = "zero":    beta_ij = 0 (after a Rayleigh--Ritz preprocessing).
+    """
+    n, k = Xh.shape
+    W = apply_b(Xh)                                     # line 1: W = A X-hat
+    Y, T = compact_wy(Xh)                               # line 2: Algorithm 1
+    alpha = np.einsum("ij,ij->j", Xh, Xh)               # line 3: alpha_j = x_j^T x_j
+    d = np.einsum("ij,ij->j", Xh, W) / alpha            # line 4: Rayleigh quotients, Eq. (Rayleigh)
+    R = W - Xh * d[None, :]                             # W - X-hat D-tilde_1
+    V = apply_ht(Y, T, R)                               # line 5: V = H-hat^T (W - X-hat D-tilde_1), Eq. (V-def)
+    E = np.empty((n, k))
+    for i in range(k):                                  # line 6: the four cases, Eqs. (Ediag), (Eoffdiag)
+        for j in range(k):
+            if i == j:
+                E[i, j] = (1.0 - alpha[i]) / 2.0
+            elif abs(d[j] - d[i]) <= delta:
+                E[i, j] = -(Xh[:, i] @ Xh[:, j]) / 2.0 if beta == "cluster" else 0.0
+            else:
+                E[i, j] = V[i, j] / (d[j] - d[i])
+    E[k:, :] = V[k:, :] / d[None, :]
+    Xt = Xh + apply_h(Y, T, E)                          # line 7: X-hat + H-hat E-tilde_L, Eq. (update-X)
+    return Xt, StepInfo(d=d, alpha=alpha, R=R, V=V, E=E, Y=Y, T=T, W=W,
+                        res_fro=float(np.linalg.norm(R)), e_fro=float(np.linalg.norm(E)))
+
+
+def normalise(X):
+    """Column normalisation after each update (Section 3.1.3, precision and
+    orthogonality)."""
+    return X / np.linalg.norm(X, axis=0)[None, :]
+
+
+def delta_threshold(norm_b, c=10.0):
+    """delta = c ||A|| u, c = 10 (Section 3.1.3, choice of delta).
+    READING: ||.|| is the norm of the refined operator B = A - alpha I,
+    bounded by ||A|| + |alpha|."""
+    return c * norm_b * U_FP64
+
+
+STOP_CORRECTION, STOP_RESIDUAL = 0, 1
+OK, E_DIVERGED, E_NOT_CONVERGED, E_NONFINITE = 0, 5, 6, 7
+
+
+def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORRECTION,
+           delta_c=10.0, beta="cluster", div_factor=10.0, div_floor=1e-4, use_sign_fix=True):
+    """Iterate Algorithm 4 with the driver choices of Section 3.1.3.
+
+    Per sweep t: R_t and E_t are computed from X_t, the update is applied and
+    the columns normalised, giving X_{t+1}.  Stopping (READING): stop with
+    X_{t+1} once ||E_t||_F <= tol (correction-size criterion) or
+    ||R_t||_F / ||A|| <= tol (backward-error criterion); tol = 0 runs exactly
+    max_iters sweeps.  Divergence (the advice closing Section 4.3.1;
+    READING): stop once ||E_t||_F >= 1 (the Neumann-series assumption
+    ||E|| < 1 of Section 3.1.2 fails) or ||E_t||_F exceeds div_factor times
+    the smallest earlier value and div_floor.  A non-finite sweep leaves the
+    last finite iterate.
+
+    Returns (X, report) with X in the caller's column signs.
+    """
+    X = np.array(X0, dtype=np.float64, order="F", copy=True)
+    k = X.shape[1]
+    sigma = sign_fix(X) if use_sign_fix else np.ones(k)
+    X = X * sigma[None, :]
+    delta = delta_threshold(norm_a + abs(shift), delta_c)
+    hist_r, hist_e = [], []
+    status, it, d = E_NOT_CONVERGED if tol > 0 else OK, 0, None
+    emin = np.inf
+    for t in range(max_iters):
+        Xn, info = refine_step(apply_b, X, delta, beta)
+        rel_r = info.res_fro / norm_a
+        if not (np.all(np.isfinite(Xn)) and np.isfinite(info.e_fro) and np.isfinite(rel_r)):
+            status = E_NONFINITE
+            break
+        hist_r.append(rel_r)
+        hist_e.append(info.e_fro)
+        d = info.d
+        X = normalise(Xn)
+        it += 1
+        crit = info.e_fro if stop == STOP_CORRECTION else rel_r
+        if tol > 0 and crit <= tol:
+            status = OK
+            break
+        if info.e_fro >= 1.0 or (info.e_fro > div_factor * emin and info.e_fro > div_floor):
+            status = E_DIVERGED
+            break
+        emin = min(emin, info.e_fro)
+    X = X * sigma[None, :]
+    return X, dict(status=status, iterations=it, d=None if d is None else d + shift,
+                   hist_res=np.array(hist_r), hist_corr=np.array(hist_e), sigma=sigma,
+                   delta=delta)
+
+
+def dense_operator(A, shift=0.0):
+    """B X = A X - shift X for a dense FP64 matrix."""
+    A = np.asarray(A)
+    return lambda X: A @ X - shift * X
+
+
+def csr_operator(row_ptr, col_idx, val, n, shift=0.0):
+    """B X = A X - shift X for a CSR matrix (scipy's sparse product as the step)."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((val, col_idx, row_ptr), shape=(n, n))
+    return lambda X: A @ X - shift * X
