@@ -1,0 +1,294 @@
+"""Benchmark: refinement sweeps per second on the dense n = 16384, k = 128
+workload (A = Q diag(lambda) Q^T, Q a product of 64 seeded Householder
+reflectors, the 128 largest-|lambda| eigenvalues separated by 1e-3 ||A||),
+through the eigref C ABI.
+
+One step = one full sweep of Algorithm 4 (product, Gram products, k x k stage,
+update, normalisation, stopping test).  Timed on the device with CUDA events
+around exactly --steps sweeps after --warmup untimed sweeps.  A (2.1 GB) is
+larger than L2, so no flush is needed between sweeps.
+
+  python bench.py [--steps K] [--warmup W] [--precision bf16|fp64]
+  python bench.py --impl reference      # the CPU oracle, same workload
+  torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas
+
+Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "refine-steps/s & % roofline at 1e-13 angle: split-precision TC vs plain FP64"
+UNIT = "refine-steps/s"
+WORKLOAD = ("dense symmetric n=16384, k=128: A = Q diag(lambda) Q^T, Q = 64 seeded Householder "
+            "reflectors, 128 largest |lambda| = 1 - 1e-3 i (random signs), graded tail 0.8*10^(-6u); "
+            "X0 = orth(fp32(q) + N(0,1e-7))")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# nominal dense rates per GPU (TFLOP/s): used only as ratios to the measured BF16 peak
+NOMINAL = {"bf16": 2250.0, "fp64": 1.25, "int8": 4500.0}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(kernel_file, precision):
+    """DRAM bytes per launch of the product kernel from the committed ncu
+    summary, or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except OSError:
+        return None
+    ent = tab.get(precision)
+    if not ent:
+        return None
+    if ent.get("source_sha256_16") != source_hash(os.path.join(ROOT, "paper_2602_23778_gb300", "csrc", kernel_file)):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def workload(seed=3000):
+    from workloads import configs as C
+    return C.config3(seed=seed)
+
+
+def max_angle(X, Q):
+    """max_j sin angle(x_j, q_j) in FP64 (absolute error ~1e-16)."""
+    Xn = X / np.linalg.norm(X, axis=0)
+    Qn = Q / np.linalg.norm(Q, axis=0)
+    c = np.sum(Xn * Qn, axis=0)
+    return float(np.max(np.linalg.norm(Xn - Qn * c[None, :], axis=0)))
+
+
+def cpu_oracle_rate(p, sweeps):
+    """The CPU oracle (as it stands) on this host: sweeps/s over a bounded sample."""
+    from oracle import refine as R
+    op = R.dense_operator(p.A)
+    X = np.asfortranarray(p.X0)
+    t0, c0 = time.perf_counter(), time.process_time()
+    R.refine(op, X, p.normA, 0.0, max_iters=sweeps)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return sweeps / wall, max(1, round(cpu / wall)), wall
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    p = workload()
+    rate_w, _, _ = cpu_oracle_rate(p, args.warmup) if args.warmup > 0 else (0, 0, 0)
+    rate, cores, wall = cpu_oracle_rate(p, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": p.n, "k": p.k, "form": "CPU oracle, paper-literal Algorithm 4"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d oracle sweeps of the full n=16384, k=128 workload (%.1f s)" % (args.steps, wall)},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="eigref", choices=["eigref", "reference"])
+    ap.add_argument("--precision", default=None, choices=["bf16", "fp64", "int8"])
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=3)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 10
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2602_23778_gb300 as eigref
+
+    precision = args.precision or "fp64"
+    if args.steps is None:
+        args.steps = 40 if precision == "fp64" else 200
+    assert args.warmup >= 3, "at least 3 warm-up sweeps"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    p = workload()
+    A = torch.from_numpy(p.A).cuda()
+    X0 = torch.from_numpy(np.ascontiguousarray(p.X0.T)).cuda().t()  # column-major n x k
+    stream = torch.cuda.Stream()
+    h = eigref.Handle(local, stream)
+    kw = dict(norm_a=p.normA, target="largest_mag", precision=precision)
+
+    def refine(X, iters, **extra):
+        return h.refine_dense(A, X, max_iters=iters, check_every=max(2, iters), **kw, **extra)
+
+    # warm-up (untimed): builds graphs, touches A, runs the same kernels
+    refine(X0.clone(), args.warmup)
+    torch.cuda.synchronize()
+
+    X = X0.clone()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        rep = refine(X, args.steps, profile=True)
+        torch.cuda.synchronize()
+        call_s = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    assert rep["iterations"] == args.steps, rep
+    ms_step = rep["sweeps_ms"] / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * 1000.0 / ms_step
+
+    pk, pk_kind = peaks()
+    n, k = p.n, p.k
+    prod_ms = rep["product_ms"] / max(1, rep["product_launches"])
+    if precision == "fp64":
+        flops = 2.0 * n * n * k
+        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        roof = {"bound": "alu", "kernel": "gemm_fp64_kernel", "peak_note":
+                "FP64 peak = measured BF16 burst x nominal FP64/BF16 ratio (1.25/2250), of %s" % pk_kind}
+        kfile = "fp64.cu"
+    else:
+        from paper_2602_23778_gb300 import sliced_info
+        info = sliced_info(precision, n, k)
+        flops = info["executed_flops"]
+        peak = pk["bf16_tflops_sustained"] if precision == "bf16" else \
+            pk["bf16_tflops_sustained"] * NOMINAL["int8"] / NOMINAL["bf16"]
+        roof = {"bound": "tensor", "kernel": info["kernel"], "peak_note": "sustained BF16, of %s" % pk_kind}
+        kfile = "sliced.cu"
+    achieved = flops / (prod_ms * 1e-3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": traffic_for(kfile, precision), "launch_ms": prod_ms,
+                 "algorithmic_flops_per_launch": flops})
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision + "-slices+f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "k": k, "form": precision, "seed": 3000,
+                      "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "setup_ms": rep["setup_ms"], "call_s": call_s, "roofline": roof,
+           "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary()}
+
+    if rank == 0 and not args.no_accuracy:
+        Xa = X0.clone()
+        # run to the residual level of the n = 8192 workload's rule, 1e-14 ||A||
+        ra = h.refine_dense(A, Xa, max_iters=600, tol=1e-14, stop="residual", check_every=50, **kw)
+        Xh = Xa.cpu().numpy()
+        out["accuracy"] = {"sweeps": ra["iterations"], "status": ra["status_string"],
+                           "final_rel_residual": ra["final_rel_residual"],
+                           "max_sin_angle": max_angle(Xh, p.Xtrue),
+                           "orth_max": float(np.abs(Xh.T @ Xh - np.eye(k)).max()),
+                           "target_angle": 1e-13}
+
+    if rank == 0 and not args.no_e2e:
+        Ah = np.ascontiguousarray(p.A)
+        Xh = np.asfortranarray(p.X0.copy())
+        t0 = time.perf_counter()
+        re = h.refine_dense(Ah, Xh, max_iters=args.steps, check_every=args.steps, **kw)
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": re["iterations"] / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": (Ah.nbytes + Xh.nbytes) / args.steps,
+                      "d2h_bytes_per_step": (Xh.nbytes + 8 * k) / args.steps,
+                      "note": "host A and X through eigref_refine_dense, copies and set-up inside the timed call"}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, wall = cpu_oracle_rate(p, args.cpu_sweeps)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "%d oracle sweeps of the same workload (%.1f s)" % (args.cpu_sweeps, wall)}
+    h.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

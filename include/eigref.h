@@ -1,0 +1,175 @@
+/*
+ * eigref -- GB300 (sm_103a) refinement of a subset of eigenvectors of a real
+ * symmetric matrix.
+ *
+ * Method: Terao, Ozaki, Imamura and Ogita, "Iterative Refinement for a Subset
+ * of Eigenvectors of Symmetric Matrices via Matrix Multiplications".  Given
+ * approximate eigenvectors X-hat (n x k, k << n) of a symmetric A, each sweep
+ * applies Algorithm 4 (Section 3.1.2): W = A X-hat, the compact-WY matrix
+ * H-hat of Algorithm 1, Rayleigh quotients (Eq. Rayleigh), the correction
+ * E-tilde_L (Eqs. Ediag, V-def, Eoffdiag), the update X-hat + H-hat E-tilde_L
+ * (Eq. update-X), then column normalisation (Section 3.1.3).
+ *
+ * C ABI.  Plain pointers and sizes, no C++ or framework types.  Every entry
+ * point returns an eigref_status; no exception crosses the boundary.
+ *
+ * Memory: matrix arguments may be device pointers (cudaMalloc, or a framework
+ * tensor's storage on the handle's device) or host pointers (pageable or
+ * pinned); the library detects which with cudaPointerGetAttributes and copies
+ * host data through its own device workspace, inside the call.  The caller
+ * owns every argument buffer; the handle owns its workspace.
+ *
+ * Layouts: A dense is n x n with leading dimension lda >= n (row i starts at
+ * A + i*lda; A is symmetric, so row- and column-major agree).  CSR A is
+ * row_ptr[n+1], col_idx[nnz] (0-based, int32), val[nnz] (FP64), and must be
+ * symmetric; column order within a row is free.  X is n x k column-major with
+ * ldx >= n: column j (an approximate eigenvector) starts at X + j*ldx.
+ *
+ * Threading: a handle is not thread-safe; all its work is issued on its
+ * stream and every entry point returns after that work has finished.
+ */
+#ifndef EIGREF_H
+#define EIGREF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eigref_ctx* eigref_handle;
+
+enum eigref_status {
+  EIGREF_OK = 0,
+  EIGREF_E_INVALID = 1,        /* bad argument; nothing was written */
+  EIGREF_E_CUDA = 2,           /* a CUDA call failed (eigref_last_error has it) */
+  EIGREF_E_NOMEM = 3,          /* workspace allocation failed */
+  EIGREF_E_SINGULAR_WY = 4,    /* Algorithm 1's Y_1 singular to working precision */
+  EIGREF_E_DIVERGED = 5,       /* correction norm grew (advice closing Section 4.3.1) */
+  EIGREF_E_NOT_CONVERGED = 6,  /* max_iters sweeps without meeting tol (tol > 0) */
+  EIGREF_E_NONFINITE = 7,      /* a sweep produced Inf/NaN; X keeps the last finite iterate */
+  EIGREF_E_TIMEOUT = 8,        /* a bounded device wait gave up */
+  EIGREF_E_UNSUPPORTED = 9     /* valid request this build does not implement */
+};
+
+/* Which eigenvectors the refinement converges to (Section 3.1 and Section 5.1).
+ * The operator refined is B = A - alpha I. */
+enum eigref_target {
+  EIGREF_LARGEST_MAG = 0,  /* k largest |lambda|, alpha = 0 (the paper's default ordering) */
+  EIGREF_LARGEST = 1,      /* k algebraically largest, alpha = (lambda_{k+1} - ||A||) / 2 */
+  EIGREF_SMALLEST = 2,     /* k algebraically smallest, alpha = (||A|| + lambda_{k+1}) / 2 (Section 5.1) */
+  EIGREF_SHIFT = 3         /* explicit alpha */
+};
+
+/* How W = B X and the Gram products are evaluated. */
+enum eigref_precision {
+  EIGREF_FP64 = 0,         /* plain FP64 on the CUDA cores */
+  EIGREF_BF16_SLICES = 1,  /* error-free BF16 slices on the tensor cores, FP32 accumulation */
+  EIGREF_INT8_SLICES = 2   /* error-free INT8 slices on the tensor cores, INT32 accumulation */
+};
+
+enum eigref_stop {
+  EIGREF_STOP_CORRECTION = 0,  /* ||E-tilde_L||_F <= tol (Section 3.1.3) */
+  EIGREF_STOP_RESIDUAL = 1     /* ||A X - X D||_F / ||A|| <= tol (Section 3.1.3) */
+};
+
+enum eigref_beta {
+  EIGREF_BETA_CLUSTER = 0,  /* beta_ij = -x_i^T x_j / 2 for |d_j - d_i| <= delta */
+  EIGREF_BETA_ZERO = 1      /* beta_ij = 0 (after Rayleigh--Ritz preprocessing) */
+};
+
+typedef struct eigref_params {
+  int target;          /* enum eigref_target */
+  double shift;        /* EIGREF_SHIFT: alpha.  EIGREF_LARGEST / EIGREF_SMALLEST: an
+                          estimate of lambda_{k+1} of A.  Ignored otherwise. */
+  double norm_a;       /* ||A|| (spectral norm or an upper bound); <= 0: ||A||_inf is computed */
+  int max_iters;       /* maximum number of sweeps (>= 0) */
+  double tol;          /* stopping tolerance; 0 = run exactly max_iters sweeps */
+  int stop;            /* enum eigref_stop */
+  int precision;       /* enum eigref_precision (dense only; CSR is always FP64) */
+  int slices;          /* split forms: slices per operand, 0 = default */
+  int beta;            /* enum eigref_beta */
+  double delta_c;      /* c of delta = c ||B|| u (Section 3.1.3); <= 0: 10 */
+  double div_factor;   /* diverged when ||E_t||_F > div_factor * min_{s<t} ||E_s||_F and
+                          ||E_t||_F > div_floor, or ||E_t||_F >= 1; <= 0: 10 */
+  double div_floor;    /* <= 0: 1e-4 */
+  int check_every;     /* sweeps between host reads of the device status; <= 0: 32 */
+  int sign_fix;        /* 1: X <- X Sigma at entry with Algorithm 2's signs (undone on exit) */
+  int use_graph;       /* 1: replay each chunk of check_every sweeps as one CUDA graph */
+  int profile;         /* 1: time the product kernel of every sweep with CUDA events */
+} eigref_params;
+
+/* Report of one refinement call.  The three array pointers are optional,
+ * caller-owned host buffers (NULL = not wanted). */
+typedef struct eigref_report {
+  int status;                 /* same value the call returns */
+  int iterations;             /* sweeps applied */
+  double final_rel_residual;  /* ||B X_t - X_t D_t||_F / ||A|| of the last sweep */
+  double final_corr_norm;     /* ||E-tilde_L||_F of the last sweep */
+  double shift;               /* alpha used */
+  double norm_a;              /* ||A|| used */
+  double delta;               /* delta used */
+  double setup_ms;            /* device time before the first sweep (copies, slicing, sign fix) */
+  double sweeps_ms;           /* device time of all sweeps */
+  double* eigenvalues;        /* [k]: Rayleigh quotients of the last sweep, plus alpha */
+  double* hist_residual;      /* [max_iters]: per-sweep ||R_t||_F / ||A|| */
+  double* hist_corr;          /* [max_iters]: per-sweep ||E_t||_F */
+  double product_ms;          /* profile = 1: summed device time of the product kernel
+                                 (W = B X) over the sweeps applied; else 0 */
+  int64_t kernel_launches;    /* kernels launched by the call (graph replays included) */
+  int product_launches;       /* product kernels timed in product_ms */
+} eigref_report;
+
+/* Defaults: LARGEST_MAG, norm_a computed, max_iters 100, tol 0, correction
+ * criterion, FP64, beta cluster, delta_c 10, div 10 / 1e-4, check 32,
+ * sign_fix 1, use_graph 1, profile 0. */
+void eigref_params_default(eigref_params* p);
+
+/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to issue work on, or NULL for a stream the handle creates and owns.
+ * Errors: EIGREF_E_INVALID (h NULL, bad device), EIGREF_E_CUDA. */
+int eigref_create(eigref_handle* h, int device, void* cuda_stream);
+
+/* Release the handle and its workspace.  NULL is a no-op. */
+int eigref_destroy(eigref_handle h);
+
+/* Refine the k columns of X in place against dense symmetric A (Algorithm 4
+ * iterated, Section 3.1.3).  1 <= k <= 128, k < n.  On EIGREF_OK,
+ * EIGREF_E_NOT_CONVERGED or EIGREF_E_DIVERGED, X holds the last iterate; on
+ * EIGREF_E_NONFINITE the last finite one; on EIGREF_E_INVALID it is untouched.
+ * rep may be NULL. */
+int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda,
+                        double* X, int64_t ldx, int k,
+                        const eigref_params* p, eigref_report* rep);
+
+/* Same for CSR A (the product is an FP64 SpMM; p->precision is ignored). */
+int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx,
+                      const double* val, int64_t n, int64_t nnz,
+                      double* X, int64_t ldx, int k,
+                      const eigref_params* p, eigref_report* rep);
+
+/* Line 1 of Algorithm 4 on its own: P = (A - shift I) X for dense A, with the
+ * chosen precision (slices as in eigref_params).  P is n x k column-major
+ * (ldp >= n), caller-owned, host or device. */
+int eigref_product_dense(eigref_handle h, const double* A, int64_t n, int64_t lda,
+                         const double* X, int64_t ldx, int k, double shift,
+                         int precision, int slices, double* P, int64_t ldp);
+
+/* P = (A - shift I) X for CSR A, FP64. */
+int eigref_product_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx,
+                       const double* val, int64_t n, int64_t nnz,
+                       const double* X, int64_t ldx, int k, double shift,
+                       double* P, int64_t ldp);
+
+/* Static text for a status code. */
+const char* eigref_status_string(int status);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call on the handle. */
+const char* eigref_last_error(eigref_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIGREF_H */

@@ -1,0 +1,676 @@
+// The C ABI of include/eigref.h: handle, workspace, argument checks, host
+// buffer staging and the sweep driver (Algorithm 4 iterated with the
+// stopping rules of Section 3.1.3).
+//
+// One sweep is a fixed sequence of kernel launches on the handle's stream;
+// check_every sweeps are captured once into a CUDA graph and replayed.  The
+// host reads the device Control block only between chunks; a sweep that
+// finds the loop finished returns from every kernel at once, so the number of
+// sweeps applied does not depend on the chunk length.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "sliced.cuh"
+
+using namespace eigref;
+
+struct eigref_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char err[512] = {0};
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  Control* host_ctl = nullptr;  // pinned
+};
+
+namespace {
+
+int set_err(eigref_ctx* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CUDA_TRY(h, expr)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return set_err(h, EIGREF_E_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                     __LINE__);                                                             \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Bump allocator over the handle's workspace; every block 256-byte aligned.
+struct Carve {
+  size_t off = 0;
+  char* base = nullptr;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int ensure_ws(eigref_ctx* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return EIGREF_OK;
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&h->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, EIGREF_E_NOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  h->ws_bytes = bytes;
+  return EIGREF_OK;
+}
+
+struct Params {
+  int target, max_iters, stop, precision, slices, beta, check_every, sign_fix, use_graph, profile;
+  double shift, norm_a, tol, delta_c, div_factor, div_floor;
+};
+
+int read_params(eigref_ctx* h, const eigref_params* p, Params* q) {
+  eigref_params d;
+  eigref_params_default(&d);
+  if (!p) p = &d;
+  q->target = p->target;
+  q->shift = p->shift;
+  q->norm_a = p->norm_a;
+  q->max_iters = p->max_iters;
+  q->tol = p->tol;
+  q->stop = p->stop;
+  q->precision = p->precision;
+  q->slices = p->slices;
+  q->beta = p->beta;
+  q->delta_c = p->delta_c > 0 ? p->delta_c : 10.0;
+  q->div_factor = p->div_factor > 0 ? p->div_factor : 10.0;
+  q->div_floor = p->div_floor > 0 ? p->div_floor : 1e-4;
+  q->check_every = p->check_every > 0 ? p->check_every : 32;
+  q->check_every += q->check_every & 1;  // even: a chunk starts on the same X buffer
+  q->sign_fix = p->sign_fix;
+  q->use_graph = p->use_graph;
+  q->profile = p->profile;
+  if (q->target < EIGREF_LARGEST_MAG || q->target > EIGREF_SHIFT)
+    return set_err(h, EIGREF_E_INVALID, "target %d out of range", q->target);
+  if (q->max_iters < 0) return set_err(h, EIGREF_E_INVALID, "max_iters < 0");
+  if (!(q->tol >= 0.0) || !isfinite(q->tol)) return set_err(h, EIGREF_E_INVALID, "tol must be finite and >= 0");
+  if (q->stop != EIGREF_STOP_CORRECTION && q->stop != EIGREF_STOP_RESIDUAL)
+    return set_err(h, EIGREF_E_INVALID, "stop %d out of range", q->stop);
+  if (q->beta != EIGREF_BETA_CLUSTER && q->beta != EIGREF_BETA_ZERO)
+    return set_err(h, EIGREF_E_INVALID, "beta %d out of range", q->beta);
+  if (q->precision < EIGREF_FP64 || q->precision > EIGREF_INT8_SLICES)
+    return set_err(h, EIGREF_E_INVALID, "precision %d out of range", q->precision);
+  if (!isfinite(q->shift) || !isfinite(q->norm_a)) return set_err(h, EIGREF_E_INVALID, "shift/norm_a not finite");
+  return EIGREF_OK;
+}
+
+// Everything one refinement call needs besides the matrix.
+struct Problem {
+  bool csr = false;
+  const double* A = nullptr;  // device
+  int64_t lda = 0;
+  const int32_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* val = nullptr;
+  int64_t n = 0, nnz = 0;
+  int k = 0;
+  SlicedA* sliced = nullptr;  // split-precision dense product, or null
+};
+
+// Returns the number of kernels launched.  ev0/ev1 (optional) bracket the
+// product kernel; ev_flags is cudaEventRecordExternal inside a graph capture.
+int launch_product(const Problem& pr, const double* X, double* P, double shift, const Control* ctl,
+                   cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, unsigned ev_flags = 0) {
+  if (pr.sliced) return pr.sliced->product(X, P, shift, ctl, s, ev0, ev1, ev_flags);
+  if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
+  if (pr.csr)
+    launch_spmm_csr(pr.rp, pr.ci, pr.val, X, P, pr.n, pr.k, shift, ctl, s);
+  else
+    launch_gemm_fp64(pr.A, pr.lda, X, P, pr.n, pr.k, shift, ctl, s);
+  if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
+  return 1;
+}
+
+int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int beta_zero, cudaStream_t s,
+                 cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags) {
+  const int64_t n = pr.n;
+  const int k = pr.k;
+  int launches = launch_product(pr, b.x, b.p, shift, b.ctl, s, ev0, ev1, ev_flags);
+  // Gram products of the rows below the leading block, then of the block
+  launch_gram(b.x, b.p, k, k, n, b.chunk_rows, b.nchunks, b.gpart, b.g2, b.ctl, s);
+  launch_gram(b.x, b.p, k, 0, k, k, 1, b.gpart, b.gtop, b.ctl, s);
+  launch_kxk_stage(b, k, delta, beta_zero, s);
+  launch_update_rows(b, n, k, s);
+  launch_finalize(b, k, delta, s);
+  launch_normalize(b, n, k, s);
+  return launches + 4 + 9 + 3;
+}
+
+int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigref_params* pin,
+                  eigref_report* rep) {
+  Params q;
+  int st = read_params(h, pin, &q);
+  if (st) return st;
+  const int64_t n = pr.n;
+  const int k = pr.k;
+  cudaStream_t s = h->stream;
+  const bool x_dev = is_device_ptr(X);
+
+  // ---- workspace ----
+  const int64_t kk = (int64_t)k * k;
+  int64_t chunk_rows = 256;
+  while ((n - k + chunk_rows - 1) / chunk_rows > 1024) chunk_rows *= 2;
+  const int nchunks = (int)std::max<int64_t>(1, (n - k + chunk_rows - 1) / chunk_rows);
+  const int ugrid = update_rows_grid();
+  const int hist_len = std::max(1, q.max_iters);
+  auto layout = [&](Carve& c, SweepBufs& b, double** xbuf, double** xstage, double** sigma, double** scal) {
+    xbuf[0] = c.take<double>(n * k);
+    xbuf[1] = c.take<double>(n * k);
+    b.p = c.take<double>(n * k);
+    *xstage = x_dev ? nullptr : c.take<double>(n * k);
+    b.gpart = c.take<double>(2 * (int64_t)nchunks * kk);
+    b.gtop = c.take<double>(2 * kk);
+    b.g2 = c.take<double>(2 * kk);
+    double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f};
+    for (double** m : mats) *m = c.take<double>(kk);
+    b.piv = c.take<int>(k);
+    double** vecs[] = {&b.alpha, &b.d, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
+    for (double** v : vecs) *v = c.take<double>(k);
+    *sigma = c.take<double>(k);
+    b.upart = c.take<double>((int64_t)ugrid * 2 * k);
+    b.hist_res = c.take<double>(hist_len);
+    b.hist_corr = c.take<double>(hist_len);
+    b.ctl = c.take<Control>(1);
+    *scal = c.take<double>(4);
+  };
+  SweepBufs b{};
+  double* xbuf[2];
+  double *xstage, *sigma, *scal;
+  Carve c0;
+  layout(c0, b, xbuf, &xstage, &sigma, &scal);
+  size_t extra = pr.sliced ? pr.sliced->workspace_bytes() : 0;
+  st = ensure_ws(h, c0.off + 256 + extra);
+  if (st) return st;
+  Carve c1;
+  c1.base = static_cast<char*>(h->ws);
+  layout(c1, b, xbuf, &xstage, &sigma, &scal);
+  if (pr.sliced) pr.sliced->bind_workspace(static_cast<char*>(h->ws) + ((c1.off + 255) & ~size_t(255)));
+  b.nchunks = nchunks;
+  b.chunk_rows = chunk_rows;
+  b.ugrid = ugrid;
+
+  CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+  // ---- set-up: ||A||, shift, delta, signs, internal X ----
+  double norm_a = q.norm_a;
+  if (!(norm_a > 0.0)) {
+    if (pr.csr)
+      launch_norm_inf_csr(pr.rp, pr.val, n, scal, s);
+    else
+      launch_norm_inf_dense(pr.A, n, pr.lda, scal, s);
+    CUDA_TRY(h, cudaMemcpyAsync(&h->host_ctl->tol, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    norm_a = h->host_ctl->tol;
+    if (!(norm_a > 0.0) || !isfinite(norm_a))
+      return set_err(h, isfinite(norm_a) ? EIGREF_E_INVALID : EIGREF_E_NONFINITE, "||A||_inf = %g", norm_a);
+  }
+  double shift = 0.0;
+  if (q.target == EIGREF_SHIFT) shift = q.shift;
+  else if (q.target == EIGREF_SMALLEST) shift = 0.5 * (norm_a + q.shift);   // Section 5.1
+  else if (q.target == EIGREF_LARGEST) shift = 0.5 * (q.shift - norm_a);    // its mirror
+  const double delta = q.delta_c * (norm_a + fabs(shift)) * kUnitRoundoff;  // Section 3.1.3
+
+  const double* xu = X;
+  if (!x_dev) {
+    CUDA_TRY(h, cudaMemcpy2DAsync(xstage, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double), k,
+                                  cudaMemcpyHostToDevice, s));
+    xu = xstage;
+  }
+  const int64_t ldu = x_dev ? ldx : n;
+  const double* sg = nullptr;
+  if (q.sign_fix) {
+    launch_sign_fix(xu, ldu, k, sigma, nullptr, s);
+    sg = sigma;
+  }
+  launch_copy_in(xu, ldu, xbuf[0], n, k, sg, s);
+  if (pr.sliced) {
+    st = pr.sliced->prepare(s);
+    if (st) return set_err(h, st, "%s", pr.sliced->error());
+  }
+  Control c{};
+  c.max_iters = q.max_iters;
+  c.stop = q.stop;
+  c.tol = q.tol;
+  c.norm_a = norm_a;
+  c.div_factor = q.div_factor;
+  c.div_floor = q.div_floor;
+  c.emin = DBL_MAX;
+  c.status = EIGREF_OK;
+  c.done = q.max_iters == 0;
+  *h->host_ctl = c;
+  CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
+
+  // ---- sweeps ----
+  const int m = q.check_every;
+  std::vector<cudaEvent_t> pev;
+  if (q.profile) {
+    pev.resize(2 * m);
+    for (auto& e : pev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        for (auto& f : pev)
+          if (f) cudaEventDestroy(f);
+        return set_err(h, EIGREF_E_CUDA, "profiling events");
+      }
+  }
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() {
+      for (auto& e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } ev_guard{pev};
+  auto issue_chunk = [&](int count, unsigned ev_flags) {
+    int launches = 0;
+    for (int t = 0; t < count; ++t) {
+      SweepBufs bt = b;
+      bt.x = xbuf[t & 1];
+      bt.xn = xbuf[(t + 1) & 1];
+      launches += launch_sweep(pr, bt, shift, delta, q.beta == EIGREF_BETA_ZERO, s,
+                               q.profile ? pev[2 * t] : nullptr, q.profile ? pev[2 * t + 1] : nullptr, ev_flags);
+    }
+    return launches;
+  };
+  cudaGraphExec_t gexec = nullptr;
+  int chunk_launches = 0;
+  if (q.use_graph && q.max_iters > 0) {
+    // capture before the sweep timer starts: instantiation is host work
+    cudaGraph_t g;
+    CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    chunk_launches = issue_chunk(m, cudaEventRecordExternal);
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (ce != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    CUDA_TRY(h, cudaGraphUpload(gexec, s));
+  }
+  struct GraphGuard {
+    cudaGraphExec_t& g;
+    ~GraphGuard() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  } graph_guard{gexec};
+  CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+  CUDA_TRY(h, cudaGetLastError());
+  int launched = 0;
+  int64_t kernel_launches = 0;
+  double product_ms = 0.0;
+  int product_launches = 0;
+  int it_before = 0;
+  while (launched < q.max_iters) {
+    if (gexec) {
+      CUDA_TRY(h, cudaGraphLaunch(gexec, s));
+      kernel_launches += chunk_launches;
+    } else {
+      kernel_launches += issue_chunk(m, cudaEventRecordDefault);
+    }
+    launched += m;
+    CUDA_TRY(h, cudaMemcpyAsync(h->host_ctl, b.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    const int ran = h->host_ctl->iterations - it_before;
+    it_before = h->host_ctl->iterations;
+    for (int t = 0; q.profile && t < ran && t < m; ++t) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pev[2 * t], pev[2 * t + 1]) == cudaSuccess) {
+        product_ms += ms;
+        ++product_launches;
+      }
+    }
+    if (h->host_ctl->done) break;
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->host_ctl, b.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  const Control fin = *h->host_ctl;
+
+  // ---- result: X_{iterations} lives in xbuf[iterations % 2] ----
+  const double* xr = xbuf[fin.iterations & 1];
+  if (x_dev) {
+    launch_copy_out(xr, X, ldx, n, k, sg, s);
+  } else {
+    launch_copy_out(xr, xstage, n, n, k, sg, s);
+    CUDA_TRY(h, cudaMemcpy2DAsync(X, ldx * sizeof(double), xstage, n * sizeof(double), n * sizeof(double), k,
+                                  cudaMemcpyDeviceToHost, s));
+  }
+  std::vector<double> dvec(k);
+  CUDA_TRY(h, cudaMemcpyAsync(dvec.data(), b.d, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (rep && rep->hist_residual && fin.iterations > 0)
+    CUDA_TRY(h, cudaMemcpyAsync(rep->hist_residual, b.hist_res, fin.iterations * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+  if (rep && rep->hist_corr && fin.iterations > 0)
+    CUDA_TRY(h, cudaMemcpyAsync(rep->hist_corr, b.hist_corr, fin.iterations * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  CUDA_TRY(h, cudaGetLastError());
+  int status = fin.status;
+  if (q.max_iters == 0) status = EIGREF_OK;
+  if (rep) {
+    rep->status = status;
+    rep->iterations = fin.iterations;
+    rep->final_rel_residual = fin.iterations ? fin.last_res : NAN;
+    rep->final_corr_norm = fin.iterations ? fin.last_corr : NAN;
+    rep->shift = shift;
+    rep->norm_a = norm_a;
+    rep->delta = delta;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    rep->setup_ms = ms;
+    cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]);
+    rep->sweeps_ms = ms;
+    rep->product_ms = product_ms;
+    rep->product_launches = product_launches;
+    rep->kernel_launches = kernel_launches;
+    if (rep->eigenvalues)
+      for (int j = 0; j < k; ++j) rep->eigenvalues[j] = fin.iterations ? dvec[j] + shift : NAN;
+  }
+  if (status != EIGREF_OK)
+    set_err(h, status, "%s after %d sweeps", eigref_status_string(status), fin.iterations);
+  return status;
+}
+
+int check_dims(eigref_ctx* h, int64_t n, int k, int64_t ldx, const double* X) {
+  if (!X) return set_err(h, EIGREF_E_INVALID, "X is NULL");
+  if (n < 2 || n > (int64_t)INT32_MAX) return set_err(h, EIGREF_E_INVALID, "n = %lld out of range", (long long)n);
+  if (k < 1 || k > kMaxK || k >= n)
+    return set_err(h, EIGREF_E_INVALID, "need 1 <= k <= %d and k < n (k = %d, n = %lld)", kMaxK, k, (long long)n);
+  if (ldx < n) return set_err(h, EIGREF_E_INVALID, "ldx < n");
+  return EIGREF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void eigref_params_default(eigref_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->target = EIGREF_LARGEST_MAG;
+  p->shift = 0.0;
+  p->norm_a = 0.0;
+  p->max_iters = 100;
+  p->tol = 0.0;
+  p->stop = EIGREF_STOP_CORRECTION;
+  p->precision = EIGREF_FP64;
+  p->slices = 0;
+  p->beta = EIGREF_BETA_CLUSTER;
+  p->delta_c = 10.0;
+  p->div_factor = 10.0;
+  p->div_floor = 1e-4;
+  p->check_every = 32;
+  p->sign_fix = 1;
+  p->use_graph = 1;
+  p->profile = 0;
+}
+
+const char* eigref_status_string(int s) {
+  switch (s) {
+    case EIGREF_OK: return "ok";
+    case EIGREF_E_INVALID: return "invalid argument";
+    case EIGREF_E_CUDA: return "CUDA error";
+    case EIGREF_E_NOMEM: return "out of device memory";
+    case EIGREF_E_SINGULAR_WY: return "leading block Y1 singular (Algorithm 1 not applicable)";
+    case EIGREF_E_DIVERGED: return "diverged";
+    case EIGREF_E_NOT_CONVERGED: return "not converged";
+    case EIGREF_E_NONFINITE: return "non-finite values";
+    case EIGREF_E_TIMEOUT: return "device wait timed out";
+    case EIGREF_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int eigref_create(eigref_handle* out, int device, void* stream) {
+  if (!out) return EIGREF_E_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return EIGREF_E_INVALID;
+  }
+  eigref_ctx* h = new eigref_ctx();
+  h->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete h; return EIGREF_E_CUDA; }
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return EIGREF_E_CUDA; }
+    h->own_stream = true;
+  }
+  for (auto& e : h->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { eigref_destroy(h); return EIGREF_E_CUDA; }
+  if (cudaMallocHost(reinterpret_cast<void**>(&h->host_ctl), sizeof(Control)) != cudaSuccess ||
+      init_fp64_attributes() != cudaSuccess || init_kxk_attributes() != cudaSuccess ||
+      init_sliced_attributes() != cudaSuccess) {
+    cudaGetLastError();
+    eigref_destroy(h);
+    return EIGREF_E_CUDA;
+  }
+  *out = h;
+  return EIGREF_OK;
+}
+
+int eigref_destroy(eigref_handle h) {
+  if (!h) return EIGREF_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->host_ctl) cudaFreeHost(h->host_ctl);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return EIGREF_OK;
+}
+
+const char* eigref_last_error(eigref_handle h) { return h ? h->err : ""; }
+
+int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda, double* X, int64_t ldx, int k,
+                        const eigref_params* p, eigref_report* rep) {
+  if (!h) return EIGREF_E_INVALID;
+  h->err[0] = 0;
+  if (!A) return set_err(h, EIGREF_E_INVALID, "A is NULL");
+  int st = check_dims(h, n, k, ldx, X);
+  if (st) return st;
+  if (lda < n) return set_err(h, EIGREF_E_INVALID, "lda < n");
+  if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
+  eigref_params dp;
+  eigref_params_default(&dp);
+  const eigref_params* pp = p ? p : &dp;
+  Problem pr;
+  pr.n = n;
+  pr.k = k;
+  pr.lda = lda;
+  double* a_dev = nullptr;
+  if (is_device_ptr(A)) {
+    pr.A = A;
+  } else {
+    // host A: one pitched copy into a separate device buffer for this call
+    cudaError_t e = cudaMalloc(&a_dev, (size_t)n * n * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); return set_err(h, EIGREF_E_NOMEM, "device copy of A"); }
+    e = cudaMemcpy2DAsync(a_dev, n * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
+                          cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { cudaFree(a_dev); return set_err(h, EIGREF_E_CUDA, "copy of A: %s", cudaGetErrorString(e)); }
+    pr.A = a_dev;
+    pr.lda = n;
+  }
+  SlicedA sl;
+  if (pp->precision != EIGREF_FP64) {
+    st = sl.configure(pr.A, n, pr.lda, k, pp->precision, pp->slices);
+    if (st) {
+      if (a_dev) cudaFree(a_dev);
+      return set_err(h, st, "%s", sl.error());
+    }
+    pr.sliced = &sl;
+  }
+  st = refine_common(h, pr, X, ldx, pp, rep);
+  if (a_dev) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(a_dev);
+  }
+  return st;
+}
+
+int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx, const double* val, int64_t n,
+                      int64_t nnz, double* X, int64_t ldx, int k, const eigref_params* p, eigref_report* rep) {
+  if (!h) return EIGREF_E_INVALID;
+  h->err[0] = 0;
+  if (!row_ptr || !col_idx || !val) return set_err(h, EIGREF_E_INVALID, "CSR array is NULL");
+  int st = check_dims(h, n, k, ldx, X);
+  if (st) return st;
+  if (nnz < 0) return set_err(h, EIGREF_E_INVALID, "nnz < 0");
+  if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
+  Problem pr;
+  pr.csr = true;
+  pr.n = n;
+  pr.k = k;
+  pr.nnz = nnz;
+  void* bufs[3] = {nullptr, nullptr, nullptr};
+  const void* src[3] = {row_ptr, col_idx, val};
+  size_t sz[3] = {(size_t)(n + 1) * 4, (size_t)nnz * 4, (size_t)nnz * 8};
+  for (int i = 0; i < 3; ++i) {
+    if (is_device_ptr(src[i]) || sz[i] == 0) continue;
+    if (cudaMalloc(&bufs[i], sz[i]) != cudaSuccess ||
+        cudaMemcpyAsync(bufs[i], src[i], sz[i], cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      for (void* q : bufs)
+        if (q) cudaFree(q);
+      return set_err(h, EIGREF_E_NOMEM, "device copy of CSR arrays");
+    }
+  }
+  pr.rp = static_cast<const int32_t*>(bufs[0] ? bufs[0] : row_ptr);
+  pr.ci = static_cast<const int32_t*>(bufs[1] ? bufs[1] : col_idx);
+  pr.val = static_cast<const double*>(bufs[2] ? bufs[2] : val);
+  st = refine_common(h, pr, X, ldx, p, rep);
+  cudaStreamSynchronize(h->stream);
+  for (void* q : bufs)
+    if (q) cudaFree(q);
+  return st;
+}
+
+// P = (A - shift I) X through the same product kernels the sweeps use.
+static int product_common(eigref_ctx* h, Problem& pr, const double* X, int64_t ldx, double shift, double* P,
+                          int64_t ldp) {
+  const int64_t n = pr.n;
+  const int k = pr.k;
+  cudaStream_t s = h->stream;
+  Carve c0;
+  c0.take<double>(n * k);
+  c0.take<double>(n * k);
+  c0.take<double>(n * k);
+  size_t extra = pr.sliced ? pr.sliced->workspace_bytes() : 0;
+  int st = ensure_ws(h, c0.off + 256 + extra);
+  if (st) return st;
+  Carve c;
+  c.base = static_cast<char*>(h->ws);
+  double* xs = c.take<double>(n * k);
+  double* xi = c.take<double>(n * k);
+  double* pi = c.take<double>(n * k);
+  if (pr.sliced) pr.sliced->bind_workspace(static_cast<char*>(h->ws) + ((c.off + 255) & ~size_t(255)));
+  const double* xu = X;
+  int64_t ldu = ldx;
+  if (!is_device_ptr(X)) {
+    CUDA_TRY(h, cudaMemcpy2DAsync(xs, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double), k,
+                                  cudaMemcpyHostToDevice, s));
+    xu = xs;
+    ldu = n;
+  }
+  launch_copy_in(xu, ldu, xi, n, k, nullptr, s);
+  if (pr.sliced) {
+    st = pr.sliced->prepare(s);
+    if (st) return set_err(h, st, "%s", pr.sliced->error());
+  }
+  launch_product(pr, xi, pi, shift, nullptr, s);
+  if (is_device_ptr(P)) {
+    launch_copy_out(pi, P, ldp, n, k, nullptr, s);
+  } else {
+    launch_copy_out(pi, xs, n, n, k, nullptr, s);
+    CUDA_TRY(h, cudaMemcpy2DAsync(P, ldp * sizeof(double), xs, n * sizeof(double), n * sizeof(double), k,
+                                  cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  CUDA_TRY(h, cudaGetLastError());
+  return EIGREF_OK;
+}
+
+int eigref_product_dense(eigref_handle h, const double* A, int64_t n, int64_t lda, const double* X, int64_t ldx,
+                         int k, double shift, int precision, int slices, double* P, int64_t ldp) {
+  if (!h) return EIGREF_E_INVALID;
+  h->err[0] = 0;
+  if (!A || !X || !P) return set_err(h, EIGREF_E_INVALID, "NULL argument");
+  if (n < 1 || k < 1 || lda < n || ldx < n || ldp < n) return set_err(h, EIGREF_E_INVALID, "bad sizes");
+  if (!is_device_ptr(A)) return set_err(h, EIGREF_E_INVALID, "product_dense needs A in device memory");
+  if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
+  Problem pr;
+  pr.n = n;
+  pr.k = k;
+  pr.A = A;
+  pr.lda = lda;
+  SlicedA sl;
+  if (precision != EIGREF_FP64) {
+    int st = sl.configure(A, n, lda, k, precision, slices);
+    if (st) return set_err(h, st, "%s", sl.error());
+    pr.sliced = &sl;
+  }
+  return product_common(h, pr, X, ldx, shift, P, ldp);
+}
+
+int eigref_product_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                       int64_t n, int64_t nnz, const double* X, int64_t ldx, int k, double shift, double* P,
+                       int64_t ldp) {
+  if (!h) return EIGREF_E_INVALID;
+  h->err[0] = 0;
+  if (!row_ptr || !col_idx || !val || !X || !P) return set_err(h, EIGREF_E_INVALID, "NULL argument");
+  if (n < 1 || k < 1 || nnz < 0 || ldx < n || ldp < n) return set_err(h, EIGREF_E_INVALID, "bad sizes");
+  if (!is_device_ptr(row_ptr) || !is_device_ptr(col_idx) || !is_device_ptr(val))
+    return set_err(h, EIGREF_E_INVALID, "product_csr needs the CSR arrays in device memory");
+  if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
+  Problem pr;
+  pr.csr = true;
+  pr.n = n;
+  pr.k = k;
+  pr.nnz = nnz;
+  pr.rp = row_ptr;
+  pr.ci = col_idx;
+  pr.val = val;
+  return product_common(h, pr, X, ldx, shift, P, ldp);
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Shared declarations of the eigref CUDA library (sm_103a).
+//
+// Internal layouts (all device memory owned by the handle):
+//   X, P     : n x k FP64, row-major, leading dimension k (row i = the k
+//              entries of row i of the approximate eigenvector block).
+//   k x k    : FP64 column-major, leading dimension k.
+// The caller's X (column-major, ldx) is converted at entry and exit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/eigref.h"
+
+namespace eigref {
+
+constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
+constexpr int kMaxK = 128;                                 // k x k stage lives in shared memory
+
+// Device-resident loop state.  Every sweep kernel returns at once when
+// `done` is set, so a CUDA graph of several sweeps stops exactly at the
+// sweep that met the criterion (or failed).
+struct Control {
+  int done;           // 1: remaining sweep kernels are no-ops
+  int status;         // eigref_status of the loop
+  int iterations;     // sweeps applied
+  int pending_norm;   // 1: this sweep's update was applied; normalise it
+  int max_iters;
+  int stop;           // eigref_stop
+  int nonfinite;
+  int singular;       // set by the LU of Y_1
+  double tol;
+  double norm_a;
+  double div_factor, div_floor;
+  double emin;        // smallest ||E_t||_F so far
+  double last_res;    // ||R_t||_F / ||A||
+  double last_corr;   // ||E_t||_F
+};
+
+// Pointers of one sweep (all device).
+struct SweepBufs {
+  const double* x;    // X_t   (n x k row-major)
+  double* xn;         // X_{t+1}
+  double* p;          // P = B X_t
+  double* gpart;      // Gram partials: [2][nchunks][k*k]
+  double* gtop;       // [2][k*k]: G1 = X1^T X1, S1 = X1^T P1
+  double* g2;         // [2][k*k]: G2 = X2^T X2, S2 = X2^T P2 (rows >= k)
+  double *r1, *t1, *z, *y1, *lu, *m, *v1, *w2, *e11, *yte, *nmat, *f;  // k x k
+  int* piv;           // [k]
+  double *alpha, *d, *cz, *cw, *nu, *r1sq, *e11sq, *x1sq;  // [k]
+  double* upart;      // update partials [ugrid][2k]
+  double *hist_res, *hist_corr;  // [max_iters]
+  Control* ctl;
+  int nchunks;
+  int64_t chunk_rows;
+  int ugrid;
+};
+
+// ---- kernels launched by the driver (definitions in the .cu files) ----
+// fp64.cu
+void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, int64_t n, int k,
+                      double shift, const Control* ctl, cudaStream_t s);
+void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
+                 int nchunks, double* part, double* out, const Control* ctl, cudaStream_t s);
+void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s);
+void launch_finalize(const SweepBufs& b, int k, double delta_unused, cudaStream_t s);
+void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s);
+void launch_copy_in(const double* Xu, int64_t ldx, double* X, int64_t n, int k, const double* sigma,
+                    cudaStream_t s);
+void launch_copy_out(const double* X, double* Xu, int64_t ldx, int64_t n, int k, const double* sigma,
+                     cudaStream_t s);
+void launch_rowmajor_to_colmajor(const double* X, double* Xu, int64_t ldx, int64_t n, int k, cudaStream_t s);
+void launch_norm_inf_dense(const double* A, int64_t n, int64_t lda, double* out, cudaStream_t s);
+void launch_norm_inf_csr(const int32_t* rp, const double* val, int64_t n, double* out, cudaStream_t s);
+int update_rows_grid();
+cudaError_t init_fp64_attributes();
+cudaError_t init_kxk_attributes();
+// spmm.cu
+void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
+                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s);
+// kxk.cu
+void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s);
+void launch_sign_fix(const double* X, int64_t ldx, int k, double* sigma, int* singular, cudaStream_t s);
+
+}  // namespace eigref

@@ -1,0 +1,436 @@
+// FP64 kernels of one refinement sweep: the product W = B X (plain FP64
+// form, line 1 of Algorithm 4), the Gram reductions X^T X and X^T W
+// (lines 3-4), the row update of the rows below the leading k x k block
+// (line 7 in the folded form), the per-sweep statistics and stopping test
+// (Section 3.1.3), and column normalisation.
+//
+// GB300 runs FP64 at about 2 DFMA per clock per SM (1.1 TFLOP/s measured for
+// the whole GPU), so every FP64 kernel here is bound by the FP64 pipe, not by
+// HBM: they are organised for enough independent DFMAs per thread, not for
+// bandwidth.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace eigref {
+
+// ---------------------------------------------------------------------------
+// P = A X - shift X.  A n x n row-major (lda), X and P n x k row-major.
+// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread.
+// ---------------------------------------------------------------------------
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+__global__ void __launch_bounds__(256) gemm_fp64_kernel(const double* __restrict__ A, int64_t lda,
+                                                        const double* __restrict__ X,
+                                                        double* __restrict__ P, int64_t n, int k,
+                                                        double shift, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  __shared__ double As[GB_K][GB_M + 1];
+  __shared__ double Bs[GB_K][GB_N];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * GB_M;
+  const int n0 = blockIdx.y * GB_N;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  double ra[4], rb[4];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      int r = e >> 4, c = e & 15;
+      int64_t gr = m0 + r, gc = k0 + c;
+      ra[q] = (gr < n && gc < n) ? A[gr * lda + gc] : 0.0;
+      int rr = e >> 6, cc = e & 63;
+      int64_t gk = k0 + rr;
+      int gn = n0 + cc;
+      rb[q] = (gk < n && gn < k) ? X[gk * k + gn] : 0.0;
+    }
+  };
+  load(0);
+  for (int64_t k0 = 0; k0 < n; k0 += GB_K) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      As[e & 15][e >> 4] = ra[q];
+      Bs[e >> 6][e & 63] = rb[q];
+    }
+    __syncthreads();
+    if (k0 + GB_K < n) load(k0 + GB_K);
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t row = m0 + ty * 4 + i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int col = n0 + tx * 4 + j;
+      if (col < k) P[row * k + col] = acc[i][j] - shift * X[row * k + col];
+    }
+  }
+}
+
+void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, int64_t n, int k,
+                      double shift, const Control* ctl, cudaStream_t s) {
+  dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((k + GB_N - 1) / GB_N));
+  gemm_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, X, P, n, k, shift, ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Gram partials over a row range: part[z][c] = (X^T Y)[rows of chunk c],
+// z = 0: Y = X (G), z = 1: Y = P (S).  32 x 32 output tile per CTA.
+// Deterministic: partials are summed in chunk order by gram_reduce.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restrict__ X,
+                                                           const double* __restrict__ P, int k, int64_t r0,
+                                                           int64_t r1, int64_t chunk_rows, int nchunks,
+                                                           double* __restrict__ part, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  __shared__ double Xa[32][33];
+  __shared__ double Xb[32][33];
+  const int c = blockIdx.x;
+  const int tiles = (k + 31) / 32;
+  const int ti = blockIdx.y % tiles, tj = blockIdx.y / tiles;
+  const int z = blockIdx.z;
+  const double* Yb = z ? P : X;
+  const int tid = threadIdx.x, i = tid & 31, jg = tid >> 5;  // outputs (i, jg*4 + q)
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t rb = r0 + (int64_t)c * chunk_rows;
+  const int64_t re = r1 < rb + chunk_rows ? r1 : rb + chunk_rows;
+  for (int64_t row0 = rb; row0 < re; row0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      int rr = e >> 5, cc = e & 31;
+      int64_t row = row0 + rr;
+      int ca = ti * 32 + cc, cb = tj * 32 + cc;
+      Xa[rr][cc] = (row < re && ca < k) ? X[row * k + ca] : 0.0;
+      Xb[rr][cc] = (row < re && cb < k) ? Yb[row * k + cb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      double a = Xa[rr][i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(a, Xb[rr][jg * 4 + q], acc[q]);
+    }
+    __syncthreads();
+  }
+  double* out = part + ((int64_t)z * nchunks + c) * k * k;
+  int gi = ti * 32 + i;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int gj = tj * 32 + jg * 4 + q;
+    if (gi < k && gj < k) out[gi + (int64_t)gj * k] = acc[q];
+  }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int nchunks, double* __restrict__ out,
+                                   const Control* ctl) {
+  if (ctl && ctl->done) return;
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * kk; e += (int64_t)gridDim.x * blockDim.x) {
+    int z = (int)(e / kk);
+    int64_t o = e % kk;
+    const double* p = part + (int64_t)z * nchunks * kk + o;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += p[(int64_t)c * kk];
+    out[e] = s;
+  }
+}
+
+void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
+                 int nchunks, double* part, double* out, const Control* ctl, cudaStream_t s) {
+  int tiles = (k + 31) / 32;
+  dim3 grid(nchunks, tiles * tiles, 2);
+  gram_partial_kernel<<<grid, 256, 0, s>>>(X, P, k, r0, r1, chunk_rows, nchunks, part, ctl);
+  int64_t work = 2LL * k * k;
+  int rg = (int)std::min<int64_t>((work + 255) / 256, 1024);
+  gram_reduce_kernel<<<rg, 256, 0, s>>>(part, k, nchunks, out, ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Row update below the leading block (rows k..n-1), folded form of line 7:
+//   x' = x + (w - x o d) / d - x F,   F = M D^-1 + N
+// with per-CTA partial column sums of x'^2 and of the residual r = w - x o d.
+// ---------------------------------------------------------------------------
+constexpr int UPD_ROWS = 16;
+constexpr int UPD_GRID = 2 * 152;
+
+int update_rows_grid() { return UPD_GRID; }
+
+// Column sums are formed in a fixed order (no atomics), so results are
+// bitwise reproducible run to run.
+__global__ void __launch_bounds__(256) update_rows_kernel(const double* __restrict__ X,
+                                                          const double* __restrict__ P,
+                                                          double* __restrict__ Xn, int64_t n, int k,
+                                                          const double* __restrict__ F,
+                                                          const double* __restrict__ d,
+                                                          double* __restrict__ upart, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  extern __shared__ double sm[];
+  double* Fs = sm;                          // Fs[l * k + j] = F(l, j)
+  double* xs = Fs + k * k;                  // [UPD_ROWS][k]
+  double* sq = xs + UPD_ROWS * k;           // [UPD_ROWS][k]: x'^2
+  double* rq = sq + UPD_ROWS * k;           // [UPD_ROWS][k]: r^2
+  double* dinv = rq + UPD_ROWS * k;         // [k]
+  double* dv = dinv + k;                    // [k]
+  const int tid = threadIdx.x;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    int l = e % k, j = e / k;               // F column-major
+    Fs[l * k + j] = F[e];
+  }
+  for (int j = tid; j < k; j += blockDim.x) {
+    dv[j] = d[j];
+    dinv[j] = 1.0 / d[j];
+  }
+  double accx = 0.0, accr = 0.0;            // column tid (k <= 128 < blockDim)
+  __syncthreads();
+  const int64_t rows = n - k;
+  const int64_t nblk = (rows + UPD_ROWS - 1) / UPD_ROWS;
+  const int per = UPD_ROWS * k;
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int64_t row0 = k + b * UPD_ROWS;
+    for (int e = tid; e < per; e += blockDim.x) {
+      int64_t row = row0 + e / k;
+      xs[e] = row < n ? X[row0 * k + e] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < per; e += blockDim.x) {
+      int r = e / k, j = e % k;
+      int64_t row = row0 + r;
+      double xn = 0.0, rr = 0.0;
+      if (row < n) {
+        const double* xr = xs + r * k;
+        double x = xr[j];
+        rr = P[row * k + j] - x * dv[j];
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s = fma(xr[l], Fs[l * k + j], s);
+        xn = x + rr * dinv[j] - s;
+        Xn[row * k + j] = xn;
+      }
+      sq[e] = xn * xn;
+      rq[e] = rr * rr;
+    }
+    __syncthreads();
+    if (tid < k)
+      for (int r = 0; r < UPD_ROWS; ++r) {
+        accx += sq[r * k + tid];
+        accr += rq[r * k + tid];
+      }
+    __syncthreads();
+  }
+  if (tid < k) {
+    upart[(int64_t)blockIdx.x * 2 * k + tid] = accx;
+    upart[(int64_t)blockIdx.x * 2 * k + k + tid] = accr;
+  }
+}
+
+static size_t update_smem(int k) {
+  return sizeof(double) * ((size_t)k * k + 3 * (size_t)UPD_ROWS * k + 2 * (size_t)k);
+}
+
+void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {
+  size_t smem = update_smem(k);
+  update_rows_kernel<<<UPD_GRID, 256, smem, s>>>(b.x, b.p, b.xn, n, k, b.f, b.d, b.upart, b.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Per-sweep statistics and control (one CTA).
+//   ||R||_F^2  = sum_j r1sq_j + sum_blocks r^2
+//   ||E||_F^2  = ||E11||_F^2 + sum_j (||r2_j||^2 - 2 (M^T Z)_jj + (M^T G2 M)_jj) / d_j^2
+//   nu_j = 1 / ||x'_j||
+// Stopping, divergence and non-finite tests of Section 3.1.3 / Section 4.3.1.
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(SweepBufs b, int k) {
+  Control* ctl = b.ctl;
+  __shared__ double red[3][256];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (ctl->done) {
+    if (tid == 0) ctl->pending_norm = 0;
+    return;
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  double rsum = 0.0, esum = 0.0, e11 = 0.0;
+  for (int j = tid; j < k; j += blockDim.x) {
+    double xsq = 0.0, r2 = 0.0;
+    for (int i = 0; i < k; ++i) {            // leading block rows of X_{t+1}
+      const double v = b.xn[(int64_t)i * k + j];
+      xsq += v * v;
+    }
+    for (int g = 0; g < b.ugrid; ++g) {
+      xsq += b.upart[(int64_t)g * 2 * k + j];
+      r2 += b.upart[(int64_t)g * 2 * k + k + j];
+    }
+    double dj = b.d[j];
+    double e21 = (r2 - 2.0 * b.cz[j] + b.cw[j]) / (dj * dj);
+    esum += e21 > 0.0 ? e21 : 0.0;
+    rsum += b.r1sq[j] + r2;
+    e11 += b.e11sq[j];
+    b.nu[j] = 1.0 / sqrt(xsq);
+    if (!isfinite(xsq) || !(xsq > 0.0)) atomicExch(&bad, 1);
+  }
+  red[0][tid] = rsum;
+  red[1][tid] = esum;
+  red[2][tid] = e11;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int q = 0; q < 3; ++q) red[q][tid] += red[q][tid + w];
+    __syncthreads();
+  }
+  if (tid != 0) return;
+  double res = sqrt(red[0][0]) / ctl->norm_a;
+  double corr = sqrt(red[1][0] + red[2][0]);
+  int it = ctl->iterations;
+  if (bad || !isfinite(res) || !isfinite(corr)) {
+    ctl->status = EIGREF_E_NONFINITE;
+    ctl->nonfinite = 1;
+    ctl->done = 1;
+    ctl->pending_norm = 0;
+    return;
+  }
+  b.hist_res[it] = res;
+  b.hist_corr[it] = corr;
+  ctl->last_res = res;
+  ctl->last_corr = corr;
+  ctl->iterations = it + 1;
+  ctl->pending_norm = 1;
+  double crit = ctl->stop == EIGREF_STOP_CORRECTION ? corr : res;
+  if (ctl->tol > 0.0 && crit <= ctl->tol) {
+    ctl->status = EIGREF_OK;
+    ctl->done = 1;
+  } else if (corr >= 1.0 || (corr > ctl->div_factor * ctl->emin && corr > ctl->div_floor)) {
+    ctl->status = EIGREF_E_DIVERGED;
+    ctl->done = 1;
+  } else if (it + 1 >= ctl->max_iters) {
+    ctl->status = ctl->tol > 0.0 ? EIGREF_E_NOT_CONVERGED : EIGREF_OK;
+    ctl->done = 1;
+  }
+  if (corr < ctl->emin) ctl->emin = corr;
+}
+
+cudaError_t init_fp64_attributes() {
+  return cudaFuncSetAttribute(update_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)update_smem(kMaxK));
+}
+
+void launch_finalize(const SweepBufs& b, int k, double, cudaStream_t s) {
+  finalize_kernel<<<1, 256, 0, s>>>(b, k);
+}
+
+__global__ void normalize_kernel(double* __restrict__ X, int64_t n, int k, const double* __restrict__ nu,
+                                 const Control* ctl) {
+  if (!ctl->pending_norm) return;
+  const int64_t total = n * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    X[e] *= nu[e % k];
+}
+
+void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {
+  int64_t total = n * k;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  normalize_kernel<<<grid, 256, 0, s>>>(b.xn, n, k, b.nu, b.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversion between the caller's column-major X (ldx) and the
+// internal row-major X, with the column signs sigma (sigma may be NULL).
+// ---------------------------------------------------------------------------
+__global__ void copy_in_kernel(const double* __restrict__ Xu, int64_t ldx, double* __restrict__ X, int64_t n,
+                               int k, const double* __restrict__ sigma) {
+  const int64_t total = n * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n;
+    int j = (int)(e / n);
+    double v = Xu[i + j * ldx];
+    X[i * k + j] = sigma ? v * sigma[j] : v;
+  }
+}
+
+__global__ void copy_out_kernel(const double* __restrict__ X, double* __restrict__ Xu, int64_t ldx, int64_t n,
+                                int k, const double* __restrict__ sigma) {
+  const int64_t total = n * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n;
+    int j = (int)(e / n);
+    double v = X[i * k + j];
+    Xu[i + j * ldx] = sigma ? v * sigma[j] : v;
+  }
+}
+
+static int grid_for(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256, 152 * 16); }
+
+void launch_copy_in(const double* Xu, int64_t ldx, double* X, int64_t n, int k, const double* sigma,
+                    cudaStream_t s) {
+  copy_in_kernel<<<grid_for(n * k), 256, 0, s>>>(Xu, ldx, X, n, k, sigma);
+}
+
+void launch_copy_out(const double* X, double* Xu, int64_t ldx, int64_t n, int k, const double* sigma,
+                     cudaStream_t s) {
+  copy_out_kernel<<<grid_for(n * k), 256, 0, s>>>(X, Xu, ldx, n, k, sigma);
+}
+
+void launch_rowmajor_to_colmajor(const double* X, double* Xu, int64_t ldx, int64_t n, int k, cudaStream_t s) {
+  copy_out_kernel<<<grid_for(n * k), 256, 0, s>>>(X, Xu, ldx, n, k, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// ||A||_inf = max_i sum_l |a_il| (the computable bound used for the shift of
+// Section 5.1).  Non-negative doubles order like their bit patterns, so the
+// maximum is an integer atomicMax.
+// ---------------------------------------------------------------------------
+__global__ void norm_inf_dense_kernel(const double* __restrict__ A, int64_t n, int64_t lda,
+                                      unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    double s = 0.0;
+    for (int64_t l = lane; l < n; l += 32) s += fabs(A[i * lda + l]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+__global__ void norm_inf_csr_kernel(const int32_t* __restrict__ rp, const double* __restrict__ val, int64_t n,
+                                    unsigned long long* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) s += fabs(val[p]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+void launch_norm_inf_dense(const double* A, int64_t n, int64_t lda, double* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(double), s);
+  norm_inf_dense_kernel<<<152 * 8, 256, 0, s>>>(A, n, lda, reinterpret_cast<unsigned long long*>(out));
+}
+
+void launch_norm_inf_csr(const int32_t* rp, const double* val, int64_t n, double* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(double), s);
+  norm_inf_csr_kernel<<<grid_for(n), 256, 0, s>>>(rp, val, n, reinterpret_cast<unsigned long long*>(out));
+}
+
+}  // namespace eigref
