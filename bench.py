@@ -117,9 +117,73 @@ def traffic_for(kernel_file, precision):
     return ent.get("dram_bytes_per_launch")
 
 
-def workload(seed=3000):
+def summarize_launches(path):
+    """Per-kernel launches, total time and share from an ncu launch list
+    (``--metrics gpu__time_duration.sum --csv``)."""
+    import collections
+    import csv
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3,
+             "s": 1e6, "second": 1e6}
+    rows = list(csv.reader(open(path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ki, mi, vi, ui = (h.index("Kernel Name"), h.index("Metric Name"), h.index("Metric Value"),
+                      h.index("Metric Unit"))
+    agg = collections.OrderedDict()
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+            continue
+        name = r[ki].split("(")[0].split("<")[0].replace("void ", "").replace("eigref::", "")
+        a = agg.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    tot = sum(v[1] for v in agg.values())
+    lines = ["%-34s %8s %12s %8s" % ("kernel", "launches", "total_us", "share")]
+    for name, (c, t) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        lines.append("%-34s %8d %12.1f %7.2f%%" % (name[:34], c, t, 100 * t / tot))
+    lines.append("%-34s %8d %12.1f" % ("TOTAL", sum(v[0] for v in agg.values()), tot))
+    return "\n".join(lines)
+
+
+def library_peaks():
+    """Library (cuBLAS through torch) rates on this GPU for the dtypes the
+    roofline needs: FP64 and INT8 are not in the measured-peaks file."""
+    import torch
+
+    def best(fn, iters):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(iters):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return min(ts)
+    n = 8192
+    out = {}
+    a = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    b = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    out["fp64_gemm_tflops"] = 2 * n ** 3 / best(lambda: a @ b, 5) / 1e9
+    del a, b
+    a = torch.randint(-127, 127, (n, n), device="cuda", dtype=torch.int8)
+    b = torch.randint(-127, 127, (n, n), device="cuda", dtype=torch.int8)
+    out["int8_gemm_tops"] = 2 * n ** 3 / best(lambda: torch._int_mm(a, b.t()), 10) / 1e9
+    del a, b
+    a = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    b = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    out["bf16_gemm_tflops"] = 2 * n ** 3 / best(lambda: a @ b, 10) / 1e9
+    out["gpu"] = torch.cuda.get_device_name(0)
+    out["torch"] = torch.__version__
+    return out
+
+
+def workload(seed=3000, n=16384, k=128):
     from workloads import configs as C
-    return C.config3(seed=seed)
+    return C.config3(seed=seed, n=n, k=k)
 
 
 def max_angle(X, Q):
@@ -144,7 +208,7 @@ def cpu_oracle_rate(p, sweeps):
 def run_reference(args, rank):
     if rank != 0:
         return
-    p = workload()
+    p = workload(n=args.n, k=args.k)
     rate_w, _, _ = cpu_oracle_rate(p, args.warmup) if args.warmup > 0 else (0, 0, 0)
     rate, cores, wall = cpu_oracle_rate(p, args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
@@ -168,7 +232,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--n", type=int, default=16384, help="smaller n / k only for profiling captures")
+    ap.add_argument("--k", type=int, default=128)
+    ap.add_argument("--summarize-launches", metavar="CSV", help="summarise an ncu launch list and exit")
+    ap.add_argument("--peaks", action="store_true", help="measure library FP64/INT8/BF16 GEMM rates and exit")
     args = ap.parse_args()
+    if args.summarize_launches:
+        print(summarize_launches(args.summarize_launches))
+        return
+    if args.peaks:
+        print(json.dumps(library_peaks()))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -192,7 +266,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    p = workload()
+    p = workload(n=args.n, k=args.k)
     A = torch.from_numpy(p.A).cuda()
     X0 = torch.from_numpy(np.ascontiguousarray(p.X0.T)).cuda().t()  # column-major n x k
     stream = torch.cuda.Stream()
