@@ -161,6 +161,36 @@ int eigref_product_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* c
                        const double* X, int64_t ldx, int k, double shift,
                        double* P, int64_t ldp);
 
+/* Largest n * k that eigref_product_dense_noalloc accepts. */
+#define EIGREF_NOALLOC_MAX_ELEMS (1LL << 20)
+
+/* P = (A - shift I) X in FP64, like eigref_product_dense with precision
+ * EIGREF_FP64, but without allocating any device memory.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc at the point
+ * they need the product -- code running while a CUDA graph is being captured
+ * on its stream (an allocation there would break or invalidate the capture),
+ * or code inside a framework or plugin whose memory pool owns the device and
+ * forbids allocations behind its back.
+ *
+ * A, X, P: device pointers on the current CUDA device (host memory is
+ * rejected), layouts as in eigref_product_dense, n * k <= 2^20.  Work is
+ * queued on `stream` (a cudaStream_t, NULL = the legacy default stream) and
+ * the call returns without waiting; P is ready when the stream reaches it.
+ *
+ * Scratch: a fixed 16 MiB array of device memory inside the library, which
+ * every GPU that loads the library holds until the process exits.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress), so
+ * make one call on each device before any stream capture.  All calls share
+ * the array and it keeps the last call's contents; calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race on it, so
+ * serialise them.  Nothing in it needs to start at zero: each call writes
+ * every entry it reads.
+ * Errors: EIGREF_E_INVALID (NULL or foreign pointers, sizes out of range,
+ * n * k above the limit), EIGREF_E_CUDA (address look-up or launch failed). */
+int eigref_product_dense_noalloc(const double* A, int64_t n, int64_t lda,
+                                 const double* X, int64_t ldx, int k, double shift,
+                                 double* P, int64_t ldp, void* cuda_stream);
+
 /* Static text for a status code. */
 const char* eigref_status_string(int status);
 

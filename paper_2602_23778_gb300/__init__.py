@@ -25,7 +25,8 @@ BETAS = {"cluster": 0, "zero": 1}
 
 SYMBOLS = ["eigref_params_default", "eigref_create", "eigref_destroy", "eigref_refine_dense",
            "eigref_refine_csr", "eigref_product_dense", "eigref_product_csr", "eigref_status_string",
-           "eigref_last_error"]
+           "eigref_last_error", "eigref_product_dense_noalloc"]
+NOALLOC_MAX_ELEMS = 1 << 20
 
 
 class Params(ctypes.Structure):
@@ -79,6 +80,7 @@ def lib():
                                         ctypes.POINTER(Report)]
         L.eigref_product_dense.argtypes = [vp, vp, i64, i64, vp, i64, i32, dbl, i32, i32, vp, i64]
         L.eigref_product_csr.argtypes = [vp, vp, vp, vp, i64, i64, vp, i64, i32, dbl, vp, i64]
+        L.eigref_product_dense_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, dbl, vp, i64, vp]
         L.eigref_status_string.argtypes = [i32]
         L.eigref_status_string.restype = ctypes.c_char_p
         L.eigref_last_error.argtypes = [vp]
@@ -92,6 +94,20 @@ def status_string(s):
 
 
 # ---- array marshalling ------------------------------------------------------
+
+def product_dense_noalloc(A, X, P, shift=0.0, stream=None):
+    """P = (A - shift I) X through eigref_product_dense_noalloc: FP64, device
+    arrays only, queued on ``stream`` (torch stream, raw handle or None) with
+    no device allocation; returns the status code."""
+    pa, n, lda, ka = _dense_a(A)
+    px, nx, k, ldx, kx = _colmajor(X)
+    pp, np_, kp, ldp, kpp = _colmajor(P, "P")
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    return lib().eigref_product_dense_noalloc(pa, n, lda, px, ldx, k, float(shift), pp, ldp, sp)
+
+
 
 def _info(a):
     """(pointer, shape, strides in elements, dtype name, is_torch, keepalive)."""
