@@ -228,6 +228,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="eigref", choices=["eigref", "reference"])
     ap.add_argument("--precision", default=None, choices=["bf16", "fp64", "int8"])
+    ap.add_argument("--slices", type=int, default=0, help="digit planes of the split form (0: library default)")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -272,6 +273,8 @@ def main():
     stream = torch.cuda.Stream()
     h = eigref.Handle(local, stream)
     kw = dict(norm_a=p.normA, target="largest_mag", precision=precision)
+    if precision != "fp64":
+        kw["slices"] = args.slices
 
     def refine(X, iters, **extra):
         return h.refine_dense(A, X, max_iters=iters, check_every=max(2, iters), **kw, **extra)
@@ -310,7 +313,7 @@ def main():
         kfile = "fp64.cu"
     else:
         from paper_2602_23778_gb300 import sliced_info
-        info = sliced_info(precision, n, k)
+        info = sliced_info(precision, n, k, slices=args.slices or 9)
         flops = info["executed_flops"]
         peak = pk["bf16_tflops_sustained"] if precision == "bf16" else \
             pk["bf16_tflops_sustained"] * NOMINAL["int8"] / NOMINAL["bf16"]
@@ -326,6 +329,7 @@ def main():
            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision + "-slices+f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": n, "k": k, "form": precision, "seed": 3000,
+                      "slices": (args.slices or 9) if precision != "fp64" else None,
                       "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
                       "parallelism": "replicas" if world > 1 else "single"},
            "setup_ms": rep["setup_ms"], "call_s": call_s, "roofline": roof,

@@ -95,6 +95,17 @@ def status_string(s):
 
 # ---- array marshalling ------------------------------------------------------
 
+def sliced_info(precision, n, k, slices=9):
+    """Work of one split-precision product W = B X as the library pads it:
+    S (S + 1) / 2 digit-plane pairs, each a 2 n_pad^2 k_pad-flop BF16 GEMM
+    (n_pad = n rounded up to 256, k_pad = k rounded up to 32)."""
+    n_pad = -(-n // 256) * 256
+    k_pad = -(-k // 32) * 32
+    pairs = slices * (slices + 1) // 2
+    return {"kernel": "sliced_gemm_kernel", "slices": slices, "pairs": pairs,
+            "executed_flops": 2.0 * n_pad * n_pad * k_pad * pairs,
+            "a_plane_bytes": 2.0 * slices * n_pad * n_pad}
+
 def product_dense_noalloc(A, X, P, shift=0.0, stream=None):
     """P = (A - shift I) X through eigref_product_dense_noalloc: FP64, device
     arrays only, queued on ``stream`` (torch stream, raw handle or None) with

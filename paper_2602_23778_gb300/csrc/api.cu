@@ -618,6 +618,7 @@ static int product_common(eigref_ctx* h, Problem& pr, const double* X, int64_t l
     if (st) return set_err(h, st, "%s", pr.sliced->error());
   }
   launch_product(pr, xi, pi, shift, nullptr, s);
+  if (pr.sliced && pr.sliced->timed_out(s)) return set_err(h, EIGREF_E_TIMEOUT, "tensor-core product wait timed out");
   if (is_device_ptr(P)) {
     launch_copy_out(pi, P, ldp, n, k, nullptr, s);
   } else {

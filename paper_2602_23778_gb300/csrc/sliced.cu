@@ -1,11 +1,539 @@
-// Split-precision dense product (placeholder until the tensor-core kernel lands).
+// Split-precision (error-free sliced) product W = (A - shift I) X on the
+// tcgen05 tensor cores, BF16 operands, FP32 accumulation in TMEM.
+//
+// Slicing (Ozaki, Ogita, Oishi and Rump's error-free splitting, BIT 2012):
+// every row i of A is scaled by 2^-e_i (e_i = exponent of the row's largest
+// |a_il|, so |a_il 2^-e_i| < 1) and written as a sum of S signed 7-bit digit
+// planes, a_il 2^-e_i = sum_s d_s 2^-7s + r with |d_1| <= 128, |d_s| <= 64
+// (s >= 2), |r| <= 2^-7S / 2.  Every column j of X gets the same treatment
+// with its own exponent f_j.  Each digit is an integer of at most 8
+// significant bits, hence exact in BF16, and a digit product is exact in
+// FP32.  The product keeps the S(S+1)/2 digit pairs with s + t <= S + 1
+// (triangular truncation):
+//     W_ij = 2^(e_i + f_j) sum_w 2^-7(w+2) C_w,   C_w = sum_{s+t=w} A_s X_t
+// (0-based s, t, w).  C_w is accumulated in FP32 over K chunks of 256:
+// the largest partial sum is bounded by 256 (2 * 128 * 64 + (S - 2) * 64 * 64)
+// <= 256 * 45056 < 2^24 (S <= 9), so every FP32 addition is exact.  After
+// each chunk the epilogue warps move C_w into two int64 registers per output
+// (hi = sum_{w<4} C_w 2^7(3-w), lo = sum_{w>=4} C_w 2^7(S-1-w)), exact
+// integer arithmetic; at the end W_ij = 2^(e_i+f_j) (hi 2^-35 + lo
+// 2^-7(S+1)) with one rounding.  The only errors are the truncated digits:
+// per product term about 2^-(7S+1) of the scaled operands.
+//
+// Kernel: one CTA per 128 rows x 32 columns of W.  Warp 0 issues TMA loads
+// (A digit tiles 128 x 64 per plane, X digit tiles of all S planes stacked:
+// 32 S rows x 64), warp 1 issues tcgen05.mma (M = 128, N = 32 (S - s) for A
+// plane s: one instruction covers every X plane that pairs with it, writing
+// the accumulators of weights s..S-1, which sit side by side in TMEM),
+// warps 2-5 drain TMEM.  (At S = 9 the plane-0 stack is 288 rows and goes
+// out as two instructions, N = 256 and N = 32.)  The accumulators are double-buffered when they fit
+// (2 x S x 32 FP32 columns <= 512, S <= 8) so draining overlaps the next
+// chunk; at S = 9 one set is used and the MMAs wait for each drain.  All waits are bounded (globaltimer); on expiry the CTA records a
+// timeout, drains what it started and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "sliced.cuh"
 
 namespace eigref {
 
-cudaError_t init_sliced_attributes() { return cudaSuccess; }
+namespace sl {
+
+constexpr int kBits = 7;           // bits per digit plane
+constexpr int kMaxS = 9;           // digit planes per operand (at most)
+constexpr int kDefaultS = 9;       // default digit planes (63 bits: FP64-level accuracy at n = 16384)
+constexpr int kBM = 128;           // rows of W per CTA
+constexpr int kBN = 32;            // columns of W per CTA
+constexpr int kBK = 64;            // K per pipeline stage (128 bytes of BF16)
+constexpr int kChunkBlocks = 4;    // K blocks per exact accumulation chunk (256)
+constexpr int kRA = 8;             // A ring stages (one per plane)
+constexpr int kRX = 2;             // X ring stages
+constexpr int kATile = kBM * kBK * 2;                // 16 KiB
+constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 36 KiB (all planes of a K block)
+constexpr int kThreads = 192;
+constexpr uint64_t kTimeoutNs = 2000000000ull;       // 2 s: no legitimate wait comes close
+constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
+
+struct __align__(8) Bars {
+  uint64_t a_full[kRA], a_empty[kRA], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the CTA is aborting or the wait ran past the limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+// Bounded wait used while leaving after an abort: lets work already issued
+// complete, gives up after 100 ms.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > 100000000ull) return;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+// K-major operand in the 128-byte swizzled layout TMA writes: rows of 128 B,
+// 8-row groups 1024 B apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+#define TC_LD32(taddr, r)                                                                                     \
+  asm volatile(                                                                                               \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                      \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),       \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), \
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),           \
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),           \
+        "=r"(r[30]), "=r"(r[31])                                                                             \
+      : "r"(taddr))
+
+struct GemmArgs {
+  const int* rowexp;     // [n_pad] e_i
+  const int* colexp;     // [k_pad] f_j
+  const double* X;       // row-major n x k (for the shift term)
+  double* P;             // row-major n x k
+  int64_t n;
+  int k, n_pad, S;
+  int xg;                // X planes per TMA load (32 xg rows, xg divides S, 32 xg <= 256)
+  double shift;
+  const Control* ctl;
+  int* err;              // set to 1 on a timed-out wait
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, GemmArgs g) {
+  // one read of the stop flag per CTA: an aborting CTA of this grid may set it
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sa = smem;                          // kRA x 16 KiB
+  unsigned char* sx = smem + kRA * kATile;           // kRX x 32 KiB
+  Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = g.S;
+  const int m0 = blockIdx.x * kBM;
+  const int nb = blockIdx.y;                         // column block of 32
+  const int KB = g.n_pad / kBK;                      // K blocks (multiple of kChunkBlocks)
+  const int NC = KB / kChunkBlocks;                  // accumulation chunks
+  const int NBUF = (2 * S * kBN <= 512) ? 2 : 1;     // TMEM accumulator sets (double-buffered if they fit)
+  volatile int* abort_flag = &bars->abort;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kRA; ++i) {
+      mbar_init(smem_u32(&bars->a_full[i]), 1);
+      mbar_init(smem_u32(&bars->a_empty[i]), 1);
+    }
+    for (int i = 0; i < kRX; ++i) {
+      mbar_init(smem_u32(&bars->x_full[i]), 1);
+      mbar_init(smem_u32(&bars->x_empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bars->acc_full[i]), 1);
+      mbar_init(smem_u32(&bars->acc_empty[i]), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
+      int issued_a = 0, issued_x = 0;
+      bool ok = true;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int xs = kb % kRX;
+        ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((kb / kRX) & 1) ^ 1, abort_flag);
+        if (!ok) break;
+        mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
+        for (int q = 0; q < S / g.xg; ++q)
+          tma_load_2d(smem_u32(sx + xs * kXTile + q * g.xg * kBN * kBK * 2), &tmX, smem_u32(&bars->x_full[xs]),
+                      kb * kBK, (nb * S + q * g.xg) * kBN);
+        ++issued_x;
+        for (int s = 0; s < S; ++s) {
+          const int i = kb * S + s, as = i % kRA;
+          ok = mbar_wait(smem_u32(&bars->a_empty[as]), ((i / kRA) & 1) ^ 1, abort_flag);
+          if (!ok) break;
+          mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
+          tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kb * kBK, s * g.n_pad + m0);
+          ++issued_a;
+        }
+      }
+      if (!ok) {
+        // let the copies this thread started land before the CTA leaves
+        for (int i = (issued_a > kRA ? issued_a - kRA : 0); i < issued_a; ++i)
+          mbar_drain(smem_u32(&bars->a_full[i % kRA]), (i / kRA) & 1);
+        for (int i = (issued_x > kRX ? issued_x - kRX : 0); i < issued_x; ++i)
+          mbar_drain(smem_u32(&bars->x_full[i % kRX]), (i / kRX) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = true;
+      int committed_chunks = 0;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int c = kb / kChunkBlocks, buf = c % NBUF;
+        if (kb % kChunkBlocks == 0) {
+          ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+        }
+        const int xs = kb % kRX;
+        ok = mbar_wait(smem_u32(&bars->x_full[xs]), (kb / kRX) & 1, abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t xaddr = smem_u32(sx + xs * kXTile);
+        for (int s = 0; s < S; ++s) {
+          const int i = kb * S + s, as = i % kRA;
+          ok = mbar_wait(smem_u32(&bars->a_full[as]), (i / kRA) & 1, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t aaddr = smem_u32(sa + as * kATile);
+          const uint32_t dt = tbase + (uint32_t)(buf * S * kBN + s * kBN);
+          // B = X planes 0 .. S-1-s stacked (N = 32 (S - s) rows); an M = 128
+          // instruction takes N <= 256, so wider stacks are issued in pieces
+          const int ntot = kBN * (S - s);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint32_t acc = (kb % kChunkBlocks == 0 && s == 0 && kk == 0) ? 0u : 1u;
+            for (int n0 = 0; n0 < ntot; n0 += 256) {
+              const int nn = ntot - n0 < 256 ? ntot - n0 : 256;
+              tc_mma(dt + (uint32_t)n0, smem_desc(aaddr + kk * 32), smem_desc(xaddr + n0 * kBK * 2 + kk * 32),
+                     idesc_bf16(kBM, nn), acc);
+            }
+          }
+          tc_commit(smem_u32(&bars->a_empty[as]));
+        }
+        if (!ok) break;
+        tc_commit(smem_u32(&bars->x_empty[xs]));
+        if (kb % kChunkBlocks == kChunkBlocks - 1) {
+          tc_commit(smem_u32(&bars->acc_full[buf]));
+          ++committed_chunks;
+        }
+      }
+      if (!ok) {
+        // wait for the MMAs already issued before the CTA releases TMEM
+        tc_commit(smem_u32(&bars->drain));
+        mbar_drain(smem_u32(&bars->drain), 0);
+      }
+      (void)committed_chunks;
+    }
+  } else {
+    // ---------------- epilogue: drain chunks into exact int64 sums ----------------
+    const int lg = warp & 3;                           // TMEM lane group of this warp
+    const int row = m0 + lg * 32 + lane;
+    long long hi[kBN], lo[kBN];
+#pragma unroll
+    for (int j = 0; j < kBN; ++j) hi[j] = lo[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < NC && ok; ++c) {
+      const int buf = c % NBUF;
+      // one lane waits, the warp follows (the TMEM loads below are warp-collective)
+      int w_ok = 0;
+      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
+      ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+      __syncwarp();
+      if (!ok) break;
+      tc_fence_after();
+      for (int w = 0; w < S; ++w) {
+        uint32_t r[kBN];
+        const uint32_t ta = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * S * kBN + w * kBN);
+        TC_LD32(ta, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (w < 4) {
+          const int sh = kBits * (3 - w);
+#pragma unroll
+          for (int j = 0; j < kBN; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        } else {
+          const int sh = kBits * (S - 1 - w);
+#pragma unroll
+          for (int j = 0; j < kBN; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[buf]));
+    }
+    if (ok && row < g.n) {
+      const double lo_scale = ldexp(1.0, -kBits * (S + 1));
+      const int er = g.rowexp[row];
+      const int64_t rk = (int64_t)row * g.k;
+#pragma unroll
+      for (int j = 0; j < kBN; ++j) {
+        const int col = nb * kBN + j;
+        if (col < g.k) {
+          const double v = fma((double)lo[j], lo_scale, (double)hi[j] * 0x1p-35);
+          const double w = ldexp(v, er + g.colexp[col]);
+          g.P[rk + col] = w - g.shift * g.X[rk + col];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (bars->abort && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+    if (g.ctl) {
+      Control* c = const_cast<Control*>(g.ctl);
+      c->status = EIGREF_E_TIMEOUT;
+      c->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Digit planes of A: rows of As[s] (n_pad x n_pad BF16, row-major), e_i per row.
+// One warp per row; 8 consecutive elements per lane and step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int row_exponent(double amax) {
+  if (!(amax > 0.0) || !isfinite(amax)) return 0;
+  int e;
+  frexp(amax, &e);       // amax = m 2^e, m in [0.5, 1): |a| < 2^e
+  return e;
+}
+
+__global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t lda, int n_pad, int S,
+                               __nv_bfloat16* __restrict__ As, int* __restrict__ rowexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t plane = (int64_t)n_pad * n_pad;
+  for (int64_t i = wid; i < n_pad; i += nw) {
+    double amax = 0.0;
+    if (i < n)
+      for (int64_t l = lane; l < n; l += 32) amax = fmax(amax, fabs(A[i * lda + l]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const int e = row_exponent(amax);
+    if (lane == 0) rowexp[i] = e;
+    for (int64_t l0 = (int64_t)lane * 8; l0 < n_pad; l0 += 32 * 8) {
+      double r[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t l = l0 + q;
+        r[q] = (i < n && l < n) ? ldexp(A[i * lda + l], kBits - e) : 0.0;
+      }
+      for (int s = 0; s < S; ++s) {
+        __align__(16) __nv_bfloat16 d[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const double di = rint(r[q]);
+          d[q] = __float2bfloat16_rn((float)di);
+          r[q] = (r[q] - di) * (double)(1 << kBits);
+        }
+        *reinterpret_cast<uint4*>(As + s * plane + i * n_pad + l0) = *reinterpret_cast<uint4*>(d);
+      }
+    }
+  }
+}
+
+// Column maxima of X (row-major n x k) as non-negative double bit patterns.
+__global__ void colmax_kernel(const double* __restrict__ X, int64_t n, int k, unsigned long long* __restrict__ cmax,
+                              const Control* ctl) {
+  if (ctl && ctl->done) return;
+  const int j = threadIdx.x % k;   // blockDim.x is a multiple of k
+  const int rpb = blockDim.x / k;
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / k; i < n; i += (int64_t)gridDim.x * rpb)
+    m = fmax(m, fabs(X[i * k + j]));
+  atomicMax(cmax + j, (unsigned long long)__double_as_longlong(m));
+}
+
+// Digit planes of X: Xs[(cb * S + t) * 32 + jj][l] (BF16), column j = 32 cb + jj.
+// A CTA takes 64 rows x 32 columns through shared memory so both the FP64 reads
+// and the BF16 writes are contiguous.
+__global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__ X, int64_t n, int k, int n_pad,
+                                                      int S, const unsigned long long* __restrict__ cmax,
+                                                      __nv_bfloat16* __restrict__ Xs, int* __restrict__ colexp,
+                                                      const Control* ctl) {
+  if (ctl && ctl->done) return;
+  __shared__ double tile[64][33];
+  __shared__ int fexp[32];
+  const int l0 = blockIdx.x * 64;
+  const int cb = blockIdx.y;
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const int j = cb * 32 + tid;
+    const int f = j < k ? row_exponent(__longlong_as_double((long long)cmax[j])) : 0;
+    fexp[tid] = f;
+    if (blockIdx.x == 0 && j < k) colexp[j] = f;
+  }
+  for (int e = tid; e < 64 * 32; e += 256) {
+    const int rr = e >> 5, jj = e & 31;
+    const int64_t l = l0 + rr;
+    const int j = cb * 32 + jj;
+    tile[rr][jj] = (l < n && j < k) ? X[l * k + j] : 0.0;
+  }
+  __syncthreads();
+  // thread -> (jj, 8 consecutive rows); writes 16 bytes per plane
+  const int jj = tid >> 3, r0 = (tid & 7) * 8;
+  double r[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) r[q] = ldexp(tile[r0 + q][jj], kBits - fexp[jj]);
+  for (int t = 0; t < S; ++t) {
+    __align__(16) __nv_bfloat16 d[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double di = rint(r[q]);
+      d[q] = __float2bfloat16_rn((float)di);
+      r[q] = (r[q] - di) * (double)(1 << kBits);
+    }
+    const int64_t rowid = ((int64_t)cb * S + t) * 32 + jj;
+    *reinterpret_cast<uint4*>(Xs + rowid * n_pad + l0 + r0) = *reinterpret_cast<uint4*>(d);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor maps (driver entry point fetched at run time; no -lcuda)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+              uint32_t box_outer) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace sl
+
+cudaError_t init_sliced_attributes() {
+  return cudaFuncSetAttribute(sl::sliced_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
+}
+
+// X planes per TMA load: the largest divisor g of S with a box of 32 g <= 256 rows.
+static int x_group(int S) {
+  for (int g = S; g > 0; --g)
+    if (S % g == 0 && g * sl::kBN <= 256) return g;
+  return 1;
+}
+
+// ---- plan / workspace ----
+struct SlicedLayout {
+  size_t a_planes, rowexp, x_planes, colexp, cmax, err, total;
+};
+
+static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int S) {
+  SlicedLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 1023) & ~size_t(1023);
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  L.a_planes = take((size_t)S * n_pad * n_pad * 2);
+  L.rowexp = take((size_t)n_pad * 4);
+  L.x_planes = take((size_t)S * k_pad * n_pad * 2);
+  L.colexp = take((size_t)k_pad * 4);
+  L.cmax = take((size_t)k_pad * 8);
+  L.err = take(64);
+  L.total = off + 1024;
+  return L;
+}
 
 int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int precision, int slices) {
   A_ = A;
@@ -13,16 +541,103 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
   lda_ = lda;
   k_ = k;
   precision_ = precision;
-  slices_ = slices;
-  snprintf(err_, sizeof(err_), "split-precision product not built yet");
-  return EIGREF_E_UNSUPPORTED;
+  slices_ = slices > 0 ? slices : sl::kDefaultS;
+  if (precision != EIGREF_BF16_SLICES) {
+    snprintf(err_, sizeof(err_), "split form %d not built (BF16 slices only)", precision);
+    return EIGREF_E_UNSUPPORTED;
+  }
+  if (slices_ < 2 || slices_ > sl::kMaxS) {
+    snprintf(err_, sizeof(err_), "slices must be in [2, %d]", sl::kMaxS);
+    return EIGREF_E_INVALID;
+  }
+  // int64 headroom of the low group: (n / 256) 2^23.5 2^(7 (S - 5)) (S - 4) < 2^63
+  const int64_t nmax = slices_ <= 8 ? ((int64_t)1 << 24) : ((int64_t)1 << 18);
+  if (n > nmax) {
+    snprintf(err_, sizeof(err_), "split form with %d slices limited to n <= %lld", slices_, (long long)nmax);
+    return EIGREF_E_INVALID;
+  }
+  if (!sl::encode_fn()) {
+    snprintf(err_, sizeof(err_), "cuTensorMapEncodeTiled unavailable");
+    return EIGREF_E_CUDA;
+  }
+  n_pad_ = (int)((n + 255) / 256 * 256);
+  k_pad_ = (k + 31) / 32 * 32;
+  return EIGREF_OK;
 }
-size_t SlicedA::workspace_bytes() const { return 0; }
-void SlicedA::bind_workspace(char* p) { ws_ = p; }
-int SlicedA::prepare(cudaStream_t) { return EIGREF_E_UNSUPPORTED; }
-int SlicedA::product(const double*, double*, double, const Control*, cudaStream_t, cudaEvent_t, cudaEvent_t,
-                     unsigned) {
-  return 0;
+
+size_t SlicedA::workspace_bytes() const { return sliced_layout(n_pad_, k_pad_, slices_).total; }
+
+void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023)); }
+
+int SlicedA::prepare(cudaStream_t s) {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, slices_);
+  auto* ap = reinterpret_cast<__nv_bfloat16*>(ws_ + L.a_planes);
+  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  // X planes: zero once, so padding rows and columns stay zero
+  if (cudaMemsetAsync(xp, 0, (size_t)slices_ * k_pad_ * n_pad_ * 2, s) != cudaSuccess ||
+      cudaMemsetAsync(ws_ + L.err, 0, 64, s) != cudaSuccess) {
+    snprintf(err_, sizeof(err_), "memset of slice planes failed");
+    return EIGREF_E_CUDA;
+  }
+  sl::slice_a_kernel<<<152 * 8, 256, 0, s>>>(A_, n_, lda_, n_pad_, slices_, ap,
+                                               reinterpret_cast<int*>(ws_ + L.rowexp));
+  if (!sl::make_map(reinterpret_cast<CUtensorMap*>(tmA_), ap, (uint64_t)n_pad_, (uint64_t)slices_ * n_pad_, sl::kBK,
+                    sl::kBM) ||
+      !sl::make_map(reinterpret_cast<CUtensorMap*>(tmX_), xp, (uint64_t)n_pad_, (uint64_t)slices_ * k_pad_, sl::kBK,
+                    (uint32_t)(x_group(slices_) * sl::kBN))) {
+    snprintf(err_, sizeof(err_), "tensor map encoding failed");
+    return EIGREF_E_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    snprintf(err_, sizeof(err_), "slicing A failed");
+    return EIGREF_E_CUDA;
+  }
+  return EIGREF_OK;
+}
+
+int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
+                     cudaEvent_t ev1, unsigned ev_flags) {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, slices_);
+  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.cmax);
+  int* colexp = reinterpret_cast<int*>(ws_ + L.colexp);
+  cudaMemsetAsync(cmax, 0, (size_t)k_ * 8, s);
+  const int rpb = 256 / k_ > 0 ? 256 / k_ : 1;
+  sl::colmax_kernel<<<152 * 4, rpb * k_, 0, s>>>(X, n_, k_, cmax, ctl);
+  dim3 gx((unsigned)(n_pad_ / 64), (unsigned)(k_pad_ / 32));
+  sl::slice_x_kernel<<<gx, 256, 0, s>>>(X, n_, k_, n_pad_, slices_, cmax, xp, colexp, ctl);
+  sl::GemmArgs g;
+  g.rowexp = reinterpret_cast<const int*>(ws_ + L.rowexp);
+  g.colexp = colexp;
+  g.X = X;
+  g.P = P;
+  g.n = n_;
+  g.k = k_;
+  g.n_pad = n_pad_;
+  g.S = slices_;
+  g.xg = x_group(slices_);
+  g.shift = shift;
+  g.ctl = ctl;
+  g.err = reinterpret_cast<int*>(ws_ + L.err);
+  dim3 grid((unsigned)(n_pad_ / sl::kBM), (unsigned)(k_pad_ / sl::kBN));
+  if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
+  sl::sliced_gemm_kernel<<<grid, sl::kThreads, sl::kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(tmA_),
+                                                                   *reinterpret_cast<const CUtensorMap*>(tmX_), g);
+  if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
+  return 3;
+}
+
+int SlicedA::timed_out(cudaStream_t s) const {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, slices_);
+  int v = 0;
+  cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return v;
+}
+
+double SlicedA::executed_flops() const {
+  const double pairs = slices_ * (slices_ + 1) / 2.0;
+  return 2.0 * (double)n_pad_ * (double)n_pad_ * (double)k_pad_ * pairs;
 }
 
 }  // namespace eigref

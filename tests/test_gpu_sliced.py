@@ -1,0 +1,155 @@
+"""The split-precision (BF16 digit-plane) tensor-core product and sweeps:
+the product against double-double at sampled entries within the bound the
+slicing gives, adversarial inputs for the exactness of the FP32 chunks, sweep
+parity with the FP64 oracle and the final accuracy of a converged run."""
+import numpy as np
+import pytest
+
+from oracle import dd, refine as R
+from tests.gpu_util import dev, host, rel_diff, sweep_tol, U
+from workloads import configs as C
+
+pytestmark = pytest.mark.gpu
+
+SLICE_BITS = 7
+
+
+@pytest.fixture(scope="module")
+def eig():
+    import paper_2602_23778_gb300 as pkg
+    h = pkg.Handle(0)
+    yield h
+    h.close()
+
+
+def dense_case(n, k, seed, m=8):
+    lam = C.separated_graded(n, k, seed, gap=min(0.01, 0.4 / k), tail=0.5)
+    return C.householder(n, m, k, lam, seed, target="largest_mag", x_noise=1e-6)
+
+
+def scale_exponents(M, axis):
+    """Exponent e with max|.| < 2^e along `axis` (rows of A / columns of X)."""
+    return np.frexp(np.abs(M).max(axis=axis))[1]
+
+
+def slice_bound(A, X, shift, slices):
+    """|W_sliced - W| <= 2^(e_i + f_j) n 2^-(7 S) + 2 u (|A||X| + |shift x|)_ij:
+    each product term loses at most ~2^-7S of its scaled size to the dropped
+    digit pairs, and the FP64 recombination rounds once."""
+    n = A.shape[0]
+    e = scale_exponents(A, 1)
+    f = scale_exponents(X, 0)
+    trunc = np.ldexp(np.ones((n, X.shape[1])), e[:, None] + f[None, :]) * n * 2.0 ** (-SLICE_BITS * slices)
+    return trunc + 2 * U * (np.abs(A) @ np.abs(X) + abs(shift) * np.abs(X))
+
+
+def product(eig, A, X, shift, precision, slices=0):
+    import torch
+    Xd = dev(np.asfortranarray(X))
+    P = torch.zeros_like(Xd)
+    eig.product_dense(dev(A), Xd, P, shift=shift, precision=precision, slices=slices)
+    return host(P)
+
+
+@pytest.mark.parametrize("n,k", [(257, 1), (300, 8), (520, 33), (1000, 40), (2000, 128)])
+def test_sliced_product_vs_double_double(eig, n, k):
+    p = dense_case(n, k, seed=300 + n)
+    shift = 0.125
+    Pb = product(eig, p.A, p.X0, shift, "bf16")
+    rng = np.random.default_rng(n)
+    rows, cols = rng.integers(0, n, 600), rng.integers(0, k, 600)
+    hi, lo = dd.product_entries(p.A, p.X0, rows, cols, shift=shift)
+    err = np.abs(Pb[rows, cols] - hi)
+    bound = slice_bound(p.A, p.X0, shift, 8)[rows, cols]
+    assert np.all(err <= bound)
+
+
+def test_sliced_exact_on_adversarial_signs(eig):
+    """All-positive A and X: every digit product has the same sign, the worst
+    case for the FP32 accumulation (partial sums grow linearly in K)."""
+    n, k = 4096, 64
+    rng = np.random.default_rng(5)
+    B = rng.random((n, n))
+    A = 0.5 * (B + B.T)
+    X = np.asfortranarray(rng.random((n, k)))
+    Pb = product(eig, A, X, 0.0, "bf16")
+    rows, cols = rng.integers(0, n, 300), rng.integers(0, k, 300)
+    hi, lo = dd.product_entries(A, X, rows, cols)
+    err = np.abs(Pb[rows, cols] - hi)
+    assert np.all(err <= slice_bound(A, X, 0.0, 8)[rows, cols])
+    assert (err / np.abs(hi)).max() < 64 * U
+
+
+@pytest.mark.parametrize("slices", [6, 7, 8, 9])
+def test_slice_count_sets_accuracy(eig, slices):
+    p = dense_case(700, 16, seed=31)
+    Pb = product(eig, p.A, p.X0, 0.0, "bf16", slices=slices)
+    rng = np.random.default_rng(slices)
+    rows, cols = rng.integers(0, 700, 400), rng.integers(0, 16, 400)
+    hi, lo = dd.product_entries(p.A, p.X0, rows, cols)
+    err = np.abs(Pb[rows, cols] - hi)
+    assert np.all(err <= slice_bound(p.A, p.X0, 0.0, slices)[rows, cols])
+
+
+def run_gpu(h, p, **kw):
+    A = dev(p.A)
+    X = dev(np.asfortranarray(p.X0))
+    rep = h.refine_dense(A, X, norm_a=p.normA, target="shift", shift=p.shift, history=True, precision="bf16", **kw)
+    return host(X), rep
+
+
+def split_tol(p):
+    """Per-sweep parity of the split form with the FP64 oracle: the product
+    differs from FP64 by about the FP64 rounding (sqrt(n) u scale), so the
+    same gap-amplified bound as two FP64 evaluations applies, with the slice
+    truncation added to u."""
+    return sweep_tol((1 + p.n ** 0.5 * 2.0 ** -(SLICE_BITS * 8) / U) * (p.normA + abs(p.shift)), p.min_gap)
+
+
+@pytest.mark.parametrize("n,k", [(300, 8), (1000, 128), (517, 17)])
+def test_sliced_sweep_parity(eig, n, k):
+    p = dense_case(n, k, seed=400 + n)
+    Xg, rg = run_gpu(eig, p, max_iters=1)
+    Xo, ro = R.refine(R.dense_operator(p.A, p.shift), p.X0, p.normA, p.shift, max_iters=1)
+    assert rg["status"] == 0 and rg["iterations"] == 1
+    assert rel_diff(Xg, Xo) <= split_tol(p)
+    assert rel_diff(rg["eigenvalues"], ro["d"]) <= 1e-12
+
+
+def test_sliced_trajectory_n512(eig):
+    p = C.config1()
+    Xg, rg = run_gpu(eig, p, max_iters=10)
+    Xo, ro = R.refine(R.dense_operator(p.A, p.shift), p.X0, p.normA, p.shift, max_iters=10)
+    assert rel_diff(Xg, Xo) <= 1e-12
+
+
+@pytest.mark.parametrize("slices", [8, 9])
+def test_sliced_converges_like_fp64(eig, slices):
+    """Both forms run to the same residual level; the split form's final angle
+    (double-double, against the construction's eigenvectors) stays within the
+    1e-13 target and close to the FP64 form's."""
+    p = dense_case(1200, 24, seed=41)
+    Xb, rb = run_gpu(eig, p, max_iters=400, tol=1e-14, stop="residual", slices=slices)
+    assert rb["status"] == 0, rb
+    sb = dd.sin_angles(Xb, p.Xtrue).max()
+    Xf = dev(np.asfortranarray(p.X0))
+    rf = eig.refine_dense(dev(p.A), Xf, norm_a=p.normA, max_iters=400, tol=1e-14, stop="residual")
+    sf = dd.sin_angles(host(Xf), p.Xtrue).max()
+    orth = np.abs(dd.orth_error(Xb)).max()
+    assert sb < 1e-13 and orth < 1e-13, (sb, sf, orth)
+    if slices == 9:      # 63 bits: as accurate as the FP64 form
+        assert sb <= 4 * sf + 2e-15 and orth < 1e-14, (sb, sf, orth)
+    assert abs(rb["iterations"] - rf["iterations"]) <= 3
+
+
+@pytest.mark.slow
+def test_full_size_split_product_and_sweep(eig):
+    p = C.config3()
+    rng = np.random.default_rng(7)
+    rows, cols = rng.integers(0, p.n, 200), rng.integers(0, p.k, 200)
+    Pb = product(eig, p.A, p.X0, 0.0, "bf16")
+    hi, lo = dd.product_entries(p.A, p.X0, rows, cols)
+    assert np.all(np.abs(Pb[rows, cols] - hi) <= slice_bound(p.A, p.X0, 0.0, 8)[rows, cols])
+    Xg, rg = run_gpu(eig, p, max_iters=1)
+    Xo, ro = R.refine(R.dense_operator(p.A), p.X0, p.normA, 0.0, max_iters=1)
+    assert rel_diff(Xg, Xo) <= split_tol(p)
