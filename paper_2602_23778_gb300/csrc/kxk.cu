@@ -68,6 +68,10 @@ __global__ void kk_prep_kernel(SweepBufs b, int k) {
   }
 }
 
+__device__ __forceinline__ double nan_max(double a, double b) {   // NaN-propagating max
+  return (a != a || b != b) ? __longlong_as_double(0x7FF8000000000000ll) : fmax(a, b);
+}
+
 // LU with partial pivoting of Y1 in shared memory (one CTA).  A pivot below
 // k u max|Y1| means Y1 is singular to working precision: Algorithm 1 cannot
 // proceed, the sweep stops with EIGREF_E_SINGULAR_WY.
@@ -82,14 +86,22 @@ __global__ void __launch_bounds__(512) kk_lu_kernel(SweepBufs b, int k) {
   double amax = 0.0;
   for (int64_t e = tid; e < kk; e += blockDim.x) {
     a[e] = b.y1[e];
-    amax = fmax(amax, fabs(a[e]));
+    amax = nan_max(amax, fabs(a[e]));
   }
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  for (int o = 16; o > 0; o >>= 1) amax = nan_max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((tid & 31) == 0) sh[tid >> 5] = amax;
   if (tid == 0) s_sing = 0;
   __syncthreads();
   amax = 0.0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) amax = fmax(amax, sh[q]);
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) amax = nan_max(amax, sh[q]);
+  if (!isfinite(amax)) {                 // Inf / NaN in X: not a singularity
+    if (tid == 0) {
+      ctl->nonfinite = 1;
+      ctl->status = EIGREF_E_NONFINITE;
+      ctl->done = 1;
+    }
+    return;
+  }
   const double thresh = k * kUnitRoundoff * amax;
   for (int p = 0; p < k; ++p) {
     if (tid < 32) {

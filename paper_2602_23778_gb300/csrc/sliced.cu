@@ -25,7 +25,7 @@
 // 32 S rows x 64), warp 1 issues tcgen05.mma (M = 128, N = 32 (S - s) for A
 // plane s: one instruction covers every X plane that pairs with it, writing
 // the accumulators of weights s..S-1, which sit side by side in TMEM),
-// warps 2-5 drain TMEM.  (At S = 9 the plane-0 stack is 288 rows and goes
+// warps 2-9 drain TMEM (two per lane group, 16 columns each).  (At S = 9 the plane-0 stack is 288 rows and goes
 // out as two instructions, N = 256 and N = 32.)  The accumulators are double-buffered when they fit
 // (2 x S x 32 FP32 columns <= 512, S <= 8) so draining overlaps the next
 // chunk; at S = 9 one set is used and the MMAs wait for each drain.  All waits are bounded (globaltimer); on expiry the CTA records a
@@ -53,7 +53,9 @@ constexpr int kRA = 8;             // A ring stages (one per plane)
 constexpr int kRX = 2;             // X ring stages
 constexpr int kATile = kBM * kBK * 2;                // 16 KiB
 constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 36 KiB (all planes of a K block)
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;       // two warps per TMEM lane group, 16 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kNonFinite = -100000;  // exponent marking a row / column holding Inf or NaN
 constexpr uint64_t kTimeoutNs = 2000000000ull;       // 2 s: no legitimate wait comes close
 constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
 
@@ -140,6 +142,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+#define TC_LD16(taddr, r)                                                                                   \
+  asm volatile(                                                                                             \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),     \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),          \
+        "=r"(r[15])                                                                                         \
+      : "r"(taddr))
+
 #define TC_LD32(taddr, r)                                                                                     \
   asm volatile(                                                                                               \
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
@@ -164,6 +174,12 @@ struct GemmArgs {
   int* err;              // set to 1 on a timed-out wait
 };
 
+// One instruction shape per (S, plane s): N = 32 (S - s), cut into pieces of
+// at most 256 columns.  Everything about the issue order is a compile-time
+// constant, so the issuing thread does no arithmetic between MMAs (measured on
+// GB300: a tcgen05.mma costs max(N/2, ~40) cycles when issued back to back,
+// and any dependent integer work in between adds to that).
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, GemmArgs g) {
   // one read of the stop flag per CTA: an aborting CTA of this grid may set it
@@ -174,15 +190,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sa = smem;                          // kRA x 16 KiB
-  unsigned char* sx = smem + kRA * kATile;           // kRX x 32 KiB
+  unsigned char* sx = smem + kRA * kATile;           // kRX x 36 KiB
   Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int S = g.S;
-  const int m0 = blockIdx.x * kBM;
-  const int nb = blockIdx.y;                         // column block of 32
+  // column blocks vary fastest, so the CTAs sharing an A row block run together
+  // and read its digit planes from HBM once
+  const int nb = blockIdx.x;                         // column block of 32
+  const int m0 = blockIdx.y * kBM;
   const int KB = g.n_pad / kBK;                      // K blocks (multiple of kChunkBlocks)
   const int NC = KB / kChunkBlocks;                  // accumulation chunks
-  const int NBUF = (2 * S * kBN <= 512) ? 2 : 1;     // TMEM accumulator sets (double-buffered if they fit)
+  constexpr int NBUF = (2 * S * kBN <= 512) ? 2 : 1; // TMEM accumulator sets (double-buffered if they fit)
+  constexpr int XG = (S * kBN <= 256) ? S : (S % 3 == 0 ? 3 : 1);  // X planes per TMA load
   volatile int* abort_flag = &bars->abort;
 
   if (threadIdx.x == 0) {
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
-      mbar_init(smem_u32(&bars->acc_empty[i]), 4);  // one arrival per epilogue warp
+      mbar_init(smem_u32(&bars->acc_empty[i]), kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bars->drain), 1);
     bars->abort = 0;
@@ -220,22 +238,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
       int issued_a = 0, issued_x = 0;
       bool ok = true;
+      int as = 0;
+      uint32_t aph = 0;                              // lap parity of the A ring
       for (int kb = 0; kb < KB && ok; ++kb) {
-        const int xs = kb % kRX;
-        ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((kb / kRX) & 1) ^ 1, abort_flag);
+        const int xs = kb & 1;
+        ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((kb >> 1) & 1) ^ 1, abort_flag);
         if (!ok) break;
         mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
-        for (int q = 0; q < S / g.xg; ++q)
-          tma_load_2d(smem_u32(sx + xs * kXTile + q * g.xg * kBN * kBK * 2), &tmX, smem_u32(&bars->x_full[xs]),
-                      kb * kBK, (nb * S + q * g.xg) * kBN);
+#pragma unroll
+        for (int q = 0; q < S / XG; ++q)
+          tma_load_2d(smem_u32(sx + xs * kXTile + q * XG * kBN * kBK * 2), &tmX, smem_u32(&bars->x_full[xs]),
+                      kb * kBK, (nb * S + q * XG) * kBN);
         ++issued_x;
+#pragma unroll
         for (int s = 0; s < S; ++s) {
-          const int i = kb * S + s, as = i % kRA;
-          ok = mbar_wait(smem_u32(&bars->a_empty[as]), ((i / kRA) & 1) ^ 1, abort_flag);
+          ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, abort_flag);
           if (!ok) break;
           mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
           tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kb * kBK, s * g.n_pad + m0);
           ++issued_a;
+          if (++as == kRA) {
+            as = 0;
+            aph ^= 1;
+          }
         }
       }
       if (!ok) {
@@ -249,65 +274,79 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
+      const uint64_t a_desc0 = smem_desc(smem_u32(sa));
+      const uint64_t x_desc0 = smem_desc(smem_u32(sx));
       bool ok = true;
-      int committed_chunks = 0;
+      int as = 0;
+      uint32_t aph = 0;
       for (int kb = 0; kb < KB && ok; ++kb) {
-        const int c = kb / kChunkBlocks, buf = c % NBUF;
-        if (kb % kChunkBlocks == 0) {
+        const int c = kb / kChunkBlocks;
+        const int buf = NBUF == 2 ? (c & 1) : 0;
+        const bool first = (kb % kChunkBlocks) == 0;
+        if (first) {
           ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
           if (!ok) break;
           tc_fence_after();
         }
-        const int xs = kb % kRX;
-        ok = mbar_wait(smem_u32(&bars->x_full[xs]), (kb / kRX) & 1, abort_flag);
+        const int xs = kb & 1;
+        ok = mbar_wait(smem_u32(&bars->x_full[xs]), (kb >> 1) & 1, abort_flag);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t xaddr = smem_u32(sx + xs * kXTile);
+        const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
+        const uint32_t dbase = tbase + (uint32_t)(buf * S * kBN);
+        const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
+#pragma unroll
         for (int s = 0; s < S; ++s) {
-          const int i = kb * S + s, as = i % kRA;
-          ok = mbar_wait(smem_u32(&bars->a_full[as]), (i / kRA) & 1, abort_flag);
+          ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t aaddr = smem_u32(sa + as * kATile);
-          const uint32_t dt = tbase + (uint32_t)(buf * S * kBN + s * kBN);
-          // B = X planes 0 .. S-1-s stacked (N = 32 (S - s) rows); an M = 128
-          // instruction takes N <= 256, so wider stacks are issued in pieces
-          const int ntot = kBN * (S - s);
-#pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint32_t acc = (kb % kChunkBlocks == 0 && s == 0 && kk == 0) ? 0u : 1u;
-            for (int n0 = 0; n0 < ntot; n0 += 256) {
-              const int nn = ntot - n0 < 256 ? ntot - n0 : 256;
-              tc_mma(dt + (uint32_t)n0, smem_desc(aaddr + kk * 32), smem_desc(xaddr + n0 * kBK * 2 + kk * 32),
-                     idesc_bf16(kBM, nn), acc);
-            }
+          const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
+          // B = X planes 0 .. S-1-s stacked: N = 32 (S - s) rows, issued as
+          // pieces of at most 256 (the M = 128 limit); +2 in the address field
+          // steps 32 bytes (16 K) inside the 128-byte swizzle row
+          const int N = kBN * (S - s);
+          const int N1 = N < 256 ? N : 256;
+          const uint32_t dt = dbase + (uint32_t)(s * kBN);
+          tc_mma(dt, ad, xd, idesc_bf16(kBM, N1), s == 0 ? acc0 : 1u);
+          tc_mma(dt, ad + 2, xd + 2, idesc_bf16(kBM, N1), 1u);
+          tc_mma(dt, ad + 4, xd + 4, idesc_bf16(kBM, N1), 1u);
+          tc_mma(dt, ad + 6, xd + 6, idesc_bf16(kBM, N1), 1u);
+          if (N > 256) {
+            const uint64_t xd2 = xd + (uint64_t)((256 * kBK * 2) >> 4);
+            const uint32_t id2 = idesc_bf16(kBM, N - 256);
+            tc_mma(dt + 256u, ad, xd2, id2, s == 0 ? acc0 : 1u);
+            tc_mma(dt + 256u, ad + 2, xd2 + 2, id2, 1u);
+            tc_mma(dt + 256u, ad + 4, xd2 + 4, id2, 1u);
+            tc_mma(dt + 256u, ad + 6, xd2 + 6, id2, 1u);
           }
           tc_commit(smem_u32(&bars->a_empty[as]));
+          if (++as == kRA) {
+            as = 0;
+            aph ^= 1;
+          }
         }
         if (!ok) break;
         tc_commit(smem_u32(&bars->x_empty[xs]));
-        if (kb % kChunkBlocks == kChunkBlocks - 1) {
-          tc_commit(smem_u32(&bars->acc_full[buf]));
-          ++committed_chunks;
-        }
+        if (kb % kChunkBlocks == kChunkBlocks - 1) tc_commit(smem_u32(&bars->acc_full[buf]));
       }
       if (!ok) {
         // wait for the MMAs already issued before the CTA releases TMEM
         tc_commit(smem_u32(&bars->drain));
         mbar_drain(smem_u32(&bars->drain), 0);
       }
-      (void)committed_chunks;
     }
   } else {
     // ---------------- epilogue: drain chunks into exact int64 sums ----------------
     const int lg = warp & 3;                           // TMEM lane group of this warp
+    const int half = (warp - 2) >> 2;                  // which 16 of the 32 columns
     const int row = m0 + lg * 32 + lane;
-    long long hi[kBN], lo[kBN];
+    constexpr int kC = kBN / 2;
+    long long hi[kC], lo[kC];
 #pragma unroll
-    for (int j = 0; j < kBN; ++j) hi[j] = lo[j] = 0;
+    for (int j = 0; j < kC; ++j) hi[j] = lo[j] = 0;
     bool ok = true;
     for (int c = 0; c < NC && ok; ++c) {
-      const int buf = c % NBUF;
+      const int buf = NBUF == 2 ? (c & 1) : 0;
       // one lane waits, the warp follows (the TMEM loads below are warp-collective)
       int w_ok = 0;
       if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
@@ -315,19 +354,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-      for (int w = 0; w < S; ++w) {
-        uint32_t r[kBN];
-        const uint32_t ta = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * S * kBN + w * kBN);
-        TC_LD32(ta, r);
+      const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * S * kBN + half * kC);
+      // several weights per round trip to TMEM (two at S >= 8, within the register budget)
+      constexpr int GW = S >= 8 ? 2 : 3;
+#pragma unroll
+      for (int w0 = 0; w0 < S; w0 += GW) {
+        uint32_t r[GW][kC];
+#pragma unroll
+        for (int q = 0; q < GW; ++q)
+          if (w0 + q < S) TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (w < 4) {
-          const int sh = kBits * (3 - w);
 #pragma unroll
-          for (int j = 0; j < kBN; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
-        } else {
-          const int sh = kBits * (S - 1 - w);
+        for (int q = 0; q < GW; ++q) {
+          const int w = w0 + q;
+          if (w >= S) continue;
+          if (w < 4) {
+            const int sh = kBits * (3 - w);
 #pragma unroll
-          for (int j = 0; j < kBN; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+            for (int j = 0; j < kC; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
+          } else {
+            const int sh = kBits * (S - 1 - w);
+#pragma unroll
+            for (int j = 0; j < kC; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
+          }
         }
       }
       tc_fence_before();
@@ -339,11 +388,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int er = g.rowexp[row];
       const int64_t rk = (int64_t)row * g.k;
 #pragma unroll
-      for (int j = 0; j < kBN; ++j) {
-        const int col = nb * kBN + j;
+      for (int j = 0; j < kC; ++j) {
+        const int col = nb * kBN + half * kC + j;
         if (col < g.k) {
-          const double v = fma((double)lo[j], lo_scale, (double)hi[j] * 0x1p-35);
-          const double w = ldexp(v, er + g.colexp[col]);
+          const int fc = g.colexp[col];
+          double w;
+          if (er == kNonFinite || fc == kNonFinite) {
+            w = __longlong_as_double(0x7FF8000000000000ll);   // NaN: A or X held Inf / NaN
+          } else {
+            const double v = fma((double)lo[j], lo_scale, (double)hi[j] * 0x1p-35);
+            w = ldexp(v, er + fc);
+          }
           g.P[rk + col] = w - g.shift * g.X[rk + col];
         }
       }
@@ -366,8 +421,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Digit planes of A: rows of As[s] (n_pad x n_pad BF16, row-major), e_i per row.
-// One warp per row; 8 consecutive elements per lane and step.
+// Digit planes.  GB300 runs FP64 at ~1/64 of FP32, so the digits are cut
+// with integer arithmetic: |a| 2^-e (< 1) is rounded once to an integer M of
+// 7S bits (the same information the S digits keep), then M is split into
+// base-128 digits with round-half-up, the first in [0, 128], the others in
+// [-64, 64]; the sign of a is applied to all of them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int row_exponent(double amax) {
   if (!(amax > 0.0) || !isfinite(amax)) return 0;
@@ -376,7 +434,33 @@ __device__ __forceinline__ int row_exponent(double amax) {
   return e;
 }
 
-__global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t lda, int n_pad, int S,
+template <int S>
+__device__ __forceinline__ void digits_of(double a, int e, int* d) {
+  const long long bits = __double_as_longlong(a);
+  int ex = (int)((bits >> 52) & 0x7FF);
+  unsigned long long mant = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  if (ex) mant |= 1ull << 52; else ex = 1;
+  // |a| 2^(7S - e) = mant 2^sh; |a| < 2^e and mant < 2^53 give M < 2^(7S) <= 2^63
+  const int sh = ex - 1075 - e + 7 * S;
+  unsigned long long M;
+  if (sh >= 0) M = sh < 64 ? mant << sh : 0ull;
+  else M = -sh < 64 ? (mant + (1ull << (-sh - 1))) >> (-sh) : 0ull;
+  const int k0 = 7 * (S - 1);
+  const unsigned long long q0 = k0 ? (M + (1ull << (k0 - 1))) >> k0 : M;
+  long long R = (long long)(M - (q0 << k0));
+  const int sg = bits < 0 ? -1 : 1;
+  d[0] = sg * (int)q0;
+#pragma unroll
+  for (int s = 1; s < S; ++s) {
+    const int k = 7 * (S - 1 - s);
+    const long long q = k ? (R + (1ll << (k - 1))) >> k : R;
+    R -= q << k;
+    d[s] = sg * (int)q;
+  }
+}
+
+template <int S>
+__global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t lda, int n_pad,
                                __nv_bfloat16* __restrict__ As, int* __restrict__ rowexp) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -384,26 +468,30 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
   const int64_t plane = (int64_t)n_pad * n_pad;
   for (int64_t i = wid; i < n_pad; i += nw) {
     double amax = 0.0;
+    bool finite = true;
     if (i < n)
-      for (int64_t l = lane; l < n; l += 32) amax = fmax(amax, fabs(A[i * lda + l]));
+      for (int64_t l = lane; l < n; l += 32) {
+        const double v = A[i * lda + l];
+        finite = finite && isfinite(v);
+        amax = fmax(amax, fabs(v));
+      }
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    finite = __all_sync(0xffffffffu, finite);
     const int e = row_exponent(amax);
-    if (lane == 0) rowexp[i] = e;
+    if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int64_t l0 = (int64_t)lane * 8; l0 < n_pad; l0 += 32 * 8) {
-      double r[8];
+      int dg[8][S];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int64_t l = l0 + q;
-        r[q] = (i < n && l < n) ? ldexp(A[i * lda + l], kBits - e) : 0.0;
+        const double v = (i < n && l < n && finite) ? A[i * lda + l] : 0.0;
+        digits_of<S>(v, e, dg[q]);
       }
+#pragma unroll
       for (int s = 0; s < S; ++s) {
         __align__(16) __nv_bfloat16 d[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const double di = rint(r[q]);
-          d[q] = __float2bfloat16_rn((float)di);
-          r[q] = (r[q] - di) * (double)(1 << kBits);
-        }
+        for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][s]);
         *reinterpret_cast<uint4*>(As + s * plane + i * n_pad + l0) = *reinterpret_cast<uint4*>(d);
       }
     }
@@ -417,16 +505,19 @@ __global__ void colmax_kernel(const double* __restrict__ X, int64_t n, int k, un
   const int j = threadIdx.x % k;   // blockDim.x is a multiple of k
   const int rpb = blockDim.x / k;
   double m = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / k; i < n; i += (int64_t)gridDim.x * rpb)
-    m = fmax(m, fabs(X[i * k + j]));
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / k; i < n; i += (int64_t)gridDim.x * rpb) {
+    const double v = fabs(X[i * k + j]);
+    m = (v > m || v != v) ? v : m;       // keeps NaN (fmax would drop it)
+  }
   atomicMax(cmax + j, (unsigned long long)__double_as_longlong(m));
 }
 
 // Digit planes of X: Xs[(cb * S + t) * 32 + jj][l] (BF16), column j = 32 cb + jj.
 // A CTA takes 64 rows x 32 columns through shared memory so both the FP64 reads
 // and the BF16 writes are contiguous.
+template <int S>
 __global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__ X, int64_t n, int k, int n_pad,
-                                                      int S, const unsigned long long* __restrict__ cmax,
+                                                      const unsigned long long* __restrict__ cmax,
                                                       __nv_bfloat16* __restrict__ Xs, int* __restrict__ colexp,
                                                       const Control* ctl) {
   if (ctl && ctl->done) return;
@@ -437,9 +528,10 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__
   const int tid = threadIdx.x;
   if (tid < 32) {
     const int j = cb * 32 + tid;
-    const int f = j < k ? row_exponent(__longlong_as_double((long long)cmax[j])) : 0;
-    fexp[tid] = f;
-    if (blockIdx.x == 0 && j < k) colexp[j] = f;
+    const double cm = j < k ? __longlong_as_double((long long)cmax[j]) : 0.0;
+    const int f = row_exponent(cm);
+    fexp[tid] = isfinite(cm) ? f : 0;
+    if (blockIdx.x == 0 && j < k) colexp[j] = isfinite(cm) ? f : kNonFinite;
   }
   for (int e = tid; e < 64 * 32; e += 256) {
     const int rr = e >> 5, jj = e & 31;
@@ -450,21 +542,43 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__
   __syncthreads();
   // thread -> (jj, 8 consecutive rows); writes 16 bytes per plane
   const int jj = tid >> 3, r0 = (tid & 7) * 8;
-  double r[8];
+  int dg[8][S];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) r[q] = ldexp(tile[r0 + q][jj], kBits - fexp[jj]);
+  for (int q = 0; q < 8; ++q) digits_of<S>(tile[r0 + q][jj], fexp[jj], dg[q]);
+#pragma unroll
   for (int t = 0; t < S; ++t) {
     __align__(16) __nv_bfloat16 d[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double di = rint(r[q]);
-      d[q] = __float2bfloat16_rn((float)di);
-      r[q] = (r[q] - di) * (double)(1 << kBits);
-    }
+    for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][t]);
     const int64_t rowid = ((int64_t)cb * S + t) * 32 + jj;
     *reinterpret_cast<uint4*>(Xs + rowid * n_pad + l0 + r0) = *reinterpret_cast<uint4*>(d);
   }
 }
+
+template <int S>
+void launch_slicers(const double* A, int64_t n, int64_t lda, int n_pad, __nv_bfloat16* As, int* rowexp,
+                    cudaStream_t s) {
+  slice_a_kernel<S><<<152 * 8, 256, 0, s>>>(A, n, lda, n_pad, As, rowexp);
+}
+
+template <int S>
+void launch_slice_x(const double* X, int64_t n, int k, int n_pad, int k_pad, const unsigned long long* cmax,
+                    __nv_bfloat16* Xs, int* colexp, const Control* ctl, cudaStream_t s) {
+  dim3 gx((unsigned)(n_pad / 64), (unsigned)(k_pad / 32));
+  slice_x_kernel<S><<<gx, 256, 0, s>>>(X, n, k, n_pad, cmax, Xs, colexp, ctl);
+}
+
+#define EIGREF_SLICE_DISPATCH(S_, CALL) \
+  switch (S_) {                         \
+    case 2: CALL(2); break;             \
+    case 3: CALL(3); break;             \
+    case 4: CALL(4); break;             \
+    case 5: CALL(5); break;             \
+    case 6: CALL(6); break;             \
+    case 7: CALL(7); break;             \
+    case 8: CALL(8); break;             \
+    default: CALL(9); break;            \
+  }
 
 // ---------------------------------------------------------------------------
 // Tensor maps (driver entry point fetched at run time; no -lcuda)
@@ -501,7 +615,14 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
 }  // namespace sl
 
 cudaError_t init_sliced_attributes() {
-  return cudaFuncSetAttribute(sl::sliced_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
+  cudaError_t e = cudaSuccess;
+#define EIGREF_SET_ATTR(S_)                                                                                  \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(sl::sliced_gemm_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
+  EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
+  EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
+#undef EIGREF_SET_ATTR
+  return e;
 }
 
 // X planes per TMA load: the largest divisor g of S with a box of 32 g <= 256 rows.
@@ -579,8 +700,10 @@ int SlicedA::prepare(cudaStream_t s) {
     snprintf(err_, sizeof(err_), "memset of slice planes failed");
     return EIGREF_E_CUDA;
   }
-  sl::slice_a_kernel<<<152 * 8, 256, 0, s>>>(A_, n_, lda_, n_pad_, slices_, ap,
-                                               reinterpret_cast<int*>(ws_ + L.rowexp));
+  int* rowexp = reinterpret_cast<int*>(ws_ + L.rowexp);
+#define EIGREF_CALL_SLICE_A(S_) sl::launch_slicers<S_>(A_, n_, lda_, n_pad_, ap, rowexp, s)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_A)
+#undef EIGREF_CALL_SLICE_A
   if (!sl::make_map(reinterpret_cast<CUtensorMap*>(tmA_), ap, (uint64_t)n_pad_, (uint64_t)slices_ * n_pad_, sl::kBK,
                     sl::kBM) ||
       !sl::make_map(reinterpret_cast<CUtensorMap*>(tmX_), xp, (uint64_t)n_pad_, (uint64_t)slices_ * k_pad_, sl::kBK,
@@ -604,8 +727,9 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
   cudaMemsetAsync(cmax, 0, (size_t)k_ * 8, s);
   const int rpb = 256 / k_ > 0 ? 256 / k_ : 1;
   sl::colmax_kernel<<<152 * 4, rpb * k_, 0, s>>>(X, n_, k_, cmax, ctl);
-  dim3 gx((unsigned)(n_pad_ / 64), (unsigned)(k_pad_ / 32));
-  sl::slice_x_kernel<<<gx, 256, 0, s>>>(X, n_, k_, n_pad_, slices_, cmax, xp, colexp, ctl);
+#define EIGREF_CALL_SLICE_X(S_) sl::launch_slice_x<S_>(X, n_, k_, n_pad_, k_pad_, cmax, xp, colexp, ctl, s)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_X)
+#undef EIGREF_CALL_SLICE_X
   sl::GemmArgs g;
   g.rowexp = reinterpret_cast<const int*>(ws_ + L.rowexp);
   g.colexp = colexp;
@@ -619,10 +743,13 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
   g.shift = shift;
   g.ctl = ctl;
   g.err = reinterpret_cast<int*>(ws_ + L.err);
-  dim3 grid((unsigned)(n_pad_ / sl::kBM), (unsigned)(k_pad_ / sl::kBN));
+  dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM));
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
-  sl::sliced_gemm_kernel<<<grid, sl::kThreads, sl::kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(tmA_),
-                                                                   *reinterpret_cast<const CUtensorMap*>(tmX_), g);
+  const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(tmA_);
+  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
+#define EIGREF_CALL_GEMM(S_) sl::sliced_gemm_kernel<S_><<<grid, sl::kThreads, sl::kSmemBytes, s>>>(ma, mx, g)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_GEMM)
+#undef EIGREF_CALL_GEMM
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
   return 3;
 }

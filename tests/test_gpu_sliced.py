@@ -153,3 +153,19 @@ def test_full_size_split_product_and_sweep(eig):
     Xg, rg = run_gpu(eig, p, max_iters=1)
     Xo, ro = R.refine(R.dense_operator(p.A), p.X0, p.normA, 0.0, max_iters=1)
     assert rel_diff(Xg, Xo) <= split_tol(p)
+
+
+def test_sliced_nonfinite_input_is_reported(eig):
+    """Inf / NaN in A or X cannot hide inside integer digits: the product
+    marks the row / column and the refinement stops with EIGREF_E_NONFINITE."""
+    p = dense_case(300, 8, seed=51)
+    A = p.A.copy()
+    A[17, 40] = A[40, 17] = np.nan
+    X = dev(np.asfortranarray(p.X0))
+    r = eig.refine_dense(dev(A), X, norm_a=p.normA, precision="bf16", max_iters=3, raise_on_error=False)
+    assert r["status"] == 7 and r["iterations"] == 0
+    X0 = np.asfortranarray(p.X0.copy())
+    X0[3, 2] = np.inf
+    X = dev(X0)
+    r = eig.refine_dense(dev(p.A), X, norm_a=p.normA, precision="bf16", max_iters=3, raise_on_error=False)
+    assert r["status"] == 7 and r["iterations"] == 0
