@@ -52,7 +52,7 @@ def build(force=False, verbose=False, extra=()):
     objs = [o for _, o, _ in jobs]
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
-               "-Xlinker", "-rpath," + cuda_lib_dir()]
+               "-Xlinker", "-rpath," + cuda_lib_dir(), "-Xlinker", "--no-undefined"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

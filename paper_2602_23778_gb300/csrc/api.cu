@@ -172,7 +172,7 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   launch_update_rows(b, n, k, s);
   launch_finalize(b, k, delta, s);
   launch_normalize(b, n, k, s);
-  return launches + 4 + 9 + 3;
+  return launches + 4 + (b.mixed ? 17 : 9) + 3;
 }
 
 int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigref_params* pin,
@@ -200,7 +200,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     b.gpart = c.take<double>(2 * (int64_t)nchunks * kk);
     b.gtop = c.take<double>(2 * kk);
     b.g2 = c.take<double>(2 * kk);
-    double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f};
+    double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f, &b.res};
     for (double** m : mats) *m = c.take<double>(kk);
     b.piv = c.take<int>(k);
     double** vecs[] = {&b.alpha, &b.d, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
@@ -227,6 +227,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   b.nchunks = nchunks;
   b.chunk_rows = chunk_rows;
   b.ugrid = ugrid;
+  b.mixed = pr.sliced != nullptr;  // the split form factors Y1 in FP32 and refines in FP64
 
   CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
   // ---- set-up: ||A||, shift, delta, signs, internal X ----

@@ -45,7 +45,8 @@ struct SweepBufs {
   double* gpart;      // Gram partials: [2][nchunks][k*k]
   double* gtop;       // [2][k*k]: G1 = X1^T X1, S1 = X1^T P1
   double* g2;         // [2][k*k]: G2 = X2^T X2, S2 = X2^T P2 (rows >= k)
-  double *r1, *t1, *z, *y1, *lu, *m, *v1, *w2, *e11, *yte, *nmat, *f;  // k x k
+  double *r1, *t1, *z, *y1, *lu, *m, *v1, *w2, *e11, *yte, *nmat, *f, *res;  // k x k
+  int mixed;          // 1: LU of Y1 in FP32 with FP64 iterative refinement of the solves
   int* piv;           // [k]
   double *alpha, *d, *cz, *cw, *nu, *r1sq, *e11sq, *x1sq;  // [k]
   double* upart;      // update partials [ugrid][2k]

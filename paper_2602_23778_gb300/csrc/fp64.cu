@@ -261,49 +261,71 @@ void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {
 //   nu_j = 1 / ||x'_j||
 // Stopping, divergence and non-finite tests of Section 3.1.3 / Section 4.3.1.
 // ---------------------------------------------------------------------------
-__global__ void finalize_kernel(SweepBufs b, int k) {
+__global__ void __launch_bounds__(1024) finalize_kernel(SweepBufs b, int k) {
   Control* ctl = b.ctl;
-  __shared__ double red[3][256];
+  __shared__ double xsq_s[kMaxK], r2_s[kMaxK];
+  __shared__ double red[3][32];
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   if (ctl->done) {
     if (tid == 0) ctl->pending_norm = 0;
     return;
   }
   if (tid == 0) bad = 0;
-  __syncthreads();
-  double rsum = 0.0, esum = 0.0, e11 = 0.0;
-  for (int j = tid; j < k; j += blockDim.x) {
+  // column sums: one warp per column, lanes over the update partials and the
+  // leading-block rows; fixed order, so the result is reproducible
+  for (int j = warp; j < k; j += nwarp) {
     double xsq = 0.0, r2 = 0.0;
-    for (int i = 0; i < k; ++i) {            // leading block rows of X_{t+1}
+    for (int i = lane; i < k; i += 32) {
       const double v = b.xn[(int64_t)i * k + j];
       xsq += v * v;
     }
-    for (int g = 0; g < b.ugrid; ++g) {
+    for (int g = lane; g < b.ugrid; g += 32) {
       xsq += b.upart[(int64_t)g * 2 * k + j];
       r2 += b.upart[(int64_t)g * 2 * k + k + j];
     }
-    double dj = b.d[j];
-    double e21 = (r2 - 2.0 * b.cz[j] + b.cw[j]) / (dj * dj);
-    esum += e21 > 0.0 ? e21 : 0.0;
-    rsum += b.r1sq[j] + r2;
-    e11 += b.e11sq[j];
+    for (int o = 16; o > 0; o >>= 1) {
+      xsq += __shfl_xor_sync(0xffffffffu, xsq, o);
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    }
+    if (lane == 0) {
+      xsq_s[j] = xsq;
+      r2_s[j] = r2;
+    }
+  }
+  __syncthreads();
+  double rsum = 0.0, esum = 0.0, e11 = 0.0;
+  if (tid < k) {
+    const int j = tid;
+    const double xsq = xsq_s[j], r2 = r2_s[j], dj = b.d[j];
+    const double e21 = (r2 - 2.0 * b.cz[j] + b.cw[j]) / (dj * dj);
+    esum = e21 > 0.0 ? e21 : 0.0;
+    rsum = b.r1sq[j] + r2;
+    e11 = b.e11sq[j];
     b.nu[j] = 1.0 / sqrt(xsq);
     if (!isfinite(xsq) || !(xsq > 0.0)) atomicExch(&bad, 1);
   }
-  red[0][tid] = rsum;
-  red[1][tid] = esum;
-  red[2][tid] = e11;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (tid < w)
-      for (int q = 0; q < 3; ++q) red[q][tid] += red[q][tid + w];
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+    esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    e11 += __shfl_xor_sync(0xffffffffu, e11, o);
   }
+  if (lane == 0) {
+    red[0][warp] = rsum;
+    red[1][warp] = esum;
+    red[2][warp] = e11;
+  }
+  __syncthreads();
   if (tid != 0) return;
-  double res = sqrt(red[0][0]) / ctl->norm_a;
-  double corr = sqrt(red[1][0] + red[2][0]);
-  int it = ctl->iterations;
+  double rs = 0.0, es = 0.0, ee = 0.0;
+  for (int w = 0; w < nwarp; ++w) {
+    rs += red[0][w];
+    es += red[1][w];
+    ee += red[2][w];
+  }
+  const double res = sqrt(rs) / ctl->norm_a;
+  const double corr = sqrt(es + ee);
+  const int it = ctl->iterations;
   if (bad || !isfinite(res) || !isfinite(corr)) {
     ctl->status = EIGREF_E_NONFINITE;
     ctl->nonfinite = 1;
@@ -317,7 +339,7 @@ __global__ void finalize_kernel(SweepBufs b, int k) {
   ctl->last_corr = corr;
   ctl->iterations = it + 1;
   ctl->pending_norm = 1;
-  double crit = ctl->stop == EIGREF_STOP_CORRECTION ? corr : res;
+  const double crit = ctl->stop == EIGREF_STOP_CORRECTION ? corr : res;
   if (ctl->tol > 0.0 && crit <= ctl->tol) {
     ctl->status = EIGREF_OK;
     ctl->done = 1;
@@ -337,7 +359,7 @@ cudaError_t init_fp64_attributes() {
 }
 
 void launch_finalize(const SweepBufs& b, int k, double, cudaStream_t s) {
-  finalize_kernel<<<1, 256, 0, s>>>(b, k);
+  finalize_kernel<<<1, 1024, 0, s>>>(b, k);
 }
 
 __global__ void normalize_kernel(double* __restrict__ X, int64_t n, int k, const double* __restrict__ nu,
