@@ -165,14 +165,30 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   const int64_t n = pr.n;
   const int k = pr.k;
   int launches = launch_product(pr, b.x, b.p, shift, b.ctl, s, ev0, ev1, ev_flags);
-  // Gram products of the rows below the leading block, then of the block
-  launch_gram(b.x, b.p, k, k, n, b.chunk_rows, b.nchunks, b.gpart, b.g2, b.ctl, s);
-  launch_gram(b.x, b.p, k, 0, k, k, 1, b.gpart, b.gtop, b.ctl, s);
+  if (pr.sliced) {
+    // split form: Gram products over all rows on the tensor cores, the
+    // leading k x k block in FP64; the k x k stage forms G2 = G - G1
+    pr.sliced->gram(b.p, nullptr, b.g2, b.ctl, s);
+    launch_top_gram(b.x, b.p, k, b.gtop, b.ctl, s);
+    launches += 5;
+  } else {
+    // Gram products of the rows below the leading block, then of the block
+    launch_gram(b.x, b.p, k, k, n, b.chunk_rows, b.nchunks, b.gpart, b.g2, b.ctl, s);
+    launch_gram(b.x, b.p, k, 0, k, k, 1, b.gpart, b.gtop, b.ctl, s);
+    launches += 4;
+  }
   launch_kxk_stage(b, k, delta, beta_zero, s);
-  launch_update_rows(b, n, k, s);
+  launches += b.mixed ? 12 : 9;
+  if (pr.sliced) {
+    pr.sliced->update(b.x, b.p, b.f, b.d, b.xn, b.upart, b.ctl, s);
+    launches += 4;
+  } else {
+    launch_update_rows(b, n, k, s);
+    launches += 1;
+  }
   launch_finalize(b, k, delta, s);
   launch_normalize(b, n, k, s);
-  return launches + 4 + (b.mixed ? 17 : 9) + 3;
+  return launches + 2;
 }
 
 int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigref_params* pin,
@@ -190,7 +206,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   int64_t chunk_rows = 256;
   while ((n - k + chunk_rows - 1) / chunk_rows > 1024) chunk_rows *= 2;
   const int nchunks = (int)std::max<int64_t>(1, (n - k + chunk_rows - 1) / chunk_rows);
-  const int ugrid = update_rows_grid();
+  const int ugrid = pr.sliced ? pr.sliced->update_grid() : update_rows_grid();
   const int hist_len = std::max(1, q.max_iters);
   auto layout = [&](Carve& c, SweepBufs& b, double** xbuf, double** xstage, double** sigma, double** scal) {
     xbuf[0] = c.take<double>(n * k);
@@ -200,7 +216,8 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     b.gpart = c.take<double>(2 * (int64_t)nchunks * kk);
     b.gtop = c.take<double>(2 * kk);
     b.g2 = c.take<double>(2 * kk);
-    double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f, &b.res};
+    double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f, &b.res,
+                       &b.zinv, &b.zinv2};
     for (double** m : mats) *m = c.take<double>(kk);
     b.piv = c.take<int>(k);
     double** vecs[] = {&b.alpha, &b.d, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
@@ -278,6 +295,11 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   c.done = q.max_iters == 0;
   *h->host_ctl = c;
   CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
+  if (b.mixed && q.max_iters > 0) {
+    SweepBufs b0 = b;
+    b0.x = xbuf[0];
+    launch_inverse_setup(b0, k, s);   // Y1^{-1} of the starting X, refined every sweep after
+  }
 
   // ---- sweeps ----
   const int m = q.check_every;

@@ -46,7 +46,8 @@ struct SweepBufs {
   double* gtop;       // [2][k*k]: G1 = X1^T X1, S1 = X1^T P1
   double* g2;         // [2][k*k]: G2 = X2^T X2, S2 = X2^T P2 (rows >= k)
   double *r1, *t1, *z, *y1, *lu, *m, *v1, *w2, *e11, *yte, *nmat, *f, *res;  // k x k
-  int mixed;          // 1: LU of Y1 in FP32 with FP64 iterative refinement of the solves
+  double *zinv, *zinv2;  // k x k: Y1^{-1} kept across sweeps (split form) and a scratch copy
+  int mixed;          // 1: Y1^{-1} by Newton-Schulz updates instead of an LU per sweep
   int* piv;           // [k]
   double *alpha, *d, *cz, *cw, *nu, *r1sq, *e11sq, *x1sq;  // [k]
   double* upart;      // update partials [ugrid][2k]
@@ -63,6 +64,8 @@ void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, 
                       double shift, const Control* ctl, cudaStream_t s);
 void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
                  int nchunks, double* part, double* out, const Control* ctl, cudaStream_t s);
+void launch_gram_reduce(const double* part, int k, int nchunks, double* out, const Control* ctl, cudaStream_t s);
+void launch_top_gram(const double* X, const double* P, int k, double* out, const Control* ctl, cudaStream_t s);
 void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s);
 void launch_finalize(const SweepBufs& b, int k, double delta_unused, cudaStream_t s);
 void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s);
@@ -82,5 +85,6 @@ void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, co
 // kxk.cu
 void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s);
 void launch_sign_fix(const double* X, int64_t ldx, int k, double* sigma, int* singular, cudaStream_t s);
+void launch_inverse_setup(const SweepBufs& b, int k, cudaStream_t s);
 
 }  // namespace eigref

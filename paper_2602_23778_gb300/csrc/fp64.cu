@@ -158,6 +158,41 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int n
   }
 }
 
+void launch_gram_reduce(const double* part, int k, int nchunks, double* out, const Control* ctl, cudaStream_t s) {
+  int64_t work = 2LL * k * k;
+  int rg = (int)std::min<int64_t>((work + 255) / 256, 1024);
+  gram_reduce_kernel<<<rg, 256, 0, s>>>(part, k, nchunks, out, ctl);
+}
+
+// Gram products of the leading k x k block: out[0] = X1^T X1, out[1] = X1^T P1
+// (16 x 16 output tiles, k-term dot products).
+__global__ void __launch_bounds__(256) top_gram_kernel(const double* __restrict__ X, const double* __restrict__ P,
+                                                       int k, double* __restrict__ out, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  __shared__ double As[16][17];
+  __shared__ double Bs[16][17];
+  const double* Y = blockIdx.z ? P : X;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+  double acc = 0.0;
+  for (int l0 = 0; l0 < k; l0 += 16) {
+    const int l = l0 + ty;
+    const int ai = blockIdx.x * 16 + tx, bj = blockIdx.y * 16 + tx;
+    As[ty][tx] = (l < k && ai < k) ? X[(int64_t)l * k + ai] : 0.0;   // X1(l, i)
+    Bs[ty][tx] = (l < k && bj < k) ? Y[(int64_t)l * k + bj] : 0.0;   // Y1(l, j)
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc = fma(As[c][tx], Bs[c][ty], acc);
+    __syncthreads();
+  }
+  if (i < k && j < k) out[(int64_t)blockIdx.z * k * k + i + (int64_t)j * k] = acc;
+}
+
+void launch_top_gram(const double* X, const double* P, int k, double* out, const Control* ctl, cudaStream_t s) {
+  dim3 g((k + 15) / 16, (k + 15) / 16, 2);
+  top_gram_kernel<<<g, 256, 0, s>>>(X, P, k, out, ctl);
+}
+
 void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
                  int nchunks, double* part, double* out, const Control* ctl, cudaStream_t s) {
   int tiles = (k + 31) / 32;

@@ -35,7 +35,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
-// One block per column j.
+// One block per column j.  In the split form g2 arrives holding the Gram
+// products over all rows; the block turns its column into G2 = G - G1,
+// S2 = S - S1 in place (only this block touches column j).
 __global__ void kk_prep_kernel(SweepBufs b, int k) {
   if (b.ctl->done) return;
   __shared__ double sh[32];
@@ -43,20 +45,29 @@ __global__ void kk_prep_kernel(SweepBufs b, int k) {
   const int64_t kk = (int64_t)k * k;
   const double* G1 = b.gtop;
   const double* S1 = b.gtop + kk;
-  const double* G2 = b.g2;
-  const double* S2 = b.g2 + kk;
+  double* G2 = b.g2;
+  double* S2 = b.g2 + kk;
+  const bool full = b.mixed != 0;
   const int64_t jj = j + (int64_t)j * k;
-  const double al = G1[jj] + G2[jj];
-  const double dj = (S1[jj] + S2[jj]) / al;
+  const double al = full ? G2[jj] : G1[jj] + G2[jj];
+  const double dj = (full ? S2[jj] : S1[jj] + S2[jj]) / al;
+  __syncthreads();
   double r1s = 0.0;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const int64_t e = i + (int64_t)j * k;
-    const double G = G1[e] + G2[e], S = S1[e] + S2[e];
+    const double G = full ? G2[e] : G1[e] + G2[e];
+    const double S = full ? S2[e] : S1[e] + S2[e];
+    const double g2 = full ? G2[e] - G1[e] : G2[e];
+    const double s2 = full ? S2[e] - S1[e] : S2[e];
+    if (full) {
+      G2[e] = g2;
+      S2[e] = s2;
+    }
     const double x = b.x[(int64_t)i * k + j];
     const double r1 = b.p[(int64_t)i * k + j] - x * dj;
     b.r1[e] = r1;
     b.t1[e] = (S - G * dj) - r1;
-    b.z[e] = S2[e] - G2[e] * dj;
+    b.z[e] = s2 - g2 * dj;
     b.y1[e] = x - (i == j ? 1.0 : 0.0);
     r1s += r1 * r1;
   }
@@ -292,163 +303,21 @@ __global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
 
 
 // ---------------------------------------------------------------------------
-// Mixed precision for the two k x k systems of the split form: Y1 is
-// factored in FP32 (64x the FP64 rate on this part), each solve is refined
-// twice against the FP64 residual, which brings the solution to FP64 accuracy
-// for cond(Y1) << 1 / u32 (the sign fix keeps cond(Y1) small).
+// Y1^{-1} for the split form.  An LU of Y1 is a long chain of dependent steps
+// on one SM; instead the inverse Z is computed once per call (LU) and then
+// corrected every sweep by two Newton-Schulz steps, Z <- Z + Z (I - Y1 Z).
+// Each step squares the error ||I - Y1 Z||, which at the start of a sweep is
+// of the order of the change of X1 in the last update.  All of it is k x k
+// FP64 GEMMs spread over many CTAs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) kk_lu32_kernel(SweepBufs b, int k) {
-  Control* ctl = b.ctl;
-  if (ctl->done) return;
-  extern __shared__ float af[];
-  __shared__ float sh[32];
-  __shared__ int s_piv, s_sing, s_bad;
-  float* lu32 = reinterpret_cast<float*>(b.lu);
-  const int tid = threadIdx.x;
-  const int64_t kk = (int64_t)k * k;
-  float amax = 0.f;
-  int bad = 0;
-  for (int64_t e = tid; e < kk; e += blockDim.x) {
-    const double v = b.y1[e];
-    bad |= !isfinite(v);
-    af[e] = (float)v;
-    amax = fmaxf(amax, fabsf(af[e]));
-  }
-  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  bad = __any_sync(0xffffffffu, bad);
-  if ((tid & 31) == 0) sh[tid >> 5] = amax;
-  if (tid == 0) {
-    s_sing = 0;
-    s_bad = 0;
-  }
-  __syncthreads();
-  if (bad) s_bad = 1;
-  __syncthreads();
-  if (s_bad) {
-    if (tid == 0) {
-      ctl->nonfinite = 1;
-      ctl->status = EIGREF_E_NONFINITE;
-      ctl->done = 1;
-    }
-    return;
-  }
-  amax = 0.f;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) amax = fmaxf(amax, sh[q]);
-  const float thresh = (float)k * 5.9604645e-08f * amax;   // k u_32 max|Y1|
-  for (int p = 0; p < k; ++p) {
-    if (tid < 32) {
-      float best = -1.f;
-      int bi = p;
-      for (int i = p + tid; i < k; i += 32) {
-        const float v = fabsf(af[i + (int64_t)p * k]);
-        if (v > best) { best = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) {
-        s_piv = bi;
-        b.piv[p] = bi;
-        if (!(best > thresh)) s_sing = 1;
-      }
-    }
-    __syncthreads();
-    if (s_sing) break;
-    const int q = s_piv;
-    if (q != p)
-      for (int c = tid; c < k; c += blockDim.x) {
-        const float t = af[p + (int64_t)c * k];
-        af[p + (int64_t)c * k] = af[q + (int64_t)c * k];
-        af[q + (int64_t)c * k] = t;
-      }
-    __syncthreads();
-    const float pv = af[p + (int64_t)p * k];
-    for (int i = p + 1 + tid; i < k; i += blockDim.x) af[i + (int64_t)p * k] /= pv;
-    __syncthreads();
-    const int m = k - p - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int i = p + 1 + e % m, c = p + 1 + e / m;
-      af[i + (int64_t)c * k] -= af[i + (int64_t)p * k] * af[p + (int64_t)c * k];
-    }
-    __syncthreads();
-  }
-  if (s_sing) {
-    if (tid == 0) {
-      ctl->singular = 1;
-      ctl->status = EIGREF_E_SINGULAR_WY;
-      ctl->done = 1;
-    }
-    return;
-  }
-  for (int64_t e = tid; e < kk; e += blockDim.x) lu32[e] = af[e];
-}
 
-// One block per right-hand side: x = op(Y1)^{-1} (neg ? -rhs : rhs) with the
-// FP32 factors, then out = x (acc = 0) or out += x (acc = 1), in FP64.
+// C = add_i I + beta C0 + alpha op(A) B  (k x k, column-major).  check > 0:
+// flags Y1 as singular when an entry of C exceeds it (Newton-Schulz diverging).
 template <int TRANS>
-__global__ void kk_solve32_kernel(const float* __restrict__ LU, const int* __restrict__ piv,
-                                  const double* __restrict__ rhs, double* __restrict__ out, int k, int neg,
-                                  int acc, const Control* ctl) {
-  if (ctl->done) return;
-  __shared__ float x[kMaxK];
-  const int j = blockIdx.x, tid = threadIdx.x;
-  for (int i = tid; i < k; i += blockDim.x) {
-    const double v = rhs[i + (int64_t)j * k];
-    x[i] = (float)(neg ? -v : v);
-  }
-  __syncthreads();
-  if (TRANS == 0) {
-    if (tid == 0)
-      for (int p = 0; p < k; ++p) {
-        const int q = piv[p];
-        const float t = x[p]; x[p] = x[q]; x[q] = t;
-      }
-    __syncthreads();
-    for (int p = 0; p < k - 1; ++p) {
-      const float xp = x[p];
-      for (int i = p + 1 + tid; i < k; i += blockDim.x) x[i] -= LU[i + (int64_t)p * k] * xp;
-      __syncthreads();
-    }
-    for (int p = k - 1; p >= 0; --p) {
-      if (tid == 0) x[p] /= LU[p + (int64_t)p * k];
-      __syncthreads();
-      const float xp = x[p];
-      for (int i = tid; i < p; i += blockDim.x) x[i] -= LU[i + (int64_t)p * k] * xp;
-      __syncthreads();
-    }
-  } else {
-    for (int p = 0; p < k; ++p) {
-      if (tid == 0) x[p] /= LU[p + (int64_t)p * k];
-      __syncthreads();
-      const float xp = x[p];
-      for (int i = p + 1 + tid; i < k; i += blockDim.x) x[i] -= LU[p + (int64_t)i * k] * xp;
-      __syncthreads();
-    }
-    for (int p = k - 1; p > 0; --p) {
-      const float xp = x[p];
-      for (int i = tid; i < p; i += blockDim.x) x[i] -= LU[p + (int64_t)i * k] * xp;
-      __syncthreads();
-    }
-    if (tid == 0)
-      for (int p = k - 1; p >= 0; --p) {
-        const int q = piv[p];
-        const float t = x[p]; x[p] = x[q]; x[q] = t;
-      }
-    __syncthreads();
-  }
-  for (int i = tid; i < k; i += blockDim.x) {
-    const int64_t e = i + (int64_t)j * k;
-    out[e] = acc ? out[e] + (double)x[i] : (double)x[i];
-  }
-}
-
-// FP64 residual of the system being refined: res = -rhs - op(Y1) sol.
-template <int TRANS>
-__global__ void __launch_bounds__(256) kk_resid_kernel(const double* __restrict__ Y1, const double* __restrict__ rhs,
-                                                       const double* __restrict__ sol, double* __restrict__ res,
-                                                       int k, const Control* ctl) {
+__global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                              const double* __restrict__ C0, double* __restrict__ C,
+                                                              int k, double alpha, double beta, int add_i,
+                                                              double check, Control* ctl) {
   if (ctl->done) return;
   __shared__ double As[16][17];
   __shared__ double Bs[16][17];
@@ -457,9 +326,9 @@ __global__ void __launch_bounds__(256) kk_resid_kernel(const double* __restrict_
   double acc = 0.0;
   for (int l0 = 0; l0 < k; l0 += 16) {
     const int ai = blockIdx.x * 16 + ty, al = l0 + tx;
-    As[ty][tx] = (ai < k && al < k) ? (TRANS ? Y1[al + (int64_t)ai * k] : Y1[ai + (int64_t)al * k]) : 0.0;
+    As[ty][tx] = (ai < k && al < k) ? (TRANS ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k]) : 0.0;
     const int bl = l0 + ty, bj = blockIdx.y * 16 + tx;
-    Bs[ty][tx] = (bl < k && bj < k) ? sol[bl + (int64_t)bj * k] : 0.0;
+    Bs[ty][tx] = (bl < k && bj < k) ? B[bl + (int64_t)bj * k] : 0.0;
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc = fma(As[tx][c], Bs[c][ty], acc);
@@ -467,28 +336,54 @@ __global__ void __launch_bounds__(256) kk_resid_kernel(const double* __restrict_
   }
   if (i < k && j < k) {
     const int64_t e = i + (int64_t)j * k;
-    res[e] = -rhs[e] - acc;
+    double v = alpha * acc;
+    if (C0) v += beta * C0[e];
+    if (add_i && i == j) v += 1.0;
+    C[e] = v;
+    if (check > 0.0 && !(fabs(v) <= check)) {
+      ctl->singular = 1;
+      ctl->status = EIGREF_E_SINGULAR_WY;
+      ctl->done = 1;
+    }
   }
 }
 
-// sol = op(Y1)^{-1} (-rhs), FP32 factors + two FP64 refinement steps.
-template <int TRANS>
-static void solve_refined(const SweepBufs& b, int k, const double* rhs, double* sol, int tpb, cudaStream_t s) {
-  const float* lu32 = reinterpret_cast<const float*>(b.lu);
+static void kk_gemm_generic(const double* A, bool transA, const double* B, const double* C0, double* C, int k,
+                            double alpha, double beta, int add_i, double check, Control* ctl, cudaStream_t s) {
   dim3 g((k + 15) / 16, (k + 15) / 16);
-  kk_solve32_kernel<TRANS><<<k, tpb, 0, s>>>(lu32, b.piv, rhs, sol, k, 1, 0, b.ctl);
-  for (int it = 0; it < 2; ++it) {
-    kk_resid_kernel<TRANS><<<g, 256, 0, s>>>(b.y1, rhs, sol, b.res, k, b.ctl);
-    kk_solve32_kernel<TRANS><<<k, tpb, 0, s>>>(lu32, b.piv, b.res, sol, k, 0, 1, b.ctl);
+  if (transA)
+    kk_gemm_generic_kernel<1><<<g, 256, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+  else
+    kk_gemm_generic_kernel<0><<<g, 256, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+}
+
+// Y1 = X1 - I from the row-major X, and rhs = -I (so that the LU solve gives Y1^{-1}).
+__global__ void kk_inverse_init_kernel(const double* __restrict__ X, int k, double* __restrict__ y1,
+                                       double* __restrict__ rhs) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e % k, j = e / k;
+    y1[e] = X[(int64_t)i * k + j] - (i == j ? 1.0 : 0.0);
+    rhs[e] = i == j ? -1.0 : 0.0;
   }
+}
+
+void launch_inverse_setup(const SweepBufs& b, int k, cudaStream_t s) {
+  const int tpb = k >= 128 ? 128 : ((k + 31) / 32) * 32;
+  kk_inverse_init_kernel<<<(k * k + 255) / 256, 256, 0, s>>>(b.x, k, b.y1, b.res);
+  kk_lu_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(b, k);
+  kk_solve_kernel<0><<<k, tpb, 0, s>>>(b.lu, b.piv, b.res, b.zinv, k, b.ctl);   // Z = -Y1^{-1}(-I)
 }
 
 void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s) {
   const int tpb = k >= 128 ? 128 : ((k + 31) / 32) * 32;
   kk_prep_kernel<<<k, tpb, 0, s>>>(b, k);
   if (b.mixed) {
-    kk_lu32_kernel<<<1, 512, sizeof(float) * (size_t)k * k, s>>>(b, k);
-    solve_refined<0>(b, k, b.t1, b.m, tpb, s);          // M = -Y1^{-1} (Y^T R)
+    // two Newton-Schulz steps bring Z to the new Y1 (ping-pong between zinv and zinv2)
+    kk_gemm_generic(b.y1, false, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, s);      // T = I - Y1 Z
+    kk_gemm_generic(b.zinv, false, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, s);     // Z' = Z + Z T
+    kk_gemm_generic(b.y1, false, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, s);     // T' = I - Y1 Z'
+    kk_gemm_generic(b.zinv2, false, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, s);    // Z = Z' + Z' T'
+    kk_gemm_generic(b.zinv, false, b.t1, nullptr, b.m, k, -1.0, 0.0, 0, 0.0, b.ctl, s);        // M = -Z (Y^T R)
   } else {
     kk_lu_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(b, k);
     kk_solve_kernel<0><<<k, tpb, 0, s>>>(b.lu, b.piv, b.t1, b.m, k, b.ctl);
@@ -499,7 +394,7 @@ void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cu
   kk_e11_kernel<<<k, tpb, 0, s>>>(b, k, delta, beta_zero);
   kk_gemm_kernel<KG_YTE><<<g, 256, 0, s>>>(b, k);
   if (b.mixed)
-    solve_refined<1>(b, k, b.yte, b.nmat, tpb, s);      // N = -Y1^{-T} (Y^T E)
+    kk_gemm_generic(b.zinv, true, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, s);     // N = -Z^T (Y^T E)
   else
     kk_solve_kernel<1><<<k, tpb, 0, s>>>(b.lu, b.piv, b.yte, b.nmat, k, b.ctl);
   kk_gemm_kernel<KG_X1><<<g, 256, 0, s>>>(b, k);
@@ -541,9 +436,6 @@ __global__ void __launch_bounds__(512) sign_fix_kernel(const double* __restrict_
 cudaError_t init_kxk_attributes() {
   cudaError_t e = cudaFuncSetAttribute(kk_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(double) * kMaxK * kMaxK));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kk_lu32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float) * kMaxK * kMaxK));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sign_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(double) * kMaxK * kMaxK));

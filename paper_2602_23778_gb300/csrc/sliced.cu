@@ -49,7 +49,7 @@ constexpr int kBM = 128;           // rows of W per CTA
 constexpr int kBN = 32;            // columns of W per CTA
 constexpr int kBK = 64;            // K per pipeline stage (128 bytes of BF16)
 constexpr int kChunkBlocks = 4;    // K blocks per exact accumulation chunk (256)
-constexpr int kRA = 8;             // A ring stages (one per plane)
+constexpr int kRA = 9;             // A ring stages (a whole K block of planes at S = 9)
 constexpr int kRX = 2;             // X ring stages
 constexpr int kATile = kBM * kBK * 2;                // 16 KiB
 constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 36 KiB (all planes of a K block)
@@ -161,29 +161,47 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
         "=r"(r[30]), "=r"(r[31])                                                                             \
       : "r"(taddr))
 
-struct GemmArgs {
-  const int* rowexp;     // [n_pad] e_i
-  const int* colexp;     // [k_pad] f_j
-  const double* X;       // row-major n x k (for the shift term)
-  double* P;             // row-major n x k
-  int64_t n;
-  int k, n_pad, S;
-  int xg;                // X planes per TMA load (32 xg rows, xg divides S, 32 xg <= 256)
-  double shift;
+// ---------------------------------------------------------------------------
+// The tensor-core kernel, for three products that share its structure:
+//   PRODUCT  W = (A - shift I) X       A-planes (rows of A)   x  column planes of X
+//   GRAM     G = X^T X, S = X^T W      column planes of X     x  column planes of X / W
+//   UPDATE   X' = X + (W - X D) D^-1 - X F  (rows >= k)       row planes of X  x  column planes of F
+// An A-side plane s holds 128 rows of a "row-scaled" operand (one exponent per
+// row), a B-side plane t 32 rows of a "column-scaled" operand; both are K-major
+// (the contraction index runs along the 128-byte rows TMA writes).
+// ---------------------------------------------------------------------------
+enum { MODE_PRODUCT = 0, MODE_GRAM = 1, MODE_UPDATE = 2 };
+
+struct MmaArgs {
+  int a_plane_rows;      // rows between consecutive A-side planes in the A tensor map
+  int b_plane_rows;      // rows between consecutive B-side planes in the B tensor maps
+  int kb_total;          // K blocks of 64 in the contraction
+  int ksplit;            // GRAM: number of K splits (blockIdx.z = job + 2 split)
+  const int* rowexp;     // exponents of the output rows (A side)
+  const int* colexp;     // exponents of the output columns (B side; GRAM job 0)
+  const int* colexp2;    // GRAM job 1: exponents of W's columns
+  int64_t m_valid;       // output rows that exist
+  int k;                 // output columns that exist
+  int row_begin;         // UPDATE: first row written (k)
+  const double* X;       // PRODUCT / UPDATE: row-major n x k
+  double* P;             // PRODUCT: row-major n x k
+  double shift;          // PRODUCT
+  double* gpart;         // GRAM: [2][ksplit][k * k] column-major partials
+  const double* W;       // UPDATE: row-major n x k
+  const double* d;       // UPDATE: Rayleigh quotients [k]
+  double* Xn;            // UPDATE: row-major n x k
+  double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
   const Control* ctl;
   int* err;              // set to 1 on a timed-out wait
 };
 
-// One instruction shape per (S, plane s): N = 32 (S - s), cut into pieces of
-// at most 256 columns.  Everything about the issue order is a compile-time
-// constant, so the issuing thread does no arithmetic between MMAs (measured on
-// GB300: a tcgen05.mma costs max(N/2, ~40) cycles when issued back to back,
-// and any dependent integer work in between adds to that).
-template <int S>
+template <int S, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, GemmArgs g) {
+    sliced_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ CUtensorMap tmB2, MmaArgs g) {
   // one read of the stop flag per CTA: an aborting CTA of this grid may set it
   __shared__ int s_skip;
+  __shared__ double s_colsum[2][4][kBN];            // UPDATE: per lane-group column sums
   if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
   __syncthreads();
   if (s_skip) return;
@@ -193,14 +211,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* sx = smem + kRA * kATile;           // kRX x 36 KiB
   Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // column blocks vary fastest, so the CTAs sharing an A row block run together
-  // and read its digit planes from HBM once
-  const int nb = blockIdx.x;                         // column block of 32
-  const int m0 = blockIdx.y * kBM;
-  const int KB = g.n_pad / kBK;                      // K blocks (multiple of kChunkBlocks)
-  const int NC = KB / kChunkBlocks;                  // accumulation chunks
+  // column blocks vary fastest, so the CTAs sharing A-side rows run together
+  const int nb = blockIdx.x;                         // output column block of 32
+  const int m0 = blockIdx.y * kBM;                   // output row tile
+  const int job = MODE == MODE_GRAM ? (int)(blockIdx.z & 1) : 0;
+  const int split = MODE == MODE_GRAM ? (int)(blockIdx.z >> 1) : 0;
+  const int nsplit = MODE == MODE_GRAM ? g.ksplit : 1;
+  const int kb_lo = (int)((int64_t)g.kb_total * split / nsplit);
+  const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / nsplit);
+  const int KB = kb_hi - kb_lo;                      // K blocks of this CTA
+  const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
   constexpr int NBUF = (2 * S * kBN <= 512) ? 2 : 1; // TMEM accumulator sets (double-buffered if they fit)
-  constexpr int XG = (S * kBN <= 256) ? S : (S % 3 == 0 ? 3 : 1);  // X planes per TMA load
+  const CUtensorMap* tB = job ? &tmB2 : &tmB;
   volatile int* abort_flag = &bars->abort;
 
   if (threadIdx.x == 0) {
@@ -235,27 +257,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(tB) : "memory");
       int issued_a = 0, issued_x = 0;
       bool ok = true;
       int as = 0;
       uint32_t aph = 0;                              // lap parity of the A ring
       for (int kb = 0; kb < KB && ok; ++kb) {
+        const int kx = (kb_lo + kb) * kBK;           // K coordinate (elements)
         const int xs = kb & 1;
         ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((kb >> 1) & 1) ^ 1, abort_flag);
         if (!ok) break;
         mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
 #pragma unroll
-        for (int q = 0; q < S / XG; ++q)
-          tma_load_2d(smem_u32(sx + xs * kXTile + q * XG * kBN * kBK * 2), &tmX, smem_u32(&bars->x_full[xs]),
-                      kb * kBK, (nb * S + q * XG) * kBN);
+        for (int t = 0; t < S; ++t)
+          tma_load_2d(smem_u32(sx + xs * kXTile + t * kBN * kBK * 2), tB, smem_u32(&bars->x_full[xs]), kx,
+                      t * g.b_plane_rows + nb * kBN);
         ++issued_x;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, abort_flag);
           if (!ok) break;
           mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
-          tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kb * kBK, s * g.n_pad + m0);
+          tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
           ++issued_a;
           if (++as == kRA) {
             as = 0;
@@ -283,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int c = kb / kChunkBlocks;
         const int buf = NBUF == 2 ? (c & 1) : 0;
         const bool first = (kb % kChunkBlocks) == 0;
+        const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
         if (first) {
           ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
           if (!ok) break;
@@ -301,9 +325,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!ok) break;
           tc_fence_after();
           const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
-          // B = X planes 0 .. S-1-s stacked: N = 32 (S - s) rows, issued as
-          // pieces of at most 256 (the M = 128 limit); +2 in the address field
-          // steps 32 bytes (16 K) inside the 128-byte swizzle row
+          // B = B-side planes 0 .. S-1-s stacked: N = 32 (S - s) rows, issued
+          // as pieces of at most 256 (the M = 128 limit); +2 in the address
+          // field steps 32 bytes (16 K) inside the 128-byte swizzle row
           const int N = kBN * (S - s);
           const int N1 = N < 256 ? N : 256;
           const uint32_t dt = dbase + (uint32_t)(s * kBN);
@@ -327,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
         tc_commit(smem_u32(&bars->x_empty[xs]));
-        if (kb % kChunkBlocks == kChunkBlocks - 1) tc_commit(smem_u32(&bars->acc_full[buf]));
+        if (last) tc_commit(smem_u32(&bars->acc_full[buf]));
       }
       if (!ok) {
         // wait for the MMAs already issued before the CTA releases TMEM
@@ -339,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: drain chunks into exact int64 sums ----------------
     const int lg = warp & 3;                           // TMEM lane group of this warp
     const int half = (warp - 2) >> 2;                  // which 16 of the 32 columns
-    const int row = m0 + lg * 32 + lane;
+    const int64_t row = m0 + lg * 32 + lane;
     constexpr int kC = kBN / 2;
     long long hi[kC], lo[kC];
 #pragma unroll
@@ -383,29 +407,68 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[buf]));
     }
-    if (ok && row < g.n) {
-      const double lo_scale = ldexp(1.0, -kBits * (S + 1));
-      const int er = g.rowexp[row];
-      const int64_t rk = (int64_t)row * g.k;
+    const double lo_scale = ldexp(1.0, -kBits * (S + 1));
+    const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
+    const int* cexp = job ? g.colexp2 : g.colexp;
+    double sq[kC], rq[kC];
 #pragma unroll
-      for (int j = 0; j < kC; ++j) {
-        const int col = nb * kBN + half * kC + j;
-        if (col < g.k) {
-          const int fc = g.colexp[col];
-          double w;
-          if (er == kNonFinite || fc == kNonFinite) {
-            w = __longlong_as_double(0x7FF8000000000000ll);   // NaN: A or X held Inf / NaN
-          } else {
-            const double v = fma((double)lo[j], lo_scale, (double)hi[j] * 0x1p-35);
-            w = ldexp(v, er + fc);
-          }
-          g.P[rk + col] = w - g.shift * g.X[rk + col];
+    for (int j = 0; j < kC; ++j) {
+      const int col = nb * kBN + half * kC + j;
+      double w = 0.0;
+      const bool live = ok && row < g.m_valid && col < g.k;
+      if (live) {
+        const int fc = cexp[col];
+        if (er == kNonFinite || fc == kNonFinite) {
+          w = __longlong_as_double(0x7FF8000000000000ll);   // NaN: an operand held Inf / NaN
+        } else {
+          const double v = fma((double)lo[j], lo_scale, (double)hi[j] * 0x1p-35);
+          w = ldexp(v, er + fc);
         }
       }
+      sq[j] = rq[j] = 0.0;
+      if (MODE == MODE_PRODUCT) {
+        if (live) g.P[row * g.k + col] = w - g.shift * g.X[row * g.k + col];
+      } else if (MODE == MODE_GRAM) {
+        if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = w;
+      } else {
+        if (live && row >= g.row_begin) {
+          const int64_t e = row * g.k + col;
+          const double x = g.X[e], dj = g.d[col];
+          const double rr = g.W[e] - x * dj;
+          const double xn = x + rr / dj - w;
+          g.Xn[e] = xn;
+          sq[j] = xn * xn;
+          rq[j] = rr * rr;
+        }
+      }
+    }
+    if (MODE == MODE_UPDATE) {
+      // column sums over this CTA's rows, in a fixed order
+#pragma unroll
+      for (int j = 0; j < kC; ++j)
+        for (int o = 16; o > 0; o >>= 1) {
+          sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], o);
+          rq[j] += __shfl_xor_sync(0xffffffffu, rq[j], o);
+        }
+      if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+          s_colsum[0][lg][half * kC + j] = sq[j];
+          s_colsum[1][lg][half * kC + j] = rq[j];
+        }
     }
   }
   tc_fence_before();
   __syncthreads();
+  if (MODE == MODE_UPDATE && threadIdx.x < 2 * kBN) {
+    const int which = threadIdx.x / kBN, cc = threadIdx.x % kBN;
+    const int col = nb * kBN + cc;
+    if (col < g.k) {
+      const double v = s_colsum[which][0][cc] + s_colsum[which][1][cc] + s_colsum[which][2][cc] +
+                       s_colsum[which][3][cc];
+      g.upart[(int64_t)blockIdx.y * 2 * g.k + which * g.k + col] = v;
+    }
+  }
   if (bars->abort && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     if (g.ctl) {
@@ -498,28 +561,30 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
   }
 }
 
-// Column maxima of X (row-major n x k) as non-negative double bit patterns.
-__global__ void colmax_kernel(const double* __restrict__ X, int64_t n, int k, unsigned long long* __restrict__ cmax,
-                              const Control* ctl) {
+// Column maxima of a strided n x k operand (element (l, j) at Y[l rs + j cs])
+// as non-negative double bit patterns; NaN survives (fmax would drop it).
+__global__ void colmax_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
+                              unsigned long long* __restrict__ cmax, const Control* ctl) {
   if (ctl && ctl->done) return;
   const int j = threadIdx.x % k;   // blockDim.x is a multiple of k
   const int rpb = blockDim.x / k;
   double m = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / k; i < n; i += (int64_t)gridDim.x * rpb) {
-    const double v = fabs(X[i * k + j]);
-    m = (v > m || v != v) ? v : m;       // keeps NaN (fmax would drop it)
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / k; i < rows; i += (int64_t)gridDim.x * rpb) {
+    const double v = fabs(Y[i * rs + j * cs]);
+    m = (v > m || v != v) ? v : m;
   }
   atomicMax(cmax + j, (unsigned long long)__double_as_longlong(m));
 }
 
-// Digit planes of X: Xs[(cb * S + t) * 32 + jj][l] (BF16), column j = 32 cb + jj.
-// A CTA takes 64 rows x 32 columns through shared memory so both the FP64 reads
-// and the BF16 writes are contiguous.
+// Column digit planes: planes[(t kp + j) K + l] (BF16) for column j of the
+// strided operand, scaled by its column exponent.  A CTA takes 64 rows x 32
+// columns through shared memory, so the BF16 writes are contiguous.
 template <int S>
-__global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__ X, int64_t n, int k, int n_pad,
-                                                      const unsigned long long* __restrict__ cmax,
-                                                      __nv_bfloat16* __restrict__ Xs, int* __restrict__ colexp,
-                                                      const Control* ctl) {
+__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs,
+                                                         int64_t cs, int K, int kp,
+                                                         const unsigned long long* __restrict__ cmax,
+                                                         __nv_bfloat16* __restrict__ planes, int* __restrict__ colexp,
+                                                         const Control* ctl) {
   if (ctl && ctl->done) return;
   __shared__ double tile[64][33];
   __shared__ int fexp[32];
@@ -537,7 +602,7 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__
     const int rr = e >> 5, jj = e & 31;
     const int64_t l = l0 + rr;
     const int j = cb * 32 + jj;
-    tile[rr][jj] = (l < n && j < k) ? X[l * k + j] : 0.0;
+    tile[rr][jj] = (l < rows && j < k) ? Y[l * rs + j * cs] : 0.0;
   }
   __syncthreads();
   // thread -> (jj, 8 consecutive rows); writes 16 bytes per plane
@@ -550,22 +615,74 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double* __restrict__
     __align__(16) __nv_bfloat16 d[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][t]);
-    const int64_t rowid = ((int64_t)cb * S + t) * 32 + jj;
-    *reinterpret_cast<uint4*>(Xs + rowid * n_pad + l0 + r0) = *reinterpret_cast<uint4*>(d);
+    const int64_t rowid = (int64_t)t * kp + cb * 32 + jj;
+    *reinterpret_cast<uint4*>(planes + rowid * K + l0 + r0) = *reinterpret_cast<uint4*>(d);
+  }
+}
+
+// Row digit planes of a row-major n x k operand: planes[(s n_pad + i) K + l],
+// one exponent per row.  One warp per row; lane c takes elements 8c..8c+7.
+template <int S>
+__global__ void slice_rows_kernel(const double* __restrict__ Y, int64_t n, int k, int n_pad, int K,
+                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ rowexp, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t plane = (int64_t)n_pad * K;
+  for (int64_t i = wid; i < n_pad; i += nw) {
+    double amax = 0.0;
+    bool finite = true;
+    if (i < n)
+      for (int l = lane; l < k; l += 32) {
+        const double v = Y[i * k + l];
+        finite = finite && isfinite(v);
+        amax = fmax(amax, fabs(v));
+      }
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    finite = __all_sync(0xffffffffu, finite);
+    const int e = row_exponent(amax);
+    if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
+    for (int c = lane; c < K / 8; c += 32) {
+      int dg[8][S];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = c * 8 + q;
+        const double v = (i < n && l < k && finite) ? Y[i * k + l] : 0.0;
+        digits_of<S>(v, e, dg[q]);
+      }
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        __align__(16) __nv_bfloat16 d[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][s]);
+        *reinterpret_cast<uint4*>(planes + s * plane + i * K + c * 8) = *reinterpret_cast<uint4*>(d);
+      }
+    }
   }
 }
 
 template <int S>
-void launch_slicers(const double* A, int64_t n, int64_t lda, int n_pad, __nv_bfloat16* As, int* rowexp,
+void launch_slice_a(const double* A, int64_t n, int64_t lda, int n_pad, __nv_bfloat16* As, int* rowexp,
                     cudaStream_t s) {
   slice_a_kernel<S><<<152 * 8, 256, 0, s>>>(A, n, lda, n_pad, As, rowexp);
 }
 
 template <int S>
-void launch_slice_x(const double* X, int64_t n, int k, int n_pad, int k_pad, const unsigned long long* cmax,
-                    __nv_bfloat16* Xs, int* colexp, const Control* ctl, cudaStream_t s) {
-  dim3 gx((unsigned)(n_pad / 64), (unsigned)(k_pad / 32));
-  slice_x_kernel<S><<<gx, 256, 0, s>>>(X, n, k, n_pad, cmax, Xs, colexp, ctl);
+void launch_slice_cols(const double* Y, int64_t rows, int k, int64_t rs, int64_t cs, int K, int kp,
+                       unsigned long long* cmax, __nv_bfloat16* planes, int* colexp, const Control* ctl,
+                       cudaStream_t s) {
+  cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
+  const int rpb = 256 / k > 0 ? 256 / k : 1;
+  colmax_kernel<<<152 * 4, rpb * k, 0, s>>>(Y, rows, k, rs, cs, cmax, ctl);
+  dim3 gx((unsigned)(K / 64), (unsigned)(kp / 32));
+  slice_cols_kernel<S><<<gx, 256, 0, s>>>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, ctl);
+}
+
+template <int S>
+void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __nv_bfloat16* planes, int* rowexp,
+                       const Control* ctl, cudaStream_t s) {
+  slice_rows_kernel<S><<<152 * 8, 256, 0, s>>>(Y, n, k, n_pad, K, planes, rowexp, ctl);
 }
 
 #define EIGREF_SLICE_DISPATCH(S_, CALL) \
@@ -616,28 +733,29 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
 
 cudaError_t init_sliced_attributes() {
   cudaError_t e = cudaSuccess;
-#define EIGREF_SET_ATTR(S_)                                                                                  \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(sl::sliced_gemm_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
+#define EIGREF_SET_ATTR(S_)                                                                                        \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_PRODUCT>,                                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             sl::kSmemBytes);                                                                      \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_UPDATE>,                                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
   EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
   EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
 #undef EIGREF_SET_ATTR
   return e;
 }
 
-// X planes per TMA load: the largest divisor g of S with a box of 32 g <= 256 rows.
-static int x_group(int S) {
-  for (int g = S; g > 0; --g)
-    if (S % g == 0 && g * sl::kBN <= 256) return g;
-  return 1;
-}
-
 // ---- plan / workspace ----
 struct SlicedLayout {
-  size_t a_planes, rowexp, x_planes, colexp, cmax, err, total;
+  size_t a_planes, rowexp, x_planes, x_colexp, x_cmax, p_planes, p_colexp, p_cmax, xr_planes, xr_rowexp, f_planes,
+      f_colexp, f_cmax, gpart, err, total;
 };
 
-static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int S) {
+static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int ksplit, int k) {
   SlicedLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -649,11 +767,24 @@ static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int S) {
   L.a_planes = take((size_t)S * n_pad * n_pad * 2);
   L.rowexp = take((size_t)n_pad * 4);
   L.x_planes = take((size_t)S * k_pad * n_pad * 2);
-  L.colexp = take((size_t)k_pad * 4);
-  L.cmax = take((size_t)k_pad * 8);
+  L.x_colexp = take((size_t)k_pad * 4);
+  L.x_cmax = take((size_t)k_pad * 8);
+  L.p_planes = take((size_t)S * k_pad * n_pad * 2);
+  L.p_colexp = take((size_t)k_pad * 4);
+  L.p_cmax = take((size_t)k_pad * 8);
+  L.xr_planes = take((size_t)S * n_pad * kr * 2);
+  L.xr_rowexp = take((size_t)n_pad * 4);
+  L.f_planes = take((size_t)S * k_pad * kr * 2);
+  L.f_colexp = take((size_t)k_pad * 4);
+  L.f_cmax = take((size_t)k_pad * 8);
+  L.gpart = take((size_t)2 * ksplit * k * k * 8);
   L.err = take(64);
   L.total = off + 1024;
   return L;
+}
+
+size_t SlicedA::layout_total() const {
+  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_).total;
 }
 
 int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int precision, int slices) {
@@ -683,31 +814,47 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
   }
   n_pad_ = (int)((n + 255) / 256 * 256);
   k_pad_ = (k + 31) / 32 * 32;
+  kr_ = (k + 63) / 64 * 64;
+  // Gram split-K: about two CTAs per SM in total (2 jobs x k_pad/32 column blocks)
+  const int per_split = 2 * (k_pad_ / 32);
+  ksplit_ = (304 + per_split - 1) / per_split;
+  const int kbt = n_pad_ / sl::kBK;
+  if (ksplit_ > kbt) ksplit_ = kbt;
+  if (ksplit_ < 1) ksplit_ = 1;
   return EIGREF_OK;
 }
 
-size_t SlicedA::workspace_bytes() const { return sliced_layout(n_pad_, k_pad_, slices_).total; }
+size_t SlicedA::workspace_bytes() const { return layout_total(); }
 
 void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023)); }
 
 int SlicedA::prepare(cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, slices_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
   auto* ap = reinterpret_cast<__nv_bfloat16*>(ws_ + L.a_planes);
-  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
-  // X planes: zero once, so padding rows and columns stay zero
-  if (cudaMemsetAsync(xp, 0, (size_t)slices_ * k_pad_ * n_pad_ * 2, s) != cudaSuccess ||
+  // B-side and row planes: zero once, so padding rows and columns stay zero
+  if (cudaMemsetAsync(ws_ + L.x_planes, 0, L.xr_rowexp - L.x_planes, s) != cudaSuccess ||
+      cudaMemsetAsync(ws_ + L.f_planes, 0, L.f_colexp - L.f_planes, s) != cudaSuccess ||
       cudaMemsetAsync(ws_ + L.err, 0, 64, s) != cudaSuccess) {
     snprintf(err_, sizeof(err_), "memset of slice planes failed");
     return EIGREF_E_CUDA;
   }
   int* rowexp = reinterpret_cast<int*>(ws_ + L.rowexp);
-#define EIGREF_CALL_SLICE_A(S_) sl::launch_slicers<S_>(A_, n_, lda_, n_pad_, ap, rowexp, s)
+#define EIGREF_CALL_SLICE_A(S_) sl::launch_slice_a<S_>(A_, n_, lda_, n_pad_, ap, rowexp, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_A)
 #undef EIGREF_CALL_SLICE_A
-  if (!sl::make_map(reinterpret_cast<CUtensorMap*>(tmA_), ap, (uint64_t)n_pad_, (uint64_t)slices_ * n_pad_, sl::kBK,
-                    sl::kBM) ||
-      !sl::make_map(reinterpret_cast<CUtensorMap*>(tmX_), xp, (uint64_t)n_pad_, (uint64_t)slices_ * k_pad_, sl::kBK,
-                    (uint32_t)(x_group(slices_) * sl::kBN))) {
+  const uint64_t S = (uint64_t)slices_;
+  bool ok = sl::make_map(reinterpret_cast<CUtensorMap*>(tmA_), ap, (uint64_t)n_pad_, S * n_pad_, sl::kBK, sl::kBM);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmX_), ws_ + L.x_planes, (uint64_t)n_pad_, S * k_pad_,
+                          sl::kBK, sl::kBN);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmXA_), ws_ + L.x_planes, (uint64_t)n_pad_, S * k_pad_,
+                          sl::kBK, sl::kBM);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmP_), ws_ + L.p_planes, (uint64_t)n_pad_, S * k_pad_,
+                          sl::kBK, sl::kBN);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmXR_), ws_ + L.xr_planes, (uint64_t)kr_, S * n_pad_,
+                          sl::kBK, sl::kBM);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmF_), ws_ + L.f_planes, (uint64_t)kr_, S * k_pad_, sl::kBK,
+                          sl::kBN);
+  if (!ok) {
     snprintf(err_, sizeof(err_), "tensor map encoding failed");
     return EIGREF_E_CUDA;
   }
@@ -718,44 +865,121 @@ int SlicedA::prepare(cudaStream_t s) {
   return EIGREF_OK;
 }
 
+static sl::MmaArgs base_args(const Control* ctl, int* err) {
+  sl::MmaArgs g;
+  memset(&g, 0, sizeof(g));
+  g.ctl = ctl;
+  g.err = err;
+  g.ksplit = 1;
+  return g;
+}
+
+template <int MODE>
+static void launch_mma(int S, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b2,
+                       const sl::MmaArgs& g, cudaStream_t s) {
+#define EIGREF_CALL_MMA(S_) sl::sliced_mma_kernel<S_, MODE><<<grid, sl::kThreads, sl::kSmemBytes, s>>>(a, b, b2, g)
+  EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_MMA)
+#undef EIGREF_CALL_MMA
+}
+
 int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
                      cudaEvent_t ev1, unsigned ev_flags) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, slices_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
   auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
-  auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.cmax);
-  int* colexp = reinterpret_cast<int*>(ws_ + L.colexp);
-  cudaMemsetAsync(cmax, 0, (size_t)k_ * 8, s);
-  const int rpb = 256 / k_ > 0 ? 256 / k_ : 1;
-  sl::colmax_kernel<<<152 * 4, rpb * k_, 0, s>>>(X, n_, k_, cmax, ctl);
-#define EIGREF_CALL_SLICE_X(S_) sl::launch_slice_x<S_>(X, n_, k_, n_pad_, k_pad_, cmax, xp, colexp, ctl, s)
+  auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
+  int* colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
+#define EIGREF_CALL_SLICE_X(S_) \
+  sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, n_pad_, k_pad_, cmax, xp, colexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_X)
 #undef EIGREF_CALL_SLICE_X
-  sl::GemmArgs g;
+  sl::MmaArgs g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g.a_plane_rows = n_pad_;
+  g.b_plane_rows = k_pad_;
+  g.kb_total = n_pad_ / sl::kBK;
   g.rowexp = reinterpret_cast<const int*>(ws_ + L.rowexp);
   g.colexp = colexp;
+  g.m_valid = n_;
+  g.k = k_;
   g.X = X;
   g.P = P;
-  g.n = n_;
-  g.k = k_;
-  g.n_pad = n_pad_;
-  g.S = slices_;
-  g.xg = x_group(slices_);
   g.shift = shift;
-  g.ctl = ctl;
-  g.err = reinterpret_cast<int*>(ws_ + L.err);
   dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM));
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
   const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(tmA_);
   const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
-#define EIGREF_CALL_GEMM(S_) sl::sliced_gemm_kernel<S_><<<grid, sl::kThreads, sl::kSmemBytes, s>>>(ma, mx, g)
-  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_GEMM)
-#undef EIGREF_CALL_GEMM
+  launch_mma<sl::MODE_PRODUCT>(slices_, grid, ma, mx, mx, g, s);
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
   return 3;
 }
 
+int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s) {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
+  int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
+#define EIGREF_CALL_SLICE_P(S_) \
+  sl::launch_slice_cols<S_>(P, n_, k_, k_, 1, n_pad_, k_pad_, cmax, pp, pexp, ctl, s)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_P)
+#undef EIGREF_CALL_SLICE_P
+  sl::MmaArgs g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g.a_plane_rows = k_pad_;
+  g.b_plane_rows = k_pad_;
+  g.kb_total = n_pad_ / sl::kBK;
+  g.ksplit = ksplit_;
+  g.rowexp = reinterpret_cast<const int*>(ws_ + L.x_colexp);   // rows of G, S = columns of X
+  g.colexp = reinterpret_cast<const int*>(ws_ + L.x_colexp);
+  g.colexp2 = pexp;
+  g.m_valid = k_;
+  g.k = k_;
+  g.gpart = part ? part : reinterpret_cast<double*>(ws_ + L.gpart);
+  dim3 grid((unsigned)(k_pad_ / sl::kBN), 1u, (unsigned)(2 * ksplit_));
+  const CUtensorMap& mxa = *reinterpret_cast<const CUtensorMap*>(tmXA_);
+  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
+  const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
+  launch_mma<sl::MODE_GRAM>(slices_, grid, mxa, mx, mp, g, s);
+  launch_gram_reduce(g.gpart, k_, ksplit_, out, ctl, s);
+  return 6;
+}
+
+int SlicedA::update(const double* X, const double* W, const double* F, const double* d, double* Xn, double* upart,
+                    const Control* ctl, cudaStream_t s) {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+  auto* xr = reinterpret_cast<__nv_bfloat16*>(ws_ + L.xr_planes);
+  auto* fp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.f_planes);
+  int* xrexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
+  int* fexp = reinterpret_cast<int*>(ws_ + L.f_colexp);
+  auto* fmax_ = reinterpret_cast<unsigned long long*>(ws_ + L.f_cmax);
+  // F is k x k column-major: element (l, j) at F[l + j k]
+#define EIGREF_CALL_SLICE_UPD(S_)                                                                       \
+  sl::launch_slice_rows<S_>(X, n_, k_, n_pad_, kr_, xr, xrexp, ctl, s);                                 \
+  sl::launch_slice_cols<S_>(F, k_, k_, 1, k_, kr_, k_pad_, fmax_, fp, fexp, ctl, s)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_UPD)
+#undef EIGREF_CALL_SLICE_UPD
+  sl::MmaArgs g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g.a_plane_rows = n_pad_;
+  g.b_plane_rows = k_pad_;
+  g.kb_total = kr_ / sl::kBK;
+  g.rowexp = xrexp;
+  g.colexp = fexp;
+  g.m_valid = n_;
+  g.k = k_;
+  g.row_begin = k_;
+  g.X = X;
+  g.W = W;
+  g.d = d;
+  g.Xn = Xn;
+  g.upart = upart;
+  dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM));
+  const CUtensorMap& mxr = *reinterpret_cast<const CUtensorMap*>(tmXR_);
+  const CUtensorMap& mf = *reinterpret_cast<const CUtensorMap*>(tmF_);
+  launch_mma<sl::MODE_UPDATE>(slices_, grid, mxr, mf, mf, g, s);
+  return 6;
+}
+
+int SlicedA::update_grid() const { return n_pad_ / sl::kBM; }
+
 int SlicedA::timed_out(cudaStream_t s) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, slices_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
   int v = 0;
   cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);

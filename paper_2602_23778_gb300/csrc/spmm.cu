@@ -24,7 +24,15 @@ __device__ __forceinline__ double ld_stream_f64(const double* p) {
   return v;
 }
 
-// LPR lanes per row; each lane owns column pairs c2 = lane, lane + LPR, ...
+// A CTA takes 64 consecutive rows at a time.  Their row pointers and then
+// their nonzeros (a contiguous range of the CSR arrays) are staged in shared
+// memory with coalesced loads; then each group of LPR lanes takes two rows
+// and requests every X row they touch before using any, so each 64-row block
+// costs three memory latencies and keeps many X rows in flight.  Blocks whose
+// nonzeros do not fit the stage read them from global memory directly.
+constexpr int SP_ROWS = 64;
+constexpr int SP_CAP = 2048;   // staged nonzeros per block
+
 template <int LPR>
 __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ ci,
@@ -32,26 +40,57 @@ __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __res
                                                             const double* __restrict__ X, double* __restrict__ P,
                                                             int64_t n, int k, double shift, const Control* ctl) {
   if (ctl && ctl->done) return;
-  const int lane = threadIdx.x % LPR;
-  const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / LPR;
+  __shared__ int32_t rps[SP_ROWS + 1];
+  __shared__ int32_t cis[SP_CAP];
+  __shared__ double vals[SP_CAP];
+  constexpr int GROUPS = 256 / LPR;
+  const int tid = threadIdx.x, lane = tid % LPR, grp = tid / LPR;
   const int k2 = k >> 1;
   const double2* X2 = reinterpret_cast<const double2*>(X);
   double2* P2 = reinterpret_cast<double2*>(P);
-  for (int64_t i = g; i < n; i += ng) {
-    const int32_t b = ld_stream_i32(rp + i), e = ld_stream_i32(rp + i + 1);
-    for (int c2 = lane; c2 < k2; c2 += LPR) {
-      double ax = 0.0, ay = 0.0;
-      for (int32_t p = b; p < e; ++p) {
-        const double a = ld_stream_f64(val + p);
-        const int64_t col = ld_stream_i32(ci + p);
-        const double2 x = __ldg(X2 + col * k2 + c2);
-        ax = fma(a, x.x, ax);
-        ay = fma(a, x.y, ay);
+  const int64_t nblk = (n + SP_ROWS - 1) / SP_ROWS;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t r0 = blk * SP_ROWS;
+    const int rows = (int)(n - r0 < SP_ROWS ? n - r0 : SP_ROWS);
+    if (tid <= rows) rps[tid] = ld_stream_i32(rp + r0 + tid);
+    __syncthreads();
+    const int32_t nb = rps[0], cnt = rps[rows] - nb;
+    const bool staged = cnt <= SP_CAP;
+    if (staged)
+      for (int q = tid; q < cnt; q += 256) {
+        cis[q] = ld_stream_i32(ci + nb + q);
+        vals[q] = ld_stream_f64(val + nb + q);
       }
-      const double2 xi = __ldg(X2 + i * k2 + c2);
-      P2[i * k2 + c2] = make_double2(ax - shift * xi.x, ay - shift * xi.y);
+    __syncthreads();
+    for (int r = grp; r < rows; r += GROUPS) {
+      const int32_t b = rps[r], e = rps[r + 1];
+      const int64_t i = r0 + r;
+      for (int c2 = lane; c2 - lane < k2; c2 += LPR) {
+        double ax = 0.0, ay = 0.0;
+        for (int32_t p0 = b; p0 < e; p0 += 8) {
+          double2 xs[8];
+          double as[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int32_t p = p0 + t;
+            const bool on = p < e && c2 < k2;
+            const int64_t col = on ? (staged ? cis[p - nb] : ci[p]) : 0;
+            as[t] = on ? (staged ? vals[p - nb] : val[p]) : 0.0;
+            xs[t] = on ? __ldg(X2 + col * k2 + c2) : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            ax = fma(as[t], xs[t].x, ax);
+            ay = fma(as[t], xs[t].y, ay);
+          }
+        }
+        if (c2 < k2) {
+          const double2 xi = __ldg(X2 + i * k2 + c2);
+          P2[i * k2 + c2] = make_double2(ax - shift * xi.x, ay - shift * xi.y);
+        }
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -76,7 +115,7 @@ __global__ void __launch_bounds__(256) spmm_csr_scalar_kernel(const int32_t* __r
 
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
                      int64_t n, int k, double shift, const Control* ctl, cudaStream_t s) {
-  const int grid = 152 * 8;  // 8 resident CTAs of 256 threads per SM, grid-stride over rows
+  const int grid = 152 * 6;  // resident CTAs of 256 threads, grid-stride over 64-row blocks
   if ((k & 1) == 0) {
     const int k2 = k >> 1;
     if (k2 <= 2)
