@@ -141,6 +141,8 @@ struct Problem {
   const int32_t* rp = nullptr;
   const int32_t* ci = nullptr;
   const double* val = nullptr;
+  double* val_folded = nullptr;  // CSR values with the shift folded into the diagonal (workspace)
+  bool folded = false;
   int64_t n = 0, nnz = 0;
   int k = 0;
   SlicedA* sliced = nullptr;  // split-precision dense product, or null
@@ -152,9 +154,12 @@ int launch_product(const Problem& pr, const double* X, double* P, double shift, 
                    cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, unsigned ev_flags = 0) {
   if (pr.sliced) return pr.sliced->product(X, P, shift, ctl, s, ev0, ev1, ev_flags);
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
-  if (pr.csr)
-    launch_spmm_csr(pr.rp, pr.ci, pr.val, X, P, pr.n, pr.k, shift, ctl, s);
-  else
+  if (pr.csr) {
+    if (pr.folded)
+      launch_spmm_csr(pr.rp, pr.ci, pr.val_folded, X, P, pr.n, pr.k, 0.0, ctl, s);
+    else
+      launch_spmm_csr(pr.rp, pr.ci, pr.val, X, P, pr.n, pr.k, shift, ctl, s);
+  } else
     launch_gemm_fp64(pr.A, pr.lda, X, P, pr.n, pr.k, shift, ctl, s);
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
   return 1;
@@ -180,7 +185,7 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   launch_kxk_stage(b, k, delta, beta_zero, s);
   launches += b.mixed ? 12 : 9;
   if (pr.sliced) {
-    pr.sliced->update(b.x, b.p, b.f, b.d, b.xn, b.upart, b.ctl, s);
+    pr.sliced->update(b.x, b.p, b.f, b.d, b.dinv, b.xn, b.upart, b.ctl, s);
     launches += 4;
   } else {
     launch_update_rows(b, n, k, s);
@@ -220,7 +225,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
                        &b.zinv, &b.zinv2};
     for (double** m : mats) *m = c.take<double>(kk);
     b.piv = c.take<int>(k);
-    double** vecs[] = {&b.alpha, &b.d, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
+    double** vecs[] = {&b.alpha, &b.d, &b.dinv, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
     for (double** v : vecs) *v = c.take<double>(k);
     *sigma = c.take<double>(k);
     b.upart = c.take<double>((int64_t)ugrid * 2 * k);
@@ -228,6 +233,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     b.hist_corr = c.take<double>(hist_len);
     b.ctl = c.take<Control>(1);
     *scal = c.take<double>(4);
+    if (pr.csr) pr.val_folded = c.take<double>(pr.nnz > 0 ? pr.nnz : 1);
   };
   SweepBufs b{};
   double* xbuf[2];
@@ -265,6 +271,16 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   else if (q.target == EIGREF_SMALLEST) shift = 0.5 * (norm_a + q.shift);   // Section 5.1
   else if (q.target == EIGREF_LARGEST) shift = 0.5 * (q.shift - norm_a);    // its mirror
   const double delta = q.delta_c * (norm_a + fabs(shift)) * kUnitRoundoff;  // Section 3.1.3
+  if (pr.csr && shift != 0.0 && pr.nnz > 0) {
+    // fold -shift into the stored diagonal once, so the SpMM has no shift term
+    int* missing = reinterpret_cast<int*>(scal + 2);
+    launch_csr_fold_diag(pr.rp, pr.ci, pr.val, n, shift, pr.val_folded, missing, s);
+    int hmiss = 1;
+    CUDA_TRY(h, cudaMemcpyAsync(&h->host_ctl->status, missing, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    hmiss = h->host_ctl->status;
+    pr.folded = hmiss == 0;
+  }
 
   const double* xu = X;
   if (!x_dev) {

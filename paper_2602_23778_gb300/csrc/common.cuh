@@ -49,7 +49,7 @@ struct SweepBufs {
   double *zinv, *zinv2;  // k x k: Y1^{-1} kept across sweeps (split form) and a scratch copy
   int mixed;          // 1: Y1^{-1} by Newton-Schulz updates instead of an LU per sweep
   int* piv;           // [k]
-  double *alpha, *d, *cz, *cw, *nu, *r1sq, *e11sq, *x1sq;  // [k]
+  double *alpha, *d, *dinv, *cz, *cw, *nu, *r1sq, *e11sq, *x1sq;  // [k]
   double* upart;      // update partials [ugrid][2k]
   double *hist_res, *hist_corr;  // [max_iters]
   Control* ctl;
@@ -82,6 +82,8 @@ cudaError_t init_kxk_attributes();
 // spmm.cu
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
                      int64_t n, int k, double shift, const Control* ctl, cudaStream_t s);
+void launch_csr_fold_diag(const int32_t* rp, const int32_t* ci, const double* val, int64_t n, double shift,
+                          double* val_out, int* missing, cudaStream_t s);
 // kxk.cu
 void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s);
 void launch_sign_fix(const double* X, int64_t ldx, int k, double* sigma, int* singular, cudaStream_t s);

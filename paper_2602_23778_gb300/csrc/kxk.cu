@@ -75,6 +75,7 @@ __global__ void kk_prep_kernel(SweepBufs b, int k) {
   if (threadIdx.x == 0) {
     b.alpha[j] = al;
     b.d[j] = dj;
+    b.dinv[j] = 1.0 / dj;
     b.r1sq[j] = r1s;
   }
 }

@@ -31,6 +31,7 @@
 // chunk; at S = 9 one set is used and the MMAs wait for each drain.  All waits are bounded (globaltimer); on expiry the CTA records a
 // timeout, drains what it started and returns.
 #include <cuda.h>
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -186,9 +187,11 @@ struct MmaArgs {
   const double* X;       // PRODUCT / UPDATE: row-major n x k
   double* P;             // PRODUCT: row-major n x k
   double shift;          // PRODUCT
+  double* ppart;         // PRODUCT with ksplit > 1: [ksplit][n x k] row-major partial products
   double* gpart;         // GRAM: [2][ksplit][k * k] column-major partials
   const double* W;       // UPDATE: row-major n x k
   const double* d;       // UPDATE: Rayleigh quotients [k]
+  const double* dinv;    // UPDATE: 1 / d
   double* Xn;            // UPDATE: row-major n x k
   double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
   const Control* ctl;
@@ -215,8 +218,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nb = blockIdx.x;                         // output column block of 32
   const int m0 = blockIdx.y * kBM;                   // output row tile
   const int job = MODE == MODE_GRAM ? (int)(blockIdx.z & 1) : 0;
-  const int split = MODE == MODE_GRAM ? (int)(blockIdx.z >> 1) : 0;
-  const int nsplit = MODE == MODE_GRAM ? g.ksplit : 1;
+  const int split = MODE == MODE_GRAM ? (int)(blockIdx.z >> 1) : (MODE == MODE_PRODUCT ? (int)blockIdx.z : 0);
+  const int nsplit = MODE == MODE_UPDATE ? 1 : g.ksplit;
   const int kb_lo = (int)((int64_t)g.kb_total * split / nsplit);
   const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / nsplit);
   const int KB = kb_hi - kb_lo;                      // K blocks of this CTA
@@ -427,7 +430,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       sq[j] = rq[j] = 0.0;
       if (MODE == MODE_PRODUCT) {
-        if (live) g.P[row * g.k + col] = w - g.shift * g.X[row * g.k + col];
+        if (live) {
+          if (nsplit == 1)
+            g.P[row * g.k + col] = w - g.shift * g.X[row * g.k + col];
+          else
+            g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = w;
+        }
       } else if (MODE == MODE_GRAM) {
         if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = w;
       } else {
@@ -435,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int64_t e = row * g.k + col;
           const double x = g.X[e], dj = g.d[col];
           const double rr = g.W[e] - x * dj;
-          const double xn = x + rr / dj - w;
+          const double xn = x + rr * g.dinv[col] - w;
           g.Xn[e] = xn;
           sq[j] = xn * xn;
           rq[j] = rr * rr;
@@ -662,6 +670,17 @@ __global__ void slice_rows_kernel(const double* __restrict__ Y, int64_t n, int k
   }
 }
 
+// P = sum of the split partial products - shift X (fixed order).
+__global__ void product_reduce_kernel(const double* __restrict__ part, int ksplit, const double* __restrict__ X,
+                                      double* __restrict__ P, int64_t total, double shift, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = part[e];
+    for (int q = 1; q < ksplit; ++q) v += part[(int64_t)q * total + e];
+    P[e] = v - shift * X[e];
+  }
+}
+
 template <int S>
 void launch_slice_a(const double* A, int64_t n, int64_t lda, int n_pad, __nv_bfloat16* As, int* rowexp,
                     cudaStream_t s) {
@@ -752,10 +771,11 @@ cudaError_t init_sliced_attributes() {
 // ---- plan / workspace ----
 struct SlicedLayout {
   size_t a_planes, rowexp, x_planes, x_colexp, x_cmax, p_planes, p_colexp, p_cmax, xr_planes, xr_rowexp, f_planes,
-      f_colexp, f_cmax, gpart, err, total;
+      f_colexp, f_cmax, gpart, ppart, err, total;
 };
 
-static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int ksplit, int k) {
+static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int ksplit, int k, int psplit = 1,
+                                  int64_t n = 0) {
   SlicedLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -778,13 +798,14 @@ static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int k
   L.f_colexp = take((size_t)k_pad * 4);
   L.f_cmax = take((size_t)k_pad * 8);
   L.gpart = take((size_t)2 * ksplit * k * k * 8);
+  L.ppart = take(psplit > 1 ? (size_t)psplit * n * k * 8 : 64);
   L.err = take(64);
   L.total = off + 1024;
   return L;
 }
 
 size_t SlicedA::layout_total() const {
-  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_).total;
+  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_).total;
 }
 
 int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int precision, int slices) {
@@ -816,6 +837,21 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
   k_pad_ = (k + 31) / 32 * 32;
   kr_ = (k + 63) / 64 * 64;
   // Gram split-K: about two CTAs per SM in total (2 jobs x k_pad/32 column blocks)
+  // product split-K: the count of CTA rounds (one CTA per SM) wastes least
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ctas = (int64_t)(k_pad_ / 32) * (n_pad_ / 128);
+  double best = 0.0;
+  psplit_ = 1;
+  for (int p = 1; p <= 4; ++p) {
+    if ((n_pad_ / 64) / p < 8) break;                  // keep at least two chunks per CTA
+    const int64_t c = ctas * p;
+    const double eff = (double)c / (double)(sms * ((c + sms - 1) / sms));
+    if (eff > best + 0.02) {
+      best = eff;
+      psplit_ = p;
+    }
+  }
   const int per_split = 2 * (k_pad_ / 32);
   ksplit_ = (304 + per_split - 1) / per_split;
   const int kbt = n_pad_ / sl::kBK;
@@ -829,7 +865,7 @@ size_t SlicedA::workspace_bytes() const { return layout_total(); }
 void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023)); }
 
 int SlicedA::prepare(cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
   auto* ap = reinterpret_cast<__nv_bfloat16*>(ws_ + L.a_planes);
   // B-side and row planes: zero once, so padding rows and columns stay zero
   if (cudaMemsetAsync(ws_ + L.x_planes, 0, L.xr_rowexp - L.x_planes, s) != cudaSuccess ||
@@ -884,7 +920,7 @@ static void launch_mma(int S, dim3 grid, const CUtensorMap& a, const CUtensorMap
 
 int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
                      cudaEvent_t ev1, unsigned ev_flags) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
   auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   int* colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
@@ -903,17 +939,24 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
   g.X = X;
   g.P = P;
   g.shift = shift;
-  dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM));
+  g.ksplit = psplit_;
+  g.ppart = reinterpret_cast<double*>(ws_ + L.ppart);
+  dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM), (unsigned)psplit_);
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
   const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(tmA_);
   const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
   launch_mma<sl::MODE_PRODUCT>(slices_, grid, ma, mx, mx, g, s);
+  if (psplit_ > 1) {
+    const int64_t total = n_ * k_;
+    const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    sl::product_reduce_kernel<<<rg, 256, 0, s>>>(g.ppart, psplit_, X, P, total, shift, ctl);
+  }
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
-  return 3;
+  return psplit_ > 1 ? 4 : 3;
 }
 
 int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
   auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
@@ -941,9 +984,9 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
   return 6;
 }
 
-int SlicedA::update(const double* X, const double* W, const double* F, const double* d, double* Xn, double* upart,
-                    const Control* ctl, cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+int SlicedA::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
+                    double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
   auto* xr = reinterpret_cast<__nv_bfloat16*>(ws_ + L.xr_planes);
   auto* fp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.f_planes);
   int* xrexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
@@ -967,6 +1010,7 @@ int SlicedA::update(const double* X, const double* W, const double* F, const dou
   g.X = X;
   g.W = W;
   g.d = d;
+  g.dinv = dinv;
   g.Xn = Xn;
   g.upart = upart;
   dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM));
@@ -979,7 +1023,7 @@ int SlicedA::update(const double* X, const double* W, const double* F, const dou
 int SlicedA::update_grid() const { return n_pad_ / sl::kBM; }
 
 int SlicedA::timed_out(cudaStream_t s) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
   int v = 0;
   cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);

@@ -30,8 +30,8 @@ class SlicedA {
   int gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s);
   // Rows k..n-1 of X' = X + (W - X D) D^-1 - X F (F k x k column-major) and
   // per-row-tile column sums of X'^2 and (W - X D)^2 into upart[update_grid()][2k].
-  int update(const double* X, const double* W, const double* F, const double* d, double* Xn, double* upart,
-             const Control* ctl, cudaStream_t s);
+  int update(const double* X, const double* W, const double* F, const double* d, const double* dinv, double* Xn,
+             double* upart, const Control* ctl, cudaStream_t s);
   int update_grid() const;
   // 1 if a bounded wait inside a tensor-core kernel gave up (synchronises s).
   int timed_out(cudaStream_t s) const;
@@ -45,7 +45,7 @@ class SlicedA {
   const double* A_ = nullptr;
   int64_t n_ = 0, lda_ = 0;
   int k_ = 0, precision_ = 0, slices_ = 0;
-  int n_pad_ = 0, k_pad_ = 0, kr_ = 0, ksplit_ = 1;
+  int n_pad_ = 0, k_pad_ = 0, kr_ = 0, ksplit_ = 1, psplit_ = 1;
   char* ws_ = nullptr;
   alignas(64) unsigned char tmA_[128];
   alignas(64) unsigned char tmX_[128];

@@ -24,74 +24,68 @@ __device__ __forceinline__ double ld_stream_f64(const double* p) {
   return v;
 }
 
-// A CTA takes 64 consecutive rows at a time.  Their row pointers and then
-// their nonzeros (a contiguous range of the CSR arrays) are staged in shared
-// memory with coalesced loads; then each group of LPR lanes takes two rows
-// and requests every X row they touch before using any, so each 64-row block
-// costs three memory latencies and keeps many X rows in flight.  Blocks whose
-// nonzeros do not fit the stage read them from global memory directly.
-constexpr int SP_ROWS = 64;
-constexpr int SP_CAP = 2048;   // staged nonzeros per block
-
-template <int LPR>
+// LPR lanes per row; each lane owns column pairs c2 = lane, lane + LPR, ...
+// GB300 issues about 2 DFMA per clock per SM, so this kernel is bound by the
+// FP64 pipe (nnz k DFMA per launch, ~130 us at n = 1,024,000, k = 16), not by
+// HBM (~48 us for its 328 MB): it is kept lean -- one X row load and two DFMA
+// per nonzero and lane.  With the shift folded into the stored diagonal
+// (SHIFT = false, see csr_fold_diag) there is no separate shift term.
+template <int LPR, bool SHIFT>
 __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ ci,
                                                             const double* __restrict__ val,
                                                             const double* __restrict__ X, double* __restrict__ P,
                                                             int64_t n, int k, double shift, const Control* ctl) {
   if (ctl && ctl->done) return;
-  __shared__ int32_t rps[SP_ROWS + 1];
-  __shared__ int32_t cis[SP_CAP];
-  __shared__ double vals[SP_CAP];
-  constexpr int GROUPS = 256 / LPR;
-  const int tid = threadIdx.x, lane = tid % LPR, grp = tid / LPR;
+  const int lane = threadIdx.x % LPR;
+  const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / LPR;
   const int k2 = k >> 1;
   const double2* X2 = reinterpret_cast<const double2*>(X);
   double2* P2 = reinterpret_cast<double2*>(P);
-  const int64_t nblk = (n + SP_ROWS - 1) / SP_ROWS;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int64_t r0 = blk * SP_ROWS;
-    const int rows = (int)(n - r0 < SP_ROWS ? n - r0 : SP_ROWS);
-    if (tid <= rows) rps[tid] = ld_stream_i32(rp + r0 + tid);
-    __syncthreads();
-    const int32_t nb = rps[0], cnt = rps[rows] - nb;
-    const bool staged = cnt <= SP_CAP;
-    if (staged)
-      for (int q = tid; q < cnt; q += 256) {
-        cis[q] = ld_stream_i32(ci + nb + q);
-        vals[q] = ld_stream_f64(val + nb + q);
+  for (int64_t i = g; i < n; i += ng) {
+    const int32_t b = ld_stream_i32(rp + i), e = ld_stream_i32(rp + i + 1);
+    for (int c2 = lane; c2 < k2; c2 += LPR) {
+      double ax = 0.0, ay = 0.0;
+#pragma unroll 4
+      for (int32_t p = b; p < e; ++p) {
+        const double a = ld_stream_f64(val + p);
+        const int64_t col = ld_stream_i32(ci + p);
+        const double2 x = __ldg(X2 + col * k2 + c2);
+        ax = fma(a, x.x, ax);
+        ay = fma(a, x.y, ay);
       }
-    __syncthreads();
-    for (int r = grp; r < rows; r += GROUPS) {
-      const int32_t b = rps[r], e = rps[r + 1];
-      const int64_t i = r0 + r;
-      for (int c2 = lane; c2 - lane < k2; c2 += LPR) {
-        double ax = 0.0, ay = 0.0;
-        for (int32_t p0 = b; p0 < e; p0 += 8) {
-          double2 xs[8];
-          double as[8];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int32_t p = p0 + t;
-            const bool on = p < e && c2 < k2;
-            const int64_t col = on ? (staged ? cis[p - nb] : ci[p]) : 0;
-            as[t] = on ? (staged ? vals[p - nb] : val[p]) : 0.0;
-            xs[t] = on ? __ldg(X2 + col * k2 + c2) : make_double2(0.0, 0.0);
-          }
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            ax = fma(as[t], xs[t].x, ax);
-            ay = fma(as[t], xs[t].y, ay);
-          }
-        }
-        if (c2 < k2) {
-          const double2 xi = __ldg(X2 + i * k2 + c2);
-          P2[i * k2 + c2] = make_double2(ax - shift * xi.x, ay - shift * xi.y);
-        }
+      if (SHIFT) {
+        const double2 xi = __ldg(X2 + i * k2 + c2);
+        ax = fma(-shift, xi.x, ax);
+        ay = fma(-shift, xi.y, ay);
       }
+      P2[i * k2 + c2] = make_double2(ax, ay);
     }
-    __syncthreads();
   }
+}
+
+// val_out = val with the shift subtracted on the diagonal; missing[0] is set
+// when some row has no stored diagonal entry (then the folded copy is unusable).
+__global__ void csr_fold_diag_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const double* __restrict__ val, int64_t n, double shift,
+                                     double* __restrict__ val_out, int* __restrict__ missing) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    bool found = false;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const bool diag = ci[p] == i;
+      val_out[p] = diag ? val[p] - shift : val[p];
+      found = found || diag;
+    }
+    if (!found) atomicExch(missing, 1);
+  }
+}
+
+void launch_csr_fold_diag(const int32_t* rp, const int32_t* ci, const double* val, int64_t n, double shift,
+                          double* val_out, int* missing, cudaStream_t s) {
+  cudaMemsetAsync(missing, 0, sizeof(int), s);
+  const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+  csr_fold_diag_kernel<<<grid, 256, 0, s>>>(rp, ci, val, n, shift, val_out, missing);
 }
 
 __global__ void __launch_bounds__(256) spmm_csr_scalar_kernel(const int32_t* __restrict__ rp,
@@ -115,19 +109,26 @@ __global__ void __launch_bounds__(256) spmm_csr_scalar_kernel(const int32_t* __r
 
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
                      int64_t n, int k, double shift, const Control* ctl, cudaStream_t s) {
-  const int grid = 152 * 6;  // resident CTAs of 256 threads, grid-stride over 64-row blocks
+  const int grid = 152 * 8;  // 8 resident CTAs of 256 threads per SM, grid-stride over rows
   if ((k & 1) == 0) {
     const int k2 = k >> 1;
-    if (k2 <= 2)
-      spmm_csr_vec2_kernel<2><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
-    else if (k2 <= 4)
-      spmm_csr_vec2_kernel<4><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
-    else if (k2 <= 8)
-      spmm_csr_vec2_kernel<8><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
-    else if (k2 <= 16)
-      spmm_csr_vec2_kernel<16><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
-    else
-      spmm_csr_vec2_kernel<32><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
+#define EIGREF_SPMM(L)                                                                                       \
+  if (shift != 0.0)                                                                                         \
+    spmm_csr_vec2_kernel<L, true><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);                 \
+  else                                                                                                      \
+    spmm_csr_vec2_kernel<L, false><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
+    if (k2 <= 2) {
+      EIGREF_SPMM(2)
+    } else if (k2 <= 4) {
+      EIGREF_SPMM(4)
+    } else if (k2 <= 8) {
+      EIGREF_SPMM(8)
+    } else if (k2 <= 16) {
+      EIGREF_SPMM(16)
+    } else {
+      EIGREF_SPMM(32)
+    }
+#undef EIGREF_SPMM
   } else {
     spmm_csr_scalar_kernel<<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
   }
