@@ -194,6 +194,23 @@ def max_angle(X, Q):
     return float(np.max(np.linalg.norm(Xn - Qn * c[None, :], axis=0)))
 
 
+def orth_max(X, rows=32):
+    """max |X^T X - I| with the row sum split into blocks of `rows` and the
+    block Gram matrices added by Neumaier's compensated summation: the
+    rounding of the measure is at most about rows * u (a plain FP64 X^T X over
+    n = 16384 rows carries up to n * u, far above the 1e-14 being checked)."""
+    n, k = X.shape
+    S = np.zeros((k, k))
+    C = np.zeros((k, k))
+    for r0 in range(0, n, rows):
+        B = X[r0:r0 + rows]
+        G = B.T @ B
+        t = S + G
+        C += np.where(np.abs(S) >= np.abs(G), (S - t) + G, (G - t) + S)
+        S = t
+    return float(np.abs((S + C) - np.eye(k)).max())
+
+
 def cpu_oracle_rate(p, sweeps):
     """The CPU oracle (as it stands) on this host: sweeps/s over a bounded sample."""
     from oracle import refine as R
@@ -249,19 +266,108 @@ def run_laplacian(args, world, rank, local):
     ms_step = rep["sweeps_ms"] / rep["iterations"]
     nnz, n, k = len(p.val), p.n, p.k
     bytes_launch = 12.0 * nnz + 4.0 * (n + 1) + 2 * 8.0 * n * k
+    flops_launch = 2.0 * nnz * k
     launch_ms = rep["product_ms"] / max(1, rep["product_launches"])
     pk, pk_kind = peaks()
     gbs = bytes_launch / (launch_ms * 1e-3) / 1e9
+    tfs = flops_launch / (launch_ms * 1e-3) / 1e12
+    fp64_peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
     out = {"metric": METRIC, "value": world * 1000.0 / ms_step, "unit": UNIT, "n_gpus": world,
            "steps": rep["iterations"], "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": LAPLACE, "n": n, "k": k, "nnz": nnz, "form": "fp64 CSR",
                       "l2": "inputs larger than L2 (CSR 65 MB + X 131 MB + P 131 MB per SpMM); no flush"},
-           "roofline": {"bound": "hbm", "kernel": "spmm_csr_vec2_kernel", "achieved": gbs, "peak": pk["hbm_gbs"],
-                        "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": None, "launch_ms": launch_ms,
-                        "algorithmic_bytes_per_launch": bytes_launch, "peak_note": "of %s" % pk_kind},
+           "roofline": {"bound": "alu", "kernel": "spmm_csr_vec2_kernel", "achieved": tfs, "peak": fp64_peak,
+                        "unit": "TFLOP/s", "frac": tfs / fp64_peak, "traffic": traffic_for("spmm.cu", "csr"),
+                        "launch_ms": launch_ms, "algorithmic_flops_per_launch": flops_launch,
+                        "peak_note": "FP64 pipe: measured BF16 burst x nominal FP64/BF16 ratio (1.25/2250), of "
+                                     + pk_kind,
+                        "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                                "algorithmic_bytes_per_launch": bytes_launch}},
            "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary(),
            "status": rep["status_string"]}
+    h.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+BATCH = ("256 dense problems, n log-uniform on [256, 4096], k uniform on {4..64} (seed 5000); "
+         "A = Q diag(lambda) Q^T with 16 seeded Householder reflectors, lambda evenly spaced on [-1, 1]; "
+         "the k algebraically largest via B = A - alpha I, alpha = (lambda_{k+1} - 1)/2; X0 = orth(fp32(Q_k))")
+
+
+def run_batched(args, world, rank, local):
+    """Batch sweeps/s: one sweep of every problem per step, all problems in one
+    graph replay (split form), beside per-problem calls of the plain FP64 form."""
+    import torch
+    import paper_2602_23778_gb300 as eigref
+    from paper_2602_23778_gb300 import sliced_info
+    from workloads import configs as C
+    if args.steps is None:
+        args.steps = 40
+    torch.cuda.set_device(local)
+    shapes = C.config5_shapes(count=args.count)
+    # weak scaling over ranks: rank r takes problems r, r + world, ...
+    mine = list(range(rank, len(shapes), world))
+    ps = [C.config5_problem(i, *shapes[i]) for i in mine]
+    stream = torch.cuda.Stream()
+    h = eigref.Handle(local, stream)
+    A = [torch.from_numpy(p.A).cuda() for p in ps]
+    X0 = [torch.from_numpy(np.ascontiguousarray(p.X0.T)).cuda().t() for p in ps]
+
+    def items():
+        return [{"A": a, "X": x.clone(), "target": "shift", "shift": p.shift, "norm_a": p.normA}
+                for a, x, p in zip(A, X0, ps)]
+
+    prec = args.precision or "bf16"
+    h.refine_batched(items(), max_iters=args.warmup, precision=prec)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        st, reps = h.refine_batched(items(), max_iters=args.steps, precision=prec)
+        torch.cuda.synchronize()
+    ms_step = reps[0]["sweeps_ms"] / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    pk, pk_kind = peaks()
+    if prec == "fp64":
+        flops = sum(2.0 * p.n * p.n * p.k for p in ps)
+        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        roof = {"bound": "alu", "peak_note": "FP64 pipe: measured BF16 burst x nominal FP64/BF16, of %s" % pk_kind}
+    else:
+        flops = sum(sliced_info(prec, p.n, p.k)["executed_flops"] for p in ps)
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "peak_note": "sustained BF16, of %s" % pk_kind}
+    ach = flops / (ms_step * 1e-3) / 1e12
+    roof.update({"kernel": "whole batch sweep (products of every problem)", "achieved": ach, "peak": peak,
+                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                 "algorithmic_flops_per_step": flops})
+    out = {"metric": METRIC, "value": world * 1000.0 / ms_step, "unit": "batch sweeps/s (every problem once)",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == "fp64" else prec + "-slices+f64", "data": "synthetic",
+           "config": {"workload": BATCH, "problems": len(ps) * world, "form": prec,
+                      "l2": "A of all problems 6.5 GB, larger than L2; no flush"},
+           "roofline": roof, "gpu_launches": int(reps[0]["kernel_launches"]), "clocks": clk.summary(),
+           "status": eigref.status_string(st), "problem_sweeps_per_s": len(ps) * 1000.0 / ms_step}
+    if rank == 0 and not args.no_fp64_compare:
+        # per-problem calls of the plain FP64 form: the launch pattern a caller
+        # without the batched entry point has
+        steps64 = 4
+        its = items()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for it in its:
+            h.refine_dense(it["A"], it["X"], max_iters=steps64, norm_a=it["norm_a"], target="shift",
+                           shift=it["shift"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps64
+        out["fp64_per_problem_calls"] = {"value": 1000.0 / ms, "unit": out["unit"], "ms_per_step": ms,
+                                         "steps": steps64, "batched_over_this": (1000.0 / ms_step) / (1000.0 / ms),
+                                         "note": "includes each call's set-up (sign fix, graph capture)"}
     h.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -279,10 +385,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 form beside the split form")
+    ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--n", type=int, default=16384, help="smaller n / k only for profiling captures")
     ap.add_argument("--k", type=int, default=128)
-    ap.add_argument("--workload", default="dense", choices=["dense", "laplacian"],
-                    help="dense: the n=16384, k=128 matrix (default); laplacian: the 1024 x 1000 CSR Laplacian, k=16")
+    ap.add_argument("--count", type=int, default=256, help="batched workload: number of problems")
+    ap.add_argument("--workload", default="dense", choices=["dense", "laplacian", "batched"],
+                    help="dense: the n=16384, k=128 matrix (default); laplacian: the 1024 x 1000 CSR Laplacian, k=16; "
+                         "batched: 256 dense problems of uneven n and k")
     ap.add_argument("--summarize-launches", metavar="CSV", help="summarise an ncu launch list and exit")
     ap.add_argument("--peaks", action="store_true", help="measure library FP64/INT8/BF16 GEMM rates and exit")
     args = ap.parse_args()
@@ -308,7 +418,15 @@ def main():
     if args.workload == "laplacian":
         run_laplacian(args, world, rank, local)
         return
-    precision = args.precision or "fp64"
+    if args.workload == "batched":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        run_batched(args, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    precision = args.precision or "bf16"
     if args.steps is None:
         args.steps = 40 if precision == "fp64" else 200
     assert args.warmup >= 3, "at least 3 warm-up sweeps"
@@ -386,16 +504,33 @@ def main():
            "setup_ms": rep["setup_ms"], "call_s": call_s, "roofline": roof,
            "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary()}
 
-    if rank == 0 and not args.no_accuracy:
+    def accuracy(form_kw):
         Xa = X0.clone()
         # run to the residual level of the n = 8192 workload's rule, 1e-14 ||A||
-        ra = h.refine_dense(A, Xa, max_iters=600, tol=1e-14, stop="residual", check_every=50, **kw)
+        ra = h.refine_dense(A, Xa, max_iters=600, tol=1e-14, stop="residual", check_every=50, **form_kw)
         Xh = Xa.cpu().numpy()
-        out["accuracy"] = {"sweeps": ra["iterations"], "status": ra["status_string"],
-                           "final_rel_residual": ra["final_rel_residual"],
-                           "max_sin_angle": max_angle(Xh, p.Xtrue),
-                           "orth_max": float(np.abs(Xh.T @ Xh - np.eye(k)).max()),
-                           "target_angle": 1e-13}
+        return {"sweeps": ra["iterations"], "status": ra["status_string"],
+                "final_rel_residual": ra["final_rel_residual"], "max_sin_angle": max_angle(Xh, p.Xtrue),
+                "orth_max": orth_max(Xh), "target_angle": 1e-13,
+                "target_orth": 1e-14}
+
+    if rank == 0 and not args.no_accuracy:
+        out["accuracy"] = accuracy(kw)
+
+    if rank == 0 and precision != "fp64" and not args.no_fp64_compare:
+        # the plain FP64 form on the same input, same timing rules, fewer sweeps
+        kw64 = dict(norm_a=p.normA, target="largest_mag", precision="fp64")
+        h.refine_dense(A, X0.clone(), max_iters=args.warmup, check_every=args.warmup, **kw64)
+        torch.cuda.synchronize()
+        r64 = h.refine_dense(A, X0.clone(), max_iters=args.fp64_steps, check_every=args.fp64_steps,
+                             profile=True, **kw64)
+        torch.cuda.synchronize()
+        v64 = 1000.0 * r64["iterations"] / r64["sweeps_ms"]
+        out["fp64_form"] = {"value": v64, "unit": UNIT, "steps": r64["iterations"],
+                            "ms_per_step": r64["sweeps_ms"] / r64["iterations"],
+                            "split_over_fp64": value / world / v64}
+        if not args.no_accuracy:
+            out["fp64_form"]["accuracy"] = accuracy(kw64)
 
     if rank == 0 and not args.no_e2e:
         Ah = np.ascontiguousarray(p.A)

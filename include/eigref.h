@@ -148,6 +148,38 @@ int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* co
                       double* X, int64_t ldx, int k,
                       const eigref_params* p, eigref_report* rep);
 
+/* One dense problem of a batch.  A (n x n, lda >= n) and X (n x k column-major,
+ * ldx >= n, in/out) are device memory; target, shift and norm_a have the
+ * meaning of the eigref_params fields of the same names and override them. */
+typedef struct eigref_problem {
+  const double* A;
+  int64_t n;
+  int64_t lda;
+  double* X;
+  int64_t ldx;
+  int k;
+  int target;
+  double shift;
+  double norm_a;
+} eigref_problem;
+
+/* Refine `count` independent dense problems at once (Algorithm 4 iterated on
+ * each, as eigref_refine_dense does).  The problems may differ in n and k.
+ * Every problem's sweeps are captured on a stream of its own and the whole
+ * batch is replayed as one CUDA graph per chunk of sweeps, so the problems run
+ * side by side on the GPU; a problem that has stopped (tol met, diverged,
+ * max_iters) does no further work while the others continue.  p gives the
+ * shared options (max_iters, tol, stop, precision, slices, beta, ...);
+ * p->check_every is capped so that one replay stays near 32k graph nodes.
+ * reps (NULL or count entries) receives one report per problem; setup_ms and
+ * sweeps_ms are those of the whole batch, product_ms is not measured.
+ * Returns EIGREF_OK when every problem ended OK, else the status of the first
+ * problem that did not (eigref_last_error names it).  On EIGREF_E_INVALID no
+ * X is touched.  Errors: as eigref_refine_dense, plus EIGREF_E_INVALID for
+ * count < 1 or host-memory A or X. */
+int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* probs,
+                          const eigref_params* p, eigref_report* reps);
+
 /* Line 1 of Algorithm 4 on its own: P = (A - shift I) X for dense A, with the
  * chosen precision (slices as in eigref_params).  P is n x k column-major
  * (ldp >= n), caller-owned, host or device. */

@@ -25,7 +25,7 @@ BETAS = {"cluster": 0, "zero": 1}
 
 SYMBOLS = ["eigref_params_default", "eigref_create", "eigref_destroy", "eigref_refine_dense",
            "eigref_refine_csr", "eigref_product_dense", "eigref_product_csr", "eigref_status_string",
-           "eigref_last_error", "eigref_product_dense_noalloc"]
+           "eigref_last_error", "eigref_product_dense_noalloc", "eigref_refine_batched"]
 NOALLOC_MAX_ELEMS = 1 << 20
 
 
@@ -48,6 +48,12 @@ class Report(ctypes.Structure):
                 ("hist_corr", ctypes.POINTER(ctypes.c_double)),
                 ("product_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("product_launches", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64), ("k", ctypes.c_int),
+                ("target", ctypes.c_int), ("shift", ctypes.c_double), ("norm_a", ctypes.c_double)]
 
 
 class EigrefError(RuntimeError):
@@ -81,6 +87,8 @@ def lib():
         L.eigref_product_dense.argtypes = [vp, vp, i64, i64, vp, i64, i32, dbl, i32, i32, vp, i64]
         L.eigref_product_csr.argtypes = [vp, vp, vp, vp, i64, i64, vp, i64, i32, dbl, vp, i64]
         L.eigref_product_dense_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, dbl, vp, i64, vp]
+        L.eigref_refine_batched.argtypes = [vp, i32, ctypes.POINTER(Problem), ctypes.POINTER(Params),
+                                            ctypes.POINTER(Report)]
         L.eigref_status_string.argtypes = [i32]
         L.eigref_status_string.restype = ctypes.c_char_p
         L.eigref_last_error.argtypes = [vp]
@@ -102,7 +110,7 @@ def sliced_info(precision, n, k, slices=9):
     n_pad = -(-n // 256) * 256
     k_pad = -(-k // 32) * 32
     pairs = slices * (slices + 1) // 2
-    return {"kernel": "sliced_gemm_kernel", "slices": slices, "pairs": pairs,
+    return {"kernel": "sliced_mma_kernel (product mode)", "slices": slices, "pairs": pairs,
             "executed_flops": 2.0 * n_pad * n_pad * k_pad * pairs,
             "a_plane_bytes": 2.0 * slices * n_pad * n_pad}
 
@@ -267,6 +275,34 @@ class Handle:
         rep, want = self._report(k, p.max_iters, history)
         st = lib().eigref_refine_csr(self._h, prp, pci, pv, n, nnz, px, ldx, k, ctypes.byref(p), ctypes.byref(rep))
         return self._finish(st, rep, k, want, raise_on_error)
+
+    def refine_batched(self, problems, history=False, raise_on_error=True, **kw):
+        """Refine many dense problems at once (eigref_refine_batched).
+
+        problems: sequence of dicts with keys A, X (device tensors, X
+        column-major, refined in place) and optionally target, shift, norm_a.
+        kw: the shared options.  Returns (status, list of per-problem reports)."""
+        count = len(problems)
+        arr = (Problem * count)()
+        keep, wants, reps = [], [], (Report * count)()
+        p = self.params(**kw)
+        for i, pb in enumerate(problems):
+            pa, n, lda, ka = _dense_a(pb["A"])
+            px, nx, k, ldx, kx = _colmajor(pb["X"])
+            if nx != n:
+                raise ValueError("problem %d: X has %d rows, A is %d x %d" % (i, nx, n, n))
+            t = pb.get("target", "largest_mag")
+            arr[i] = Problem(pa, n, lda, px, ldx, k, TARGETS[t] if isinstance(t, str) else int(t),
+                             float(pb.get("shift", 0.0)), float(pb.get("norm_a", 0.0)))
+            rep, want = self._report(k, p.max_iters, history)
+            reps[i] = rep
+            keep.append((ka, kx))
+            wants.append((k, want))
+        st = lib().eigref_refine_batched(self._h, count, arr, ctypes.byref(p), reps)
+        outs = [self._finish(reps[i].status, reps[i], k, want, False) for i, (k, want) in enumerate(wants)]
+        if raise_on_error and st in (E_INVALID, E_CUDA, E_NOMEM, E_UNSUPPORTED):
+            raise EigrefError(st, self.last_error())
+        return st, outs
 
     def product_dense(self, A, X, P, shift=0.0, precision="fp64", slices=0):
         """P = (A - shift I) X (eigref_product_dense); P column-major, written in place."""

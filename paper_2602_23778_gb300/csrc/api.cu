@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -196,126 +197,243 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   return launches + 2;
 }
 
+// One refinement in flight: the problem, its parameters and its workspace.
+// refine_common drives one Run; eigref_refine_batched drives many at once.
+struct Run {
+  Problem pr;
+  Params q;
+  double* X = nullptr;  // caller's X
+  int64_t ldx = 0;
+  bool x_dev = true;
+  SweepBufs b{};
+  double* xbuf[2] = {nullptr, nullptr};
+  double* xstage = nullptr;
+  double* sigma = nullptr;
+  double* scal = nullptr;
+  const double* sg = nullptr;  // sign vector when the sign fix is on
+  int64_t chunk_rows = 0;
+  int nchunks = 0;
+  int ugrid = 0;
+  int hist_len = 0;
+  double norm_a = 0.0, shift = 0.0, delta = 0.0;
+};
+
+void run_plan(Run& r) {
+  const int64_t n = r.pr.n;
+  const int k = r.pr.k;
+  r.chunk_rows = 256;
+  while ((n - k + r.chunk_rows - 1) / r.chunk_rows > 1024) r.chunk_rows *= 2;
+  r.nchunks = (int)std::max<int64_t>(1, (n - k + r.chunk_rows - 1) / r.chunk_rows);
+  r.ugrid = r.pr.sliced ? r.pr.sliced->update_grid() : update_rows_grid();
+  r.hist_len = std::max(1, r.q.max_iters);
+}
+
+// Carves the Run's buffers; with c.base == nullptr it only sizes them.  The
+// Control block comes from `ctl` when given (one array for a whole batch).
+void run_layout(Run& r, Carve& c, Control* ctl) {
+  const int64_t n = r.pr.n;
+  const int k = r.pr.k;
+  const int64_t kk = (int64_t)k * k;
+  SweepBufs& b = r.b;
+  r.xbuf[0] = c.take<double>(n * k);
+  r.xbuf[1] = c.take<double>(n * k);
+  b.p = c.take<double>(n * k);
+  r.xstage = r.x_dev ? nullptr : c.take<double>(n * k);
+  b.gpart = c.take<double>(2 * (int64_t)r.nchunks * kk);
+  b.gtop = c.take<double>(2 * kk);
+  b.g2 = c.take<double>(2 * kk);
+  double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f, &b.res,
+                     &b.zinv, &b.zinv2};
+  for (double** m : mats) *m = c.take<double>(kk);
+  b.piv = c.take<int>(k);
+  double** vecs[] = {&b.alpha, &b.d, &b.dinv, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
+  for (double** v : vecs) *v = c.take<double>(k);
+  r.sigma = c.take<double>(k);
+  b.upart = c.take<double>((int64_t)r.ugrid * 2 * k);
+  b.hist_res = c.take<double>(r.hist_len);
+  b.hist_corr = c.take<double>(r.hist_len);
+  b.ctl = ctl ? ctl : c.take<Control>(1);
+  r.scal = c.take<double>(4);
+  if (r.pr.csr) r.pr.val_folded = c.take<double>(r.pr.nnz > 0 ? r.pr.nnz : 1);
+  b.nchunks = r.nchunks;
+  b.chunk_rows = r.chunk_rows;
+  b.ugrid = r.ugrid;
+  b.mixed = r.pr.sliced != nullptr;  // the split form keeps Y1^{-1} by Newton-Schulz steps
+}
+
+// Bytes of workspace the Run needs (its buffers, then the sliced planes).
+size_t run_bytes(Run& r, bool own_ctl) {
+  Carve c;
+  run_layout(r, c, own_ctl ? nullptr : reinterpret_cast<Control*>(16));
+  const size_t extra = r.pr.sliced ? r.pr.sliced->workspace_bytes() : 0;
+  return ((c.off + 255) & ~size_t(255)) + 1024 + extra;
+}
+
+void run_bind(Run& r, char* base, Control* ctl) {
+  Carve c;
+  c.base = base;
+  run_layout(r, c, ctl);
+  if (r.pr.sliced) r.pr.sliced->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
+}
+
+// Shift and delta from ||A|| and the target (Sections 3.1.3 and 5.1).
+void run_shift(Run& r) {
+  r.shift = 0.0;
+  if (r.q.target == EIGREF_SHIFT) r.shift = r.q.shift;
+  else if (r.q.target == EIGREF_SMALLEST) r.shift = 0.5 * (r.norm_a + r.q.shift);   // Section 5.1
+  else if (r.q.target == EIGREF_LARGEST) r.shift = 0.5 * (r.q.shift - r.norm_a);    // its mirror
+  r.delta = r.q.delta_c * (r.norm_a + fabs(r.shift)) * kUnitRoundoff;              // Section 3.1.3
+}
+
+Control run_control(const Run& r) {
+  Control c{};
+  c.max_iters = r.q.max_iters;
+  c.stop = r.q.stop;
+  c.tol = r.q.tol;
+  c.norm_a = r.norm_a;
+  c.div_factor = r.q.div_factor;
+  c.div_floor = r.q.div_floor;
+  c.emin = DBL_MAX;
+  c.status = EIGREF_OK;
+  c.done = r.q.max_iters == 0;
+  return c;
+}
+
+// Device half of the set-up after ||A|| and the shift are known: the internal
+// X (staged, sign-fixed) and the slices of A.
+int run_setup_device(eigref_ctx* h, Run& r, cudaStream_t s) {
+  const int64_t n = r.pr.n;
+  const int k = r.pr.k;
+  const double* xu = r.X;
+  if (!r.x_dev) {
+    CUDA_TRY(h, cudaMemcpy2DAsync(r.xstage, n * sizeof(double), r.X, r.ldx * sizeof(double), n * sizeof(double), k,
+                                  cudaMemcpyHostToDevice, s));
+    xu = r.xstage;
+  }
+  const int64_t ldu = r.x_dev ? r.ldx : n;
+  r.sg = nullptr;
+  if (r.q.sign_fix) {
+    launch_sign_fix(xu, ldu, k, r.sigma, nullptr, s);
+    r.sg = r.sigma;
+  }
+  launch_copy_in(xu, ldu, r.xbuf[0], n, k, r.sg, s);
+  if (r.pr.sliced) {
+    const int st = r.pr.sliced->prepare(s);
+    if (st) return set_err(h, st, "%s", r.pr.sliced->error());
+  }
+  return EIGREF_OK;
+}
+
+// Split form: Y1^{-1} of the starting X, refined every sweep after.  Runs
+// after the Control block holds run_control(r).
+void run_setup_inverse(const Run& r, cudaStream_t s) {
+  if (r.b.mixed && r.q.max_iters > 0) {
+    SweepBufs b0 = r.b;
+    b0.x = r.xbuf[0];
+    launch_inverse_setup(b0, r.pr.k, s);
+  }
+}
+
+// Issues sweeps t0 .. t0 + count - 1 (X_t lives in xbuf[t % 2]); returns the
+// number of kernels launched.
+int run_issue(const Run& r, int count, cudaStream_t s, cudaEvent_t* pev, unsigned ev_flags) {
+  int launches = 0;
+  for (int t = 0; t < count; ++t) {
+    SweepBufs bt = r.b;
+    bt.x = r.xbuf[t & 1];
+    bt.xn = r.xbuf[(t + 1) & 1];
+    launches += launch_sweep(r.pr, bt, r.shift, r.delta, r.q.beta == EIGREF_BETA_ZERO, s,
+                             pev ? pev[2 * t] : nullptr, pev ? pev[2 * t + 1] : nullptr, ev_flags);
+  }
+  return launches;
+}
+
+// Copies the final iterate back into the caller's X (signs restored).
+int run_copy_out(eigref_ctx* h, const Run& r, int iterations, cudaStream_t s) {
+  const int64_t n = r.pr.n;
+  const int k = r.pr.k;
+  const double* xr = r.xbuf[iterations & 1];
+  if (r.x_dev) {
+    launch_copy_out(xr, r.X, r.ldx, n, k, r.sg, s);
+  } else {
+    launch_copy_out(xr, r.xstage, n, n, k, r.sg, s);
+    CUDA_TRY(h, cudaMemcpy2DAsync(r.X, r.ldx * sizeof(double), r.xstage, n * sizeof(double), n * sizeof(double), k,
+                                  cudaMemcpyDeviceToHost, s));
+  }
+  return EIGREF_OK;
+}
+
+void fill_report(const Run& r, const Control& fin, const double* dvec, eigref_report* rep) {
+  int status = fin.status;
+  if (r.q.max_iters == 0) status = EIGREF_OK;
+  rep->status = status;
+  rep->iterations = fin.iterations;
+  rep->final_rel_residual = fin.iterations ? fin.last_res : NAN;
+  rep->final_corr_norm = fin.iterations ? fin.last_corr : NAN;
+  rep->shift = r.shift;
+  rep->norm_a = r.norm_a;
+  rep->delta = r.delta;
+  if (rep->eigenvalues)
+    for (int j = 0; j < r.pr.k; ++j) rep->eigenvalues[j] = fin.iterations ? dvec[j] + r.shift : NAN;
+}
+
+// A CUDA graph of one chunk of sweeps, destroyed with the guard.
+struct GraphGuard {
+  cudaGraphExec_t g = nullptr;
+  ~GraphGuard() {
+    if (g) cudaGraphExecDestroy(g);
+  }
+};
+
 int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigref_params* pin,
                   eigref_report* rep) {
-  Params q;
-  int st = read_params(h, pin, &q);
+  Run r;
+  r.pr = pr;
+  int st = read_params(h, pin, &r.q);
   if (st) return st;
+  const Params& q = r.q;
   const int64_t n = pr.n;
   const int k = pr.k;
   cudaStream_t s = h->stream;
-  const bool x_dev = is_device_ptr(X);
+  r.X = X;
+  r.ldx = ldx;
+  r.x_dev = is_device_ptr(X);
 
   // ---- workspace ----
-  const int64_t kk = (int64_t)k * k;
-  int64_t chunk_rows = 256;
-  while ((n - k + chunk_rows - 1) / chunk_rows > 1024) chunk_rows *= 2;
-  const int nchunks = (int)std::max<int64_t>(1, (n - k + chunk_rows - 1) / chunk_rows);
-  const int ugrid = pr.sliced ? pr.sliced->update_grid() : update_rows_grid();
-  const int hist_len = std::max(1, q.max_iters);
-  auto layout = [&](Carve& c, SweepBufs& b, double** xbuf, double** xstage, double** sigma, double** scal) {
-    xbuf[0] = c.take<double>(n * k);
-    xbuf[1] = c.take<double>(n * k);
-    b.p = c.take<double>(n * k);
-    *xstage = x_dev ? nullptr : c.take<double>(n * k);
-    b.gpart = c.take<double>(2 * (int64_t)nchunks * kk);
-    b.gtop = c.take<double>(2 * kk);
-    b.g2 = c.take<double>(2 * kk);
-    double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f, &b.res,
-                       &b.zinv, &b.zinv2};
-    for (double** m : mats) *m = c.take<double>(kk);
-    b.piv = c.take<int>(k);
-    double** vecs[] = {&b.alpha, &b.d, &b.dinv, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
-    for (double** v : vecs) *v = c.take<double>(k);
-    *sigma = c.take<double>(k);
-    b.upart = c.take<double>((int64_t)ugrid * 2 * k);
-    b.hist_res = c.take<double>(hist_len);
-    b.hist_corr = c.take<double>(hist_len);
-    b.ctl = c.take<Control>(1);
-    *scal = c.take<double>(4);
-    if (pr.csr) pr.val_folded = c.take<double>(pr.nnz > 0 ? pr.nnz : 1);
-  };
-  SweepBufs b{};
-  double* xbuf[2];
-  double *xstage, *sigma, *scal;
-  Carve c0;
-  layout(c0, b, xbuf, &xstage, &sigma, &scal);
-  size_t extra = pr.sliced ? pr.sliced->workspace_bytes() : 0;
-  st = ensure_ws(h, c0.off + 256 + extra);
+  run_plan(r);
+  st = ensure_ws(h, run_bytes(r, true));
   if (st) return st;
-  Carve c1;
-  c1.base = static_cast<char*>(h->ws);
-  layout(c1, b, xbuf, &xstage, &sigma, &scal);
-  if (pr.sliced) pr.sliced->bind_workspace(static_cast<char*>(h->ws) + ((c1.off + 255) & ~size_t(255)));
-  b.nchunks = nchunks;
-  b.chunk_rows = chunk_rows;
-  b.ugrid = ugrid;
-  b.mixed = pr.sliced != nullptr;  // the split form factors Y1 in FP32 and refines in FP64
+  run_bind(r, static_cast<char*>(h->ws), nullptr);
+  SweepBufs& b = r.b;
 
   CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
   // ---- set-up: ||A||, shift, delta, signs, internal X ----
-  double norm_a = q.norm_a;
-  if (!(norm_a > 0.0)) {
-    if (pr.csr)
-      launch_norm_inf_csr(pr.rp, pr.val, n, scal, s);
+  r.norm_a = q.norm_a;
+  if (!(r.norm_a > 0.0)) {
+    if (r.pr.csr)
+      launch_norm_inf_csr(r.pr.rp, r.pr.val, n, r.scal, s);
     else
-      launch_norm_inf_dense(pr.A, n, pr.lda, scal, s);
-    CUDA_TRY(h, cudaMemcpyAsync(&h->host_ctl->tol, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      launch_norm_inf_dense(r.pr.A, n, r.pr.lda, r.scal, s);
+    CUDA_TRY(h, cudaMemcpyAsync(&h->host_ctl->tol, r.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    norm_a = h->host_ctl->tol;
-    if (!(norm_a > 0.0) || !isfinite(norm_a))
-      return set_err(h, isfinite(norm_a) ? EIGREF_E_INVALID : EIGREF_E_NONFINITE, "||A||_inf = %g", norm_a);
+    r.norm_a = h->host_ctl->tol;
+    if (!(r.norm_a > 0.0) || !isfinite(r.norm_a))
+      return set_err(h, isfinite(r.norm_a) ? EIGREF_E_INVALID : EIGREF_E_NONFINITE, "||A||_inf = %g", r.norm_a);
   }
-  double shift = 0.0;
-  if (q.target == EIGREF_SHIFT) shift = q.shift;
-  else if (q.target == EIGREF_SMALLEST) shift = 0.5 * (norm_a + q.shift);   // Section 5.1
-  else if (q.target == EIGREF_LARGEST) shift = 0.5 * (q.shift - norm_a);    // its mirror
-  const double delta = q.delta_c * (norm_a + fabs(shift)) * kUnitRoundoff;  // Section 3.1.3
-  if (pr.csr && shift != 0.0 && pr.nnz > 0) {
+  run_shift(r);
+  if (r.pr.csr && r.shift != 0.0 && r.pr.nnz > 0) {
     // fold -shift into the stored diagonal once, so the SpMM has no shift term
-    int* missing = reinterpret_cast<int*>(scal + 2);
-    launch_csr_fold_diag(pr.rp, pr.ci, pr.val, n, shift, pr.val_folded, missing, s);
-    int hmiss = 1;
+    int* missing = reinterpret_cast<int*>(r.scal + 2);
+    launch_csr_fold_diag(r.pr.rp, r.pr.ci, r.pr.val, n, r.shift, r.pr.val_folded, missing, s);
     CUDA_TRY(h, cudaMemcpyAsync(&h->host_ctl->status, missing, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    hmiss = h->host_ctl->status;
-    pr.folded = hmiss == 0;
+    r.pr.folded = h->host_ctl->status == 0;
   }
-
-  const double* xu = X;
-  if (!x_dev) {
-    CUDA_TRY(h, cudaMemcpy2DAsync(xstage, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double), k,
-                                  cudaMemcpyHostToDevice, s));
-    xu = xstage;
-  }
-  const int64_t ldu = x_dev ? ldx : n;
-  const double* sg = nullptr;
-  if (q.sign_fix) {
-    launch_sign_fix(xu, ldu, k, sigma, nullptr, s);
-    sg = sigma;
-  }
-  launch_copy_in(xu, ldu, xbuf[0], n, k, sg, s);
-  if (pr.sliced) {
-    st = pr.sliced->prepare(s);
-    if (st) return set_err(h, st, "%s", pr.sliced->error());
-  }
-  Control c{};
-  c.max_iters = q.max_iters;
-  c.stop = q.stop;
-  c.tol = q.tol;
-  c.norm_a = norm_a;
-  c.div_factor = q.div_factor;
-  c.div_floor = q.div_floor;
-  c.emin = DBL_MAX;
-  c.status = EIGREF_OK;
-  c.done = q.max_iters == 0;
-  *h->host_ctl = c;
+  st = run_setup_device(h, r, s);
+  if (st) return st;
+  *h->host_ctl = run_control(r);
   CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
-  if (b.mixed && q.max_iters > 0) {
-    SweepBufs b0 = b;
-    b0.x = xbuf[0];
-    launch_inverse_setup(b0, k, s);   // Y1^{-1} of the starting X, refined every sweep after
-  }
+  run_setup_inverse(r, s);
 
   // ---- sweeps ----
   const int m = q.check_every;
@@ -336,37 +454,21 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
         if (e) cudaEventDestroy(e);
     }
   } ev_guard{pev};
-  auto issue_chunk = [&](int count, unsigned ev_flags) {
-    int launches = 0;
-    for (int t = 0; t < count; ++t) {
-      SweepBufs bt = b;
-      bt.x = xbuf[t & 1];
-      bt.xn = xbuf[(t + 1) & 1];
-      launches += launch_sweep(pr, bt, shift, delta, q.beta == EIGREF_BETA_ZERO, s,
-                               q.profile ? pev[2 * t] : nullptr, q.profile ? pev[2 * t + 1] : nullptr, ev_flags);
-    }
-    return launches;
-  };
-  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t* pe = q.profile ? pev.data() : nullptr;
+  GraphGuard graph;
   int chunk_launches = 0;
   if (q.use_graph && q.max_iters > 0) {
     // capture before the sweep timer starts: instantiation is host work
     cudaGraph_t g;
     CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    chunk_launches = issue_chunk(m, cudaEventRecordExternal);
+    chunk_launches = run_issue(r, m, s, pe, cudaEventRecordExternal);
     cudaError_t ce = cudaStreamEndCapture(s, &g);
     if (ce != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&gexec, g, 0);
+    ce = cudaGraphInstantiate(&graph.g, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-    CUDA_TRY(h, cudaGraphUpload(gexec, s));
+    CUDA_TRY(h, cudaGraphUpload(graph.g, s));
   }
-  struct GraphGuard {
-    cudaGraphExec_t& g;
-    ~GraphGuard() {
-      if (g) cudaGraphExecDestroy(g);
-    }
-  } graph_guard{gexec};
   CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
   CUDA_TRY(h, cudaGetLastError());
   int launched = 0;
@@ -375,11 +477,11 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   int product_launches = 0;
   int it_before = 0;
   while (launched < q.max_iters) {
-    if (gexec) {
-      CUDA_TRY(h, cudaGraphLaunch(gexec, s));
+    if (graph.g) {
+      CUDA_TRY(h, cudaGraphLaunch(graph.g, s));
       kernel_launches += chunk_launches;
     } else {
-      kernel_launches += issue_chunk(m, cudaEventRecordDefault);
+      kernel_launches += run_issue(r, m, s, pe, cudaEventRecordDefault);
     }
     launched += m;
     CUDA_TRY(h, cudaMemcpyAsync(h->host_ctl, b.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
@@ -401,14 +503,8 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   const Control fin = *h->host_ctl;
 
   // ---- result: X_{iterations} lives in xbuf[iterations % 2] ----
-  const double* xr = xbuf[fin.iterations & 1];
-  if (x_dev) {
-    launch_copy_out(xr, X, ldx, n, k, sg, s);
-  } else {
-    launch_copy_out(xr, xstage, n, n, k, sg, s);
-    CUDA_TRY(h, cudaMemcpy2DAsync(X, ldx * sizeof(double), xstage, n * sizeof(double), n * sizeof(double), k,
-                                  cudaMemcpyDeviceToHost, s));
-  }
+  st = run_copy_out(h, r, fin.iterations, s);
+  if (st) return st;
   std::vector<double> dvec(k);
   CUDA_TRY(h, cudaMemcpyAsync(dvec.data(), b.d, k * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (rep && rep->hist_residual && fin.iterations > 0)
@@ -420,16 +516,9 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
   CUDA_TRY(h, cudaGetLastError());
-  int status = fin.status;
-  if (q.max_iters == 0) status = EIGREF_OK;
+  const int status = q.max_iters == 0 ? EIGREF_OK : fin.status;
   if (rep) {
-    rep->status = status;
-    rep->iterations = fin.iterations;
-    rep->final_rel_residual = fin.iterations ? fin.last_res : NAN;
-    rep->final_corr_norm = fin.iterations ? fin.last_corr : NAN;
-    rep->shift = shift;
-    rep->norm_a = norm_a;
-    rep->delta = delta;
+    fill_report(r, fin, dvec.data(), rep);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
     rep->setup_ms = ms;
@@ -438,8 +527,6 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     rep->product_ms = product_ms;
     rep->product_launches = product_launches;
     rep->kernel_launches = kernel_launches;
-    if (rep->eigenvalues)
-      for (int j = 0; j < k; ++j) rep->eigenvalues[j] = fin.iterations ? dvec[j] + shift : NAN;
   }
   if (status != EIGREF_OK)
     set_err(h, status, "%s after %d sweeps", eigref_status_string(status), fin.iterations);
@@ -622,6 +709,222 @@ int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* co
   for (void* q : bufs)
     if (q) cudaFree(q);
   return st;
+}
+
+// Many independent problems in one CUDA graph: every problem's sweep chain is
+// captured on a stream of its own, forked from and joined back into the
+// handle's stream, so one graph launch advances every problem by a chunk of
+// sweeps and the GPU runs the chains side by side.  A finished problem's
+// kernels return at once (its Control block is done), so problems of uneven
+// difficulty share the launches without changing each other's results.
+int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* probs, const eigref_params* p,
+                          eigref_report* reps) {
+  if (!h) return EIGREF_E_INVALID;
+  h->err[0] = 0;
+  if (count < 1 || !probs) return set_err(h, EIGREF_E_INVALID, "need count >= 1 and a problem array");
+  if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
+  Params q;
+  int st = read_params(h, p, &q);
+  if (st) return st;
+  std::vector<Run> runs(count);
+  std::unique_ptr<SlicedA[]> sls(new SlicedA[count]);
+  for (int i = 0; i < count; ++i) {
+    const eigref_problem& pb = probs[i];
+    if (!pb.A || !is_device_ptr(pb.A)) return set_err(h, EIGREF_E_INVALID, "problem %d: A must be device memory", i);
+    st = check_dims(h, pb.n, pb.k, pb.ldx, pb.X);
+    if (st) {
+      char why[sizeof(h->err)];
+      memcpy(why, h->err, sizeof(why));
+      return set_err(h, st, "problem %d: %s", i, why);
+    }
+    if (!is_device_ptr(pb.X)) return set_err(h, EIGREF_E_INVALID, "problem %d: X must be device memory", i);
+    if (pb.lda < pb.n) return set_err(h, EIGREF_E_INVALID, "problem %d: lda < n", i);
+    if (pb.target < EIGREF_LARGEST_MAG || pb.target > EIGREF_SHIFT)
+      return set_err(h, EIGREF_E_INVALID, "problem %d: target %d out of range", i, pb.target);
+    if (!isfinite(pb.shift) || !isfinite(pb.norm_a))
+      return set_err(h, EIGREF_E_INVALID, "problem %d: shift/norm_a not finite", i);
+    Run& r = runs[i];
+    r.q = q;
+    r.q.target = pb.target;
+    r.q.shift = pb.shift;
+    r.q.norm_a = pb.norm_a;
+    r.pr.n = pb.n;
+    r.pr.k = pb.k;
+    r.pr.A = pb.A;
+    r.pr.lda = pb.lda;
+    r.X = pb.X;
+    r.ldx = pb.ldx;
+    r.x_dev = true;
+    if (q.precision != EIGREF_FP64) {
+      st = sls[i].configure(pb.A, pb.n, pb.lda, pb.k, q.precision, q.slices);
+      if (st) return set_err(h, st, "problem %d: %s", i, sls[i].error());
+      sls[i].share_gpu(count);
+      r.pr.sliced = &sls[i];
+    }
+    run_plan(r);
+  }
+  // ---- workspace: the Control array first, then one region per problem ----
+  const size_t ctl_bytes = ((size_t)count * sizeof(Control) + 1023) & ~size_t(1023);
+  std::vector<size_t> off(count);
+  size_t total = ctl_bytes;
+  for (int i = 0; i < count; ++i) {
+    off[i] = total;
+    total += (run_bytes(runs[i], false) + 1023) & ~size_t(1023);
+  }
+  st = ensure_ws(h, total);
+  if (st) return st;
+  char* base = static_cast<char*>(h->ws);
+  Control* ctls = reinterpret_cast<Control*>(base);
+  for (int i = 0; i < count; ++i) run_bind(runs[i], base + off[i], ctls + i);
+
+  // host-side resources of the call, released by the guard
+  struct Res {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    Control* hc = nullptr;
+    ~Res() {
+      for (auto e : events)
+        if (e) cudaEventDestroy(e);
+      for (auto s : streams)
+        if (s) cudaStreamDestroy(s);
+      if (hc) cudaFreeHost(hc);
+    }
+  } res;
+  CUDA_TRY(h, cudaMallocHost(reinterpret_cast<void**>(&res.hc), (size_t)count * sizeof(Control)));
+  cudaStream_t s = h->stream;
+  CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+
+  // ---- set-up ----
+  bool need_norm = false;
+  for (int i = 0; i < count; ++i) {
+    Run& r = runs[i];
+    r.norm_a = r.q.norm_a;
+    if (!(r.norm_a > 0.0)) {
+      launch_norm_inf_dense(r.pr.A, r.pr.n, r.pr.lda, r.scal, s);
+      CUDA_TRY(h, cudaMemcpyAsync(&res.hc[i].tol, r.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      need_norm = true;
+    }
+  }
+  if (need_norm) CUDA_TRY(h, cudaStreamSynchronize(s));
+  for (int i = 0; i < count; ++i) {
+    Run& r = runs[i];
+    if (!(r.norm_a > 0.0)) {
+      r.norm_a = res.hc[i].tol;
+      if (!(r.norm_a > 0.0) || !isfinite(r.norm_a))
+        return set_err(h, isfinite(r.norm_a) ? EIGREF_E_INVALID : EIGREF_E_NONFINITE, "problem %d: ||A||_inf = %g", i,
+                       r.norm_a);
+    }
+    run_shift(r);
+    st = run_setup_device(h, r, s);
+    if (st) return st;
+    res.hc[i] = run_control(r);
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(ctls, res.hc, (size_t)count * sizeof(Control), cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < count; ++i) run_setup_inverse(runs[i], s);
+
+  // ---- one stream per problem, forked from and joined into the handle's stream ----
+  res.streams.assign(count, nullptr);
+  res.events.assign(count + 1, nullptr);
+  for (auto& x : res.streams) CUDA_TRY(h, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  for (auto& e : res.events) CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // chunk length: about 32k graph nodes per replay, even, at least 2
+  int per_sweep = 0;
+  for (const Run& r : runs) per_sweep += r.pr.sliced ? 34 : 25;
+  int m = std::min(q.check_every, std::max(2, 32768 / std::max(1, per_sweep)));
+  m += m & 1;
+  auto issue_all = [&](int count_sweeps) {
+    int launches = 0;
+    cudaEventRecord(res.events[count], s);
+    for (int i = 0; i < count; ++i) {
+      cudaStreamWaitEvent(res.streams[i], res.events[count], 0);
+      launches += run_issue(runs[i], count_sweeps, res.streams[i], nullptr, 0);
+      cudaEventRecord(res.events[i], res.streams[i]);
+      cudaStreamWaitEvent(s, res.events[i], 0);
+    }
+    return launches;
+  };
+  GraphGuard graph;
+  int chunk_launches = 0;
+  if (q.use_graph && q.max_iters > 0) {
+    cudaGraph_t g;
+    CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    chunk_launches = issue_all(m);
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (ce != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&graph.g, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    CUDA_TRY(h, cudaGraphUpload(graph.g, s));
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+  CUDA_TRY(h, cudaGetLastError());
+
+  // ---- sweeps ----
+  int launched = 0;
+  int64_t kernel_launches = 0;
+  while (launched < q.max_iters) {
+    if (graph.g) {
+      CUDA_TRY(h, cudaGraphLaunch(graph.g, s));
+      kernel_launches += chunk_launches;
+    } else {
+      kernel_launches += issue_all(m);
+    }
+    launched += m;
+    CUDA_TRY(h, cudaMemcpyAsync(res.hc, ctls, (size_t)count * sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    bool all_done = true;
+    for (int i = 0; i < count; ++i) all_done = all_done && res.hc[i].done;
+    if (all_done) break;
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+  CUDA_TRY(h, cudaMemcpyAsync(res.hc, ctls, (size_t)count * sizeof(Control), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+
+  // ---- results ----
+  int kmax = 0;
+  for (const Run& r : runs) kmax = std::max(kmax, r.pr.k);
+  std::vector<double> dvec((size_t)count * kmax);
+  for (int i = 0; i < count; ++i) {
+    const Run& r = runs[i];
+    const Control& fin = res.hc[i];
+    st = run_copy_out(h, r, fin.iterations, s);
+    if (st) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(dvec.data() + (size_t)i * kmax, r.b.d, r.pr.k * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    eigref_report* rep = reps ? reps + i : nullptr;
+    if (rep && rep->hist_residual && fin.iterations > 0)
+      CUDA_TRY(h, cudaMemcpyAsync(rep->hist_residual, r.b.hist_res, fin.iterations * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
+    if (rep && rep->hist_corr && fin.iterations > 0)
+      CUDA_TRY(h, cudaMemcpyAsync(rep->hist_corr, r.b.hist_corr, fin.iterations * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  CUDA_TRY(h, cudaGetLastError());
+  float setup_ms = 0.f, sweeps_ms = 0.f;
+  cudaEventElapsedTime(&setup_ms, h->ev[0], h->ev[1]);
+  cudaEventElapsedTime(&sweeps_ms, h->ev[1], h->ev[2]);
+  int status = EIGREF_OK, first_bad = -1;
+  for (int i = 0; i < count; ++i) {
+    const int si = q.max_iters == 0 ? EIGREF_OK : res.hc[i].status;
+    if (si != EIGREF_OK && first_bad < 0) {
+      first_bad = i;
+      status = si;
+    }
+    if (reps) {
+      fill_report(runs[i], res.hc[i], dvec.data() + (size_t)i * kmax, reps + i);
+      reps[i].setup_ms = setup_ms;
+      reps[i].sweeps_ms = sweeps_ms;
+      reps[i].product_ms = 0.0;
+      reps[i].product_launches = 0;
+      reps[i].kernel_launches = kernel_launches;
+    }
+  }
+  if (status != EIGREF_OK)
+    set_err(h, status, "problem %d: %s after %d sweeps", first_bad, eigref_status_string(status),
+            res.hc[first_bad].iterations);
+  return status;
 }
 
 // P = (A - shift I) X through the same product kernels the sweeps use.

@@ -97,70 +97,82 @@ void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, 
 
 // ---------------------------------------------------------------------------
 // Gram partials over a row range: part[z][c] = (X^T Y)[rows of chunk c],
-// z = 0: Y = X (G), z = 1: Y = P (S).  32 x 32 output tile per CTA.
-// Deterministic: partials are summed in chunk order by gram_reduce.
+// z = 0: Y = X (G), z = 1: Y = P (S).  T x T output tile per CTA (T = 16 for
+// k <= 16, else 32), 256 threads.  Deterministic: partials are summed in
+// chunk order by gram_reduce.
 // ---------------------------------------------------------------------------
+template <int T>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restrict__ X,
                                                            const double* __restrict__ P, int k, int64_t r0,
                                                            int64_t r1, int64_t chunk_rows, int nchunks,
                                                            double* __restrict__ part, const Control* ctl) {
   if (ctl && ctl->done) return;
-  __shared__ double Xa[32][33];
-  __shared__ double Xb[32][33];
+  constexpr int RB = 2048 / T;              // rows staged per step (T x RB doubles per operand, < 48 KB)
+  constexpr int OUT = T * T / 256;          // outputs per thread
+  __shared__ double Xa[RB][T + 1];
+  __shared__ double Xb[RB][T + 1];
   const int c = blockIdx.x;
-  const int tiles = (k + 31) / 32;
+  const int tiles = (k + T - 1) / T;
   const int ti = blockIdx.y % tiles, tj = blockIdx.y / tiles;
   const int z = blockIdx.z;
   const double* Yb = z ? P : X;
-  const int tid = threadIdx.x, i = tid & 31, jg = tid >> 5;  // outputs (i, jg*4 + q)
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int tid = threadIdx.x;
+  const int i = tid % T, jg = tid / T;      // outputs (i, jg * OUT + q)
+  double acc[OUT];
+#pragma unroll
+  for (int q = 0; q < OUT; ++q) acc[q] = 0.0;
   const int64_t rb = r0 + (int64_t)c * chunk_rows;
   const int64_t re = r1 < rb + chunk_rows ? r1 : rb + chunk_rows;
-  for (int64_t row0 = rb; row0 < re; row0 += 32) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      int rr = e >> 5, cc = e & 31;
-      int64_t row = row0 + rr;
-      int ca = ti * 32 + cc, cb = tj * 32 + cc;
+  for (int64_t row0 = rb; row0 < re; row0 += RB) {
+    for (int e = tid; e < RB * T; e += 256) {
+      const int rr = e / T, cc = e % T;
+      const int64_t row = row0 + rr;
+      const int ca = ti * T + cc, cb = tj * T + cc;
       Xa[rr][cc] = (row < re && ca < k) ? X[row * k + ca] : 0.0;
       Xb[rr][cc] = (row < re && cb < k) ? Yb[row * k + cb] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-      double a = Xa[rr][i];
+    for (int rr = 0; rr < RB; ++rr) {
+      const double a = Xa[rr][i];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(a, Xb[rr][jg * 4 + q], acc[q]);
+      for (int q = 0; q < OUT; ++q) acc[q] = fma(a, Xb[rr][jg * OUT + q], acc[q]);
     }
     __syncthreads();
   }
   double* out = part + ((int64_t)z * nchunks + c) * k * k;
-  int gi = ti * 32 + i;
+  const int gi = ti * T + i;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int gj = tj * 32 + jg * 4 + q;
+  for (int q = 0; q < OUT; ++q) {
+    const int gj = tj * T + jg * OUT + q;
     if (gi < k && gj < k) out[gi + (int64_t)gj * k] = acc[q];
   }
 }
 
+// One warp per output: lane l sums chunks l, l + 32, ... in order, then a
+// fixed butterfly combines the lanes, so the result is the same every run.
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int nchunks, double* __restrict__ out,
                                    const Control* ctl) {
   if (ctl && ctl->done) return;
   const int64_t kk = (int64_t)k * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * kk; e += (int64_t)gridDim.x * blockDim.x) {
-    int z = (int)(e / kk);
-    int64_t o = e % kk;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w0; e < 2 * kk; e += nw) {
+    const int z = (int)(e / kk);
+    const int64_t o = e % kk;
     const double* p = part + (int64_t)z * nchunks * kk + o;
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += p[(int64_t)c * kk];
-    out[e] = s;
+    for (int c = lane; c < nchunks; c += 32) s += p[(int64_t)c * kk];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) out[e] = s;
   }
 }
 
 void launch_gram_reduce(const double* part, int k, int nchunks, double* out, const Control* ctl, cudaStream_t s) {
-  int64_t work = 2LL * k * k;
-  int rg = (int)std::min<int64_t>((work + 255) / 256, 1024);
+  const int64_t warps = 2LL * k * k;
+  const int rg = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
   gram_reduce_kernel<<<rg, 256, 0, s>>>(part, k, nchunks, out, ctl);
 }
 
@@ -195,12 +207,15 @@ void launch_top_gram(const double* X, const double* P, int k, double* out, const
 
 void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
                  int nchunks, double* part, double* out, const Control* ctl, cudaStream_t s) {
-  int tiles = (k + 31) / 32;
-  dim3 grid(nchunks, tiles * tiles, 2);
-  gram_partial_kernel<<<grid, 256, 0, s>>>(X, P, k, r0, r1, chunk_rows, nchunks, part, ctl);
-  int64_t work = 2LL * k * k;
-  int rg = (int)std::min<int64_t>((work + 255) / 256, 1024);
-  gram_reduce_kernel<<<rg, 256, 0, s>>>(part, k, nchunks, out, ctl);
+  if (k <= 16) {
+    dim3 grid(nchunks, 1, 2);
+    gram_partial_kernel<16><<<grid, 256, 0, s>>>(X, P, k, r0, r1, chunk_rows, nchunks, part, ctl);
+  } else {
+    const int tiles = (k + 31) / 32;
+    dim3 grid(nchunks, tiles * tiles, 2);
+    gram_partial_kernel<32><<<grid, 256, 0, s>>>(X, P, k, r0, r1, chunk_rows, nchunks, part, ctl);
+  }
+  launch_gram_reduce(part, k, nchunks, out, ctl, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -208,10 +223,12 @@ void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1
 //   x' = x + (w - x o d) / d - x F,   F = M D^-1 + N
 // with per-CTA partial column sums of x'^2 and of the residual r = w - x o d.
 // ---------------------------------------------------------------------------
-constexpr int UPD_ROWS = 16;
+constexpr int UPD_ROWS = 16;     // rows per step at k = 128; smaller k takes UPD_ROWS * 128 / k
 constexpr int UPD_GRID = 2 * 152;
 
 int update_rows_grid() { return UPD_GRID; }
+
+__host__ __device__ inline int update_rows_per_step(int k) { return (UPD_ROWS * kMaxK) / k > 0 ? (UPD_ROWS * kMaxK) / k : 1; }
 
 // Column sums are formed in a fixed order (no atomics), so results are
 // bitwise reproducible run to run.
@@ -223,11 +240,12 @@ __global__ void __launch_bounds__(256) update_rows_kernel(const double* __restri
                                                           double* __restrict__ upart, const Control* ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ double sm[];
+  const int rb = update_rows_per_step(k);   // rows per step: rb k ~ 2048 outputs
   double* Fs = sm;                          // Fs[l * k + j] = F(l, j)
-  double* xs = Fs + k * k;                  // [UPD_ROWS][k]
-  double* sq = xs + UPD_ROWS * k;           // [UPD_ROWS][k]: x'^2
-  double* rq = sq + UPD_ROWS * k;           // [UPD_ROWS][k]: r^2
-  double* dinv = rq + UPD_ROWS * k;         // [k]
+  double* xs = Fs + k * k;                  // [rb][k]
+  double* sq = xs + rb * k;                 // [rb][k]: x'^2
+  double* rq = sq + rb * k;                 // [rb][k]: r^2
+  double* dinv = rq + rb * k;               // [k]
   double* dv = dinv + k;                    // [k]
   const int tid = threadIdx.x;
   for (int e = tid; e < k * k; e += blockDim.x) {
@@ -238,13 +256,16 @@ __global__ void __launch_bounds__(256) update_rows_kernel(const double* __restri
     dv[j] = d[j];
     dinv[j] = 1.0 / d[j];
   }
-  double accx = 0.0, accr = 0.0;            // column tid (k <= 128 < blockDim)
+  // column sums: thread tid owns column tid % k and rows tid / k, tid / k + gstride, ...
+  const int gstride = blockDim.x / k > 0 ? blockDim.x / k : 1;
+  const int scol = tid % k, srow0 = tid / k;
+  double accx = 0.0, accr = 0.0;
   __syncthreads();
   const int64_t rows = n - k;
-  const int64_t nblk = (rows + UPD_ROWS - 1) / UPD_ROWS;
-  const int per = UPD_ROWS * k;
+  const int64_t nblk = (rows + rb - 1) / rb;
+  const int per = rb * k;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const int64_t row0 = k + b * UPD_ROWS;
+    const int64_t row0 = k + b * rb;
     for (int e = tid; e < per; e += blockDim.x) {
       int64_t row = row0 + e / k;
       xs[e] = row < n ? X[row0 * k + e] : 0.0;
@@ -267,21 +288,31 @@ __global__ void __launch_bounds__(256) update_rows_kernel(const double* __restri
       rq[e] = rr * rr;
     }
     __syncthreads();
-    if (tid < k)
-      for (int r = 0; r < UPD_ROWS; ++r) {
-        accx += sq[r * k + tid];
-        accr += rq[r * k + tid];
+    if (srow0 < gstride && tid < gstride * k)
+      for (int r = srow0; r < rb; r += gstride) {
+        accx += sq[r * k + scol];
+        accr += rq[r * k + scol];
       }
     __syncthreads();
   }
+  // combine the gstride partial sums of each column in a fixed order
+  __shared__ double cs[2][256];
+  cs[0][tid] = accx;
+  cs[1][tid] = accr;
+  __syncthreads();
   if (tid < k) {
-    upart[(int64_t)blockIdx.x * 2 * k + tid] = accx;
-    upart[(int64_t)blockIdx.x * 2 * k + k + tid] = accr;
+    double sx = 0.0, sr = 0.0;
+    for (int g = 0; g < gstride; ++g) {
+      sx += cs[0][g * k + tid];
+      sr += cs[1][g * k + tid];
+    }
+    upart[(int64_t)blockIdx.x * 2 * k + tid] = sx;
+    upart[(int64_t)blockIdx.x * 2 * k + k + tid] = sr;
   }
 }
 
 static size_t update_smem(int k) {
-  return sizeof(double) * ((size_t)k * k + 3 * (size_t)UPD_ROWS * k + 2 * (size_t)k);
+  return sizeof(double) * ((size_t)k * k + 3 * (size_t)update_rows_per_step(k) * k + 2 * (size_t)k);
 }
 
 void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {

@@ -31,11 +31,12 @@
 // chunk; at S = 9 one set is used and the MMAs wait for each drain.  All waits are bounded (globaltimer); on expiry the CTA records a
 // timeout, drains what it started and returns.
 #include <cuda.h>
-#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include "sliced.cuh"
 
@@ -861,6 +862,13 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
 }
 
 size_t SlicedA::workspace_bytes() const { return layout_total(); }
+
+void SlicedA::share_gpu(int problems) {
+  if (problems <= 1) return;
+  psplit_ = 1;
+  const int kbt = n_pad_ / sl::kBK;
+  ksplit_ = std::max(1, std::min(kbt, n_pad_ / 4096));
+}
 
 void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023)); }
 

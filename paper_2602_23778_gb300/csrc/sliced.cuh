@@ -16,6 +16,10 @@ class SlicedA {
  public:
   // Host-side plan for A (device, n x n, lda) and k columns; no device work.
   int configure(const double* A, int64_t n, int64_t lda, int k, int precision, int slices);
+  // The GPU is shared with `problems` - 1 other problems running side by side:
+  // no product split-K, Gram split-K only down to about 4096 rows per CTA.
+  // Call before workspace_bytes().
+  void share_gpu(int problems);
   size_t workspace_bytes() const;
   void bind_workspace(char* p);
   // Slice A into its digit planes and encode the tensor maps (once per call).

@@ -40,10 +40,10 @@ def test_params_default(L):
 
 
 def test_struct_layout_matches_header(tmp_path):
-    """ctypes mirrors of eigref_params / eigref_report agree with the C compiler's layout."""
+    """ctypes mirrors of eigref_params / eigref_report / eigref_problem agree with the C compiler's layout."""
     import subprocess
     import paper_2602_23778_gb300 as pkg
-    fields = {"eigref_params": pkg.Params, "eigref_report": pkg.Report}
+    fields = {"eigref_params": pkg.Params, "eigref_report": pkg.Report, "eigref_problem": pkg.Problem}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "eigref.h"', "int main(void) {"]
     for cname, cls in fields.items():
         src.append('printf("%%zu\\n", sizeof(%s));' % cname)
