@@ -435,8 +435,8 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
   run_setup_inverse(r, s);
 
-  // ---- sweeps ----
-  const int m = q.check_every;
+  // ---- sweeps: chunks of check_every (no longer than the run), even ----
+  const int m = std::min(q.check_every, std::max(2, q.max_iters + (q.max_iters & 1)));
   std::vector<cudaEvent_t> pev;
   if (q.profile) {
     pev.resize(2 * m);
@@ -830,7 +830,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
   // chunk length: about 32k graph nodes per replay, even, at least 2
   int per_sweep = 0;
   for (const Run& r : runs) per_sweep += r.pr.sliced ? 34 : 25;
-  int m = std::min(q.check_every, std::max(2, 32768 / std::max(1, per_sweep)));
+  int m = std::min(std::min(q.check_every, std::max(2, q.max_iters)), std::max(2, 32768 / std::max(1, per_sweep)));
   m += m & 1;
   auto issue_all = [&](int count_sweeps) {
     int launches = 0;
