@@ -194,6 +194,21 @@ def max_angle(X, Q):
     return float(np.max(np.linalg.norm(Xn - Qn * c[None, :], axis=0)))
 
 
+def shard_indices(count, rank, world):
+    """Problems of a batch that rank `rank` of `world` refines: r, r + N, ...
+    (independent problems, no exchange between ranks)."""
+    return list(range(rank, count, world))
+
+
+def max_over_ranks(value, device):
+    """The largest `value` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def orth_max(X, rows=32):
     """max |X^T X - I| with the row sum split into blocks of `rows` and the
     block Gram matrices added by Neumaier's compensated summation: the
@@ -308,7 +323,7 @@ def run_batched(args, world, rank, local):
     torch.cuda.set_device(local)
     shapes = C.config5_shapes(count=args.count)
     # weak scaling over ranks: rank r takes problems r, r + world, ...
-    mine = list(range(rank, len(shapes), world))
+    mine = shard_indices(len(shapes), rank, world)
     ps = [C.config5_problem(i, *shapes[i]) for i in mine]
     stream = torch.cuda.Stream()
     h = eigref.Handle(local, stream)
@@ -327,10 +342,7 @@ def run_batched(args, world, rank, local):
         torch.cuda.synchronize()
     ms_step = reps[0]["sweeps_ms"] / args.steps
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, "cuda")
     pk, pk_kind = peaks()
     if prec == "fp64":
         flops = sum(2.0 * p.n * p.n * p.k for p in ps)
@@ -466,9 +478,7 @@ def main():
     assert rep["iterations"] == args.steps, rep
     ms_step = rep["sweeps_ms"] / args.steps
     if dist:
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, "cuda")
     value = world * 1000.0 / ms_step
 
     pk, pk_kind = peaks()

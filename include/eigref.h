@@ -58,7 +58,10 @@ enum eigref_target {
   EIGREF_LARGEST_MAG = 0,  /* k largest |lambda|, alpha = 0 (the paper's default ordering) */
   EIGREF_LARGEST = 1,      /* k algebraically largest, alpha = (lambda_{k+1} - ||A||) / 2 */
   EIGREF_SMALLEST = 2,     /* k algebraically smallest, alpha = (||A|| + lambda_{k+1}) / 2 (Section 5.1) */
-  EIGREF_SHIFT = 3         /* explicit alpha */
+  EIGREF_SHIFT = 3,        /* explicit alpha */
+  EIGREF_SMALLEST_MAG = 4  /* k smallest |lambda| through B = A^2 - alpha I, alpha = (||A||^2 +
+                              lambda_{k+1}^2) / 2 (Section 5.2); W = A (A X) - alpha X, A^2 never
+                              formed; eigenvalues reports lambda^2 */
 };
 
 /* How W = B X and the Gram products are evaluated. */
@@ -97,6 +100,16 @@ typedef struct eigref_params {
   int sign_fix;        /* 1: X <- X Sigma at entry with Algorithm 2's signs (undone on exit) */
   int use_graph;       /* 1: replay each chunk of check_every sweeps as one CUDA graph */
   int profile;         /* 1: time the product kernel of every sweep with CUDA events */
+  int rayleigh_ritz;   /* 1: replace X by its Ritz vectors for B first (Section 3.3): solve
+                          (X^T B X) S = (X^T X) S D, X <- X S, ordered by |D| descending with each
+                          column's largest entry positive; X is returned in that basis.  Pairs
+                          with beta = EIGREF_BETA_ZERO for clustered targets. */
+  int judge_cols;      /* > 0 and < k: only the correction of columns 0..judge_cols-1 decides the
+                          stop and divergence tests (K = k refined vectors, convergence judged on
+                          the leading ones, Section 4.1); 0 = all columns */
+  int reorth;          /* 1: reorthogonalise the result before returning it (the option of Section
+                          3.1.3): two symmetric (Loewdin) steps X <- X (3 I - X^T X) / 2, each
+                          squaring ||X^T X - I||, so the columns move by O(||X^T X - I||) */
 } eigref_params;
 
 /* Report of one refinement call.  The three array pointers are optional,
@@ -122,7 +135,7 @@ typedef struct eigref_report {
 
 /* Defaults: LARGEST_MAG, norm_a computed, max_iters 100, tol 0, correction
  * criterion, FP64, beta cluster, delta_c 10, div 10 / 1e-4, check 32,
- * sign_fix 1, use_graph 1, profile 0. */
+ * sign_fix 1, use_graph 1, profile 0, rayleigh_ritz 0, judge_cols 0, reorth 0. */
 void eigref_params_default(eigref_params* p);
 
 /* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t

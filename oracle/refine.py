@@ -132,6 +132,16 @@ def refine_step(apply_b, Xh, delta, beta="cluster"):
                         res_fro=float(np.linalg.norm(R)), e_fro=float(np.linalg.norm(E)))
 
 
+def reorthonormalise(X, steps=2):
+    """The optional reorthogonalisation of Section 3.1.3.  READING: symmetric
+    (Loewdin) steps X <- X (3 I - X^T X) / 2, the first-order expansion of
+    X (X^T X)^{-1/2}; each step squares ||X^T X - I||."""
+    k = X.shape[1]
+    for _ in range(steps):
+        X = X @ (1.5 * np.eye(k) - 0.5 * (X.T @ X))
+    return X
+
+
 def normalise(X):
     """Column normalisation after each update (Section 3.1.3, precision and
     orthogonality)."""
@@ -149,8 +159,31 @@ STOP_CORRECTION, STOP_RESIDUAL = 0, 1
 OK, E_DIVERGED, E_NOT_CONVERGED, E_NONFINITE = 0, 5, 6, 7
 
 
+def rayleigh_ritz(apply_b, X):
+    """Rayleigh--Ritz preprocessing (Section 3.3, handling clustered
+    eigenvalues): solve (X^T B X) S = (X^T X) S D and return Z = X S with
+    Z^T Z = I and Z^T B Z = D.  The generalized symmetric eigensolver of scipy
+    is the step for the k x k problem.  READING: the Ritz pairs are ordered by
+    |D| descending (the refinement targets the largest |eigenvalues| of B), and
+    each Ritz vector's sign makes its largest-magnitude entry positive.
+    Returns (Z, d)."""
+    import scipy.linalg as sla
+    W = apply_b(X)
+    G = X.T @ X
+    Sm = X.T @ W
+    Sm = 0.5 * (Sm + Sm.T)           # X^T B X is symmetric; drop its rounding asymmetry
+    d, S = sla.eigh(Sm, G)
+    order = np.argsort(-np.abs(d), kind="stable")
+    d, S = d[order], S[:, order]
+    Z = X @ S
+    piv = np.argmax(np.abs(Z), axis=0)
+    sg = np.where(Z[piv, np.arange(Z.shape[1])] < 0, -1.0, 1.0)
+    return np.asfortranarray(Z * sg[None, :]), d
+
+
 def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORRECTION,
-           delta_c=10.0, beta="cluster", div_factor=10.0, div_floor=1e-4, use_sign_fix=True):
+           delta_c=10.0, beta="cluster", div_factor=10.0, div_floor=1e-4, use_sign_fix=True,
+           rayleigh_ritz_first=False, judge_cols=0, norm_b=None):
     """Iterate Algorithm 4 with the driver choices of Section 3.1.3.
 
     Per sweep t: R_t and E_t are computed from X_t, the update is applied and
@@ -163,35 +196,48 @@ def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORR
     the smallest earlier value and div_floor.  A non-finite sweep leaves the
     last finite iterate.
 
-    Returns (X, report) with X in the caller's column signs.
+    rayleigh_ritz_first: replace X0 by its Ritz vectors first (Section 3.3).
+    judge_cols: with K = X0's column count > judge_cols > 0, the stop and
+    divergence tests use the correction of the leading judge_cols columns only
+    (Section 4.1: K vectors refined, convergence judged on the leading k).
+    norm_b: ||B|| for delta and the residual test when B is not A - shift I
+    (the shifted square of Section 5.2); default ||A|| + |shift| and ||A||.
+
+    Returns (X, report) with X in the caller's column signs (or, after the
+    Rayleigh--Ritz step, in its order and signs).
     """
     X = np.array(X0, dtype=np.float64, order="F", copy=True)
     k = X.shape[1]
+    if rayleigh_ritz_first:
+        X, _ = rayleigh_ritz(apply_b, X)
     sigma = sign_fix(X) if use_sign_fix else np.ones(k)
     X = X * sigma[None, :]
-    delta = delta_threshold(norm_a + abs(shift), delta_c)
+    delta = delta_threshold(norm_a + abs(shift) if norm_b is None else norm_b, delta_c)
+    res_scale = norm_a if norm_b is None else norm_b
+    kj = judge_cols if 0 < judge_cols < k else k
     hist_r, hist_e = [], []
     status, it, d = E_NOT_CONVERGED if tol > 0 else OK, 0, None
     emin = np.inf
     for t in range(max_iters):
         Xn, info = refine_step(apply_b, X, delta, beta)
-        rel_r = info.res_fro / norm_a
-        if not (np.all(np.isfinite(Xn)) and np.isfinite(info.e_fro) and np.isfinite(rel_r)):
+        rel_r = info.res_fro / res_scale
+        e_fro = info.e_fro if kj == k else float(np.linalg.norm(info.E[:, :kj]))
+        if not (np.all(np.isfinite(Xn)) and np.isfinite(e_fro) and np.isfinite(rel_r)):
             status = E_NONFINITE
             break
         hist_r.append(rel_r)
-        hist_e.append(info.e_fro)
+        hist_e.append(e_fro)
         d = info.d
         X = normalise(Xn)
         it += 1
-        crit = info.e_fro if stop == STOP_CORRECTION else rel_r
+        crit = e_fro if stop == STOP_CORRECTION else rel_r
         if tol > 0 and crit <= tol:
             status = OK
             break
-        if info.e_fro >= 1.0 or (info.e_fro > div_factor * emin and info.e_fro > div_floor):
+        if e_fro >= 1.0 or (e_fro > div_factor * emin and e_fro > div_floor):
             status = E_DIVERGED
             break
-        emin = min(emin, info.e_fro)
+        emin = min(emin, e_fro)
     X = X * sigma[None, :]
     return X, dict(status=status, iterations=it, d=None if d is None else d + shift,
                    hist_res=np.array(hist_r), hist_corr=np.array(hist_e), sigma=sigma,
@@ -204,8 +250,22 @@ def dense_operator(A, shift=0.0):
     return lambda X: A @ X - shift * X
 
 
+def square_operator(A, alpha):
+    """B X = A (A X) - alpha X: the shifted square of Section 5.2 (smallest
+    |eigenvalues|), A^2 never formed."""
+    A = np.asarray(A)
+    return lambda X: A @ (A @ X) - alpha * X
+
+
 def csr_operator(row_ptr, col_idx, val, n, shift=0.0):
     """B X = A X - shift X for a CSR matrix (scipy's sparse product as the step)."""
     import scipy.sparse as sp
     A = sp.csr_matrix((val, col_idx, row_ptr), shape=(n, n))
     return lambda X: A @ X - shift * X
+
+
+def csr_square_operator(row_ptr, col_idx, val, n, alpha):
+    """B X = A (A X) - alpha X for a CSR matrix."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((val, col_idx, row_ptr), shape=(n, n))
+    return lambda X: A @ (A @ X) - alpha * X

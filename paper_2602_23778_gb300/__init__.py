@@ -18,7 +18,7 @@ _LIB = None
 
 OK, E_INVALID, E_CUDA, E_NOMEM, E_SINGULAR_WY, E_DIVERGED, E_NOT_CONVERGED, E_NONFINITE, E_TIMEOUT, \
     E_UNSUPPORTED = range(10)
-TARGETS = {"largest_mag": 0, "largest": 1, "smallest": 2, "shift": 3}
+TARGETS = {"largest_mag": 0, "largest": 1, "smallest": 2, "shift": 3, "smallest_mag": 4}
 PRECISIONS = {"fp64": 0, "bf16": 1, "int8": 2}
 STOPS = {"correction": 0, "residual": 1}
 BETAS = {"cluster": 0, "zero": 1}
@@ -35,7 +35,8 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("slices", ctypes.c_int), ("beta", ctypes.c_int),
                 ("delta_c", ctypes.c_double), ("div_factor", ctypes.c_double), ("div_floor", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("sign_fix", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("rayleigh_ritz", ctypes.c_int), ("judge_cols", ctypes.c_int),
+                ("reorth", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -221,7 +222,7 @@ class Handle:
                 v = STOPS[v] if isinstance(v, str) else v
             elif key == "beta":
                 v = BETAS[v] if isinstance(v, str) else v
-            elif key in ("sign_fix", "use_graph", "profile"):
+            elif key in ("sign_fix", "use_graph", "profile", "rayleigh_ritz", "reorth"):
                 v = int(bool(v))
             setattr(p, key, v)
         return p

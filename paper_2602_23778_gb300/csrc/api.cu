@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <memory>
 #include <string>
 #include <vector>
@@ -95,7 +96,8 @@ int ensure_ws(eigref_ctx* h, size_t bytes) {
 }
 
 struct Params {
-  int target, max_iters, stop, precision, slices, beta, check_every, sign_fix, use_graph, profile;
+  int target, max_iters, stop, precision, slices, beta, check_every, sign_fix, use_graph, profile, rayleigh_ritz,
+      judge_cols, reorth;
   double shift, norm_a, tol, delta_c, div_factor, div_floor;
 };
 
@@ -120,7 +122,11 @@ int read_params(eigref_ctx* h, const eigref_params* p, Params* q) {
   q->sign_fix = p->sign_fix;
   q->use_graph = p->use_graph;
   q->profile = p->profile;
-  if (q->target < EIGREF_LARGEST_MAG || q->target > EIGREF_SHIFT)
+  q->rayleigh_ritz = p->rayleigh_ritz;
+  q->judge_cols = p->judge_cols;
+  q->reorth = p->reorth;
+  if (q->judge_cols < 0) return set_err(h, EIGREF_E_INVALID, "judge_cols < 0");
+  if (q->target < EIGREF_LARGEST_MAG || q->target > EIGREF_SMALLEST_MAG)
     return set_err(h, EIGREF_E_INVALID, "target %d out of range", q->target);
   if (q->max_iters < 0) return set_err(h, EIGREF_E_INVALID, "max_iters < 0");
   if (!(q->tol >= 0.0) || !isfinite(q->tol)) return set_err(h, EIGREF_E_INVALID, "tol must be finite and >= 0");
@@ -147,12 +153,28 @@ struct Problem {
   int64_t n = 0, nnz = 0;
   int k = 0;
   SlicedA* sliced = nullptr;  // split-precision dense product, or null
+  bool square = false;        // B = A^2 - alpha I (Section 5.2): W = A (A X) - alpha X
+  double* tbuf = nullptr;     // A X of the shifted square (workspace)
 };
 
 // Returns the number of kernels launched.  ev0/ev1 (optional) bracket the
 // product kernel; ev_flags is cudaEventRecordExternal inside a graph capture.
 int launch_product(const Problem& pr, const double* X, double* P, double shift, const Control* ctl,
                    cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, unsigned ev_flags = 0) {
+  if (pr.square) {
+    // the shifted square of Section 5.2, A^2 never formed: T = A X, W = A T - alpha X
+    if (pr.sliced) return pr.sliced->product_sq(X, pr.tbuf, P, shift, ctl, s, ev0, ev1, ev_flags);
+    if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
+    if (pr.csr) {
+      launch_spmm_csr(pr.rp, pr.ci, pr.val, X, pr.tbuf, pr.n, pr.k, 0.0, ctl, s);
+      launch_spmm_csr(pr.rp, pr.ci, pr.val, pr.tbuf, P, pr.n, pr.k, shift, ctl, s, X);
+    } else {
+      launch_gemm_fp64(pr.A, pr.lda, X, pr.tbuf, pr.n, pr.k, 0.0, ctl, s);
+      launch_gemm_fp64(pr.A, pr.lda, pr.tbuf, P, pr.n, pr.k, shift, ctl, s, X);
+    }
+    if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
+    return 2;
+  }
   if (pr.sliced) return pr.sliced->product(X, P, shift, ctl, s, ev0, ev1, ev_flags);
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
   if (pr.csr) {
@@ -216,6 +238,7 @@ struct Run {
   int ugrid = 0;
   int hist_len = 0;
   double norm_a = 0.0, shift = 0.0, delta = 0.0;
+  double norm_res = 0.0;  // scale of the residual test: ||B|| (||A|| unless B is the shifted square)
 };
 
 void run_plan(Run& r) {
@@ -255,6 +278,7 @@ void run_layout(Run& r, Carve& c, Control* ctl) {
   b.ctl = ctl ? ctl : c.take<Control>(1);
   r.scal = c.take<double>(4);
   if (r.pr.csr) r.pr.val_folded = c.take<double>(r.pr.nnz > 0 ? r.pr.nnz : 1);
+  r.pr.tbuf = r.pr.square ? c.take<double>(n * k) : nullptr;
   b.nchunks = r.nchunks;
   b.chunk_rows = r.chunk_rows;
   b.ugrid = r.ugrid;
@@ -276,13 +300,17 @@ void run_bind(Run& r, char* base, Control* ctl) {
   if (r.pr.sliced) r.pr.sliced->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
 }
 
-// Shift and delta from ||A|| and the target (Sections 3.1.3 and 5.1).
+// Shift and delta from ||A|| and the target (Sections 3.1.3, 5.1 and 5.2).
 void run_shift(Run& r) {
   r.shift = 0.0;
   if (r.q.target == EIGREF_SHIFT) r.shift = r.q.shift;
   else if (r.q.target == EIGREF_SMALLEST) r.shift = 0.5 * (r.norm_a + r.q.shift);   // Section 5.1
   else if (r.q.target == EIGREF_LARGEST) r.shift = 0.5 * (r.q.shift - r.norm_a);    // its mirror
-  r.delta = r.q.delta_c * (r.norm_a + fabs(r.shift)) * kUnitRoundoff;              // Section 3.1.3
+  else if (r.q.target == EIGREF_SMALLEST_MAG)                                       // Section 5.2, on A^2
+    r.shift = 0.5 * (r.norm_a * r.norm_a + r.q.shift * r.q.shift);
+  const double norm_b = r.pr.square ? r.norm_a * r.norm_a + fabs(r.shift) : r.norm_a + fabs(r.shift);
+  r.norm_res = r.pr.square ? norm_b : r.norm_a;
+  r.delta = r.q.delta_c * norm_b * kUnitRoundoff;                                   // Section 3.1.3
 }
 
 Control run_control(const Run& r) {
@@ -290,7 +318,8 @@ Control run_control(const Run& r) {
   c.max_iters = r.q.max_iters;
   c.stop = r.q.stop;
   c.tol = r.q.tol;
-  c.norm_a = r.norm_a;
+  c.norm_a = r.norm_res;
+  c.judge = (r.q.judge_cols > 0 && r.q.judge_cols < r.pr.k) ? r.q.judge_cols : r.pr.k;
   c.div_factor = r.q.div_factor;
   c.div_floor = r.q.div_floor;
   c.emin = DBL_MAX;
@@ -312,14 +341,33 @@ int run_setup_device(eigref_ctx* h, Run& r, cudaStream_t s) {
   }
   const int64_t ldu = r.x_dev ? r.ldx : n;
   r.sg = nullptr;
-  if (r.q.sign_fix) {
-    launch_sign_fix(xu, ldu, k, r.sigma, nullptr, s);
-    r.sg = r.sigma;
+  if (!r.q.rayleigh_ritz) {
+    if (r.q.sign_fix) {
+      launch_sign_fix(xu, ldu, k, r.sigma, nullptr, s);
+      r.sg = r.sigma;
+    }
+    launch_copy_in(xu, ldu, r.xbuf[0], n, k, r.sg, s);
+  } else {
+    launch_copy_in(xu, ldu, r.xbuf[0], n, k, nullptr, s);
   }
-  launch_copy_in(xu, ldu, r.xbuf[0], n, k, r.sg, s);
   if (r.pr.sliced) {
     const int st = r.pr.sliced->prepare(s);
     if (st) return set_err(h, st, "%s", r.pr.sliced->error());
+  }
+  if (r.q.rayleigh_ritz) {
+    // Section 3.3: X <- its Ritz vectors for B, then the signs of Algorithm 2
+    // on that X.  The Ritz vectors are what the call refines and returns.
+    SweepBufs& b = r.b;
+    // (no Control on these launches: they run even when max_iters = 0)
+    launch_product(r.pr, r.xbuf[0], b.p, r.shift, nullptr, s);
+    launch_gram(r.xbuf[0], b.p, k, k, n, r.chunk_rows, r.nchunks, b.gpart, b.g2, nullptr, s);
+    launch_gram(r.xbuf[0], b.p, k, 0, k, k, 1, b.gpart, b.gtop, nullptr, s);
+    launch_rayleigh_ritz(b, n, k, r.xbuf[0], r.xbuf[1], s);
+    if (r.q.sign_fix) {
+      launch_sign_fix_rowmajor(r.xbuf[0], k, r.sigma, s);
+      launch_scale_cols(r.xbuf[0], r.xbuf[0], n, k, r.sigma, s);
+      r.sg = r.sigma;
+    }
   }
   return EIGREF_OK;
 }
@@ -348,11 +396,15 @@ int run_issue(const Run& r, int count, cudaStream_t s, cudaEvent_t* pev, unsigne
   return launches;
 }
 
-// Copies the final iterate back into the caller's X (signs restored).
+// Copies the final iterate back into the caller's X (signs restored), after
+// the optional reorthogonalisation.
 int run_copy_out(eigref_ctx* h, const Run& r, int iterations, cudaStream_t s) {
   const int64_t n = r.pr.n;
   const int k = r.pr.k;
   const double* xr = r.xbuf[iterations & 1];
+  if (r.q.reorth)
+    launch_reorthonormalise(r.b, n, k, r.xbuf[iterations & 1], r.xbuf[(iterations + 1) & 1], r.chunk_rows, r.nchunks,
+                            s);
   if (r.x_dev) {
     launch_copy_out(xr, r.X, r.ldx, n, k, r.sg, s);
   } else {
@@ -421,18 +473,19 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
       return set_err(h, isfinite(r.norm_a) ? EIGREF_E_INVALID : EIGREF_E_NONFINITE, "||A||_inf = %g", r.norm_a);
   }
   run_shift(r);
-  if (r.pr.csr && r.shift != 0.0 && r.pr.nnz > 0) {
+  *h->host_ctl = run_control(r);
+  CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
+  if (r.pr.csr && r.shift != 0.0 && r.pr.nnz > 0 && !r.pr.square) {
     // fold -shift into the stored diagonal once, so the SpMM has no shift term
     int* missing = reinterpret_cast<int*>(r.scal + 2);
     launch_csr_fold_diag(r.pr.rp, r.pr.ci, r.pr.val, n, r.shift, r.pr.val_folded, missing, s);
-    CUDA_TRY(h, cudaMemcpyAsync(&h->host_ctl->status, missing, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int* hmiss = &h->host_ctl->singular;   // the host copy of the Control block is spare here
+    CUDA_TRY(h, cudaMemcpyAsync(hmiss, missing, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    r.pr.folded = h->host_ctl->status == 0;
+    r.pr.folded = *hmiss == 0;
   }
   st = run_setup_device(h, r, s);
   if (st) return st;
-  *h->host_ctl = run_control(r);
-  CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
   run_setup_inverse(r, s);
 
   // ---- sweeps: chunks of check_every (no longer than the run), even ----
@@ -565,6 +618,9 @@ void eigref_params_default(eigref_params* p) {
   p->sign_fix = 1;
   p->use_graph = 1;
   p->profile = 0;
+  p->rayleigh_ritz = 0;
+  p->judge_cols = 0;
+  p->reorth = 0;
 }
 
 const char* eigref_status_string(int s) {
@@ -644,6 +700,7 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
   pr.n = n;
   pr.k = k;
   pr.lda = lda;
+  pr.square = pp->target == EIGREF_SMALLEST_MAG;
   double* a_dev = nullptr;
   if (is_device_ptr(A)) {
     pr.A = A;
@@ -688,6 +745,7 @@ int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* co
   pr.n = n;
   pr.k = k;
   pr.nnz = nnz;
+  pr.square = p && p->target == EIGREF_SMALLEST_MAG;
   void* bufs[3] = {nullptr, nullptr, nullptr};
   const void* src[3] = {row_ptr, col_idx, val};
   size_t sz[3] = {(size_t)(n + 1) * 4, (size_t)nnz * 4, (size_t)nnz * 8};
@@ -755,6 +813,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
     r.X = pb.X;
     r.ldx = pb.ldx;
     r.x_dev = true;
+    r.pr.square = pb.target == EIGREF_SMALLEST_MAG;
     if (q.precision != EIGREF_FP64) {
       st = sls[i].configure(pb.A, pb.n, pb.lda, pb.k, q.precision, q.slices);
       if (st) return set_err(h, st, "problem %d: %s", i, sls[i].error());
@@ -763,10 +822,17 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
     }
     run_plan(r);
   }
-  // ---- workspace: the Control array first, then one region per problem ----
+  // split form: every stage is one grouped launch over all problems
+  const bool grouped = q.precision != EIGREF_FP64;
+  if (grouped)
+    for (int i = 0; i < count; ++i)
+      if (runs[i].pr.square)
+        return set_err(h, EIGREF_E_UNSUPPORTED, "problem %d: the shifted square is not batched in the split form", i);
+  // ---- workspace: the Control array, the GroupItem array, one region per problem ----
   const size_t ctl_bytes = ((size_t)count * sizeof(Control) + 1023) & ~size_t(1023);
+  const size_t item_bytes = grouped ? (((size_t)count * sizeof(GroupItem) + 1023) & ~size_t(1023)) : 0;
   std::vector<size_t> off(count);
-  size_t total = ctl_bytes;
+  size_t total = ctl_bytes + item_bytes;
   for (int i = 0; i < count; ++i) {
     off[i] = total;
     total += (run_bytes(runs[i], false) + 1023) & ~size_t(1023);
@@ -775,6 +841,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
   if (st) return st;
   char* base = static_cast<char*>(h->ws);
   Control* ctls = reinterpret_cast<Control*>(base);
+  GroupItem* items_dev = reinterpret_cast<GroupItem*>(base + ctl_bytes);
   for (int i = 0; i < count; ++i) run_bind(runs[i], base + off[i], ctls + i);
 
   // host-side resources of the call, released by the guard
@@ -815,34 +882,97 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
                        r.norm_a);
     }
     run_shift(r);
-    st = run_setup_device(h, r, s);
-    if (st) return st;
     res.hc[i] = run_control(r);
   }
   CUDA_TRY(h, cudaMemcpyAsync(ctls, res.hc, (size_t)count * sizeof(Control), cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < count; ++i) {
+    st = run_setup_device(h, runs[i], s);
+    if (st) return st;
+  }
   for (int i = 0; i < count; ++i) run_setup_inverse(runs[i], s);
 
-  // ---- one stream per problem, forked from and joined into the handle's stream ----
-  res.streams.assign(count, nullptr);
-  res.events.assign(count + 1, nullptr);
-  for (auto& x : res.streams) CUDA_TRY(h, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
-  for (auto& e : res.events) CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  // chunk length: about 32k graph nodes per replay, even, at least 2
-  int per_sweep = 0;
-  for (const Run& r : runs) per_sweep += r.pr.sliced ? 34 : 25;
-  int m = std::min(std::min(q.check_every, std::max(2, q.max_iters)), std::max(2, 32768 / std::max(1, per_sweep)));
-  m += m & 1;
-  auto issue_all = [&](int count_sweeps) {
-    int launches = 0;
-    cudaEventRecord(res.events[count], s);
-    for (int i = 0; i < count; ++i) {
-      cudaStreamWaitEvent(res.streams[i], res.events[count], 0);
-      launches += run_issue(runs[i], count_sweeps, res.streams[i], nullptr, 0);
-      cudaEventRecord(res.events[i], res.streams[i]);
-      cudaStreamWaitEvent(s, res.events[i], 0);
+  int m = std::min(q.check_every, std::max(2, q.max_iters));
+  std::function<int(int)> issue_all;
+  // grouped form: per-problem items and tensor-core tasks for both sweep parities
+  std::vector<GroupItem> items;
+  std::vector<MmaTask> prod[2], gram, upd[2];
+  GroupDims gd{count, 0, 0};
+  int max_n_pad = 0;
+  if (grouped) {
+    items.resize(count);
+    gram.resize(count);
+    for (int par = 0; par < 2; ++par) {
+      prod[par].resize(count);
+      upd[par].resize(count);
     }
-    return launches;
-  };
+    for (int i = 0; i < count; ++i) {
+      const Run& r = runs[i];
+      GroupItem& it = items[i];
+      memset(&it, 0, sizeof(it));
+      for (int par = 0; par < 2; ++par) {
+        it.b[par] = r.b;
+        it.b[par].x = r.xbuf[par];
+        it.b[par].xn = r.xbuf[par ^ 1];
+        prod[par][i] = sls[i].product_task(r.xbuf[par], r.b.p, r.shift, r.b.ctl);
+        upd[par][i] = sls[i].update_task(r.xbuf[par], r.b.p, r.b.d, r.b.dinv, r.xbuf[par ^ 1], r.b.upart, r.b.ctl);
+      }
+      gram[i] = sls[i].gram_task(nullptr, r.b.ctl);
+      it.n = r.pr.n;
+      it.k = r.pr.k;
+      it.beta_zero = q.beta == EIGREF_BETA_ZERO;
+      it.delta = r.delta;
+      sls[i].fill_group_item(&it);
+      gd.max_k = std::max(gd.max_k, r.pr.k);
+      gd.max_n = std::max(gd.max_n, r.pr.n);
+      max_n_pad = std::max(max_n_pad, it.n_pad);
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(items_dev, items.data(), (size_t)count * sizeof(GroupItem), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    const int S = sls[0].slices();
+    m += m & 1;
+    issue_all = [&, S](int count_sweeps) {
+      int launches = 0;
+      const int groups = (count + 39) / 40;
+      for (int t = 0; t < count_sweeps; ++t) {
+        const int par = t & 1;
+        launch_slice_grouped(S, SLICE_ZERO_MAX, items_dev, gd, max_n_pad, par, s);
+        launch_slice_grouped(S, SLICE_X_COLS, items_dev, gd, max_n_pad, par, s);
+        launch_mma_tasks(S, sl::MODE_PRODUCT, prod[par].data(), count, s);
+        launch_slice_grouped(S, SLICE_P_COLS, items_dev, gd, max_n_pad, par, s);
+        launch_mma_tasks(S, sl::MODE_GRAM, gram.data(), count, s);
+        launch_gram_reduce_grouped(items_dev, gd, 0, s);
+        launch_top_gram_grouped(items_dev, gd, par, s);
+        launch_kxk_stage_grouped(items_dev, gd, par, s);
+        launch_slice_grouped(S, SLICE_X_ROWS, items_dev, gd, max_n_pad, par, s);
+        launch_slice_grouped(S, SLICE_F_COLS, items_dev, gd, max_n_pad, par, s);
+        launch_mma_tasks(S, sl::MODE_UPDATE, upd[par].data(), count, s);
+        launch_finalize_grouped(items_dev, gd, par, s);
+        launch_normalize_grouped(items_dev, gd, par, s);
+        launches += 24 + 3 * groups;
+      }
+      return launches;
+    };
+  } else {
+    // ---- one stream per problem, forked from and joined into the handle's stream ----
+    res.streams.assign(count, nullptr);
+    res.events.assign(count + 1, nullptr);
+    for (auto& x : res.streams) CUDA_TRY(h, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    for (auto& e : res.events) CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // chunk length: about 32k graph nodes per replay, even, at least 2
+    m = std::min(m, std::max(2, 32768 / (25 * count)));
+    m += m & 1;
+    issue_all = [&](int count_sweeps) {
+      int launches = 0;
+      cudaEventRecord(res.events[count], s);
+      for (int i = 0; i < count; ++i) {
+        cudaStreamWaitEvent(res.streams[i], res.events[count], 0);
+        launches += run_issue(runs[i], count_sweeps, res.streams[i], nullptr, 0);
+        cudaEventRecord(res.events[i], res.streams[i]);
+        cudaStreamWaitEvent(s, res.events[i], 0);
+      }
+      return launches;
+    };
+  }
   GraphGuard graph;
   int chunk_launches = 0;
   if (q.use_graph && q.max_iters > 0) {

@@ -29,6 +29,7 @@ struct Control {
   int stop;           // eigref_stop
   int nonfinite;
   int singular;       // set by the LU of Y_1
+  int judge;          // columns 0..judge-1 decide the stop and divergence tests
   double tol;
   double norm_a;
   double div_factor, div_floor;
@@ -58,10 +59,37 @@ struct SweepBufs {
   int ugrid;
 };
 
+// One problem of a batch run with grouped launches: every stage of a sweep is
+// one launch over all problems, blockIdx.z (or a tile table) selecting the
+// problem.  Lives in device memory; b[t & 1] holds the pointers of sweep t.
+struct GroupItem {
+  SweepBufs b[2];
+  int64_t n;
+  int k;
+  int beta_zero;
+  double delta;
+  // split-form operands of this problem (see SlicedA)
+  int n_pad, k_pad, kr, ksplit;
+  void* x_planes;            // BF16 [S][k_pad][n_pad]
+  void* p_planes;            // BF16 [S][k_pad][n_pad]
+  void* xr_planes;           // BF16 [S][n_pad][kr]
+  void* f_planes;            // BF16 [S][k_pad][kr]
+  int *x_colexp, *p_colexp, *xr_rowexp, *f_colexp;
+  unsigned long long *x_cmax, *p_cmax, *f_cmax;
+  double* sgpart;            // tensor-core Gram partials [2][ksplit][k k]
+};
+
+// Extent of a grouped launch: blockIdx.z = problem, x/y sized for the largest.
+struct GroupDims {
+  int count;
+  int max_k;
+  int64_t max_n;
+};
+
 // ---- kernels launched by the driver (definitions in the .cu files) ----
 // fp64.cu
 void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, int64_t n, int k,
-                      double shift, const Control* ctl, cudaStream_t s);
+                      double shift, const Control* ctl, cudaStream_t s, const double* Xs = nullptr);
 void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
                  int nchunks, double* part, double* out, const Control* ctl, cudaStream_t s);
 void launch_gram_reduce(const double* part, int k, int nchunks, double* out, const Control* ctl, cudaStream_t s);
@@ -81,12 +109,28 @@ cudaError_t init_fp64_attributes();
 cudaError_t init_kxk_attributes();
 // spmm.cu
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
-                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s);
+                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s, const double* Xs = nullptr);
 void launch_csr_fold_diag(const int32_t* rp, const int32_t* ci, const double* val, int64_t n, double shift,
                           double* val_out, int* missing, cudaStream_t s);
 // kxk.cu
 void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s);
 void launch_sign_fix(const double* X, int64_t ldx, int k, double* sigma, int* singular, cudaStream_t s);
 void launch_inverse_setup(const SweepBufs& b, int k, cudaStream_t s);
+void launch_sign_fix_rowmajor(const double* X, int k, double* sigma, cudaStream_t s);
+void launch_scale_cols(const double* In, double* Out, int64_t n, int k, const double* sg, cudaStream_t s);
+// Rayleigh--Ritz (Section 3.3): G, S of Xbuf in b.gtop + b.g2; Xbuf <- its Ritz
+// vectors (|Ritz value| descending, largest entry of each positive); Zbuf scratch.
+void launch_rayleigh_ritz(const SweepBufs& b, int64_t n, int k, double* Xbuf, double* Zbuf, cudaStream_t s);
+// Optional reorthogonalisation (Section 3.1.3): two first-order Loewdin steps
+// Xbuf <- Xbuf (3 I - X^T X) / 2; Zbuf scratch.
+void launch_reorthonormalise(const SweepBufs& b, int64_t n, int k, double* Xbuf, double* Zbuf, int64_t chunk_rows,
+                             int nchunks, cudaStream_t s);
+
+// grouped launches over a batch (parity = t & 1 of the sweep)
+void launch_top_gram_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
+void launch_gram_reduce_grouped(const GroupItem* items, const GroupDims& gd, int max_ksplit, cudaStream_t s);
+void launch_finalize_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
+void launch_normalize_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
+void launch_kxk_stage_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
 
 }  // namespace eigref

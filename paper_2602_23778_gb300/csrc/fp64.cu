@@ -18,7 +18,8 @@
 namespace eigref {
 
 // ---------------------------------------------------------------------------
-// P = A X - shift X.  A n x n row-major (lda), X and P n x k row-major.
+// P = A X - shift Xs (Xs = X unless given).  A n x n row-major (lda), X, Xs
+// and P n x k row-major.
 // 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread.
 // ---------------------------------------------------------------------------
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
@@ -26,7 +27,8 @@ constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(const double* __restrict__ A, int64_t lda,
                                                         const double* __restrict__ X,
                                                         double* __restrict__ P, int64_t n, int k,
-                                                        double shift, const Control* ctl) {
+                                                        double shift, const double* __restrict__ Xs,
+                                                        const Control* ctl) {
   if (ctl && ctl->done) return;
   __shared__ double As[GB_K][GB_M + 1];
   __shared__ double Bs[GB_K][GB_N];
@@ -84,15 +86,15 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const double* __restrict
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int col = n0 + tx * 4 + j;
-      if (col < k) P[row * k + col] = acc[i][j] - shift * X[row * k + col];
+      if (col < k) P[row * k + col] = acc[i][j] - shift * Xs[row * k + col];
     }
   }
 }
 
 void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, int64_t n, int k,
-                      double shift, const Control* ctl, cudaStream_t s) {
+                      double shift, const Control* ctl, cudaStream_t s, const double* Xs) {
   dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((k + GB_N - 1) / GB_N));
-  gemm_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, X, P, n, k, shift, ctl);
+  gemm_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, X, P, n, k, shift, Xs ? Xs : X, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -151,13 +153,10 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restr
 
 // One warp per output: lane l sums chunks l, l + 32, ... in order, then a
 // fixed butterfly combines the lanes, so the result is the same every run.
-__global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int nchunks, double* __restrict__ out,
-                                   const Control* ctl) {
-  if (ctl && ctl->done) return;
+__device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part, int k, int nchunks,
+                                                 double* __restrict__ out, int64_t w0, int64_t nw) {
   const int64_t kk = (int64_t)k * k;
   const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t e = w0; e < 2 * kk; e += nw) {
     const int z = (int)(e / kk);
     const int64_t o = e % kk;
@@ -170,6 +169,27 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int n
   }
 }
 
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int nchunks, double* __restrict__ out,
+                                   const Control* ctl) {
+  if (ctl && ctl->done) return;
+  gram_reduce_body(part, k, nchunks, out, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                   ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// Batch: the tensor-core Gram partials of problem blockIdx.z into its G, S.
+__global__ void gram_reduce_grouped_kernel(const GroupItem* __restrict__ items) {
+  const GroupItem& it = items[blockIdx.z];
+  if (it.b[0].ctl->done) return;
+  gram_reduce_body(it.sgpart, it.k, it.ksplit, it.b[0].g2, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                   ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+void launch_gram_reduce_grouped(const GroupItem* items, const GroupDims& gd, int, cudaStream_t s) {
+  const int64_t warps = 2LL * gd.max_k * gd.max_k;
+  const int rg = (int)std::min<int64_t>((warps + 7) / 8, 64);
+  gram_reduce_grouped_kernel<<<dim3(rg, 1, gd.count), 256, 0, s>>>(items);
+}
+
 void launch_gram_reduce(const double* part, int k, int nchunks, double* out, const Control* ctl, cudaStream_t s) {
   const int64_t warps = 2LL * k * k;
   const int rg = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
@@ -178,18 +198,17 @@ void launch_gram_reduce(const double* part, int k, int nchunks, double* out, con
 
 // Gram products of the leading k x k block: out[0] = X1^T X1, out[1] = X1^T P1
 // (16 x 16 output tiles, k-term dot products).
-__global__ void __launch_bounds__(256) top_gram_kernel(const double* __restrict__ X, const double* __restrict__ P,
-                                                       int k, double* __restrict__ out, const Control* ctl) {
-  if (ctl && ctl->done) return;
+__device__ __forceinline__ void top_gram_body(const double* __restrict__ X, const double* __restrict__ P, int k,
+                                              double* __restrict__ out, int bx, int by, int bz) {
   __shared__ double As[16][17];
   __shared__ double Bs[16][17];
-  const double* Y = blockIdx.z ? P : X;
+  const double* Y = bz ? P : X;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+  const int i = bx * 16 + tx, j = by * 16 + ty;
   double acc = 0.0;
   for (int l0 = 0; l0 < k; l0 += 16) {
     const int l = l0 + ty;
-    const int ai = blockIdx.x * 16 + tx, bj = blockIdx.y * 16 + tx;
+    const int ai = bx * 16 + tx, bj = by * 16 + tx;
     As[ty][tx] = (l < k && ai < k) ? X[(int64_t)l * k + ai] : 0.0;   // X1(l, i)
     Bs[ty][tx] = (l < k && bj < k) ? Y[(int64_t)l * k + bj] : 0.0;   // Y1(l, j)
     __syncthreads();
@@ -197,12 +216,31 @@ __global__ void __launch_bounds__(256) top_gram_kernel(const double* __restrict_
     for (int c = 0; c < 16; ++c) acc = fma(As[c][tx], Bs[c][ty], acc);
     __syncthreads();
   }
-  if (i < k && j < k) out[(int64_t)blockIdx.z * k * k + i + (int64_t)j * k] = acc;
+  if (i < k && j < k) out[(int64_t)bz * k * k + i + (int64_t)j * k] = acc;
+}
+
+__global__ void __launch_bounds__(256) top_gram_kernel(const double* __restrict__ X, const double* __restrict__ P,
+                                                       int k, double* __restrict__ out, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  top_gram_body(X, P, k, out, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 void launch_top_gram(const double* X, const double* P, int k, double* out, const Control* ctl, cudaStream_t s) {
   dim3 g((k + 15) / 16, (k + 15) / 16, 2);
   top_gram_kernel<<<g, 256, 0, s>>>(X, P, k, out, ctl);
+}
+
+// Batch: blockIdx.z = 2 problem + (0: G1, 1: S1).
+__global__ void __launch_bounds__(256) top_gram_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z >> 1];
+  const SweepBufs& b = it.b[parity];
+  if ((int)blockIdx.x * 16 >= it.k || (int)blockIdx.y * 16 >= it.k || b.ctl->done) return;
+  top_gram_body(b.x, b.p, it.k, b.gtop, blockIdx.x, blockIdx.y, blockIdx.z & 1);
+}
+
+void launch_top_gram_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
+  const int t = (gd.max_k + 15) / 16;
+  top_gram_grouped_kernel<<<dim3(t, t, 2 * gd.count), 256, 0, s>>>(items, parity);
 }
 
 void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1, int64_t chunk_rows,
@@ -327,7 +365,7 @@ void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {
 //   nu_j = 1 / ||x'_j||
 // Stopping, divergence and non-finite tests of Section 3.1.3 / Section 4.3.1.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) finalize_kernel(SweepBufs b, int k) {
+__device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
   Control* ctl = b.ctl;
   __shared__ double xsq_s[kMaxK], r2_s[kMaxK];
   __shared__ double red[3][32];
@@ -365,9 +403,10 @@ __global__ void __launch_bounds__(1024) finalize_kernel(SweepBufs b, int k) {
     const int j = tid;
     const double xsq = xsq_s[j], r2 = r2_s[j], dj = b.d[j];
     const double e21 = (r2 - 2.0 * b.cz[j] + b.cw[j]) / (dj * dj);
-    esum = e21 > 0.0 ? e21 : 0.0;
+    // the correction of the judged leading columns decides stop and divergence
+    esum = (j < ctl->judge && e21 > 0.0) ? e21 : 0.0;
     rsum = b.r1sq[j] + r2;
-    e11 = b.e11sq[j];
+    e11 = j < ctl->judge ? b.e11sq[j] : 0.0;
     b.nu[j] = 1.0 / sqrt(xsq);
     if (!isfinite(xsq) || !(xsq > 0.0)) atomicExch(&bad, 1);
   }
@@ -419,6 +458,18 @@ __global__ void __launch_bounds__(1024) finalize_kernel(SweepBufs b, int k) {
   if (corr < ctl->emin) ctl->emin = corr;
 }
 
+__global__ void __launch_bounds__(1024) finalize_kernel(SweepBufs b, int k) { finalize_body(b, k); }
+
+// Batch: one CTA per problem.
+__global__ void __launch_bounds__(1024) finalize_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.x];
+  finalize_body(it.b[parity], it.k);
+}
+
+void launch_finalize_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
+  finalize_grouped_kernel<<<gd.count, 1024, 0, s>>>(items, parity);
+}
+
 cudaError_t init_fp64_attributes() {
   return cudaFuncSetAttribute(update_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)update_smem(kMaxK));
@@ -428,12 +479,30 @@ void launch_finalize(const SweepBufs& b, int k, double, cudaStream_t s) {
   finalize_kernel<<<1, 1024, 0, s>>>(b, k);
 }
 
+__device__ __forceinline__ void normalize_body(double* __restrict__ X, int64_t n, int k, const double* __restrict__ nu,
+                                               int64_t t0, int64_t stride) {
+  const int64_t total = n * k;
+  for (int64_t e = t0; e < total; e += stride) X[e] *= nu[e % k];
+}
+
 __global__ void normalize_kernel(double* __restrict__ X, int64_t n, int k, const double* __restrict__ nu,
                                  const Control* ctl) {
   if (!ctl->pending_norm) return;
-  const int64_t total = n * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    X[e] *= nu[e % k];
+  normalize_body(X, n, k, nu, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+__global__ void normalize_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  if (!b.ctl->pending_norm) return;
+  normalize_body(b.xn, it.n, it.k, b.nu, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                 (int64_t)gridDim.x * blockDim.x);
+}
+
+void launch_normalize_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
+  const int64_t total = gd.max_n * gd.max_k;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 64);
+  normalize_grouped_kernel<<<dim3(grid, 1, gd.count), 256, 0, s>>>(items, parity);
 }
 
 void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {

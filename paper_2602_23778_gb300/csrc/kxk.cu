@@ -19,6 +19,9 @@
 // All k x k matrices are FP64 column-major with leading dimension k.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -38,10 +41,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // One block per column j.  In the split form g2 arrives holding the Gram
 // products over all rows; the block turns its column into G2 = G - G1,
 // S2 = S - S1 in place (only this block touches column j).
-__global__ void kk_prep_kernel(SweepBufs b, int k) {
-  if (b.ctl->done) return;
+__device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j) {
   __shared__ double sh[32];
-  const int j = blockIdx.x;
   const int64_t kk = (int64_t)k * k;
   const double* G1 = b.gtop;
   const double* S1 = b.gtop + kk;
@@ -78,6 +79,11 @@ __global__ void kk_prep_kernel(SweepBufs b, int k) {
     b.dinv[j] = 1.0 / dj;
     b.r1sq[j] = r1s;
   }
+}
+
+__global__ void kk_prep_kernel(SweepBufs b, int k) {
+  if (b.ctl->done) return;
+  kk_prep_body(b, k, blockIdx.x);
 }
 
 __device__ __forceinline__ double nan_max(double a, double b) {   // NaN-propagating max
@@ -223,12 +229,11 @@ enum { KG_V1 = 0, KG_W2 = 1, KG_YTE = 2, KG_X1 = 3 };
 
 // 16 x 16 output tile per CTA, one output per thread:  s = op(A)(i,:) . Bm(:,j)
 template <int MODE>
-__global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
-  if (b.ctl->done) return;
+__device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, int by) {
   __shared__ double As[16][17];
   __shared__ double Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+  const int i = bx * 16 + tx, j = by * 16 + ty;
   const int64_t kk = (int64_t)k * k;
   const double* A = (MODE == KG_W2) ? b.g2 : b.y1;   // G2 = b.g2[0 .. k*k)
   const double* Bm = (MODE == KG_YTE) ? b.e11 : (MODE == KG_X1 ? b.nmat : b.m);
@@ -238,11 +243,11 @@ __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
     // As[r][c] = op(A)(blockIdx.x*16 + r, l0 + c); Bs[r][c] = Bm(l0 + r, blockIdx.y*16 + c)
     {
       const int r = ty, c = tx;  // each thread loads one element of each tile
-      const int ai = blockIdx.x * 16 + r, al = l0 + c;
+      const int ai = bx * 16 + r, al = l0 + c;
       double av = 0.0;
       if (ai < k && al < k) av = transA ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k];
       As[r][c] = av;
-      const int bl = l0 + r, bj = blockIdx.y * 16 + c;
+      const int bl = l0 + r, bj = by * 16 + c;
       Bs[r][c] = (bl < k && bj < k) ? Bm[bl + (int64_t)bj * k] : 0.0;
     }
     __syncthreads();
@@ -265,12 +270,16 @@ __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
   (void)kk;
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
+  if (b.ctl->done) return;
+  kk_gemm_body<MODE>(b, k, blockIdx.x, blockIdx.y);
+}
+
 // E11 by the cases of line 6 of Algorithm 4, one block per column j, plus the
 // column sums the finalize step needs: ||E11(:,j)||^2, (M^T Z)_jj, (M^T G2 M)_jj.
-__global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
-  if (b.ctl->done) return;
+__device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double delta, int beta_zero, int j) {
   __shared__ double sh[32];
-  const int j = blockIdx.x;
   const int64_t kk = (int64_t)k * k;
   const double dj = b.d[j];
   double es = 0.0, cz = 0.0, cw = 0.0;
@@ -302,6 +311,11 @@ __global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
   (void)kk;
 }
 
+__global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
+  if (b.ctl->done) return;
+  kk_e11_body(b, k, delta, beta_zero, blockIdx.x);
+}
+
 
 // ---------------------------------------------------------------------------
 // Y1^{-1} for the split form.  An LU of Y1 is a long chain of dependent steps
@@ -315,20 +329,19 @@ __global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
 // C = add_i I + beta C0 + alpha op(A) B  (k x k, column-major).  check > 0:
 // flags Y1 as singular when an entry of C exceeds it (Newton-Schulz diverging).
 template <int TRANS>
-__global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __restrict__ A, const double* __restrict__ B,
-                                                              const double* __restrict__ C0, double* __restrict__ C,
-                                                              int k, double alpha, double beta, int add_i,
-                                                              double check, Control* ctl) {
-  if (ctl->done) return;
+__device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ A, const double* __restrict__ B,
+                                                     const double* __restrict__ C0, double* __restrict__ C, int k,
+                                                     double alpha, double beta, int add_i, double check, Control* ctl,
+                                                     int bx, int by) {
   __shared__ double As[16][17];
   __shared__ double Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+  const int i = bx * 16 + tx, j = by * 16 + ty;
   double acc = 0.0;
   for (int l0 = 0; l0 < k; l0 += 16) {
-    const int ai = blockIdx.x * 16 + ty, al = l0 + tx;
+    const int ai = bx * 16 + ty, al = l0 + tx;
     As[ty][tx] = (ai < k && al < k) ? (TRANS ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k]) : 0.0;
-    const int bl = l0 + ty, bj = blockIdx.y * 16 + tx;
+    const int bl = l0 + ty, bj = by * 16 + tx;
     Bs[ty][tx] = (bl < k && bj < k) ? B[bl + (int64_t)bj * k] : 0.0;
     __syncthreads();
 #pragma unroll
@@ -347,6 +360,15 @@ __global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __re
       ctl->done = 1;
     }
   }
+}
+
+template <int TRANS>
+__global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                              const double* __restrict__ C0, double* __restrict__ C,
+                                                              int k, double alpha, double beta, int add_i,
+                                                              double check, Control* ctl) {
+  if (ctl->done) return;
+  kk_gemm_generic_body<TRANS>(A, B, C0, C, k, alpha, beta, add_i, check, ctl, blockIdx.x, blockIdx.y);
 }
 
 static void kk_gemm_generic(const double* A, bool transA, const double* B, const double* C0, double* C, int k,
@@ -401,16 +423,353 @@ void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cu
   kk_gemm_kernel<KG_X1><<<g, 256, 0, s>>>(b, k);
 }
 
+// ---------------------------------------------------------------------------
+// The same stage for a batch (split form, Newton-Schulz inverse): each launch
+// covers every problem, blockIdx.z selecting it; CTAs outside a problem's
+// k x k extent return at once.
+// ---------------------------------------------------------------------------
+__global__ void kk_prep_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  if ((int)blockIdx.x >= it.k || b.ctl->done) return;
+  kk_prep_body(b, it.k, blockIdx.x);
+}
+
+__global__ void kk_e11_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  if ((int)blockIdx.x >= it.k || b.ctl->done) return;
+  kk_e11_body(b, it.k, it.delta, it.beta_zero, blockIdx.x);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) kk_gemm_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  if ((int)blockIdx.x * 16 >= it.k || (int)blockIdx.y * 16 >= it.k || b.ctl->done) return;
+  kk_gemm_body<MODE>(b, it.k, blockIdx.x, blockIdx.y);
+}
+
+// The products of the Newton-Schulz refresh and of M, N (see launch_kxk_stage).
+enum { NS_T1 = 0, NS_Z1 = 1, NS_T2 = 2, NS_Z2 = 3, NS_M = 4, NS_N = 5 };
+
+template <int OP>
+__global__ void __launch_bounds__(256) kk_ns_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  const int k = it.k;
+  if ((int)blockIdx.x * 16 >= k || (int)blockIdx.y * 16 >= k || b.ctl->done) return;
+  if (OP == NS_T1) kk_gemm_generic_body<0>(b.y1, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, blockIdx.x, blockIdx.y);
+  if (OP == NS_Z1) kk_gemm_generic_body<0>(b.zinv, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
+  if (OP == NS_T2) kk_gemm_generic_body<0>(b.y1, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, blockIdx.x, blockIdx.y);
+  if (OP == NS_Z2) kk_gemm_generic_body<0>(b.zinv2, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
+  if (OP == NS_M) kk_gemm_generic_body<0>(b.zinv, b.t1, nullptr, b.m, k, -1.0, 0.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
+  if (OP == NS_N) kk_gemm_generic_body<1>(b.zinv, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
+}
+
+void launch_kxk_stage_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
+  const int k = gd.max_k;
+  const int tpb = k >= 128 ? 128 : ((k + 31) / 32) * 32;
+  const dim3 gk(k, 1, gd.count);
+  const dim3 gt((k + 15) / 16, (k + 15) / 16, gd.count);
+  kk_prep_grouped_kernel<<<gk, tpb, 0, s>>>(items, parity);
+  kk_ns_grouped_kernel<NS_T1><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_grouped_kernel<NS_Z1><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_grouped_kernel<NS_T2><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_grouped_kernel<NS_Z2><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_grouped_kernel<NS_M><<<gt, 256, 0, s>>>(items, parity);
+  kk_gemm_grouped_kernel<KG_V1><<<gt, 256, 0, s>>>(items, parity);
+  kk_gemm_grouped_kernel<KG_W2><<<gt, 256, 0, s>>>(items, parity);
+  kk_e11_grouped_kernel<<<gk, tpb, 0, s>>>(items, parity);
+  kk_gemm_grouped_kernel<KG_YTE><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_grouped_kernel<NS_N><<<gt, 256, 0, s>>>(items, parity);
+  kk_gemm_grouped_kernel<KG_X1><<<gt, 256, 0, s>>>(items, parity);
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh--Ritz preprocessing (Section 3.3): with G = X^T X and S = X^T B X,
+// solve S V = G V D, then Z = X V has Z^T Z = I and Z^T B Z = D.  One CTA:
+// Cholesky G = L L^T, C = L^-1 S L^-T, cyclic Jacobi C = Q D Q^T (parallel
+// round-robin ordering: each round rotates k/2 disjoint pairs), Ritz pairs
+// ordered by |D| descending, V = L^-T Q.  C lives in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) rr_kernel(const double* __restrict__ gtop, const double* __restrict__ g2,
+                                                  int k, double* __restrict__ L, double* __restrict__ W,
+                                                  double* __restrict__ Q, double* __restrict__ V,
+                                                  double* __restrict__ lam, Control* ctl) {
+  extern __shared__ double C[];                  // k x k, column-major
+  __shared__ double red[32];
+  __shared__ int s_bad;
+  __shared__ int perm[kMaxK];
+  __shared__ double rot_c[kMaxK / 2 + 1], rot_s[kMaxK / 2 + 1];
+  __shared__ int rot_p[kMaxK / 2 + 1], rot_q[kMaxK / 2 + 1];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t kk = (int64_t)k * k;
+  if (tid == 0) s_bad = 0;
+  // G, S over all rows = leading block + the rest
+  for (int64_t e = tid; e < kk; e += nt) {
+    L[e] = gtop[e] + g2[e];
+    C[e] = gtop[kk + e] + g2[kk + e];
+  }
+  __syncthreads();
+  // symmetrise S (its rounding asymmetry carries no information)
+  for (int64_t e = tid; e < kk; e += nt) {
+    const int i = (int)(e % k), j = (int)(e / k);
+    if (i < j) {
+      const double v = 0.5 * (C[e] + C[j + (int64_t)i * k]);
+      C[e] = v;
+      C[j + (int64_t)i * k] = v;
+    }
+  }
+  // Cholesky of G (right-looking, lower triangle of L)
+  for (int p = 0; p < k; ++p) {
+    __syncthreads();
+    if (tid == 0) {
+      const double a = L[p + (int64_t)p * k];
+      if (!(a > 0.0) || !isfinite(a)) s_bad = 1;
+      L[p + (int64_t)p * k] = sqrt(a);
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const double lpp = L[p + (int64_t)p * k];
+    for (int i = p + 1 + tid; i < k; i += nt) L[i + (int64_t)p * k] /= lpp;
+    __syncthreads();
+    const int m = k - p - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = p + 1 + e % m, j = p + 1 + e / m;
+      if (i >= j) L[i + (int64_t)j * k] -= L[i + (int64_t)p * k] * L[j + (int64_t)p * k];
+    }
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) {
+      ctl->singular = 1;
+      ctl->status = EIGREF_E_SINGULAR_WY;
+      ctl->done = 1;
+    }
+    return;
+  }
+  // W = L^-1 S (one column per thread), then C = L^-1 W^T
+  for (int c = tid; c < k; c += nt)
+    for (int i = 0; i < k; ++i) {
+      double v = C[i + (int64_t)c * k];
+      for (int l = 0; l < i; ++l) v -= L[i + (int64_t)l * k] * W[l + (int64_t)c * k];
+      W[i + (int64_t)c * k] = v / L[i + (int64_t)i * k];
+    }
+  __syncthreads();
+  for (int c = tid; c < k; c += nt)
+    for (int i = 0; i < k; ++i) {
+      double v = W[c + (int64_t)i * k];                     // (W^T)(i, c)
+      for (int l = 0; l < i; ++l) v -= L[i + (int64_t)l * k] * C[l + (int64_t)c * k];
+      C[i + (int64_t)c * k] = v / L[i + (int64_t)i * k];
+    }
+  __syncthreads();
+  for (int64_t e = tid; e < kk; e += nt) {
+    const int i = (int)(e % k), j = (int)(e / k);
+    Q[e] = i == j ? 1.0 : 0.0;
+    if (i < j) {
+      const double v = 0.5 * (C[e] + C[j + (int64_t)i * k]);
+      C[e] = v;
+      C[j + (int64_t)i * k] = v;
+    }
+  }
+  // cyclic Jacobi, round-robin pairs over m = k rounded up to even players
+  const int m = k + (k & 1);
+  const int half = m / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    __syncthreads();
+    double off = 0.0, tot = 0.0;
+    for (int64_t e = tid; e < kk; e += nt) {
+      const double v = C[e] * C[e];
+      tot += v;
+      if (e % k != e / k) off += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    double offs = 0.0;
+    for (int q = 0; q < (nt >> 5); ++q) offs += red[q];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = tot;
+    __syncthreads();
+    double tots = 0.0;
+    for (int q = 0; q < (nt >> 5); ++q) tots += red[q];
+    if (!(offs > kUnitRoundoff * kUnitRoundoff * tots)) break;   // also leaves on NaN
+    for (int r = 0; r < m - 1; ++r) {
+      __syncthreads();
+      if (tid < half) {
+        int p, q;
+        if (tid == 0) {
+          p = r;
+          q = m - 1;
+        } else {
+          p = (r + tid) % (m - 1);
+          q = (r - tid + (m - 1)) % (m - 1);
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < k) {
+          const double apq = C[p + (int64_t)q * k];
+          if (apq != 0.0) {
+            const double th = (C[q + (int64_t)q * k] - C[p + (int64_t)p * k]) / (2.0 * apq);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        rot_p[tid] = p;
+        rot_q[tid] = q;
+        rot_c[tid] = c;
+        rot_s[tid] = sn;
+      }
+      __syncthreads();
+      // C <- C J (columns p, q), Q <- Q J
+      for (int e = tid; e < half * k; e += nt) {
+        const int a = e / k, i = e % k;
+        const int p = rot_p[a], q = rot_q[a];
+        if (q >= k) continue;
+        const double c = rot_c[a], sn = rot_s[a];
+        const double cp = C[i + (int64_t)p * k], cq = C[i + (int64_t)q * k];
+        C[i + (int64_t)p * k] = c * cp - sn * cq;
+        C[i + (int64_t)q * k] = sn * cp + c * cq;
+        const double qp = Q[i + (int64_t)p * k], qq = Q[i + (int64_t)q * k];
+        Q[i + (int64_t)p * k] = c * qp - sn * qq;
+        Q[i + (int64_t)q * k] = sn * qp + c * qq;
+      }
+      __syncthreads();
+      // C <- J^T C (rows p, q)
+      for (int e = tid; e < half * k; e += nt) {
+        const int a = e / k, j = e % k;
+        const int p = rot_p[a], q = rot_q[a];
+        if (q >= k) continue;
+        const double c = rot_c[a], sn = rot_s[a];
+        const double cp = C[p + (int64_t)j * k], cq = C[q + (int64_t)j * k];
+        C[p + (int64_t)j * k] = c * cp - sn * cq;
+        C[q + (int64_t)j * k] = sn * cp + c * cq;
+      }
+    }
+  }
+  __syncthreads();
+  // order by |eigenvalue| descending (stable)
+  if (tid == 0) {
+    for (int i = 0; i < k; ++i) perm[i] = i;
+    for (int i = 1; i < k; ++i) {
+      const int v = perm[i];
+      const double av = fabs(C[v + (int64_t)v * k]);
+      int j = i - 1;
+      while (j >= 0 && fabs(C[perm[j] + (int64_t)perm[j] * k]) < av) {
+        perm[j + 1] = perm[j];
+        --j;
+      }
+      perm[j + 1] = v;
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < k; j += nt) lam[j] = C[perm[j] + (int64_t)perm[j] * k];
+  // V = L^-T Q(:, perm): back substitution with the upper factor L^T
+  for (int c = tid; c < k; c += nt) {
+    const int pc = perm[c];
+    for (int i = k - 1; i >= 0; --i) {
+      double v = Q[i + (int64_t)pc * k];
+      for (int l = i + 1; l < k; ++l) v -= L[l + (int64_t)i * k] * V[l + (int64_t)c * k];
+      V[i + (int64_t)c * k] = v / L[i + (int64_t)i * k];
+    }
+  }
+}
+
+// Z = X V for row-major X, Z (n x k) and column-major V (k x k), V in shared memory.
+__global__ void __launch_bounds__(256) xv_kernel(const double* __restrict__ X, const double* __restrict__ V,
+                                                 double* __restrict__ Z, int64_t n, int k) {
+  extern __shared__ double Vs[];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Vs[e] = V[e];
+  __syncthreads();
+  const int64_t total = n * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    const int j = (int)(e % k);
+    const double* xr = X + i * k;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s = fma(xr[l], Vs[l + j * k], s);
+    Z[e] = s;
+  }
+}
+
+// Column signs that make each column's largest-magnitude entry (first on ties) positive.
+__global__ void colsign_kernel(const double* __restrict__ Z, int64_t n, int k, double* __restrict__ sg) {
+  const int lane = threadIdx.x & 31;
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (j >= k) return;
+  double best = -1.0, val = 0.0;
+  int64_t bi = INT64_MAX;
+  for (int64_t i = lane; i < n; i += 32) {
+    const double v = Z[i * k + j];
+    if (fabs(v) > best) { best = fabs(v); val = v; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; val = ov; bi = oi; }
+  }
+  if (lane == 0) sg[j] = val < 0.0 ? -1.0 : 1.0;
+}
+
+// Out = In diag(sg) (row-major n x k).
+__global__ void scale_cols_kernel(const double* __restrict__ In, double* __restrict__ Out, int64_t n, int k,
+                                  const double* __restrict__ sg) {
+  const int64_t total = n * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    Out[e] = In[e] * sg[e % k];
+}
+
+// V = (3 I - G) / 2 with G = G1 + G2 (leading block + rest): the first-order
+// symmetric (Loewdin) orthonormaliser, X V = X (X^T X)^{-1/2} + O(||G - I||^2).
+__global__ void loewdin_kernel(const double* __restrict__ gtop, const double* __restrict__ g2, int k,
+                               double* __restrict__ V) {
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kk; e += (int64_t)gridDim.x * blockDim.x) {
+    const double g = gtop[e] + g2[e];
+    V[e] = (e % k == e / k ? 1.5 : 0.0) - 0.5 * g;
+  }
+}
+
+void launch_reorthonormalise(const SweepBufs& b, int64_t n, int k, double* Xbuf, double* Zbuf, int64_t chunk_rows,
+                             int nchunks, cudaStream_t s) {
+  const int64_t total = n * k;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  for (int step = 0; step < 2; ++step) {   // each step squares ||X^T X - I||
+    launch_gram(Xbuf, Xbuf, k, k, n, chunk_rows, nchunks, b.gpart, b.g2, nullptr, s);
+    launch_gram(Xbuf, Xbuf, k, 0, k, k, 1, b.gpart, b.gtop, nullptr, s);
+    loewdin_kernel<<<(k * k + 255) / 256, 256, 0, s>>>(b.gtop, b.g2, k, b.f);
+    xv_kernel<<<grid, 256, sizeof(double) * (size_t)k * k, s>>>(Xbuf, b.f, Zbuf, n, k);
+    cudaMemcpyAsync(Xbuf, Zbuf, (size_t)total * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+}
+
+void launch_rayleigh_ritz(const SweepBufs& b, int64_t n, int k, double* Xbuf, double* Zbuf, cudaStream_t s) {
+  // G, S of X (gtop + g2) must be in place; b.lu, b.res, b.z are k x k scratch, b.f receives V
+  rr_kernel<<<1, 1024, sizeof(double) * (size_t)k * k, s>>>(b.gtop, b.g2, k, b.lu, b.res, b.z, b.f, b.d, b.ctl);
+  const int64_t total = n * k;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  xv_kernel<<<grid, 256, sizeof(double) * (size_t)k * k, s>>>(Xbuf, b.f, Zbuf, n, k);
+  colsign_kernel<<<(k * 32 + 255) / 256, 256, 0, s>>>(Zbuf, n, k, b.nu);
+  scale_cols_kernel<<<grid, 256, 0, s>>>(Zbuf, Xbuf, n, k, b.nu);
+}
+
 // Signs of Algorithm 2 on the leading k x k block of the caller's X
 // (column-major, ldx): sigma_j = -sign(q_jj), sign(0) = +1, unpivoted
 // elimination of Q - Sigma.  The shifted pivot |q_jj| + 1 is never zero.
-__global__ void __launch_bounds__(512) sign_fix_kernel(const double* __restrict__ X, int64_t ldx, int k,
+__global__ void __launch_bounds__(512) sign_fix_kernel(const double* __restrict__ X, int64_t rs, int64_t cs, int k,
                                                        double* __restrict__ sigma) {
   extern __shared__ double a[];
   const int tid = threadIdx.x;
   for (int64_t e = tid; e < (int64_t)k * k; e += blockDim.x) {
     int i = (int)(e % k), c = (int)(e / k);
-    a[e] = X[i + (int64_t)c * ldx];
+    a[e] = X[i * rs + (int64_t)c * cs];
   }
   __syncthreads();
   for (int p = 0; p < k; ++p) {
@@ -438,12 +797,26 @@ cudaError_t init_kxk_attributes() {
   cudaError_t e = cudaFuncSetAttribute(kk_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(double) * kMaxK * kMaxK));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * kMaxK * kMaxK));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(xv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * kMaxK * kMaxK));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sign_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(double) * kMaxK * kMaxK));
 }
 
 void launch_sign_fix(const double* X, int64_t ldx, int k, double* sigma, int* /*singular*/, cudaStream_t s) {
-  sign_fix_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(X, ldx, k, sigma);
+  sign_fix_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(X, 1, ldx, k, sigma);
+}
+
+void launch_sign_fix_rowmajor(const double* X, int k, double* sigma, cudaStream_t s) {
+  sign_fix_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(X, k, 1, k, sigma);
+}
+
+void launch_scale_cols(const double* In, double* Out, int64_t n, int k, const double* sg, cudaStream_t s) {
+  const int64_t total = n * k;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  scale_cols_kernel<<<grid, 256, 0, s>>>(In, Out, n, k, sg);
 }
 
 }  // namespace eigref

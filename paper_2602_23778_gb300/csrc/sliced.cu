@@ -172,37 +172,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // row), a B-side plane t 32 rows of a "column-scaled" operand; both are K-major
 // (the contraction index runs along the 128-byte rows TMA writes).
 // ---------------------------------------------------------------------------
-enum { MODE_PRODUCT = 0, MODE_GRAM = 1, MODE_UPDATE = 2 };
 
-struct MmaArgs {
-  int a_plane_rows;      // rows between consecutive A-side planes in the A tensor map
-  int b_plane_rows;      // rows between consecutive B-side planes in the B tensor maps
-  int kb_total;          // K blocks of 64 in the contraction
-  int ksplit;            // GRAM: number of K splits (blockIdx.z = job + 2 split)
-  const int* rowexp;     // exponents of the output rows (A side)
-  const int* colexp;     // exponents of the output columns (B side; GRAM job 0)
-  const int* colexp2;    // GRAM job 1: exponents of W's columns
-  int64_t m_valid;       // output rows that exist
-  int k;                 // output columns that exist
-  int row_begin;         // UPDATE: first row written (k)
-  const double* X;       // PRODUCT / UPDATE: row-major n x k
-  double* P;             // PRODUCT: row-major n x k
-  double shift;          // PRODUCT
-  double* ppart;         // PRODUCT with ksplit > 1: [ksplit][n x k] row-major partial products
-  double* gpart;         // GRAM: [2][ksplit][k * k] column-major partials
-  const double* W;       // UPDATE: row-major n x k
-  const double* d;       // UPDATE: Rayleigh quotients [k]
-  const double* dinv;    // UPDATE: 1 / d
-  double* Xn;            // UPDATE: row-major n x k
-  double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
-  const Control* ctl;
-  int* err;              // set to 1 on a timed-out wait
-};
 
+// One CTA's tile: output column block nb, row tile mb, K split / job zb.
 template <int S, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
-    sliced_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const __grid_constant__ CUtensorMap tmB2, MmaArgs g) {
+__device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                                const CUtensorMap* tmB2, const MmaArgs& g, int nb, int mb, int zb) {
   // one read of the stop flag per CTA: an aborting CTA of this grid may set it
   __shared__ int s_skip;
   __shared__ double s_colsum[2][4][kBN];            // UPDATE: per lane-group column sums
@@ -216,17 +191,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column blocks vary fastest, so the CTAs sharing A-side rows run together
-  const int nb = blockIdx.x;                         // output column block of 32
-  const int m0 = blockIdx.y * kBM;                   // output row tile
-  const int job = MODE == MODE_GRAM ? (int)(blockIdx.z & 1) : 0;
-  const int split = MODE == MODE_GRAM ? (int)(blockIdx.z >> 1) : (MODE == MODE_PRODUCT ? (int)blockIdx.z : 0);
+  const int m0 = mb * kBM;                           // output row tile
+  const int job = MODE == MODE_GRAM ? (zb & 1) : 0;
+  const int split = MODE == MODE_GRAM ? (zb >> 1) : (MODE == MODE_PRODUCT ? zb : 0);
   const int nsplit = MODE == MODE_UPDATE ? 1 : g.ksplit;
   const int kb_lo = (int)((int64_t)g.kb_total * split / nsplit);
   const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / nsplit);
   const int KB = kb_hi - kb_lo;                      // K blocks of this CTA
   const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
   constexpr int NBUF = (2 * S * kBN <= 512) ? 2 : 1; // TMEM accumulator sets (double-buffered if they fit)
-  const CUtensorMap* tB = job ? &tmB2 : &tmB;
+  const CUtensorMap* tB = job ? tmB2 : tmB;
   volatile int* abort_flag = &bars->abort;
 
   if (threadIdx.x == 0) {
@@ -260,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(tB) : "memory");
       int issued_a = 0, issued_x = 0;
       bool ok = true;
@@ -282,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, abort_flag);
           if (!ok) break;
           mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
-          tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
+          tma_load_2d(smem_u32(sa + as * kATile), tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
           ++issued_a;
           if (++as == kRA) {
             as = 0;
@@ -433,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (MODE == MODE_PRODUCT) {
         if (live) {
           if (nsplit == 1)
-            g.P[row * g.k + col] = w - g.shift * g.X[row * g.k + col];
+            g.P[row * g.k + col] = w - g.shift * g.Xs[row * g.k + col];
           else
             g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = w;
         }
@@ -475,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (col < g.k) {
       const double v = s_colsum[which][0][cc] + s_colsum[which][1][cc] + s_colsum[which][2][cc] +
                        s_colsum[which][3][cc];
-      g.upart[(int64_t)blockIdx.y * 2 * g.k + which * g.k + col] = v;
+      g.upart[(int64_t)mb * 2 * g.k + which * g.k + col] = v;
     }
   }
   if (bars->abort && threadIdx.x == 0) {
@@ -490,6 +464,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
   }
+}
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    sliced_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ CUtensorMap tmB2, MmaArgs g) {
+  sliced_mma_body<S, MODE>(&tmA, &tmB, &tmB2, g, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Many problems' tiles in one launch (a batch).  The tensor maps travel in
+// the kernel's parameter block, as for the single-problem kernel; CTA c
+// takes tile c - cta_begin[t] of task t, ordered column block fastest, then
+// row tile, then split.
+constexpr int kGroupMax = 40;
+struct GroupMma {
+  CUtensorMap tmA[kGroupMax];
+  CUtensorMap tmB[kGroupMax];
+  CUtensorMap tmB2[kGroupMax];
+  MmaArgs args[kGroupMax];
+  int cta_begin[kGroupMax + 1];
+  int gx[kGroupMax], gy[kGroupMax];
+  int count;
+};
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const __grid_constant__ GroupMma p) {
+  const int c = blockIdx.x;
+  int t = 0;
+  while (t + 1 < p.count && c >= p.cta_begin[t + 1]) ++t;
+  const int local = c - p.cta_begin[t];
+  const int gx = p.gx[t], gy = p.gy[t];
+  sliced_mma_body<S, MODE>(&p.tmA[t], &p.tmB[t], &p.tmB2[t], p.args[t], local % gx, (local / gx) % gy,
+                           local / (gx * gy));
 }
 
 // ---------------------------------------------------------------------------
@@ -572,40 +579,43 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
 
 // Column maxima of a strided n x k operand (element (l, j) at Y[l rs + j cs])
 // as non-negative double bit patterns; NaN survives (fmax would drop it).
-__global__ void colmax_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
-                              unsigned long long* __restrict__ cmax, const Control* ctl) {
-  if (ctl && ctl->done) return;
-  const int j = threadIdx.x % k;   // blockDim.x is a multiple of k
-  const int rpb = blockDim.x / k;
+__device__ __forceinline__ void colmax_body(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
+                                            unsigned long long* __restrict__ cmax, int bx, int nbx) {
+  const int rpb = blockDim.x / k;  // threads beyond rpb k idle
+  if ((int)threadIdx.x >= rpb * k) return;
+  const int j = threadIdx.x % k;
   double m = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / k; i < rows; i += (int64_t)gridDim.x * rpb) {
+  for (int64_t i = bx * (int64_t)rpb + threadIdx.x / k; i < rows; i += (int64_t)nbx * rpb) {
     const double v = fabs(Y[i * rs + j * cs]);
     m = (v > m || v != v) ? v : m;
   }
   atomicMax(cmax + j, (unsigned long long)__double_as_longlong(m));
 }
 
+__global__ void colmax_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
+                              unsigned long long* __restrict__ cmax, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  colmax_body(Y, rows, k, rs, cs, cmax, blockIdx.x, gridDim.x);
+}
+
 // Column digit planes: planes[(t kp + j) K + l] (BF16) for column j of the
 // strided operand, scaled by its column exponent.  A CTA takes 64 rows x 32
 // columns through shared memory, so the BF16 writes are contiguous.
 template <int S>
-__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs,
-                                                         int64_t cs, int K, int kp,
-                                                         const unsigned long long* __restrict__ cmax,
-                                                         __nv_bfloat16* __restrict__ planes, int* __restrict__ colexp,
-                                                         const Control* ctl) {
-  if (ctl && ctl->done) return;
+__device__ __forceinline__ void slice_cols_body(const double* __restrict__ Y, int64_t rows, int k, int64_t rs,
+                                                int64_t cs, int K, int kp, const unsigned long long* __restrict__ cmax,
+                                                __nv_bfloat16* __restrict__ planes, int* __restrict__ colexp, int bx,
+                                                int cb) {
   __shared__ double tile[64][33];
   __shared__ int fexp[32];
-  const int l0 = blockIdx.x * 64;
-  const int cb = blockIdx.y;
+  const int l0 = bx * 64;
   const int tid = threadIdx.x;
   if (tid < 32) {
     const int j = cb * 32 + tid;
     const double cm = j < k ? __longlong_as_double((long long)cmax[j]) : 0.0;
     const int f = row_exponent(cm);
     fexp[tid] = isfinite(cm) ? f : 0;
-    if (blockIdx.x == 0 && j < k) colexp[j] = isfinite(cm) ? f : kNonFinite;
+    if (bx == 0 && j < k) colexp[j] = isfinite(cm) ? f : kNonFinite;
   }
   for (int e = tid; e < 64 * 32; e += 256) {
     const int rr = e >> 5, jj = e & 31;
@@ -629,15 +639,23 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
   }
 }
 
+template <int S>
+__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs,
+                                                         int64_t cs, int K, int kp,
+                                                         const unsigned long long* __restrict__ cmax,
+                                                         __nv_bfloat16* __restrict__ planes, int* __restrict__ colexp,
+                                                         const Control* ctl) {
+  if (ctl && ctl->done) return;
+  slice_cols_body<S>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, blockIdx.x, blockIdx.y);
+}
+
 // Row digit planes of a row-major n x k operand: planes[(s n_pad + i) K + l],
 // one exponent per row.  One warp per row; lane c takes elements 8c..8c+7.
 template <int S>
-__global__ void slice_rows_kernel(const double* __restrict__ Y, int64_t n, int k, int n_pad, int K,
-                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ rowexp, const Control* ctl) {
-  if (ctl && ctl->done) return;
+__device__ __forceinline__ void slice_rows_body(const double* __restrict__ Y, int64_t n, int k, int n_pad, int K,
+                                                __nv_bfloat16* __restrict__ planes, int* __restrict__ rowexp,
+                                                int64_t wid, int64_t nw) {
   const int lane = threadIdx.x & 31;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t plane = (int64_t)n_pad * K;
   for (int64_t i = wid; i < n_pad; i += nw) {
     double amax = 0.0;
@@ -669,6 +687,78 @@ __global__ void slice_rows_kernel(const double* __restrict__ Y, int64_t n, int k
       }
     }
   }
+}
+
+template <int S>
+__global__ void slice_rows_kernel(const double* __restrict__ Y, int64_t n, int k, int n_pad, int K,
+                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ rowexp, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  slice_rows_body<S>(Y, n, k, n_pad, K, planes, rowexp, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                     ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// ---- the same slicing for a batch: blockIdx.z selects the problem ----
+enum { OPD_XCOLS = 0, OPD_PCOLS = 1, OPD_FCOLS = 2 };
+
+__global__ void zero_cmax_grouped_kernel(const GroupItem* __restrict__ items) {
+  const GroupItem& it = items[blockIdx.x];
+  if (it.b[0].ctl->done) return;
+  for (int j = threadIdx.x; j < it.k; j += blockDim.x) it.x_cmax[j] = it.p_cmax[j] = it.f_cmax[j] = 0ull;
+}
+
+// Operand OP of problem `it` in sweep parity `parity`: rows, row / column strides.
+__device__ __forceinline__ const double* grouped_operand(const GroupItem& it, int parity, int op, int64_t* rows,
+                                                        int64_t* rs, int64_t* cs, unsigned long long** cmax,
+                                                        __nv_bfloat16** planes, int** colexp, int* K) {
+  const SweepBufs& b = it.b[parity];
+  if (op == OPD_FCOLS) {   // F is k x k column-major: element (l, j) at F[l + j k]
+    *rows = it.k; *rs = 1; *cs = it.k; *cmax = it.f_cmax;
+    *planes = static_cast<__nv_bfloat16*>(it.f_planes); *colexp = it.f_colexp; *K = it.kr;
+    return b.f;
+  }
+  *rows = it.n; *rs = it.k; *cs = 1;
+  *K = it.n_pad;
+  if (op == OPD_XCOLS) {
+    *cmax = it.x_cmax; *planes = static_cast<__nv_bfloat16*>(it.x_planes); *colexp = it.x_colexp;
+    return b.x;
+  }
+  *cmax = it.p_cmax; *planes = static_cast<__nv_bfloat16*>(it.p_planes); *colexp = it.p_colexp;
+  return b.p;
+}
+
+template <int OP>
+__global__ void colmax_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  if (it.b[0].ctl->done) return;
+  int64_t rows, rs, cs;
+  unsigned long long* cmax;
+  __nv_bfloat16* planes;
+  int* colexp;
+  int K;
+  const double* Y = grouped_operand(it, parity, OP, &rows, &rs, &cs, &cmax, &planes, &colexp, &K);
+  colmax_body(Y, rows, it.k, rs, cs, cmax, blockIdx.x, gridDim.x);
+}
+
+template <int S, int OP>
+__global__ void __launch_bounds__(256) slice_cols_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  int64_t rows, rs, cs;
+  unsigned long long* cmax;
+  __nv_bfloat16* planes;
+  int* colexp;
+  int K;
+  const double* Y = grouped_operand(it, parity, OP, &rows, &rs, &cs, &cmax, &planes, &colexp, &K);
+  if ((int)blockIdx.x * 64 >= K || (int)blockIdx.y * 32 >= it.k_pad || it.b[0].ctl->done) return;
+  slice_cols_body<S>(Y, rows, it.k, rs, cs, K, it.k_pad, cmax, planes, colexp, blockIdx.x, blockIdx.y);
+}
+
+template <int S>
+__global__ void slice_rows_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  if (it.b[0].ctl->done) return;
+  slice_rows_body<S>(it.b[parity].x, it.n, it.k, it.n_pad, it.kr, static_cast<__nv_bfloat16*>(it.xr_planes),
+                     it.xr_rowexp, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                     ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 // P = sum of the split partial products - shift X (fixed order).
@@ -762,6 +852,15 @@ cudaError_t init_sliced_attributes() {
                              sl::kSmemBytes);                                                                      \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_UPDATE>,                                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_PRODUCT>,                                \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_GRAM>,                                   \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_UPDATE>,                                 \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
   EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
   EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
@@ -926,6 +1025,112 @@ static void launch_mma(int S, dim3 grid, const CUtensorMap& a, const CUtensorMap
 #undef EIGREF_CALL_MMA
 }
 
+static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
+  const dim3 grid((unsigned)t.gx, (unsigned)t.gy, (unsigned)t.gz);
+  if (mode == sl::MODE_PRODUCT) launch_mma<sl::MODE_PRODUCT>(S, grid, t.a, t.b, t.b2, t.g, s);
+  else if (mode == sl::MODE_GRAM) launch_mma<sl::MODE_GRAM>(S, grid, t.a, t.b, t.b2, t.g, s);
+  else launch_mma<sl::MODE_UPDATE>(S, grid, t.a, t.b, t.b2, t.g, s);
+}
+
+MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Control* ctl, const double* Xs,
+                              bool b_from_p) const {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  MmaTask t;
+  t.a = *reinterpret_cast<const CUtensorMap*>(tmA_);
+  t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(b_from_p ? tmP_ : tmX_);
+  sl::MmaArgs& g = t.g;
+  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g.a_plane_rows = n_pad_;
+  g.b_plane_rows = k_pad_;
+  g.kb_total = n_pad_ / sl::kBK;
+  g.rowexp = reinterpret_cast<const int*>(ws_ + L.rowexp);
+  g.colexp = reinterpret_cast<const int*>(ws_ + (b_from_p ? L.p_colexp : L.x_colexp));
+  g.m_valid = n_;
+  g.k = k_;
+  g.X = X;
+  g.Xs = Xs ? Xs : X;
+  g.P = P;
+  g.shift = shift;
+  g.ksplit = psplit_;
+  g.ppart = reinterpret_cast<double*>(ws_ + L.ppart);
+  t.gx = k_pad_ / sl::kBN;
+  t.gy = n_pad_ / sl::kBM;
+  t.gz = psplit_;
+  return t;
+}
+
+MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  MmaTask t;
+  t.a = *reinterpret_cast<const CUtensorMap*>(tmXA_);
+  t.b = *reinterpret_cast<const CUtensorMap*>(tmX_);
+  t.b2 = *reinterpret_cast<const CUtensorMap*>(tmP_);
+  sl::MmaArgs& g = t.g;
+  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g.a_plane_rows = k_pad_;
+  g.b_plane_rows = k_pad_;
+  g.kb_total = n_pad_ / sl::kBK;
+  g.ksplit = ksplit_;
+  g.rowexp = reinterpret_cast<const int*>(ws_ + L.x_colexp);   // rows of G, S = columns of X
+  g.colexp = reinterpret_cast<const int*>(ws_ + L.x_colexp);
+  g.colexp2 = reinterpret_cast<const int*>(ws_ + L.p_colexp);
+  g.m_valid = k_;
+  g.k = k_;
+  g.gpart = part ? part : reinterpret_cast<double*>(ws_ + L.gpart);
+  t.gx = k_pad_ / sl::kBN;
+  t.gy = 1;
+  t.gz = 2 * ksplit_;
+  return t;
+}
+
+MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, const double* dinv, double* Xn,
+                             double* upart, const Control* ctl) const {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  MmaTask t;
+  t.a = *reinterpret_cast<const CUtensorMap*>(tmXR_);
+  t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(tmF_);
+  sl::MmaArgs& g = t.g;
+  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g.a_plane_rows = n_pad_;
+  g.b_plane_rows = k_pad_;
+  g.kb_total = kr_ / sl::kBK;
+  g.rowexp = reinterpret_cast<const int*>(ws_ + L.xr_rowexp);
+  g.colexp = reinterpret_cast<const int*>(ws_ + L.f_colexp);
+  g.m_valid = n_;
+  g.k = k_;
+  g.row_begin = k_;
+  g.X = X;
+  g.W = W;
+  g.d = d;
+  g.dinv = dinv;
+  g.Xn = Xn;
+  g.upart = upart;
+  t.gx = k_pad_ / sl::kBN;
+  t.gy = n_pad_ / sl::kBM;
+  t.gz = 1;
+  return t;
+}
+
+void SlicedA::fill_group_item(GroupItem* it) const {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  it->n_pad = n_pad_;
+  it->k_pad = k_pad_;
+  it->kr = kr_;
+  it->ksplit = ksplit_;
+  it->x_planes = ws_ + L.x_planes;
+  it->p_planes = ws_ + L.p_planes;
+  it->xr_planes = ws_ + L.xr_planes;
+  it->f_planes = ws_ + L.f_planes;
+  it->x_colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
+  it->p_colexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
+  it->xr_rowexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
+  it->f_colexp = reinterpret_cast<int*>(ws_ + L.f_colexp);
+  it->x_cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
+  it->p_cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
+  it->f_cmax = reinterpret_cast<unsigned long long*>(ws_ + L.f_cmax);
+  it->sgpart = reinterpret_cast<double*>(ws_ + L.gpart);
+}
+
 int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
                      cudaEvent_t ev1, unsigned ev_flags) {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
@@ -936,31 +1141,48 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
   sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, n_pad_, k_pad_, cmax, xp, colexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_X)
 #undef EIGREF_CALL_SLICE_X
-  sl::MmaArgs g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
-  g.a_plane_rows = n_pad_;
-  g.b_plane_rows = k_pad_;
-  g.kb_total = n_pad_ / sl::kBK;
-  g.rowexp = reinterpret_cast<const int*>(ws_ + L.rowexp);
-  g.colexp = colexp;
-  g.m_valid = n_;
-  g.k = k_;
-  g.X = X;
-  g.P = P;
-  g.shift = shift;
-  g.ksplit = psplit_;
-  g.ppart = reinterpret_cast<double*>(ws_ + L.ppart);
-  dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM), (unsigned)psplit_);
+  const MmaTask t = product_task(X, P, shift, ctl);
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
-  const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(tmA_);
-  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
-  launch_mma<sl::MODE_PRODUCT>(slices_, grid, ma, mx, mx, g, s);
+  launch_task(slices_, sl::MODE_PRODUCT, t, s);
   if (psplit_ > 1) {
     const int64_t total = n_ * k_;
     const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-    sl::product_reduce_kernel<<<rg, 256, 0, s>>>(g.ppart, psplit_, X, P, total, shift, ctl);
+    sl::product_reduce_kernel<<<rg, 256, 0, s>>>(t.g.ppart, psplit_, X, P, total, shift, ctl);
   }
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
   return psplit_ > 1 ? 4 : 3;
+}
+
+int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, const Control* ctl, cudaStream_t s,
+                        cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags) {
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const int64_t total = n_ * k_;
+  const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  // T = A X: X's column planes in the X slot (kept for gram())
+  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  auto* xmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
+  int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
+#define EIGREF_CALL_SLICE_X2(S_) \
+  sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, n_pad_, k_pad_, xmax, xp, xexp, ctl, s)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_X2)
+#undef EIGREF_CALL_SLICE_X2
+  if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
+  const MmaTask t1 = product_task(X, T, 0.0, ctl);
+  launch_task(slices_, sl::MODE_PRODUCT, t1, s);
+  if (psplit_ > 1) sl::product_reduce_kernel<<<rg, 256, 0, s>>>(t1.g.ppart, psplit_, X, T, total, 0.0, ctl);
+  // P = A T - alpha X: T's column planes in the W slot (gram() re-slices W there)
+  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* pmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
+  int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
+#define EIGREF_CALL_SLICE_T(S_) \
+  sl::launch_slice_cols<S_>(T, n_, k_, k_, 1, n_pad_, k_pad_, pmax, pp, pexp, ctl, s)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_T)
+#undef EIGREF_CALL_SLICE_T
+  const MmaTask t2 = product_task(T, P, alpha, ctl, X, true);
+  launch_task(slices_, sl::MODE_PRODUCT, t2, s);
+  if (psplit_ > 1) sl::product_reduce_kernel<<<rg, 256, 0, s>>>(t2.g.ppart, psplit_, X, P, total, alpha, ctl);
+  if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
+  return psplit_ > 1 ? 10 : 8;
 }
 
 int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s) {
@@ -972,23 +1194,9 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
   sl::launch_slice_cols<S_>(P, n_, k_, k_, 1, n_pad_, k_pad_, cmax, pp, pexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_P)
 #undef EIGREF_CALL_SLICE_P
-  sl::MmaArgs g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
-  g.a_plane_rows = k_pad_;
-  g.b_plane_rows = k_pad_;
-  g.kb_total = n_pad_ / sl::kBK;
-  g.ksplit = ksplit_;
-  g.rowexp = reinterpret_cast<const int*>(ws_ + L.x_colexp);   // rows of G, S = columns of X
-  g.colexp = reinterpret_cast<const int*>(ws_ + L.x_colexp);
-  g.colexp2 = pexp;
-  g.m_valid = k_;
-  g.k = k_;
-  g.gpart = part ? part : reinterpret_cast<double*>(ws_ + L.gpart);
-  dim3 grid((unsigned)(k_pad_ / sl::kBN), 1u, (unsigned)(2 * ksplit_));
-  const CUtensorMap& mxa = *reinterpret_cast<const CUtensorMap*>(tmXA_);
-  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
-  const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
-  launch_mma<sl::MODE_GRAM>(slices_, grid, mxa, mx, mp, g, s);
-  launch_gram_reduce(g.gpart, k_, ksplit_, out, ctl, s);
+  const MmaTask t = gram_task(part, ctl);
+  launch_task(slices_, sl::MODE_GRAM, t, s);
+  launch_gram_reduce(t.g.gpart, k_, ksplit_, out, ctl, s);
   return 6;
 }
 
@@ -1006,26 +1214,80 @@ int SlicedA::update(const double* X, const double* W, const double* F, const dou
   sl::launch_slice_cols<S_>(F, k_, k_, 1, k_, kr_, k_pad_, fmax_, fp, fexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_UPD)
 #undef EIGREF_CALL_SLICE_UPD
-  sl::MmaArgs g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
-  g.a_plane_rows = n_pad_;
-  g.b_plane_rows = k_pad_;
-  g.kb_total = kr_ / sl::kBK;
-  g.rowexp = xrexp;
-  g.colexp = fexp;
-  g.m_valid = n_;
-  g.k = k_;
-  g.row_begin = k_;
-  g.X = X;
-  g.W = W;
-  g.d = d;
-  g.dinv = dinv;
-  g.Xn = Xn;
-  g.upart = upart;
-  dim3 grid((unsigned)(k_pad_ / sl::kBN), (unsigned)(n_pad_ / sl::kBM));
-  const CUtensorMap& mxr = *reinterpret_cast<const CUtensorMap*>(tmXR_);
-  const CUtensorMap& mf = *reinterpret_cast<const CUtensorMap*>(tmF_);
-  launch_mma<sl::MODE_UPDATE>(slices_, grid, mxr, mf, mf, g, s);
+  const MmaTask t = update_task(X, W, d, dinv, Xn, upart, ctl);
+  launch_task(slices_, sl::MODE_UPDATE, t, s);
   return 6;
+}
+
+// ---- grouped launches (a batch) ----
+template <int MODE>
+static void launch_mma_group(int S, const sl::GroupMma& p, int ctas, cudaStream_t s) {
+#define EIGREF_CALL_MMA_G(S_) \
+  sl::sliced_mma_grouped_kernel<S_, MODE><<<ctas, sl::kThreads, sl::kSmemBytes, s>>>(p)
+  EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_MMA_G)
+#undef EIGREF_CALL_MMA_G
+}
+
+void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s) {
+  static sl::GroupMma p;   // host staging of the parameter block (copied at launch)
+  for (int t0 = 0; t0 < count; t0 += sl::kGroupMax) {
+    const int nt = std::min(sl::kGroupMax, count - t0);
+    memset(&p, 0, sizeof(p));
+    int ctas = 0;
+    for (int i = 0; i < nt; ++i) {
+      const MmaTask& t = tasks[t0 + i];
+      p.tmA[i] = t.a;
+      p.tmB[i] = t.b;
+      p.tmB2[i] = t.b2;
+      p.args[i] = t.g;
+      p.gx[i] = t.gx;
+      p.gy[i] = t.gy;
+      p.cta_begin[i] = ctas;
+      ctas += t.gx * t.gy * t.gz;
+    }
+    p.cta_begin[nt] = ctas;
+    p.count = nt;
+    if (mode == sl::MODE_PRODUCT) launch_mma_group<sl::MODE_PRODUCT>(S, p, ctas, s);
+    else if (mode == sl::MODE_GRAM) launch_mma_group<sl::MODE_GRAM>(S, p, ctas, s);
+    else launch_mma_group<sl::MODE_UPDATE>(S, p, ctas, s);
+  }
+}
+
+template <int S>
+static void slice_grouped(int op, const GroupItem* items, const GroupDims& gd, int max_n_pad, int parity,
+                          cudaStream_t s) {
+  const int kp = (gd.max_k + 31) / 32;
+  const int rpb = 256 / gd.max_k > 0 ? 256 / gd.max_k : 1;
+  (void)rpb;
+  switch (op) {
+    case SLICE_ZERO_MAX:
+      sl::zero_cmax_grouped_kernel<<<gd.count, 128, 0, s>>>(items);
+      break;
+    case SLICE_X_COLS:
+      sl::colmax_grouped_kernel<sl::OPD_XCOLS><<<dim3(16, 1, gd.count), 256, 0, s>>>(items, parity);
+      sl::slice_cols_grouped_kernel<S, sl::OPD_XCOLS><<<dim3(max_n_pad / 64, kp, gd.count), 256, 0, s>>>(items, parity);
+      break;
+    case SLICE_P_COLS:
+      sl::colmax_grouped_kernel<sl::OPD_PCOLS><<<dim3(16, 1, gd.count), 256, 0, s>>>(items, parity);
+      sl::slice_cols_grouped_kernel<S, sl::OPD_PCOLS><<<dim3(max_n_pad / 64, kp, gd.count), 256, 0, s>>>(items, parity);
+      break;
+    case SLICE_F_COLS: {
+      const int kr = (gd.max_k + 63) / 64 * 64;
+      sl::colmax_grouped_kernel<sl::OPD_FCOLS><<<dim3(1, 1, gd.count), 256, 0, s>>>(items, parity);
+      sl::slice_cols_grouped_kernel<S, sl::OPD_FCOLS><<<dim3(kr / 64, kp, gd.count), 256, 0, s>>>(items, parity);
+      break;
+    }
+    default:
+      sl::slice_rows_grouped_kernel<S><<<dim3(16, 1, gd.count), 256, 0, s>>>(items, parity);
+      break;
+  }
+}
+
+void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims& gd, int max_n_pad, int parity,
+                          cudaStream_t s) {
+#define EIGREF_CALL_SLICE_G(S_) slice_grouped<S_>(op, items, gd, max_n_pad, parity, s)
+  EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_SLICE_G)
+#undef EIGREF_CALL_SLICE_G
 }
 
 int SlicedA::update_grid() const { return n_pad_ / sl::kBM; }

@@ -3,12 +3,58 @@
 // X^T W, and the row update X - X F.  See sliced.cu.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "common.cuh"
 
 namespace eigref {
+
+namespace sl {
+enum { MODE_PRODUCT = 0, MODE_GRAM = 1, MODE_UPDATE = 2 };
+
+// Arguments of the tensor-core kernel (one problem, one mode).
+struct MmaArgs {
+  int a_plane_rows;      // rows between consecutive A-side planes in the A tensor map
+  int b_plane_rows;      // rows between consecutive B-side planes in the B tensor maps
+  int kb_total;          // K blocks of 64 in the contraction
+  int ksplit;            // GRAM: number of K splits (blockIdx.z = job + 2 split)
+  const int* rowexp;     // exponents of the output rows (A side)
+  const int* colexp;     // exponents of the output columns (B side; GRAM job 0)
+  const int* colexp2;    // GRAM job 1: exponents of W's columns
+  int64_t m_valid;       // output rows that exist
+  int k;                 // output columns that exist
+  int row_begin;         // UPDATE: first row written (k)
+  const double* X;       // PRODUCT / UPDATE: row-major n x k
+  double* P;             // PRODUCT: row-major n x k
+  double shift;          // PRODUCT
+  const double* Xs;      // PRODUCT: operand of the shift term (row-major n x k)
+  double* ppart;         // PRODUCT with ksplit > 1: [ksplit][n x k] row-major partial products
+  double* gpart;         // GRAM: [2][ksplit][k * k] column-major partials
+  const double* W;       // UPDATE: row-major n x k
+  const double* d;       // UPDATE: Rayleigh quotients [k]
+  const double* dinv;    // UPDATE: 1 / d
+  double* Xn;            // UPDATE: row-major n x k
+  double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
+  const Control* ctl;
+  int* err;              // set to 1 on a timed-out wait
+};
+}  // namespace sl
+
+// One launch's worth of tensor-core work for one problem: its tensor maps,
+// arguments and tile grid (gx column blocks, gy row tiles, gz splits/jobs).
+struct MmaTask {
+  CUtensorMap a, b, b2;
+  sl::MmaArgs g;
+  int gx, gy, gz;
+};
+
+// Grouped launches of the split form over a batch (all problems share S).
+void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s);
+enum { SLICE_X_COLS = 0, SLICE_P_COLS = 1, SLICE_F_COLS = 2, SLICE_X_ROWS = 3, SLICE_ZERO_MAX = 4 };
+void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims& gd, int max_n_pad, int parity,
+                          cudaStream_t s);
 
 cudaError_t init_sliced_attributes();
 
@@ -29,6 +75,10 @@ class SlicedA {
   // kernel; returns the kernels launched.
   int product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s,
               cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, unsigned ev_flags = 0);
+  // P = A (A X) - alpha X (the shifted square of Section 5.2) through T; X's
+  // planes stay in place for gram().
+  int product_sq(const double* X, double* T, double* P, double alpha, const Control* ctl, cudaStream_t s,
+                 cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, unsigned ev_flags = 0);
   // out[0] = X^T X, out[1] = X^T P (k x k column-major, all n rows), with X the
   // operand of the last product(); part = split-K scratch (null: internal).
   int gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s);
@@ -37,6 +87,16 @@ class SlicedA {
   int update(const double* X, const double* W, const double* F, const double* d, const double* dinv, double* Xn,
              double* upart, const Control* ctl, cudaStream_t s);
   int update_grid() const;
+  // The same three stages as launchable tasks (the batch groups them), and the
+  // fields of this problem's GroupItem that describe its planes.
+  // b_from_p: the B operand is the planes sliced into the W slot (the second
+  // product of the shifted square); Xs: operand of the shift term (default X).
+  MmaTask product_task(const double* X, double* P, double shift, const Control* ctl, const double* Xs = nullptr,
+                       bool b_from_p = false) const;
+  MmaTask gram_task(double* part, const Control* ctl) const;
+  MmaTask update_task(const double* X, const double* W, const double* d, const double* dinv, double* Xn,
+                      double* upart, const Control* ctl) const;
+  void fill_group_item(GroupItem* it) const;
   // 1 if a bounded wait inside a tensor-core kernel gave up (synchronises s).
   int timed_out(cudaStream_t s) const;
   // Tensor-core flops one product executes (all digit pairs, padded sizes).

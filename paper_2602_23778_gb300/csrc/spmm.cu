@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __res
                                                             const int32_t* __restrict__ ci,
                                                             const double* __restrict__ val,
                                                             const double* __restrict__ X, double* __restrict__ P,
-                                                            int64_t n, int k, double shift, const Control* ctl) {
+                                                            int64_t n, int k, double shift,
+                                                            const double* __restrict__ Xs, const Control* ctl) {
   if (ctl && ctl->done) return;
   const int lane = threadIdx.x % LPR;
   const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __res
         ay = fma(a, x.y, ay);
       }
       if (SHIFT) {
-        const double2 xi = __ldg(X2 + i * k2 + c2);
+        const double2 xi = __ldg(reinterpret_cast<const double2*>(Xs) + i * k2 + c2);
         ax = fma(-shift, xi.x, ax);
         ay = fma(-shift, xi.y, ay);
       }
@@ -92,7 +93,8 @@ __global__ void __launch_bounds__(256) spmm_csr_scalar_kernel(const int32_t* __r
                                                               const int32_t* __restrict__ ci,
                                                               const double* __restrict__ val,
                                                               const double* __restrict__ X, double* __restrict__ P,
-                                                              int64_t n, int k, double shift, const Control* ctl) {
+                                                              int64_t n, int k, double shift,
+                                                              const double* __restrict__ Xs, const Control* ctl) {
   if (ctl && ctl->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -102,21 +104,22 @@ __global__ void __launch_bounds__(256) spmm_csr_scalar_kernel(const int32_t* __r
     for (int c = lane; c < k; c += 32) {
       double acc = 0.0;
       for (int32_t p = b; p < e; ++p) acc = fma(val[p], X[(int64_t)ci[p] * k + c], acc);
-      P[i * k + c] = acc - shift * X[i * k + c];
+      P[i * k + c] = acc - shift * Xs[i * k + c];
     }
   }
 }
 
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
-                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s) {
+                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s, const double* Xs) {
+  if (!Xs) Xs = X;
   const int grid = 152 * 8;  // 8 resident CTAs of 256 threads per SM, grid-stride over rows
   if ((k & 1) == 0) {
     const int k2 = k >> 1;
 #define EIGREF_SPMM(L)                                                                                       \
   if (shift != 0.0)                                                                                         \
-    spmm_csr_vec2_kernel<L, true><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);                 \
+    spmm_csr_vec2_kernel<L, true><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl);             \
   else                                                                                                      \
-    spmm_csr_vec2_kernel<L, false><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
+    spmm_csr_vec2_kernel<L, false><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl);
     if (k2 <= 2) {
       EIGREF_SPMM(2)
     } else if (k2 <= 4) {
@@ -130,7 +133,7 @@ void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, co
     }
 #undef EIGREF_SPMM
   } else {
-    spmm_csr_scalar_kernel<<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, ctl);
+    spmm_csr_scalar_kernel<<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl);
   }
 }
 

@@ -127,3 +127,18 @@ def test_batch_rejects_host_memory_and_leaves_x(eig, problems):
     with pytest.raises(pkg.EigrefError):
         eig.refine_batched(items, max_iters=2)
     assert np.array_equal(host(items[0]["X"]), x_before)
+
+
+def test_split_batch_spanning_several_launch_groups(eig):
+    """More problems than one grouped tensor-core launch holds (40), with
+    k = 1 and odd sizes among them: every problem still matches the oracle."""
+    shapes = [(96 + 37 * (i % 7), 1 + (5 * i) % 23) for i in range(45)]
+    ps = [C.config5_problem(i, n, k, seed=5200) for i, (n, k) in enumerate(shapes)]
+    items = batch_inputs(ps)
+    st, reps = eig.refine_batched(items, max_iters=2, precision="bf16")
+    assert st == 0
+    for p, it, rep in zip(ps, items, reps):
+        Xo, ro = R.refine(R.dense_operator(p.A, p.shift), p.X0, p.normA, p.shift, max_iters=2)
+        tol = sweep_tol((1 + p.n ** 0.5 * 2.0 ** -56 / U) * (p.normA + abs(p.shift)), p.min_gap)
+        assert rep["iterations"] == 2
+        assert rel_diff(host(it["X"]), Xo) <= tol, (p.n, p.k)

@@ -1,0 +1,154 @@
+"""The method's variants on the GPU against the oracle: Rayleigh--Ritz
+preprocessing (Section 3.3), convergence judged on the leading k of K
+columns (Section 4.1), the shifted square for the smallest |eigenvalues|
+(Section 5.2) and the optional reorthogonalisation (Section 3.1.3)."""
+import numpy as np
+import pytest
+
+from oracle import refine as R
+from tests.gpu_util import dev, host, rel_diff, sweep_tol, U
+from workloads import configs as C
+from workloads import laplacian as LP
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eig():
+    import paper_2602_23778_gb300 as pkg
+    h = pkg.Handle(0)
+    yield h
+    h.close()
+
+
+def spread_problem(n=300, k=6, seed=11, noise=1e-7):
+    lam = np.linspace(-1.0, 1.0, n)
+    lam[np.argsort(-np.abs(lam))[:k]] = np.array([1.0, -0.95, 0.9, -0.85, 0.8, -0.75])[:k]
+    return C.householder(n, 8, k, lam, seed, target="largest_mag", x_noise=noise)
+
+
+def small_mag_problem(n=260, seed=31, noise=1e-6):
+    rest = np.linspace(0.5, 1.0, n - 3) * np.where(np.arange(n - 3) % 2 == 0, 1.0, -1.0)
+    lam = np.concatenate([[0.1, -0.2, 0.3], rest])
+    return C.householder(n, 8, 3, lam, seed, target="smallest_mag", x_noise=noise)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_rayleigh_ritz_vectors_match_oracle(eig, precision):
+    p = spread_problem()
+    X0 = np.asfortranarray(p.X0 + 1e-3 * np.random.default_rng(1).standard_normal(p.X0.shape))
+    Z, _ = R.rayleigh_ritz(R.dense_operator(p.A), X0)
+    X = dev(X0)
+    rep = eig.refine_dense(dev(p.A), X, max_iters=0, norm_a=p.normA, rayleigh_ritz=True, precision=precision)
+    assert rep["status"] == 0
+    assert rel_diff(host(X), Z) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_rayleigh_ritz_recovers_rotated_scaled_eigenbasis(eig, precision):
+    p = spread_problem(noise=0.0)
+    q, r = np.linalg.qr(np.random.default_rng(3).standard_normal((p.k, p.k)))
+    M = q @ np.diag(np.linspace(0.5, 2.0, p.k))
+    X = dev(np.asfortranarray(p.Xtrue @ M))
+    eig.refine_dense(dev(p.A), X, max_iters=0, norm_a=p.normA, rayleigh_ritz=True, precision=precision)
+    Z = host(X)
+    order = np.argsort(-np.abs(p.lam), kind="stable")
+    c = np.abs(np.einsum("ij,ij->j", Z, p.Xtrue[:, order]))
+    assert np.all(c > 1 - 1e-13)
+
+
+def test_rayleigh_ritz_then_sweeps_match_oracle(eig):
+    p = spread_problem()
+    X0 = np.asfortranarray(p.X0 + 1e-4 * np.random.default_rng(2).standard_normal(p.X0.shape))
+    Xo, ro = R.refine(R.dense_operator(p.A), X0, p.normA, max_iters=3, rayleigh_ritz_first=True, beta="zero")
+    X = dev(X0)
+    rg = eig.refine_dense(dev(p.A), X, max_iters=3, norm_a=p.normA, rayleigh_ritz=True, beta="zero",
+                          history=True)
+    assert rg["iterations"] == 3
+    assert rel_diff(host(X), Xo) <= sweep_tol(p.normA, p.min_gap)
+    assert np.allclose(rg["hist_corr"], ro["hist_corr"], rtol=1e-8)
+
+
+def test_judged_columns_match_oracle(eig):
+    p = spread_problem(k=6)
+    X0 = p.X0.copy()
+    X0[:, 3:] += 1e-4 * np.random.default_rng(4).standard_normal((p.n, 3))
+    X0 = C.orthonormalise(X0)
+    _, ro = R.refine(R.dense_operator(p.A), X0, p.normA, max_iters=4, judge_cols=3)
+    rg = eig.refine_dense(dev(p.A), dev(X0), max_iters=4, norm_a=p.normA, judge_cols=3, history=True)
+    assert np.allclose(rg["hist_corr"], ro["hist_corr"], rtol=1e-8)
+    _, rf = R.refine(R.dense_operator(p.A), X0, p.normA, max_iters=1)
+    assert rg["hist_corr"][0] < 0.1 * rf["hist_corr"][0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_smallest_magnitude_sweeps_match_oracle(eig, precision):
+    p = small_mag_problem()
+    norm_b = p.normA ** 2 + abs(p.shift)
+    Xo, ro = R.refine(R.square_operator(p.A, p.shift), p.X0, p.normA, p.shift, max_iters=2, norm_b=norm_b)
+    X = dev(np.asfortranarray(p.X0))
+    rg = eig.refine_dense(dev(p.A), X, max_iters=2, norm_a=p.normA, target="smallest_mag", shift=p.lam_kp1,
+                          precision=precision)
+    assert rg["status"] == 0 and rg["iterations"] == 2
+    assert abs(rg["shift"] - p.shift) <= 1e-15
+    gaps = np.diff(np.sort(p.lam ** 2))
+    assert rel_diff(host(X), Xo) <= sweep_tol(norm_b, gaps.min())
+    assert rel_diff(rg["eigenvalues"], ro["d"]) <= 1e-12
+
+
+def test_smallest_magnitude_converges(eig):
+    p = small_mag_problem()
+    X = dev(np.asfortranarray(p.X0))
+    rg = eig.refine_dense(dev(p.A), X, max_iters=300, tol=1e-14, norm_a=p.normA, target="smallest_mag",
+                          shift=p.lam_kp1)
+    assert rg["status"] == 0
+    Xh = host(X)
+    c = np.abs(np.einsum("ij,ij->j", Xh / np.linalg.norm(Xh, axis=0), p.Xtrue))
+    assert np.all(1 - c < 1e-12)
+
+
+def test_smallest_magnitude_csr_matches_oracle(eig):
+    """The Laplacian is positive definite, so its smallest |eigenvalues| are its
+    smallest: the shifted square must track the oracle's CSR square operator."""
+    lp = LP.Laplacian2D(40, 30, 1.0, 2.0 ** 0.5)
+    rp, ci, val = lp.csr()
+    k = 4
+    pqs = lp.smallest(k + 1)
+    lam_sm = np.array([lp.eigenvalue(pq) for pq in pqs])
+    Xt = np.stack([lp.eigenvector(pq) for pq in pqs[:k]], axis=1)
+    rng = np.random.default_rng(9)
+    X0 = C.orthonormalise(Xt + 1e-6 * rng.standard_normal(Xt.shape))
+    normA = lp.norm_inf()
+    lam_kp1 = float(lam_sm[k])
+    alpha = C.shift_smallest_mag(normA, lam_kp1)
+    norm_b = normA ** 2 + abs(alpha)
+    Xo, ro = R.refine(R.csr_square_operator(rp, ci, val, lp.n, alpha), X0, normA, alpha, max_iters=2,
+                      norm_b=norm_b)
+    X = dev(np.asfortranarray(X0))
+    rg = eig.refine_csr(dev(rp), dev(ci), dev(val), X, max_iters=2, norm_a=normA, target="smallest_mag",
+                        shift=lam_kp1)
+    assert rg["iterations"] == 2
+    gaps = np.diff(lam_sm ** 2)
+    assert rel_diff(host(X), Xo) <= sweep_tol(norm_b, gaps.min())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_reorth_orthonormalises_the_result(eig, precision):
+    p = spread_problem()
+    X = dev(np.asfortranarray(p.X0))
+    eig.refine_dense(dev(p.A), X, max_iters=5, norm_a=p.normA, precision=precision)
+    Xa = host(X)
+    Xr = dev(np.asfortranarray(p.X0))
+    eig.refine_dense(dev(p.A), Xr, max_iters=5, norm_a=p.normA, precision=precision, reorth=True)
+    Xb = host(Xr)
+    assert np.abs(Xb.T @ Xb - np.eye(p.k)).max() < 2e-15
+    assert rel_diff(Xb, R.reorthonormalise(Xa)) <= 1e-13
+
+
+def test_grouped_batch_rejects_the_shifted_square(eig):
+    import paper_2602_23778_gb300 as pkg
+    p = small_mag_problem()
+    items = [{"A": dev(p.A), "X": dev(np.asfortranarray(p.X0)), "target": "smallest_mag", "shift": p.lam_kp1,
+              "norm_a": p.normA}]
+    with pytest.raises(pkg.EigrefError):
+        eig.refine_batched(items, max_iters=2, precision="bf16")

@@ -40,6 +40,13 @@ def shift_smallest(normA, lam_kp1):
     return (normA + lam_kp1) / 2.0
 
 
+def shift_smallest_mag(normA, lam_kp1):
+    """alpha = (||A||^2 + lambda_{k+1}^2) / 2 for the k smallest |lambda|
+    through B = A^2 - alpha I (Section 5.2; the midpoint of the squared
+    spectrum's range above the targets)."""
+    return (normA * normA + lam_kp1 * lam_kp1) / 2.0
+
+
 def householder(n, m, k, lam, seed, target="largest_mag", x_noise=1e-7,
                 noise_before_round=False, build_matrix=True):
     """Dense A = Q diag(lam) Q^T; target the k largest |lam| (no shift) or the
@@ -51,6 +58,8 @@ def householder(n, m, k, lam, seed, target="largest_mag", x_noise=1e-7,
         order = np.argsort(-lam, kind="stable")
     elif target == "smallest":
         order = np.argsort(lam, kind="stable")
+    elif target == "smallest_mag":
+        order = np.argsort(np.abs(lam), kind="stable")
     else:
         raise ValueError(target)
     idx = order[:k]
@@ -58,14 +67,15 @@ def householder(n, m, k, lam, seed, target="largest_mag", x_noise=1e-7,
     normA = float(np.max(np.abs(lam)))
     shift = {"largest_mag": 0.0,
              "largest": shift_largest(normA, lam_kp1),
-             "smallest": shift_smallest(normA, lam_kp1)}[target]
+             "smallest": shift_smallest(normA, lam_kp1),
+             "smallest_mag": shift_smallest_mag(normA, lam_kp1)}[target]
     Xt = hp.eigenvectors(idx)
     if noise_before_round:
         X0 = fp32_round(Xt + _noise(seed, 7, Xt.shape, x_noise))
     else:
         X0 = fp32_round(Xt) + _noise(seed, 7, Xt.shape, x_noise)
     X0 = orthonormalise(X0)
-    lb = lam - shift
+    lb = (lam * lam if target == "smallest_mag" else lam) - shift
     rest = np.delete(lb, idx)
     gamma = float(np.max(np.abs(rest)) / np.min(np.abs(lb[idx])))
     tl = lam[idx]
