@@ -110,6 +110,14 @@ typedef struct eigref_params {
   int reorth;          /* 1: reorthogonalise the result before returning it (the option of Section
                           3.1.3): two symmetric (Loewdin) steps X <- X (3 I - X^T X) / 2, each
                           squaring ||X^T X - I||, so the columns move by O(||X^T X - I||) */
+  int resign;          /* 1: when Y_1 = X_1 - I turns singular mid-run (EIGREF_E_SINGULAR_WY), take
+                          the signs of Algorithm 2 for the current X -- the choice Algorithm 3 builds
+                          into its WY factors -- and resume from the same iterate (at most 4 times
+                          per call; the signs are undone on exit).  refine_dense / refine_csr only. */
+  int autotune;        /* 1: the first split-form call for a given (n, k, slices) times the split-K
+                          candidates of its tensor-core product and Gram products and keeps the
+                          fastest on the handle (results are identical for every choice: the split
+                          partials are exact).  0: the built-in choice. */
 } eigref_params;
 
 /* Report of one refinement call.  The three array pointers are optional,
@@ -131,11 +139,13 @@ typedef struct eigref_report {
                                  (W = B X) over the sweeps applied; else 0 */
   int64_t kernel_launches;    /* kernels launched by the call (graph replays included) */
   int product_launches;       /* product kernels timed in product_ms */
+  int psplit;                 /* split form: split-K of the product used (0: FP64 form) */
+  int ksplit;                 /* split form: split-K of the Gram products used */
 } eigref_report;
 
 /* Defaults: LARGEST_MAG, norm_a computed, max_iters 100, tol 0, correction
  * criterion, FP64, beta cluster, delta_c 10, div 10 / 1e-4, check 32,
- * sign_fix 1, use_graph 1, profile 0, rayleigh_ritz 0, judge_cols 0, reorth 0. */
+ * sign_fix 1, use_graph 1, profile 0, rayleigh_ritz 0, judge_cols 0, reorth 0, resign 0, autotune 1. */
 void eigref_params_default(eigref_params* p);
 
 /* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t

@@ -183,7 +183,7 @@ def rayleigh_ritz(apply_b, X):
 
 def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORRECTION,
            delta_c=10.0, beta="cluster", div_factor=10.0, div_floor=1e-4, use_sign_fix=True,
-           rayleigh_ritz_first=False, judge_cols=0, norm_b=None):
+           rayleigh_ritz_first=False, judge_cols=0, norm_b=None, resign=False):
     """Iterate Algorithm 4 with the driver choices of Section 3.1.3.
 
     Per sweep t: R_t and E_t are computed from X_t, the update is applied and
@@ -202,6 +202,9 @@ def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORR
     (Section 4.1: K vectors refined, convergence judged on the leading k).
     norm_b: ||B|| for delta and the residual test when B is not A - shift I
     (the shifted square of Section 5.2); default ||A|| + |shift| and ||A||.
+    resign: when Algorithm 1 meets a singular Y_1 mid-run, take the signs of
+    Algorithm 2 for the current X (the choice Algorithm 3 builds into its WY
+    factors), X <- X Sigma, and redo the sweep (at most 4 times per call).
 
     Returns (X, report) with X in the caller's column signs (or, after the
     Rayleigh--Ritz step, in its order and signs).
@@ -218,8 +221,19 @@ def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORR
     hist_r, hist_e = [], []
     status, it, d = E_NOT_CONVERGED if tol > 0 else OK, 0, None
     emin = np.inf
+    resigned = 0
     for t in range(max_iters):
-        Xn, info = refine_step(apply_b, X, delta, beta)
+        while True:
+            try:
+                Xn, info = refine_step(apply_b, X, delta, beta)
+                break
+            except SingularWY:
+                if not resign or resigned >= 4:
+                    raise
+                s2 = sign_fix(X)
+                X = X * s2[None, :]
+                sigma = sigma * s2
+                resigned += 1
         rel_r = info.res_fro / res_scale
         e_fro = info.e_fro if kj == k else float(np.linalg.norm(info.E[:, :kj]))
         if not (np.all(np.isfinite(Xn)) and np.isfinite(e_fro) and np.isfinite(rel_r)):
@@ -241,7 +255,7 @@ def refine(apply_b, X0, norm_a, shift=0.0, max_iters=10, tol=0.0, stop=STOP_CORR
     X = X * sigma[None, :]
     return X, dict(status=status, iterations=it, d=None if d is None else d + shift,
                    hist_res=np.array(hist_r), hist_corr=np.array(hist_e), sigma=sigma,
-                   delta=delta)
+                   delta=delta, resigned=resigned)
 
 
 def dense_operator(A, shift=0.0):

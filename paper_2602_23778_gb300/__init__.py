@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
                 ("delta_c", ctypes.c_double), ("div_factor", ctypes.c_double), ("div_floor", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("sign_fix", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("rayleigh_ritz", ctypes.c_int), ("judge_cols", ctypes.c_int),
-                ("reorth", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("resign", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -48,7 +48,7 @@ class Report(ctypes.Structure):
                 ("hist_residual", ctypes.POINTER(ctypes.c_double)),
                 ("hist_corr", ctypes.POINTER(ctypes.c_double)),
                 ("product_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("product_launches", ctypes.c_int)]
+                ("product_launches", ctypes.c_int), ("psplit", ctypes.c_int), ("ksplit", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -222,7 +222,7 @@ class Handle:
                 v = STOPS[v] if isinstance(v, str) else v
             elif key == "beta":
                 v = BETAS[v] if isinstance(v, str) else v
-            elif key in ("sign_fix", "use_graph", "profile", "rayleigh_ritz", "reorth"):
+            elif key in ("sign_fix", "use_graph", "profile", "rayleigh_ritz", "reorth", "resign", "autotune"):
                 v = int(bool(v))
             setattr(p, key, v)
         return p
@@ -232,7 +232,8 @@ class Handle:
                    final_rel_residual=rep.final_rel_residual, final_corr_norm=rep.final_corr_norm,
                    shift=rep.shift, norm_a=rep.norm_a, delta=rep.delta, setup_ms=rep.setup_ms,
                    sweeps_ms=rep.sweeps_ms, product_ms=rep.product_ms, product_launches=rep.product_launches,
-                   kernel_launches=rep.kernel_launches, error=self.last_error())
+                   kernel_launches=rep.kernel_launches, psplit=rep.psplit, ksplit=rep.ksplit,
+                   error=self.last_error())
         ev, hr, hc = want
         out["eigenvalues"] = ev
         if hr is not None:

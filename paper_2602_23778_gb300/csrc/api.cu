@@ -16,7 +16,9 @@
 
 #include <algorithm>
 #include <functional>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -34,6 +36,8 @@ struct eigref_ctx {
   size_t ws_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   Control* host_ctl = nullptr;  // pinned
+  // split-K choices the autotuner measured, by (n, k, slices)
+  std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
 };
 
 namespace {
@@ -97,7 +101,7 @@ int ensure_ws(eigref_ctx* h, size_t bytes) {
 
 struct Params {
   int target, max_iters, stop, precision, slices, beta, check_every, sign_fix, use_graph, profile, rayleigh_ritz,
-      judge_cols, reorth;
+      judge_cols, reorth, resign, autotune;
   double shift, norm_a, tol, delta_c, div_factor, div_floor;
 };
 
@@ -125,6 +129,8 @@ int read_params(eigref_ctx* h, const eigref_params* p, Params* q) {
   q->rayleigh_ritz = p->rayleigh_ritz;
   q->judge_cols = p->judge_cols;
   q->reorth = p->reorth;
+  q->resign = p->resign;
+  q->autotune = p->autotune;
   if (q->judge_cols < 0) return set_err(h, EIGREF_E_INVALID, "judge_cols < 0");
   if (q->target < EIGREF_LARGEST_MAG || q->target > EIGREF_SMALLEST_MAG)
     return set_err(h, EIGREF_E_INVALID, "target %d out of range", q->target);
@@ -239,6 +245,7 @@ struct Run {
   int hist_len = 0;
   double norm_a = 0.0, shift = 0.0, delta = 0.0;
   double norm_res = 0.0;  // scale of the residual test: ||B|| (||A|| unless B is the shifted square)
+  int xoff = 0;           // X_t lives in xbuf[(t + xoff) & 1] (changes when the signs are retaken)
 };
 
 void run_plan(Run& r) {
@@ -401,10 +408,10 @@ int run_issue(const Run& r, int count, cudaStream_t s, cudaEvent_t* pev, unsigne
 int run_copy_out(eigref_ctx* h, const Run& r, int iterations, cudaStream_t s) {
   const int64_t n = r.pr.n;
   const int k = r.pr.k;
-  const double* xr = r.xbuf[iterations & 1];
+  const int cur = (iterations + r.xoff) & 1;
+  const double* xr = r.xbuf[cur];
   if (r.q.reorth)
-    launch_reorthonormalise(r.b, n, k, r.xbuf[iterations & 1], r.xbuf[(iterations + 1) & 1], r.chunk_rows, r.nchunks,
-                            s);
+    launch_reorthonormalise(r.b, n, k, r.xbuf[cur], r.xbuf[cur ^ 1], r.chunk_rows, r.nchunks, s);
   if (r.x_dev) {
     launch_copy_out(xr, r.X, r.ldx, n, k, r.sg, s);
   } else {
@@ -436,6 +443,55 @@ struct GraphGuard {
     if (g) cudaGraphExecDestroy(g);
   }
 };
+
+// The autotuner: times each split-K candidate of the tensor-core product and
+// of the Gram products on this problem (3 runs after a warm-up, CUDA events)
+// and keeps the fastest for the handle.  The split partials are exact, so the
+// choice changes the time only, never the results.
+int tune_splits(eigref_ctx* h, Run& r, cudaStream_t s) {
+  SlicedA* sl = r.pr.sliced;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_err(h, EIGREF_E_CUDA, "autotune events");
+  }
+  auto time_it = [&](const std::function<void()>& f) {
+    f();
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < 3; ++i) f();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  int best_p = sl->psplit(), best_k = sl->ksplit();
+  float best = 1e30f;
+  for (int p : sl->psplit_candidates()) {
+    sl->set_splits(p, best_k);
+    const float ms = time_it([&] { launch_product(r.pr, r.xbuf[0], r.b.p, r.shift, nullptr, s); });
+    if (ms < best) {
+      best = ms;
+      best_p = p;
+    }
+  }
+  best = 1e30f;
+  for (int kq : sl->ksplit_candidates()) {
+    sl->set_splits(best_p, kq);
+    const float ms = time_it([&] { sl->gram(r.b.p, nullptr, r.b.g2, nullptr, s); });
+    if (ms < best) {
+      best = ms;
+      best_k = kq;
+    }
+  }
+  sl->set_splits(best_p, best_k);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CUDA_TRY(h, cudaGetLastError());
+  h->tuned[std::make_tuple(r.pr.n, r.pr.k, sl->slices())] = std::make_pair(best_p, best_k);
+  return EIGREF_OK;
+}
 
 int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigref_params* pin,
                   eigref_report* rep) {
@@ -486,6 +542,11 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   }
   st = run_setup_device(h, r, s);
   if (st) return st;
+  if (r.pr.sliced && q.autotune && q.max_iters > 0 &&
+      !h->tuned.count(std::make_tuple(r.pr.n, r.pr.k, r.pr.sliced->slices()))) {
+    st = tune_splits(h, r, s);
+    if (st) return st;
+  }
   run_setup_inverse(r, s);
 
   // ---- sweeps: chunks of check_every (no longer than the run), even ----
@@ -529,6 +590,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   double product_ms = 0.0;
   int product_launches = 0;
   int it_before = 0;
+  int resigned = 0;
   while (launched < q.max_iters) {
     if (graph.g) {
       CUDA_TRY(h, cudaGraphLaunch(graph.g, s));
@@ -539,6 +601,34 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     launched += m;
     CUDA_TRY(h, cudaMemcpyAsync(h->host_ctl, b.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (q.resign && h->host_ctl->status == EIGREF_E_SINGULAR_WY && resigned < 4) {
+      // Y1 lost its conditioning: take the signs of Algorithm 2 for the current
+      // X (the choice Algorithm 3 builds into its WY factors), X <- X Sigma, and
+      // resume from the same iterate.  The next chunk starts on xbuf[0].
+      const int it = h->host_ctl->iterations;
+      double* xc = r.xbuf[(it + r.xoff) & 1];
+      double* s2 = b.nu;   // scratch: recomputed by every sweep
+      launch_sign_fix_rowmajor(xc, k, s2, s);
+      launch_scale_cols(xc, r.xbuf[0], n, k, s2, s);
+      if (r.sg) {
+        launch_scale_cols(r.sigma, r.sigma, 1, k, s2, s);
+      } else {
+        CUDA_TRY(h, cudaMemcpyAsync(r.sigma, s2, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        r.sg = r.sigma;
+      }
+      r.xoff = it & 1;
+      Control c = *h->host_ctl;
+      c.status = EIGREF_OK;
+      c.done = 0;
+      c.singular = 0;
+      *h->host_ctl = c;
+      CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
+      run_setup_inverse(r, s);
+      ++resigned;
+      launched = it;
+      it_before = it;
+      continue;
+    }
     const int ran = h->host_ctl->iterations - it_before;
     it_before = h->host_ctl->iterations;
     for (int t = 0; q.profile && t < ran && t < m; ++t) {
@@ -555,7 +645,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   CUDA_TRY(h, cudaStreamSynchronize(s));
   const Control fin = *h->host_ctl;
 
-  // ---- result: X_{iterations} lives in xbuf[iterations % 2] ----
+  // ---- result: X_{iterations} lives in xbuf[(iterations + xoff) % 2] ----
   st = run_copy_out(h, r, fin.iterations, s);
   if (st) return st;
   std::vector<double> dvec(k);
@@ -580,6 +670,8 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     rep->product_ms = product_ms;
     rep->product_launches = product_launches;
     rep->kernel_launches = kernel_launches;
+    rep->psplit = r.pr.sliced ? r.pr.sliced->psplit() : 0;
+    rep->ksplit = r.pr.sliced ? r.pr.sliced->ksplit() : 0;
   }
   if (status != EIGREF_OK)
     set_err(h, status, "%s after %d sweeps", eigref_status_string(status), fin.iterations);
@@ -621,6 +713,8 @@ void eigref_params_default(eigref_params* p) {
   p->rayleigh_ritz = 0;
   p->judge_cols = 0;
   p->reorth = 0;
+  p->resign = 0;
+  p->autotune = 1;
 }
 
 const char* eigref_status_string(int s) {
@@ -721,6 +815,8 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
       if (a_dev) cudaFree(a_dev);
       return set_err(h, st, "%s", sl.error());
     }
+    auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices()));
+    if (tk != h->tuned.end()) sl.set_splits(tk->second.first, tk->second.second);
     pr.sliced = &sl;
   }
   st = refine_common(h, pr, X, ldx, pp, rep);
@@ -940,7 +1036,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
         launch_mma_tasks(S, sl::MODE_PRODUCT, prod[par].data(), count, s);
         launch_slice_grouped(S, SLICE_P_COLS, items_dev, gd, max_n_pad, par, s);
         launch_mma_tasks(S, sl::MODE_GRAM, gram.data(), count, s);
-        launch_gram_reduce_grouped(items_dev, gd, 0, s);
+        launch_sgram_reduce_grouped(S, items_dev, gd, s);
         launch_top_gram_grouped(items_dev, gd, par, s);
         launch_kxk_stage_grouped(items_dev, gd, par, s);
         launch_slice_grouped(S, SLICE_X_ROWS, items_dev, gd, max_n_pad, par, s);
@@ -1049,6 +1145,8 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
       reps[i].product_ms = 0.0;
       reps[i].product_launches = 0;
       reps[i].kernel_launches = kernel_launches;
+      reps[i].psplit = runs[i].pr.sliced ? runs[i].pr.sliced->psplit() : 0;
+      reps[i].ksplit = runs[i].pr.sliced ? runs[i].pr.sliced->ksplit() : 0;
     }
   }
   if (status != EIGREF_OK)
@@ -1120,6 +1218,8 @@ int eigref_product_dense(eigref_handle h, const double* A, int64_t n, int64_t ld
   if (precision != EIGREF_FP64) {
     int st = sl.configure(A, n, lda, k, precision, slices);
     if (st) return set_err(h, st, "%s", sl.error());
+    auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices()));
+    if (tk != h->tuned.end()) sl.set_splits(tk->second.first, tk->second.second);
     pr.sliced = &sl;
   }
   return product_common(h, pr, X, ldx, shift, P, ldp);

@@ -76,7 +76,7 @@ struct GroupItem {
   void* f_planes;            // BF16 [S][k_pad][kr]
   int *x_colexp, *p_colexp, *xr_rowexp, *f_colexp;
   unsigned long long *x_cmax, *p_cmax, *f_cmax;
-  double* sgpart;            // tensor-core Gram partials [2][ksplit][k k]
+  void* sgpart;              // tensor-core Gram partials: [2][ksplit][k k] exact (hi, lo) int64 pairs
 };
 
 // Extent of a grouped launch: blockIdx.z = problem, x/y sized for the largest.
@@ -128,7 +128,6 @@ void launch_reorthonormalise(const SweepBufs& b, int64_t n, int k, double* Xbuf,
 
 // grouped launches over a batch (parity = t & 1 of the sweep)
 void launch_top_gram_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
-void launch_gram_reduce_grouped(const GroupItem* items, const GroupDims& gd, int max_ksplit, cudaStream_t s);
 void launch_finalize_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
 void launch_normalize_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);
 void launch_kxk_stage_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s);

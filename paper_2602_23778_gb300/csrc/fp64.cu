@@ -176,20 +176,6 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int k, int n
                    ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
-// Batch: the tensor-core Gram partials of problem blockIdx.z into its G, S.
-__global__ void gram_reduce_grouped_kernel(const GroupItem* __restrict__ items) {
-  const GroupItem& it = items[blockIdx.z];
-  if (it.b[0].ctl->done) return;
-  gram_reduce_body(it.sgpart, it.k, it.ksplit, it.b[0].g2, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
-                   ((int64_t)gridDim.x * blockDim.x) >> 5);
-}
-
-void launch_gram_reduce_grouped(const GroupItem* items, const GroupDims& gd, int, cudaStream_t s) {
-  const int64_t warps = 2LL * gd.max_k * gd.max_k;
-  const int rg = (int)std::min<int64_t>((warps + 7) / 8, 64);
-  gram_reduce_grouped_kernel<<<dim3(rg, 1, gd.count), 256, 0, s>>>(items);
-}
-
 void launch_gram_reduce(const double* part, int k, int nchunks, double* out, const Control* ctl, cudaStream_t s) {
   const int64_t warps = 2LL * k * k;
   const int rg = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);

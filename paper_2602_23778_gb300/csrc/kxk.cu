@@ -27,9 +27,12 @@
 
 namespace eigref {
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// Sum over the first vb threads of the block (the others pass 0), in a fixed
+// order that depends on vb only: a grouped launch with more threads gives the
+// same bits as a launch of exactly vb threads.
+__device__ __forceinline__ double block_sum(double v, double* sh, int vb) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = vb >> 5;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
@@ -41,7 +44,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // One block per column j.  In the split form g2 arrives holding the Gram
 // products over all rows; the block turns its column into G2 = G - G1,
 // S2 = S - S1 in place (only this block touches column j).
-__device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j) {
+__device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j, int vb) {
   __shared__ double sh[32];
   const int64_t kk = (int64_t)k * k;
   const double* G1 = b.gtop;
@@ -54,7 +57,7 @@ __device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j) {
   const double dj = (full ? S2[jj] : S1[jj] + S2[jj]) / al;
   __syncthreads();
   double r1s = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+  for (int i = threadIdx.x; i < k && (int)threadIdx.x < vb; i += vb) {
     const int64_t e = i + (int64_t)j * k;
     const double G = full ? G2[e] : G1[e] + G2[e];
     const double S = full ? S2[e] : S1[e] + S2[e];
@@ -72,7 +75,7 @@ __device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j) {
     b.y1[e] = x - (i == j ? 1.0 : 0.0);
     r1s += r1 * r1;
   }
-  r1s = block_sum(r1s, sh);
+  r1s = block_sum(r1s, sh, vb);
   if (threadIdx.x == 0) {
     b.alpha[j] = al;
     b.d[j] = dj;
@@ -81,9 +84,12 @@ __device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j) {
   }
 }
 
+// Threads of the one-column-per-block kernels for a given k.
+__host__ __device__ __forceinline__ int kk_threads(int k) { return k >= 128 ? 128 : ((k + 31) / 32) * 32; }
+
 __global__ void kk_prep_kernel(SweepBufs b, int k) {
   if (b.ctl->done) return;
-  kk_prep_body(b, k, blockIdx.x);
+  kk_prep_body(b, k, blockIdx.x, blockDim.x);
 }
 
 __device__ __forceinline__ double nan_max(double a, double b) {   // NaN-propagating max
@@ -278,12 +284,12 @@ __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
 
 // E11 by the cases of line 6 of Algorithm 4, one block per column j, plus the
 // column sums the finalize step needs: ||E11(:,j)||^2, (M^T Z)_jj, (M^T G2 M)_jj.
-__device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double delta, int beta_zero, int j) {
+__device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double delta, int beta_zero, int j, int vb) {
   __shared__ double sh[32];
   const int64_t kk = (int64_t)k * k;
   const double dj = b.d[j];
   double es = 0.0, cz = 0.0, cw = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+  for (int i = threadIdx.x; i < k && (int)threadIdx.x < vb; i += vb) {
     const int64_t e = i + (int64_t)j * k;
     const double di = b.d[i];
     double v;
@@ -300,9 +306,9 @@ __device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double de
     cz += mij * b.z[e];
     cw += mij * b.w2[e];
   }
-  es = block_sum(es, sh);
-  cz = block_sum(cz, sh);
-  cw = block_sum(cw, sh);
+  es = block_sum(es, sh, vb);
+  cz = block_sum(cz, sh, vb);
+  cw = block_sum(cw, sh, vb);
   if (threadIdx.x == 0) {
     b.e11sq[j] = es;
     b.cz[j] = cz;
@@ -313,7 +319,7 @@ __device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double de
 
 __global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
   if (b.ctl->done) return;
-  kk_e11_body(b, k, delta, beta_zero, blockIdx.x);
+  kk_e11_body(b, k, delta, beta_zero, blockIdx.x, blockDim.x);
 }
 
 
@@ -391,14 +397,14 @@ __global__ void kk_inverse_init_kernel(const double* __restrict__ X, int k, doub
 }
 
 void launch_inverse_setup(const SweepBufs& b, int k, cudaStream_t s) {
-  const int tpb = k >= 128 ? 128 : ((k + 31) / 32) * 32;
+  const int tpb = kk_threads(k);
   kk_inverse_init_kernel<<<(k * k + 255) / 256, 256, 0, s>>>(b.x, k, b.y1, b.res);
   kk_lu_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(b, k);
   kk_solve_kernel<0><<<k, tpb, 0, s>>>(b.lu, b.piv, b.res, b.zinv, k, b.ctl);   // Z = -Y1^{-1}(-I)
 }
 
 void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s) {
-  const int tpb = k >= 128 ? 128 : ((k + 31) / 32) * 32;
+  const int tpb = kk_threads(k);
   kk_prep_kernel<<<k, tpb, 0, s>>>(b, k);
   if (b.mixed) {
     // two Newton-Schulz steps bring Z to the new Y1 (ping-pong between zinv and zinv2)
@@ -432,14 +438,14 @@ __global__ void kk_prep_grouped_kernel(const GroupItem* __restrict__ items, int 
   const GroupItem& it = items[blockIdx.z];
   const SweepBufs& b = it.b[parity];
   if ((int)blockIdx.x >= it.k || b.ctl->done) return;
-  kk_prep_body(b, it.k, blockIdx.x);
+  kk_prep_body(b, it.k, blockIdx.x, kk_threads(it.k));
 }
 
 __global__ void kk_e11_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
   const GroupItem& it = items[blockIdx.z];
   const SweepBufs& b = it.b[parity];
   if ((int)blockIdx.x >= it.k || b.ctl->done) return;
-  kk_e11_body(b, it.k, it.delta, it.beta_zero, blockIdx.x);
+  kk_e11_body(b, it.k, it.delta, it.beta_zero, blockIdx.x, kk_threads(it.k));
 }
 
 template <int MODE>
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(256) kk_ns_grouped_kernel(const GroupItem* __r
 
 void launch_kxk_stage_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
   const int k = gd.max_k;
-  const int tpb = k >= 128 ? 128 : ((k + 31) / 32) * 32;
+  const int tpb = kk_threads(k);
   const dim3 gk(k, 1, gd.count);
   const dim3 gt((k + 15) / 16, (k + 15) / 16, gd.count);
   kk_prep_grouped_kernel<<<gk, tpb, 0, s>>>(items, parity);

@@ -37,6 +37,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "sliced.cuh"
 
@@ -173,6 +174,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // (the contraction index runs along the 128-byte rows TMA writes).
 // ---------------------------------------------------------------------------
 
+
+// The value of one output from its two exact int64 sums (digit-pair groups
+// w < 4 and w >= 4, see the epilogue) and the row / column exponents.
+template <int S>
+__device__ __forceinline__ double recombine(long long hi, long long lo, int er, int fc) {
+  if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);  // Inf / NaN operand
+  const double v = fma((double)lo, ldexp(1.0, -kBits * (S + 1)), (double)hi * 0x1p-35);
+  return ldexp(v, er + fc);
+}
 
 // One CTA's tile: output column block nb, row tile mb, K split / job zb.
 template <int S, int MODE>
@@ -385,34 +395,27 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[buf]));
     }
-    const double lo_scale = ldexp(1.0, -kBits * (S + 1));
     const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
     const int* cexp = job ? g.colexp2 : g.colexp;
     double sq[kC], rq[kC];
 #pragma unroll
     for (int j = 0; j < kC; ++j) {
       const int col = nb * kBN + half * kC + j;
-      double w = 0.0;
       const bool live = ok && row < g.m_valid && col < g.k;
-      if (live) {
-        const int fc = cexp[col];
-        if (er == kNonFinite || fc == kNonFinite) {
-          w = __longlong_as_double(0x7FF8000000000000ll);   // NaN: an operand held Inf / NaN
-        } else {
-          const double v = fma((double)lo[j], lo_scale, (double)hi[j] * 0x1p-35);
-          w = ldexp(v, er + fc);
-        }
-      }
+      // split-K partials stay exact int64 pairs: the sum over splits is exact,
+      // so the result does not depend on how K was split
+      const bool raw = (MODE == MODE_GRAM) || (MODE == MODE_PRODUCT && nsplit > 1);
+      const double w = (live && !raw) ? recombine<S>(hi[j], lo[j], er, cexp[col]) : 0.0;
       sq[j] = rq[j] = 0.0;
       if (MODE == MODE_PRODUCT) {
         if (live) {
           if (nsplit == 1)
             g.P[row * g.k + col] = w - g.shift * g.Xs[row * g.k + col];
           else
-            g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = w;
+            g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
         }
       } else if (MODE == MODE_GRAM) {
-        if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = w;
+        if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = make_longlong2(hi[j], lo[j]);
       } else {
         if (live && row >= g.row_begin) {
           const int64_t e = row * g.k + col;
@@ -761,15 +764,66 @@ __global__ void slice_rows_grouped_kernel(const GroupItem* __restrict__ items, i
                      ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
-// P = sum of the split partial products - shift X (fixed order).
-__global__ void product_reduce_kernel(const double* __restrict__ part, int ksplit, const double* __restrict__ X,
+// P = (exact sum of the split partial products) - shift Xs.
+template <int S>
+__global__ void product_reduce_kernel(const longlong2* __restrict__ part, int ksplit, const int* __restrict__ rowexp,
+                                      const int* __restrict__ colexp, int k, const double* __restrict__ Xs,
                                       double* __restrict__ P, int64_t total, double shift, const Control* ctl) {
   if (ctl && ctl->done) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    double v = part[e];
-    for (int q = 1; q < ksplit; ++q) v += part[(int64_t)q * total + e];
-    P[e] = v - shift * X[e];
+    long long hi = 0, lo = 0;
+    for (int q = 0; q < ksplit; ++q) {
+      const longlong2 v = part[(int64_t)q * total + e];
+      hi += v.x;
+      lo += v.y;
+    }
+    P[e] = recombine<S>(hi, lo, rowexp[e / k], colexp[e % k]) - shift * Xs[e];
   }
+}
+
+// G = X^T X (z = 0), S = X^T W (z = 1) from the exact split partials; one
+// warp per output, lanes over the splits.
+template <int S>
+__device__ __forceinline__ void sgram_reduce_body(const longlong2* __restrict__ part, int k, int nsplit,
+                                                  const int* __restrict__ xexp, const int* __restrict__ wexp,
+                                                  double* __restrict__ out, int64_t w0, int64_t nw) {
+  const int64_t kk = (int64_t)k * k;
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = w0; e < 2 * kk; e += nw) {
+    const int z = (int)(e / kk);
+    const int64_t o = e % kk;
+    const longlong2* p = part + (int64_t)z * nsplit * kk + o;
+    long long hi = 0, lo = 0;
+    for (int c = lane; c < nsplit; c += 32) {
+      const longlong2 v = p[(int64_t)c * kk];
+      hi += v.x;
+      lo += v.y;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      hi += __shfl_xor_sync(0xffffffffu, hi, m);
+      lo += __shfl_xor_sync(0xffffffffu, lo, m);
+    }
+    const int row = (int)(o % k), col = (int)(o / k);
+    if (lane == 0) out[e] = recombine<S>(hi, lo, xexp[row], z ? wexp[col] : xexp[col]);
+  }
+}
+
+template <int S>
+__global__ void sgram_reduce_kernel(const longlong2* __restrict__ part, int k, int nsplit, const int* __restrict__ xexp,
+                                    const int* __restrict__ wexp, double* __restrict__ out, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  sgram_reduce_body<S>(part, k, nsplit, xexp, wexp, out, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                       ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+template <int S>
+__global__ void sgram_reduce_grouped_kernel(const GroupItem* __restrict__ items) {
+  const GroupItem& it = items[blockIdx.z];
+  if (it.b[0].ctl->done) return;
+  sgram_reduce_body<S>(static_cast<const longlong2*>(it.sgpart), it.k, it.ksplit, it.x_colexp, it.p_colexp,
+                       it.b[0].g2, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                       ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 template <int S>
@@ -897,15 +951,15 @@ static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int k
   L.f_planes = take((size_t)S * k_pad * kr * 2);
   L.f_colexp = take((size_t)k_pad * 4);
   L.f_cmax = take((size_t)k_pad * 8);
-  L.gpart = take((size_t)2 * ksplit * k * k * 8);
-  L.ppart = take(psplit > 1 ? (size_t)psplit * n * k * 8 : 64);
+  L.gpart = take((size_t)2 * ksplit * k * k * 16);
+  L.ppart = take(psplit > 1 ? (size_t)psplit * n * k * 16 : 64);
   L.err = take(64);
   L.total = off + 1024;
   return L;
 }
 
 size_t SlicedA::layout_total() const {
-  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_).total;
+  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_).total;
 }
 
 int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int precision, int slices) {
@@ -957,22 +1011,46 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
   const int kbt = n_pad_ / sl::kBK;
   if (ksplit_ > kbt) ksplit_ = kbt;
   if (ksplit_ < 1) ksplit_ = 1;
+  // the workspace holds partials for the largest split an autotuner may try
+  psplit_max_ = 1;
+  for (int p = 2; p <= 4; ++p)
+    if ((n_pad_ / 64) / p >= 8) psplit_max_ = p;
+  ksplit_max_ = std::min(kbt, 2 * ksplit_);
   return EIGREF_OK;
+}
+
+std::vector<int> SlicedA::psplit_candidates() const {
+  std::vector<int> v;
+  for (int p = 1; p <= psplit_max_; ++p) v.push_back(p);
+  return v;
+}
+
+std::vector<int> SlicedA::ksplit_candidates() const {
+  std::vector<int> v;
+  const int h = ksplit_;
+  for (int c : {std::max(1, h / 2), h, ksplit_max_})
+    if (v.empty() || v.back() != c) v.push_back(c);
+  return v;
+}
+
+void SlicedA::set_splits(int psplit, int ksplit) {
+  psplit_ = std::max(1, std::min(psplit, psplit_max_));
+  ksplit_ = std::max(1, std::min(ksplit, ksplit_max_));
 }
 
 size_t SlicedA::workspace_bytes() const { return layout_total(); }
 
 void SlicedA::share_gpu(int problems) {
   if (problems <= 1) return;
-  psplit_ = 1;
+  psplit_ = psplit_max_ = 1;
   const int kbt = n_pad_ / sl::kBK;
-  ksplit_ = std::max(1, std::min(kbt, n_pad_ / 4096));
+  ksplit_ = ksplit_max_ = std::max(1, std::min(kbt, n_pad_ / 4096));
 }
 
 void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023)); }
 
 int SlicedA::prepare(cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   auto* ap = reinterpret_cast<__nv_bfloat16*>(ws_ + L.a_planes);
   // B-side and row planes: zero once, so padding rows and columns stay zero
   if (cudaMemsetAsync(ws_ + L.x_planes, 0, L.xr_rowexp - L.x_planes, s) != cudaSuccess ||
@@ -1025,6 +1103,16 @@ static void launch_mma(int S, dim3 grid, const CUtensorMap& a, const CUtensorMap
 #undef EIGREF_CALL_MMA
 }
 
+static void launch_product_reduce(int S, const MmaTask& t, int psplit, const double* Xs, double* P, int64_t total,
+                                  double shift, const Control* ctl, cudaStream_t s) {
+  const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+#define EIGREF_CALL_PR(S_)                                                                                   \
+  sl::product_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.ppart, psplit, t.g.rowexp, t.g.colexp, t.g.k, Xs, P, total, \
+                                                   shift, ctl)
+  EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_PR)
+#undef EIGREF_CALL_PR
+}
+
 static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
   const dim3 grid((unsigned)t.gx, (unsigned)t.gy, (unsigned)t.gz);
   if (mode == sl::MODE_PRODUCT) launch_mma<sl::MODE_PRODUCT>(S, grid, t.a, t.b, t.b2, t.g, s);
@@ -1034,7 +1122,7 @@ static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
 
 MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Control* ctl, const double* Xs,
                               bool b_from_p) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   MmaTask t;
   t.a = *reinterpret_cast<const CUtensorMap*>(tmA_);
   t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(b_from_p ? tmP_ : tmX_);
@@ -1052,7 +1140,7 @@ MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Co
   g.P = P;
   g.shift = shift;
   g.ksplit = psplit_;
-  g.ppart = reinterpret_cast<double*>(ws_ + L.ppart);
+  g.ppart = reinterpret_cast<longlong2*>(ws_ + L.ppart);
   t.gx = k_pad_ / sl::kBN;
   t.gy = n_pad_ / sl::kBM;
   t.gz = psplit_;
@@ -1060,7 +1148,7 @@ MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Co
 }
 
 MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   MmaTask t;
   t.a = *reinterpret_cast<const CUtensorMap*>(tmXA_);
   t.b = *reinterpret_cast<const CUtensorMap*>(tmX_);
@@ -1076,7 +1164,8 @@ MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
   g.colexp2 = reinterpret_cast<const int*>(ws_ + L.p_colexp);
   g.m_valid = k_;
   g.k = k_;
-  g.gpart = part ? part : reinterpret_cast<double*>(ws_ + L.gpart);
+  g.gpart = reinterpret_cast<longlong2*>(ws_ + L.gpart);
+  (void)part;
   t.gx = k_pad_ / sl::kBN;
   t.gy = 1;
   t.gz = 2 * ksplit_;
@@ -1085,7 +1174,7 @@ MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
 
 MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, const double* dinv, double* Xn,
                              double* upart, const Control* ctl) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   MmaTask t;
   t.a = *reinterpret_cast<const CUtensorMap*>(tmXR_);
   t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(tmF_);
@@ -1112,7 +1201,7 @@ MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, 
 }
 
 void SlicedA::fill_group_item(GroupItem* it) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   it->n_pad = n_pad_;
   it->k_pad = k_pad_;
   it->kr = kr_;
@@ -1128,12 +1217,12 @@ void SlicedA::fill_group_item(GroupItem* it) const {
   it->x_cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   it->p_cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   it->f_cmax = reinterpret_cast<unsigned long long*>(ws_ + L.f_cmax);
-  it->sgpart = reinterpret_cast<double*>(ws_ + L.gpart);
+  it->sgpart = ws_ + L.gpart;
 }
 
 int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
                      cudaEvent_t ev1, unsigned ev_flags) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   int* colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
@@ -1147,7 +1236,7 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
   if (psplit_ > 1) {
     const int64_t total = n_ * k_;
     const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-    sl::product_reduce_kernel<<<rg, 256, 0, s>>>(t.g.ppart, psplit_, X, P, total, shift, ctl);
+    launch_product_reduce(slices_, t, psplit_, X, P, total, shift, ctl, s);
   }
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
   return psplit_ > 1 ? 4 : 3;
@@ -1155,7 +1244,7 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
 
 int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, const Control* ctl, cudaStream_t s,
                         cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   const int64_t total = n_ * k_;
   const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   // T = A X: X's column planes in the X slot (kept for gram())
@@ -1169,7 +1258,7 @@ int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, con
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
   const MmaTask t1 = product_task(X, T, 0.0, ctl);
   launch_task(slices_, sl::MODE_PRODUCT, t1, s);
-  if (psplit_ > 1) sl::product_reduce_kernel<<<rg, 256, 0, s>>>(t1.g.ppart, psplit_, X, T, total, 0.0, ctl);
+  if (psplit_ > 1) launch_product_reduce(slices_, t1, psplit_, X, T, total, 0.0, ctl, s);
   // P = A T - alpha X: T's column planes in the W slot (gram() re-slices W there)
   auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
   auto* pmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
@@ -1180,13 +1269,13 @@ int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, con
 #undef EIGREF_CALL_SLICE_T
   const MmaTask t2 = product_task(T, P, alpha, ctl, X, true);
   launch_task(slices_, sl::MODE_PRODUCT, t2, s);
-  if (psplit_ > 1) sl::product_reduce_kernel<<<rg, 256, 0, s>>>(t2.g.ppart, psplit_, X, P, total, alpha, ctl);
+  if (psplit_ > 1) launch_product_reduce(slices_, t2, psplit_, X, P, total, alpha, ctl, s);
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
   return psplit_ > 1 ? 10 : 8;
 }
 
 int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
@@ -1196,13 +1285,17 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
 #undef EIGREF_CALL_SLICE_P
   const MmaTask t = gram_task(part, ctl);
   launch_task(slices_, sl::MODE_GRAM, t, s);
-  launch_gram_reduce(t.g.gpart, k_, ksplit_, out, ctl, s);
+#define EIGREF_CALL_SGR(S_)                                                                                   \
+  sl::sgram_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.gpart, k_, ksplit_, t.g.colexp, t.g.colexp2, out, ctl)
+  const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SGR)
+#undef EIGREF_CALL_SGR
   return 6;
 }
 
 int SlicedA::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
                     double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   auto* xr = reinterpret_cast<__nv_bfloat16*>(ws_ + L.xr_planes);
   auto* fp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.f_planes);
   int* xrexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
@@ -1283,6 +1376,14 @@ static void slice_grouped(int op, const GroupItem* items, const GroupDims& gd, i
   }
 }
 
+void launch_sgram_reduce_grouped(int S, const GroupItem* items, const GroupDims& gd, cudaStream_t s) {
+  const int64_t warps = 2LL * gd.max_k * gd.max_k;
+  const int rg = (int)std::min<int64_t>((warps + 7) / 8, 64);
+#define EIGREF_CALL_SGRG(S_) sl::sgram_reduce_grouped_kernel<S_><<<dim3(rg, 1, gd.count), 256, 0, s>>>(items)
+  EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_SGRG)
+#undef EIGREF_CALL_SGRG
+}
+
 void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims& gd, int max_n_pad, int parity,
                           cudaStream_t s) {
 #define EIGREF_CALL_SLICE_G(S_) slice_grouped<S_>(op, items, gd, max_n_pad, parity, s)
@@ -1293,7 +1394,7 @@ void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims
 int SlicedA::update_grid() const { return n_pad_ / sl::kBM; }
 
 int SlicedA::timed_out(cudaStream_t s) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_, k_, psplit_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
   int v = 0;
   cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);

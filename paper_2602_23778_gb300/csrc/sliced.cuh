@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace eigref {
@@ -30,8 +32,8 @@ struct MmaArgs {
   double* P;             // PRODUCT: row-major n x k
   double shift;          // PRODUCT
   const double* Xs;      // PRODUCT: operand of the shift term (row-major n x k)
-  double* ppart;         // PRODUCT with ksplit > 1: [ksplit][n x k] row-major partial products
-  double* gpart;         // GRAM: [2][ksplit][k * k] column-major partials
+  longlong2* ppart;      // PRODUCT with ksplit > 1: [ksplit][n x k] row-major exact (hi, lo) partials
+  longlong2* gpart;      // GRAM: [2][ksplit][k * k] column-major exact (hi, lo) partials
   const double* W;       // UPDATE: row-major n x k
   const double* d;       // UPDATE: Rayleigh quotients [k]
   const double* dinv;    // UPDATE: 1 / d
@@ -53,6 +55,7 @@ struct MmaTask {
 // Grouped launches of the split form over a batch (all problems share S).
 void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s);
 enum { SLICE_X_COLS = 0, SLICE_P_COLS = 1, SLICE_F_COLS = 2, SLICE_X_ROWS = 3, SLICE_ZERO_MAX = 4 };
+void launch_sgram_reduce_grouped(int S, const GroupItem* items, const GroupDims& gd, cudaStream_t s);
 void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims& gd, int max_n_pad, int parity,
                           cudaStream_t s);
 
@@ -102,6 +105,14 @@ class SlicedA {
   // Tensor-core flops one product executes (all digit pairs, padded sizes).
   double executed_flops() const;
   int slices() const { return slices_; }
+  // Split-K of the product (psplit) and of the Gram products (ksplit).  The
+  // split partials are exact, so any choice gives the same results bitwise;
+  // only the time differs (what the autotuner measures).
+  std::vector<int> psplit_candidates() const;
+  std::vector<int> ksplit_candidates() const;
+  void set_splits(int psplit, int ksplit);
+  int psplit() const { return psplit_; }
+  int ksplit() const { return ksplit_; }
   const char* error() const { return err_; }
 
  private:
@@ -109,7 +120,7 @@ class SlicedA {
   const double* A_ = nullptr;
   int64_t n_ = 0, lda_ = 0;
   int k_ = 0, precision_ = 0, slices_ = 0;
-  int n_pad_ = 0, k_pad_ = 0, kr_ = 0, ksplit_ = 1, psplit_ = 1;
+  int n_pad_ = 0, k_pad_ = 0, kr_ = 0, ksplit_ = 1, psplit_ = 1, ksplit_max_ = 1, psplit_max_ = 1;
   char* ws_ = nullptr;
   alignas(64) unsigned char tmA_[128];
   alignas(64) unsigned char tmX_[128];

@@ -71,15 +71,19 @@ def test_split_batch_matches_oracle(eig, problems):
         assert rel_diff(host(it["X"]), Xo) <= tol, (p.n, p.k)
 
 
-def test_split_batch_equals_single_split_calls_closely(eig, problems):
+def test_split_batch_equals_single_split_calls(eig, problems):
+    """The grouped launches split K differently from a single call (no product
+    split-K, shorter Gram split-K), but the split partials are exact int64 sums
+    and every reduction order is fixed per problem: the results are the same
+    bits."""
     items = batch_inputs(problems)
     st, reps = eig.refine_batched(items, max_iters=4, precision="bf16")
     assert st == 0
-    for p, it in zip(problems, items):
+    for p, it, rep in zip(problems, items, reps):
         X = dev(np.asfortranarray(p.X0))
-        eig.refine_dense(dev(p.A), X, max_iters=4, norm_a=p.normA, target="shift", shift=p.shift,
-                         precision="bf16")
-        assert rel_diff(host(it["X"]), host(X)) <= sweep_tol(p.normA + abs(p.shift), p.min_gap)
+        r1 = eig.refine_dense(dev(p.A), X, max_iters=4, norm_a=p.normA, target="shift", shift=p.shift,
+                              precision="bf16")
+        assert np.array_equal(host(it["X"]), host(X)), (p.n, p.k, rep["ksplit"], r1["ksplit"])
 
 
 def test_problems_stop_on_their_own_schedules(eig):

@@ -169,3 +169,18 @@ def test_sliced_nonfinite_input_is_reported(eig):
     X = dev(X0)
     r = eig.refine_dense(dev(p.A), X, norm_a=p.normA, precision="bf16", max_iters=3, raise_on_error=False)
     assert r["status"] == 7 and r["iterations"] == 0
+
+
+def test_autotuned_splits_do_not_change_results():
+    """The autotuner picks the product's and the Gram products' split-K by
+    timing; the split partials are exact, so a fresh handle with the tuner on
+    and one with it off give bitwise equal sweeps."""
+    import paper_2602_23778_gb300 as pkg
+    p = dense_case(1000, 128, seed=77)
+    out = []
+    for tune in (0, 1):
+        with pkg.Handle(0) as h:
+            X = dev(np.asfortranarray(p.X0))
+            r = h.refine_dense(dev(p.A), X, norm_a=p.normA, max_iters=3, precision="bf16", autotune=tune)
+            out.append((host(X), r["psplit"], r["ksplit"]))
+    assert np.array_equal(out[0][0], out[1][0]), (out[0][1:], out[1][1:])

@@ -22,8 +22,8 @@ def eig():
 
 
 def spread_problem(n=300, k=6, seed=11, noise=1e-7):
-    lam = np.linspace(-1.0, 1.0, n)
-    lam[np.argsort(-np.abs(lam))[:k]] = np.array([1.0, -0.95, 0.9, -0.85, 0.8, -0.75])[:k]
+    # targets of distinct magnitude, the rest below them (|lambda| <= 0.7)
+    lam = np.concatenate([np.array([1.0, -0.95, 0.9, -0.85, 0.8, -0.75])[:k], np.linspace(-0.7, 0.7, n - k)])
     return C.householder(n, 8, k, lam, seed, target="largest_mag", x_noise=noise)
 
 
@@ -152,3 +152,31 @@ def test_grouped_batch_rejects_the_shifted_square(eig):
               "norm_a": p.normA}]
     with pytest.raises(pkg.EigrefError):
         eig.refine_batched(items, max_iters=2, precision="bf16")
+
+
+def axis_problem(n=60, k=3, seed=41):
+    lam = np.concatenate([[1.0, 0.9, 0.8], np.linspace(-0.5, 0.5, n - 3)])
+    p = C.householder(n, 0, k, lam, seed, target="largest_mag", x_noise=0.0)
+    X0 = p.Xtrue.copy()
+    X0[k:, 1:] += 1e-6 * np.random.default_rng(seed).standard_normal((n - k, k - 1))
+    return p, C.orthonormalise(X0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_singular_leading_block_is_reported_or_resigned(eig, precision):
+    """Without the entry sign flip Y_1 has a zero column: the plain call stops
+    with EIGREF_E_SINGULAR_WY and leaves X; with resign the signs of Algorithm 2
+    are taken mid-run and the refinement follows the oracle's."""
+    import paper_2602_23778_gb300 as pkg
+    p, X0 = axis_problem()
+    X = dev(np.asfortranarray(X0))
+    r1 = eig.refine_dense(dev(p.A), X, max_iters=4, norm_a=p.normA, sign_fix=False, precision=precision,
+                          raise_on_error=False)
+    assert r1["status"] == pkg.E_SINGULAR_WY and r1["iterations"] == 0
+    assert np.array_equal(host(X), X0)
+    Xo, ro = R.refine(R.dense_operator(p.A), X0, p.normA, max_iters=12, use_sign_fix=False, resign=True)
+    X = dev(np.asfortranarray(X0))
+    r2 = eig.refine_dense(dev(p.A), X, max_iters=12, norm_a=p.normA, sign_fix=False, resign=True,
+                          precision=precision, check_every=4)
+    assert r2["status"] == 0 and r2["iterations"] == 12
+    assert rel_diff(host(X), Xo) <= 1e-12

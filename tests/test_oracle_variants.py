@@ -15,8 +15,8 @@ def random_orthogonal(k, seed):
 
 
 def spread_problem(n=120, k=6, seed=11):
-    lam = np.linspace(-1.0, 1.0, n)
-    lam[np.argsort(-np.abs(lam))[:k]] = np.array([1.0, -0.95, 0.9, -0.85, 0.8, -0.75])[:k]
+    # targets of distinct magnitude, the rest below them (|lambda| <= 0.7)
+    lam = np.concatenate([np.array([1.0, -0.95, 0.9, -0.85, 0.8, -0.75])[:k], np.linspace(-0.7, 0.7, n - k)])
     return C.householder(n, 8, k, lam, seed, target="largest_mag", x_noise=0.0)
 
 
@@ -103,3 +103,31 @@ def test_reorthonormalise_reaches_the_polar_factor():
     Xr = R.reorthonormalise(X)
     assert np.abs(Xr.T @ Xr - np.eye(7)).max() < 2e-15
     assert np.abs(Xr - U @ Vt).max() < 1e-14
+
+
+def axis_problem(n=60, k=3, seed=41):
+    """A = diag(lambda) (no reflectors): the eigenvectors are unit vectors.
+    X0 keeps column 0 exactly e_0 and perturbs the others below the leading
+    block, so Y_1 = X_1 - I has a zero column unless the signs flip it."""
+    lam = np.concatenate([[1.0, 0.9, 0.8], np.linspace(-0.5, 0.5, n - 3)])
+    p = C.householder(n, 0, k, lam, seed, target="largest_mag", x_noise=0.0)
+    X0 = p.Xtrue.copy()
+    X0[k:, 1:] += 1e-6 * np.random.default_rng(seed).standard_normal((n - k, k - 1))
+    return p, C.orthonormalise(X0)
+
+
+def test_singular_leading_block_needs_the_signs():
+    p, X0 = axis_problem()
+    assert np.array_equal(X0[:, 0], p.Xtrue[:, 0])        # Y_1(:, 0) = 0 without the sign flip
+    op = R.dense_operator(p.A)
+    try:
+        R.refine(op, X0, p.normA, max_iters=3, use_sign_fix=False)
+        raised = False
+    except R.SingularWY:
+        raised = True
+    assert raised
+    X, rep = R.refine(op, X0, p.normA, max_iters=120, tol=1e-14, use_sign_fix=False, resign=True)
+    assert rep["status"] == R.OK and rep["resigned"] == 1
+    assert np.array_equal(rep["sigma"], [-1.0, -1.0, -1.0])
+    c = np.abs(np.einsum("ij,ij->j", X / np.linalg.norm(X, axis=0), p.Xtrue))
+    assert np.all(1 - c < 1e-14)
