@@ -1001,6 +1001,22 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
       prod[par].resize(count);
       upd[par].resize(count);
     }
+    // tensor-core tasks heaviest first (longest CTAs start first; launch groups
+    // hold problems of like size, so a group's CTAs end together)
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (int64_t)runs[a].pr.n * runs[a].pr.k > (int64_t)runs[b].pr.n * runs[b].pr.k;
+    });
+    for (int slot = 0; slot < count; ++slot) {
+      const int i = order[slot];
+      const Run& r = runs[i];
+      for (int par = 0; par < 2; ++par) {
+        prod[par][slot] = sls[i].product_task(r.xbuf[par], r.b.p, r.shift, r.b.ctl);
+        upd[par][slot] = sls[i].update_task(r.xbuf[par], r.b.p, r.b.d, r.b.dinv, r.xbuf[par ^ 1], r.b.upart, r.b.ctl);
+      }
+      gram[slot] = sls[i].gram_task(nullptr, r.b.ctl);
+    }
     for (int i = 0; i < count; ++i) {
       const Run& r = runs[i];
       GroupItem& it = items[i];
@@ -1009,10 +1025,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
         it.b[par] = r.b;
         it.b[par].x = r.xbuf[par];
         it.b[par].xn = r.xbuf[par ^ 1];
-        prod[par][i] = sls[i].product_task(r.xbuf[par], r.b.p, r.shift, r.b.ctl);
-        upd[par][i] = sls[i].update_task(r.xbuf[par], r.b.p, r.b.d, r.b.dinv, r.xbuf[par ^ 1], r.b.upart, r.b.ctl);
       }
-      gram[i] = sls[i].gram_task(nullptr, r.b.ctl);
       it.n = r.pr.n;
       it.k = r.pr.k;
       it.beta_zero = q.beta == EIGREF_BETA_ZERO;
@@ -1026,22 +1039,28 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
     CUDA_TRY(h, cudaStreamSynchronize(s));
     const int S = sls[0].slices();
     m += m & 1;
-    issue_all = [&, S](int count_sweeps) {
+    const int groups = (count + 39) / 40;
+    res.streams.assign(groups, nullptr);
+    res.events.assign(groups + 1, nullptr);
+    for (auto& x : res.streams) CUDA_TRY(h, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    for (auto& e : res.events) CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    const cudaStream_t* side = groups > 1 ? res.streams.data() : nullptr;
+    const cudaEvent_t* evs = res.events.data();
+    issue_all = [&, S, groups, side, evs](int count_sweeps) {
       int launches = 0;
-      const int groups = (count + 39) / 40;
       for (int t = 0; t < count_sweeps; ++t) {
         const int par = t & 1;
         launch_slice_grouped(S, SLICE_ZERO_MAX, items_dev, gd, max_n_pad, par, s);
         launch_slice_grouped(S, SLICE_X_COLS, items_dev, gd, max_n_pad, par, s);
-        launch_mma_tasks(S, sl::MODE_PRODUCT, prod[par].data(), count, s);
+        launch_mma_tasks(S, sl::MODE_PRODUCT, prod[par].data(), count, s, side, evs);
         launch_slice_grouped(S, SLICE_P_COLS, items_dev, gd, max_n_pad, par, s);
-        launch_mma_tasks(S, sl::MODE_GRAM, gram.data(), count, s);
+        launch_mma_tasks(S, sl::MODE_GRAM, gram.data(), count, s, side, evs);
         launch_sgram_reduce_grouped(S, items_dev, gd, s);
         launch_top_gram_grouped(items_dev, gd, par, s);
         launch_kxk_stage_grouped(items_dev, gd, par, s);
         launch_slice_grouped(S, SLICE_X_ROWS, items_dev, gd, max_n_pad, par, s);
         launch_slice_grouped(S, SLICE_F_COLS, items_dev, gd, max_n_pad, par, s);
-        launch_mma_tasks(S, sl::MODE_UPDATE, upd[par].data(), count, s);
+        launch_mma_tasks(S, sl::MODE_UPDATE, upd[par].data(), count, s, side, evs);
         launch_finalize_grouped(items_dev, gd, par, s);
         launch_normalize_grouped(items_dev, gd, par, s);
         launches += 24 + 3 * groups;

@@ -101,7 +101,10 @@ void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, 
 // Gram partials over a row range: part[z][c] = (X^T Y)[rows of chunk c],
 // z = 0: Y = X (G), z = 1: Y = P (S).  T x T output tile per CTA (T = 16 for
 // k <= 16, else 32), 256 threads.  Deterministic: partials are summed in
-// chunk order by gram_reduce.
+// chunk order by gram_reduce.  G is symmetric and fma(a, b, c) = fma(b, a, c),
+// so for z = 0 only tiles ti <= tj are formed (and at T = 16 only the 136
+// outputs i <= j, on 5 of the 8 warps) and mirrored on the way out, with the
+// same bits as forming both.
 // ---------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restrict__ X,
@@ -117,9 +120,23 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restr
   const int tiles = (k + T - 1) / T;
   const int ti = blockIdx.y % tiles, tj = blockIdx.y / tiles;
   const int z = blockIdx.z;
+  if (z == 0 && ti > tj) return;            // the mirror of tile (tj, ti)
   const double* Yb = z ? P : X;
   const int tid = threadIdx.x;
-  const int i = tid % T, jg = tid / T;      // outputs (i, jg * OUT + q)
+  int i = tid % T, jg = tid / T;            // outputs (i, jg * OUT + q)
+  const bool tri = (T == 16 && z == 0);     // upper triangle of the single G tile
+  bool active = true;
+  if (tri) {
+    // thread t < 136 takes the t-th pair (i, j), i <= j, row by row
+    int t = tid, r = 0;
+    while (r < 16 && t >= 16 - r) {
+      t -= 16 - r;
+      ++r;
+    }
+    active = r < 16;
+    i = active ? r : 0;
+    jg = active ? r + t : 0;
+  }
   double acc[OUT];
 #pragma unroll
   for (int q = 0; q < OUT; ++q) acc[q] = 0.0;
@@ -134,20 +151,26 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restr
       Xb[rr][cc] = (row < re && cb < k) ? Yb[row * k + cb] : 0.0;
     }
     __syncthreads();
+    if (active) {
 #pragma unroll 8
-    for (int rr = 0; rr < RB; ++rr) {
-      const double a = Xa[rr][i];
+      for (int rr = 0; rr < RB; ++rr) {
+        const double a = Xa[rr][i];
 #pragma unroll
-      for (int q = 0; q < OUT; ++q) acc[q] = fma(a, Xb[rr][jg * OUT + q], acc[q]);
+        for (int q = 0; q < OUT; ++q) acc[q] = fma(a, Xb[rr][jg * OUT + q], acc[q]);
+      }
     }
     __syncthreads();
   }
   double* out = part + ((int64_t)z * nchunks + c) * k * k;
   const int gi = ti * T + i;
+  if (!active) return;
 #pragma unroll
   for (int q = 0; q < OUT; ++q) {
     const int gj = tj * T + jg * OUT + q;
-    if (gi < k && gj < k) out[gi + (int64_t)gj * k] = acc[q];
+    if (gi < k && gj < k) {
+      out[gi + (int64_t)gj * k] = acc[q];
+      if (z == 0) out[gj + (int64_t)gi * k] = acc[q];   // G(j, i) = G(i, j)
+    }
   }
 }
 

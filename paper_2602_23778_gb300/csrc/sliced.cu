@@ -64,6 +64,7 @@ constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 102
 
 struct __align__(8) Bars {
   uint64_t a_full[kRA], a_empty[kRA], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
+  uint64_t g01;                      // rotating accumulators: weight groups 0, 1 of a chunk drained
   uint32_t tmem_base;
   int abort;
 };
@@ -210,6 +211,14 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   const int KB = kb_hi - kb_lo;                      // K blocks of this CTA
   const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
   constexpr int NBUF = (2 * S * kBN <= 512) ? 2 : 1; // TMEM accumulator sets (double-buffered if they fit)
+  // When two sets do not fit (S = 9: 288 of 512 columns each), even chunks
+  // sit at columns [0, 288) and odd chunks at [224, 512): consecutive chunks
+  // share 64 columns, weight groups 7, 8 of an even chunk and 0, 1 of an odd
+  // one.  The epilogue drains those two groups first (even chunks from w = 8
+  // down, odd chunks from w = 0 up), so the next chunk's MMAs wait for two
+  // groups instead of the whole drain.
+  constexpr bool ROT = NBUF == 1;
+  constexpr uint32_t kOddBase = 512u - (uint32_t)(S * kBN);
   const CUtensorMap* tB = job ? tmB2 : tmB;
   volatile int* abort_flag = &bars->abort;
 
@@ -227,6 +236,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       mbar_init(smem_u32(&bars->acc_empty[i]), kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bars->drain), 1);
+    mbar_init(smem_u32(&bars->g01), kEpiWarps);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -296,7 +306,11 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         const bool first = (kb % kChunkBlocks) == 0;
         const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
         if (first) {
-          ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
+          if (ROT) {
+            if (c > 0) ok = mbar_wait(smem_u32(&bars->g01), (uint32_t)((c - 1) & 1), abort_flag);
+          } else {
+            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
+          }
           if (!ok) break;
           tc_fence_after();
         }
@@ -305,7 +319,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         if (!ok) break;
         tc_fence_after();
         const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
-        const uint32_t dbase = tbase + (uint32_t)(buf * S * kBN);
+        const uint32_t cbase = ROT ? ((c & 1) ? kOddBase : 0u) : (uint32_t)(buf * S * kBN);
         const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -313,12 +327,13 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           if (!ok) break;
           tc_fence_after();
           const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
-          // B = B-side planes 0 .. S-1-s stacked: N = 32 (S - s) rows, issued
-          // as pieces of at most 256 (the M = 128 limit); +2 in the address
-          // field steps 32 bytes (16 K) inside the 128-byte swizzle row
+          // B = B-side planes 0 .. S-1-s stacked: N = 32 (S - s) rows (weight
+          // groups w = s .. S-1 at columns cbase + 32 w), issued as pieces of
+          // at most 256 (the M = 128 limit); +2 in the address field steps 32
+          // bytes (16 K) inside the 128-byte swizzle row
           const int N = kBN * (S - s);
           const int N1 = N < 256 ? N : 256;
-          const uint32_t dt = dbase + (uint32_t)(s * kBN);
+          const uint32_t dt = tbase + cbase + (uint32_t)(s * kBN);
           tc_mma(dt, ad, xd, idesc_bf16(kBM, N1), s == 0 ? acc0 : 1u);
           tc_mma(dt, ad + 2, xd + 2, idesc_bf16(kBM, N1), 1u);
           tc_mma(dt, ad + 4, xd + 4, idesc_bf16(kBM, N1), 1u);
@@ -366,20 +381,23 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-      const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * S * kBN + half * kC);
+      const uint32_t cbase = ROT ? ((c & 1) ? kOddBase : 0u) : (uint32_t)(buf * S * kBN);
+      const bool down = ROT && (c & 1) == 0;            // even chunks drain from w = S-1 down
+      const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + cbase + (uint32_t)(half * kC);
       // several weights per round trip to TMEM (two at S >= 8, within the register budget)
       constexpr int GW = S >= 8 ? 2 : 3;
+      static_assert(!ROT || GW >= 2, "the next chunk may only wait for weight groups 0 and 1");
 #pragma unroll
       for (int w0 = 0; w0 < S; w0 += GW) {
         uint32_t r[GW][kC];
 #pragma unroll
         for (int q = 0; q < GW; ++q)
-          if (w0 + q < S) TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
+          if (w0 + q < S) TC_LD16(tw + (uint32_t)((down ? S - 1 - (w0 + q) : w0 + q) * kBN), r[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < GW; ++q) {
-          const int w = w0 + q;
-          if (w >= S) continue;
+          if (w0 + q >= S) continue;
+          const int w = down ? S - 1 - (w0 + q) : w0 + q;
           if (w < 4) {
             const int sh = kBits * (3 - w);
 #pragma unroll
@@ -389,6 +407,12 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
 #pragma unroll
             for (int j = 0; j < kC; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
           }
+        }
+        if (ROT && w0 == 0) {
+          // the two shared weight groups are in registers: the next chunk may overwrite them
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars->g01));
         }
       }
       tc_fence_before();
@@ -1321,10 +1345,19 @@ static void launch_mma_group(int S, const sl::GroupMma& p, int ctas, cudaStream_
 #undef EIGREF_CALL_MMA_G
 }
 
-void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s) {
+void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s, const cudaStream_t* side,
+                      const cudaEvent_t* ev) {
   static sl::GroupMma p;   // host staging of the parameter block (copied at launch)
-  for (int t0 = 0; t0 < count; t0 += sl::kGroupMax) {
+  const int groups = (count + sl::kGroupMax - 1) / sl::kGroupMax;
+  // groups on side streams (forked from s, joined back): their tails overlap
+  if (side) cudaEventRecord(ev[groups], s);
+  for (int t0 = 0, gi = 0; t0 < count; t0 += sl::kGroupMax, ++gi) {
     const int nt = std::min(sl::kGroupMax, count - t0);
+    cudaStream_t ls = s;
+    if (side) {
+      ls = side[gi];
+      cudaStreamWaitEvent(ls, ev[groups], 0);
+    }
     memset(&p, 0, sizeof(p));
     int ctas = 0;
     for (int i = 0; i < nt; ++i) {
@@ -1340,9 +1373,13 @@ void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStre
     }
     p.cta_begin[nt] = ctas;
     p.count = nt;
-    if (mode == sl::MODE_PRODUCT) launch_mma_group<sl::MODE_PRODUCT>(S, p, ctas, s);
-    else if (mode == sl::MODE_GRAM) launch_mma_group<sl::MODE_GRAM>(S, p, ctas, s);
-    else launch_mma_group<sl::MODE_UPDATE>(S, p, ctas, s);
+    if (mode == sl::MODE_PRODUCT) launch_mma_group<sl::MODE_PRODUCT>(S, p, ctas, ls);
+    else if (mode == sl::MODE_GRAM) launch_mma_group<sl::MODE_GRAM>(S, p, ctas, ls);
+    else launch_mma_group<sl::MODE_UPDATE>(S, p, ctas, ls);
+    if (side) {
+      cudaEventRecord(ev[gi], ls);
+      cudaStreamWaitEvent(s, ev[gi], 0);
+    }
   }
 }
 

@@ -53,7 +53,11 @@ struct MmaTask {
 };
 
 // Grouped launches of the split form over a batch (all problems share S).
-void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s);
+// Up to 40 tasks per launch, CTAs in task order.  side (optional): one stream
+// per launch group, forked from s and joined back with ev[0..groups]
+// (groups + 1 events), so the groups run side by side.
+void launch_mma_tasks(int S, int mode, const MmaTask* tasks, int count, cudaStream_t s,
+                      const cudaStream_t* side = nullptr, const cudaEvent_t* ev = nullptr);
 enum { SLICE_X_COLS = 0, SLICE_P_COLS = 1, SLICE_F_COLS = 2, SLICE_X_ROWS = 3, SLICE_ZERO_MAX = 4 };
 void launch_sgram_reduce_grouped(int S, const GroupItem* items, const GroupDims& gd, cudaStream_t s);
 void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims& gd, int max_n_pad, int parity,
