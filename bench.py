@@ -259,26 +259,35 @@ LAPLACE = ("sparse CSR 5-point Dirichlet Laplacian on a 1024 x 1000 grid (n=1,02
 
 
 def run_laplacian(args, world, rank, local):
-    """Sweeps/s on the sparse workload; the SpMM is the HBM-bound product."""
+    """Sweeps/s on the sparse workload: FP64 SpMM, the Gram products on the
+    tensor cores (split form, default) or in FP64, FP64 k x k stage and update."""
     import torch
     import paper_2602_23778_gb300 as eigref
     from workloads import configs as C
     if args.steps is None:
         args.steps = 100
+    precision = args.precision or "bf16"
     torch.cuda.set_device(local)
     p = C.config4(per_column=True)
     rp, ci, val = (torch.from_numpy(a).cuda() for a in (p.row_ptr, p.col_idx, p.val))
     X0 = torch.from_numpy(np.ascontiguousarray(p.X0.T)).cuda().t()
     stream = torch.cuda.Stream()
     h = eigref.Handle(local, stream)
-    kw = dict(norm_a=p.normA, target="smallest", shift=p.lam_kp1)
-    h.refine_csr(rp, ci, val, X0.clone(), max_iters=args.warmup, check_every=max(2, args.warmup), **kw)
-    torch.cuda.synchronize()
-    X = X0.clone()
-    with ClockSampler(local) as clk:
-        rep = h.refine_csr(rp, ci, val, X, max_iters=args.steps, check_every=args.steps, profile=True, **kw)
+    kw = dict(norm_a=p.normA, target="smallest", shift=p.lam_kp1, precision=precision)
+
+    def timed(form_kw, steps):
+        h.refine_csr(rp, ci, val, X0.clone(), max_iters=args.warmup, check_every=max(2, args.warmup), **form_kw)
         torch.cuda.synchronize()
+        X = X0.clone()
+        r = h.refine_csr(rp, ci, val, X, max_iters=steps, check_every=steps, profile=True, **form_kw)
+        torch.cuda.synchronize()
+        return r
+
+    with ClockSampler(local) as clk:
+        rep = timed(kw, args.steps)
     ms_step = rep["sweeps_ms"] / rep["iterations"]
+    if world > 1:
+        ms_step = max_over_ranks(ms_step, "cuda")
     nnz, n, k = len(p.val), p.n, p.k
     bytes_launch = 12.0 * nnz + 4.0 * (n + 1) + 2 * 8.0 * n * k
     flops_launch = 2.0 * nnz * k
@@ -289,8 +298,12 @@ def run_laplacian(args, world, rank, local):
     fp64_peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
     out = {"metric": METRIC, "value": world * 1000.0 / ms_step, "unit": UNIT, "n_gpus": world,
            "steps": rep["iterations"], "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": LAPLACE, "n": n, "k": k, "nnz": nnz, "form": "fp64 CSR",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f64+bf16-slices",
+           "data": "synthetic",
+           "config": {"workload": LAPLACE, "n": n, "k": k, "nnz": nnz,
+                      "form": "FP64 SpMM, " + ("FP64 Gram products" if precision == "fp64" else
+                                               "Gram products as BF16 digit planes on the tensor cores"),
+                      "split_k_gram": rep["ksplit"] or None,
                       "l2": "inputs larger than L2 (CSR 65 MB + X 131 MB + P 131 MB per SpMM); no flush"},
            "roofline": {"bound": "alu", "kernel": "spmm_csr_vec2_kernel", "achieved": tfs, "peak": fp64_peak,
                         "unit": "TFLOP/s", "frac": tfs / fp64_peak, "traffic": traffic_for("spmm.cu", "csr"),
@@ -301,6 +314,11 @@ def run_laplacian(args, world, rank, local):
                                 "algorithmic_bytes_per_launch": bytes_launch}},
            "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary(),
            "status": rep["status_string"]}
+    if rank == 0 and precision != "fp64" and not args.no_fp64_compare:
+        r64 = timed(dict(kw, precision="fp64"), args.steps)
+        v64 = 1000.0 * r64["iterations"] / r64["sweeps_ms"]
+        out["fp64_form"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["sweeps_ms"] / r64["iterations"],
+                            "split_over_fp64": out["value"] / world / v64}
     h.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -396,7 +414,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--cpu-sweeps", type=int, default=60, help="oracle sweeps timed for cpu_baseline (about 10 s)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 form beside the split form")
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--n", type=int, default=16384, help="smaller n / k only for profiling captures")
@@ -510,7 +528,8 @@ def main():
            "config": {"workload": WORKLOAD, "n": n, "k": k, "form": precision, "seed": 3000,
                       "slices": (args.slices or 9) if precision != "fp64" else None,
                       "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
-                      "parallelism": "replicas" if world > 1 else "single"},
+                      "parallelism": "replicas" if world > 1 else "single",
+                      "split_k": {"product": rep["psplit"], "gram": rep["ksplit"]} if precision != "fp64" else None},
            "setup_ms": rep["setup_ms"], "call_s": call_s, "roofline": roof,
            "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary()}
 
@@ -553,15 +572,18 @@ def main():
             out["fp64_form"]["accuracy"] = accuracy(kw64)
 
     if rank == 0 and not args.no_e2e:
-        Ah = np.ascontiguousarray(p.A)
-        Xh = np.asfortranarray(p.X0.copy())
+        # pinned host buffers (page-locked, as a serving host keeps its inputs)
+        Ah = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()
+        Xh = torch.from_numpy(np.ascontiguousarray(p.X0.T)).pin_memory().t()   # column-major n x k
         t0 = time.perf_counter()
         re = h.refine_dense(Ah, Xh, max_iters=args.steps, check_every=args.steps, **kw)
         e2e_s = time.perf_counter() - t0
+        nb_a, nb_x = Ah.numel() * 8, Xh.numel() * 8
         out["e2e"] = {"value": re["iterations"] / e2e_s, "unit": UNIT,
-                      "h2d_bytes_per_step": (Ah.nbytes + Xh.nbytes) / args.steps,
-                      "d2h_bytes_per_step": (Xh.nbytes + 8 * k) / args.steps,
-                      "note": "host A and X through eigref_refine_dense, copies and set-up inside the timed call"}
+                      "h2d_bytes_per_step": (nb_a + nb_x) / args.steps,
+                      "d2h_bytes_per_step": (nb_x + 8 * k) / args.steps,
+                      "note": "pinned host A and X through eigref_refine_dense; the H2D copies, slicing of A "
+                              "and all set-up inside the timed call"}
 
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, wall = cpu_oracle_rate(p, args.cpu_sweeps)

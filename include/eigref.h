@@ -165,7 +165,10 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
                         double* X, int64_t ldx, int k,
                         const eigref_params* p, eigref_report* rep);
 
-/* Same for CSR A (the product is an FP64 SpMM; p->precision is ignored). */
+/* Same for CSR A.  The product is an FP64 SpMM.  p->precision EIGREF_FP64:
+ * FP64 Gram products; EIGREF_BF16_SLICES: the Gram products X^T X and X^T W
+ * as error-free BF16 digit planes on the tensor cores (k <= 16, else
+ * EIGREF_E_UNSUPPORTED); the k x k stage and the row update stay FP64. */
 int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx,
                       const double* val, int64_t n, int64_t nnz,
                       double* X, int64_t ldx, int k,
@@ -202,6 +205,17 @@ typedef struct eigref_problem {
  * count < 1 or host-memory A or X. */
 int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* probs,
                           const eigref_params* p, eigref_report* reps);
+
+/* Lines 3-4 of Algorithm 4 on their own: G = X^T X and S = X^T P over all n
+ * rows, k x k column-major (ld k) into caller-owned G and S (host or device).
+ * X (ldx) and P (ldp) are n x k column-major in device memory.  precision
+ * EIGREF_FP64: FP64 dot products; EIGREF_BF16_SLICES: error-free BF16 digit
+ * planes on the tensor cores (the split form used by eigref_refine_csr),
+ * k <= 16, each entry exact up to the slice truncation and one rounding.
+ * Errors: EIGREF_E_INVALID (NULL, sizes, host X/P), EIGREF_E_UNSUPPORTED
+ * (other precisions, k > 16 in the split form), EIGREF_E_CUDA, EIGREF_E_TIMEOUT. */
+int eigref_gram(eigref_handle h, const double* X, int64_t ldx, const double* P, int64_t ldp,
+                int64_t n, int k, int precision, int slices, double* G, double* S);
 
 /* Line 1 of Algorithm 4 on its own: P = (A - shift I) X for dense A, with the
  * chosen precision (slices as in eigref_params).  P is n x k column-major

@@ -25,7 +25,7 @@ BETAS = {"cluster": 0, "zero": 1}
 
 SYMBOLS = ["eigref_params_default", "eigref_create", "eigref_destroy", "eigref_refine_dense",
            "eigref_refine_csr", "eigref_product_dense", "eigref_product_csr", "eigref_status_string",
-           "eigref_last_error", "eigref_product_dense_noalloc", "eigref_refine_batched"]
+           "eigref_last_error", "eigref_product_dense_noalloc", "eigref_refine_batched", "eigref_gram"]
 NOALLOC_MAX_ELEMS = 1 << 20
 
 
@@ -90,6 +90,7 @@ def lib():
         L.eigref_product_dense_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, dbl, vp, i64, vp]
         L.eigref_refine_batched.argtypes = [vp, i32, ctypes.POINTER(Problem), ctypes.POINTER(Params),
                                             ctypes.POINTER(Report)]
+        L.eigref_gram.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, i32, vp, vp]
         L.eigref_status_string.argtypes = [i32]
         L.eigref_status_string.restype = ctypes.c_char_p
         L.eigref_last_error.argtypes = [vp]
@@ -305,6 +306,20 @@ class Handle:
         if raise_on_error and st in (E_INVALID, E_CUDA, E_NOMEM, E_UNSUPPORTED):
             raise EigrefError(st, self.last_error())
         return st, outs
+
+    def gram(self, X, P, G, S, precision="fp64", slices=0):
+        """G = X^T X, S = X^T P (eigref_gram); X, P column-major device arrays,
+        G, S k x k column-major, written in place."""
+        px, n, k, ldx, kx = _colmajor(X)
+        pp, n2, k2, ldp, kp = _colmajor(P, "P")
+        pg, _, _, _, kg = _colmajor(G, "G")
+        ps, _, _, _, ks = _colmajor(S, "S")
+        if n2 != n or k2 != k:
+            raise ValueError("X and P shapes differ")
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        st = lib().eigref_gram(self._h, px, ldx, pp, ldp, n, k, prec, int(slices), pg, ps)
+        if st != OK:
+            raise EigrefError(st, self.last_error())
 
     def product_dense(self, A, X, P, shift=0.0, precision="fp64", slices=0):
         """P = (A - shift I) X (eigref_product_dense); P column-major, written in place."""

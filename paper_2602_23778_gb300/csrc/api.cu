@@ -159,6 +159,7 @@ struct Problem {
   int64_t n = 0, nnz = 0;
   int k = 0;
   SlicedA* sliced = nullptr;  // split-precision dense product, or null
+  SlicedGram* sgram = nullptr;  // CSR split form: tensor-core Gram products (k <= 16), or null
   bool square = false;        // B = A^2 - alpha I (Section 5.2): W = A (A X) - alpha X
   double* tbuf = nullptr;     // A X of the shifted square (workspace)
 };
@@ -199,6 +200,17 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   const int64_t n = pr.n;
   const int k = pr.k;
   int launches = launch_product(pr, b.x, b.p, shift, b.ctl, s, ev0, ev1, ev_flags);
+  if (pr.sgram) {
+    // CSR split form: Gram products over all rows on the tensor cores, the
+    // leading block in FP64 (the k x k stage forms G2 = G - G1); FP64 update
+    launches += pr.sgram->gram(b.x, b.p, b.g2, b.ctl, s);
+    launch_top_gram(b.x, b.p, k, b.gtop, b.ctl, s);
+    launch_kxk_stage(b, k, delta, beta_zero, s);
+    launch_update_rows(b, n, k, s);
+    launch_finalize(b, k, delta, s);
+    launch_normalize(b, n, k, s);
+    return launches + 1 + 12 + 1 + 2;
+  }
   if (pr.sliced) {
     // split form: Gram products over all rows on the tensor cores, the
     // leading k x k block in FP64; the k x k stage forms G2 = G - G1
@@ -289,14 +301,14 @@ void run_layout(Run& r, Carve& c, Control* ctl) {
   b.nchunks = r.nchunks;
   b.chunk_rows = r.chunk_rows;
   b.ugrid = r.ugrid;
-  b.mixed = r.pr.sliced != nullptr;  // the split form keeps Y1^{-1} by Newton-Schulz steps
+  b.mixed = r.pr.sliced != nullptr || r.pr.sgram != nullptr;  // the split form keeps Y1^{-1} by Newton-Schulz steps
 }
 
 // Bytes of workspace the Run needs (its buffers, then the sliced planes).
 size_t run_bytes(Run& r, bool own_ctl) {
   Carve c;
   run_layout(r, c, own_ctl ? nullptr : reinterpret_cast<Control*>(16));
-  const size_t extra = r.pr.sliced ? r.pr.sliced->workspace_bytes() : 0;
+  const size_t extra = r.pr.sliced ? r.pr.sliced->workspace_bytes() : (r.pr.sgram ? r.pr.sgram->workspace_bytes() : 0);
   return ((c.off + 255) & ~size_t(255)) + 1024 + extra;
 }
 
@@ -305,6 +317,7 @@ void run_bind(Run& r, char* base, Control* ctl) {
   c.base = base;
   run_layout(r, c, ctl);
   if (r.pr.sliced) r.pr.sliced->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
+  if (r.pr.sgram) r.pr.sgram->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
 }
 
 // Shift and delta from ||A|| and the target (Sections 3.1.3, 5.1 and 5.2).
@@ -360,6 +373,10 @@ int run_setup_device(eigref_ctx* h, Run& r, cudaStream_t s) {
   if (r.pr.sliced) {
     const int st = r.pr.sliced->prepare(s);
     if (st) return set_err(h, st, "%s", r.pr.sliced->error());
+  }
+  if (r.pr.sgram) {
+    const int st = r.pr.sgram->prepare(s);
+    if (st) return set_err(h, st, "%s", r.pr.sgram->error());
   }
   if (r.q.rayleigh_ritz) {
     // Section 3.3: X <- its Ritz vectors for B, then the signs of Algorithm 2
@@ -671,7 +688,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
     rep->product_launches = product_launches;
     rep->kernel_launches = kernel_launches;
     rep->psplit = r.pr.sliced ? r.pr.sliced->psplit() : 0;
-    rep->ksplit = r.pr.sliced ? r.pr.sliced->ksplit() : 0;
+    rep->ksplit = r.pr.sliced ? r.pr.sliced->ksplit() : (r.pr.sgram ? r.pr.sgram->ksplit() : 0);
   }
   if (status != EIGREF_OK)
     set_err(h, status, "%s after %d sweeps", eigref_status_string(status), fin.iterations);
@@ -858,7 +875,18 @@ int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* co
   pr.rp = static_cast<const int32_t*>(bufs[0] ? bufs[0] : row_ptr);
   pr.ci = static_cast<const int32_t*>(bufs[1] ? bufs[1] : col_idx);
   pr.val = static_cast<const double*>(bufs[2] ? bufs[2] : val);
-  st = refine_common(h, pr, X, ldx, p, rep);
+  SlicedGram sg;
+  if (p && p->precision == EIGREF_BF16_SLICES) {
+    st = sg.configure(n, k, p->slices);
+    if (st) {
+      set_err(h, st, "%s", sg.error());
+    } else {
+      pr.sgram = &sg;
+    }
+  } else if (p && p->precision != EIGREF_FP64) {
+    st = set_err(h, EIGREF_E_UNSUPPORTED, "CSR: precision %d not built (FP64 or BF16 slices)", p->precision);
+  }
+  if (st == EIGREF_OK) st = refine_common(h, pr, X, ldx, p, rep);
   cudaStreamSynchronize(h->stream);
   for (void* q : bufs)
     if (q) cudaFree(q);
@@ -1172,6 +1200,63 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
     set_err(h, status, "problem %d: %s after %d sweeps", first_bad, eigref_status_string(status),
             res.hc[first_bad].iterations);
   return status;
+}
+
+// G = X^T X, S = X^T P over all n rows (lines 3-4 of Algorithm 4 on their
+// own) through the kernels the sweeps use.
+int eigref_gram(eigref_handle h, const double* X, int64_t ldx, const double* P, int64_t ldp, int64_t n, int k,
+                int precision, int slices, double* G, double* S) {
+  if (!h) return EIGREF_E_INVALID;
+  h->err[0] = 0;
+  if (!X || !P || !G || !S) return set_err(h, EIGREF_E_INVALID, "NULL argument");
+  if (n < 1 || k < 1 || k > kMaxK || ldx < n || ldp < n) return set_err(h, EIGREF_E_INVALID, "bad sizes");
+  if (!is_device_ptr(X) || !is_device_ptr(P)) return set_err(h, EIGREF_E_INVALID, "gram needs X and P in device memory");
+  if (precision != EIGREF_FP64 && precision != EIGREF_BF16_SLICES)
+    return set_err(h, EIGREF_E_UNSUPPORTED, "precision %d not built for the Gram products", precision);
+  if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
+  cudaStream_t s = h->stream;
+  SlicedGram sg;
+  if (precision == EIGREF_BF16_SLICES) {
+    const int st = sg.configure(n, k, slices);
+    if (st) return set_err(h, st, "%s", sg.error());
+  }
+  int64_t chunk_rows = 256;
+  while ((n + chunk_rows - 1) / chunk_rows > 1024) chunk_rows *= 2;
+  const int nchunks = (int)std::max<int64_t>(1, (n + chunk_rows - 1) / chunk_rows);
+  const int64_t kk = (int64_t)k * k;
+  auto lay = [&](Carve& c, double** xi, double** pi, double** gpart, double** out) {
+    *xi = c.take<double>(n * k);
+    *pi = c.take<double>(n * k);
+    *gpart = c.take<double>(2 * (int64_t)nchunks * kk);
+    *out = c.take<double>(2 * kk);
+  };
+  double *xi, *pi, *gpart, *out;
+  Carve c0;
+  lay(c0, &xi, &pi, &gpart, &out);
+  const size_t extra = precision == EIGREF_BF16_SLICES ? sg.workspace_bytes() : 0;
+  int st = ensure_ws(h, c0.off + 1024 + extra);
+  if (st) return st;
+  Carve c;
+  c.base = static_cast<char*>(h->ws);
+  lay(c, &xi, &pi, &gpart, &out);
+  launch_copy_in(X, ldx, xi, n, k, nullptr, s);
+  launch_copy_in(P, ldp, pi, n, k, nullptr, s);
+  if (precision == EIGREF_BF16_SLICES) {
+    sg.bind_workspace(static_cast<char*>(h->ws) + ((c.off + 255) & ~size_t(255)));
+    st = sg.prepare(s);
+    if (st) return set_err(h, st, "%s", sg.error());
+    sg.gram(xi, pi, out, nullptr, s);
+    if (sg.timed_out(s)) return set_err(h, EIGREF_E_TIMEOUT, "tensor-core Gram wait timed out");
+  } else {
+    launch_gram(xi, pi, k, 0, n, chunk_rows, nchunks, gpart, out, nullptr, s);
+  }
+  const cudaMemcpyKind kg = is_device_ptr(G) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const cudaMemcpyKind ks = is_device_ptr(S) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(h, cudaMemcpyAsync(G, out, kk * sizeof(double), kg, s));
+  CUDA_TRY(h, cudaMemcpyAsync(S, out + kk, kk * sizeof(double), ks, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  CUDA_TRY(h, cudaGetLastError());
+  return EIGREF_OK;
 }
 
 // P = (A - shift I) X through the same product kernels the sweeps use.

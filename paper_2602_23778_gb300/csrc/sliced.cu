@@ -11,9 +11,9 @@
 // FP32.  The product keeps the S(S+1)/2 digit pairs with s + t <= S + 1
 // (triangular truncation):
 //     W_ij = 2^(e_i + f_j) sum_w 2^-7(w+2) C_w,   C_w = sum_{s+t=w} A_s X_t
-// (0-based s, t, w).  C_w is accumulated in FP32 over K chunks of 256:
-// the largest partial sum is bounded by 256 (2 * 128 * 64 + (S - 2) * 64 * 64)
-// <= 256 * 45056 < 2^24 (S <= 9), so every FP32 addition is exact.  After
+// (0-based s, t, w).  C_w is accumulated in FP32 over K chunks of 320:
+// the largest partial sum is bounded by 320 (2 * 128 * 64 + (S - 2) * 64 * 64)
+// <= 320 * 45056 = 14417920 < 2^24 (S <= 9), so every FP32 addition is exact.  After
 // each chunk the epilogue warps move C_w into two int64 registers per output
 // (hi = sum_{w<4} C_w 2^7(3-w), lo = sum_{w>=4} C_w 2^7(S-1-w)), exact
 // integer arithmetic; at the end W_ij = 2^(e_i+f_j) (hi 2^-35 + lo
@@ -28,8 +28,10 @@
 // warps 2-9 drain TMEM (two per lane group, 16 columns each).  (At S = 9 the plane-0 stack is 288 rows and goes
 // out as two instructions, N = 256 and N = 32.)  The accumulators are double-buffered when they fit
 // (2 x S x 32 FP32 columns <= 512, S <= 8) so draining overlaps the next
-// chunk; at S = 9 one set is used and the MMAs wait for each drain.  All waits are bounded (globaltimer); on expiry the CTA records a
-// timeout, drains what it started and returns.
+// chunk; at S = 9 consecutive chunks alternate between columns [0, 288) and
+// [224, 512) and share only the two weight groups the epilogue drains first.
+// All waits are bounded (globaltimer); on expiry the CTA records a timeout,
+// drains what it started and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -51,7 +53,7 @@ constexpr int kDefaultS = 9;       // default digit planes (63 bits: FP64-level 
 constexpr int kBM = 128;           // rows of W per CTA
 constexpr int kBN = 32;            // columns of W per CTA
 constexpr int kBK = 64;            // K per pipeline stage (128 bytes of BF16)
-constexpr int kChunkBlocks = 4;    // K blocks per exact accumulation chunk (256)
+constexpr int kChunkBlocks = 5;    // K blocks per exact accumulation chunk (320: 320 x 45056 < 2^24)
 constexpr int kRA = 9;             // A ring stages (a whole K block of planes at S = 9)
 constexpr int kRX = 2;             // X ring stages
 constexpr int kATile = kBM * kBK * 2;                // 16 KiB
@@ -527,6 +529,295 @@ __global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const _
 }
 
 // ---------------------------------------------------------------------------
+// Gram products G = X^T X and S = X^T W for k <= 16 columns over very many
+// rows (the sparse workloads).  With 16-row planes, S planes of a K block
+// stack into one tile of 16 S rows: the MMA takes A = planes 0..7 of X
+// (128 rows) and B = all S planes of Y (N = 16 S), so one instruction forms
+// every plane pair (s, t) -- each TMEM element holds exactly one pair, at
+// lane 16 s + i, column 16 t + j.  Plane 8 of X (S = 9) is a second M = 128
+// instruction whose rows 16..127 read past the plane and are ignored, paired
+// with plane 0 of Y (N = 16).  One CTA per K split forms both products from
+// one load of each tile.  A single pair's sum stays below 2^24 for 960 K
+// (960 x 128 x 128 < 2^24), so chunks are 15 K blocks long.  The epilogue
+// keeps, per thread, the int64 (hi, lo) sums of its plane row s for 16
+// columns j and weights w = s + t <= S - 1; at the end the 16 threads that
+// hold a row i add their sums in shared memory, and one exact int64 pair per
+// output and split is written.
+// ---------------------------------------------------------------------------
+constexpr int kG16Stages = 5;
+constexpr int kG16Chunk = 15;                       // K blocks per exact chunk (960)
+constexpr int kG16Tile = 144 * kBK * 2;             // 16 S rows x 64 K, BF16 (S = 9: 18 KiB)
+constexpr int kG16Stage = 2 * kG16Tile;             // X tile + Y tile
+constexpr int kG16Smem = kG16Stages * kG16Stage + 1024 + 1024;
+
+struct Gram16Args {
+  int kb_total;            // K blocks of 64 over all rows
+  int ksplit;              // CTAs (K splits)
+  int k;                   // columns that exist (<= 16)
+  longlong2* part;         // [2][ksplit][k k] exact partials, column-major k x k
+  const Control* ctl;
+  int* err;
+};
+
+struct __align__(8) Bars16 {
+  uint64_t full[kG16Stages], empty[kG16Stages], acc_full, acc_empty, drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                             const __grid_constant__ CUtensorMap tmY,
+                                                             Gram16Args g) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Bars16* bars = reinterpret_cast<Bars16*>(smem + kG16Stages * kG16Stage);
+  constexpr int kRows = 16 * S;                      // rows of a stacked tile
+  constexpr int kTileBytes = kRows * kBK * 2;
+  constexpr int kColsJob = kRows + (S == 9 ? 16 : 0);   // TMEM columns per product
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int split = blockIdx.x;
+  const int kb_lo = (int)((int64_t)g.kb_total * split / g.ksplit);
+  const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / g.ksplit);
+  const int KB = kb_hi - kb_lo;
+  const int NC = (KB + kG16Chunk - 1) / kG16Chunk;
+  volatile int* abort_flag = &bars->abort;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kG16Stages; ++i) {
+      mbar_init(smem_u32(&bars->full[i]), 1);
+      mbar_init(smem_u32(&bars->empty[i]), 1);
+    }
+    mbar_init(smem_u32(&bars->acc_full), 1);
+    mbar_init(smem_u32(&bars->acc_empty), kEpiWarps);
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: the X and Y tiles of each K block ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmY) : "memory");
+      bool ok = true;
+      int issued = 0;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int st = kb % kG16Stages, lap = kb / kG16Stages;
+        ok = mbar_wait(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), abort_flag);
+        if (!ok) break;
+        const int kx = (kb_lo + kb) * kBK;
+        mbar_expect_tx(smem_u32(&bars->full[st]), (uint32_t)(2 * kTileBytes));
+        tma_load_2d(smem_u32(smem + st * kG16Stage), &tmX, smem_u32(&bars->full[st]), kx, 0);
+        tma_load_2d(smem_u32(smem + st * kG16Stage + kG16Tile), &tmY, smem_u32(&bars->full[st]), kx, 0);
+        ++issued;
+      }
+      if (!ok)
+        for (int i = (issued > kG16Stages ? issued - kG16Stages : 0); i < issued; ++i)
+          mbar_drain(smem_u32(&bars->full[i % kG16Stages]), (uint32_t)((i / kG16Stages) & 1));
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = true;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int c = kb / kG16Chunk;
+        const bool first = (kb % kG16Chunk) == 0;
+        const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
+        if (first && c > 0) {   // one accumulator set: the previous chunk must be drained
+          ok = mbar_wait(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+        }
+        const int st = kb % kG16Stages, lap = kb / kG16Stages;
+        ok = mbar_wait(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        const uint64_t xd = smem_desc(smem_u32(smem + st * kG16Stage));
+        const uint64_t xd8 = smem_desc(smem_u32(smem + st * kG16Stage + 128 * kBK * 2));   // X rows 128.. (plane 8)
+        const uint64_t yd = smem_desc(smem_u32(smem + st * kG16Stage + kG16Tile));
+        constexpr uint32_t id1 = idesc_bf16(kBM, kRows);
+        constexpr uint32_t id2 = idesc_bf16(kBM, 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t acc = (first && q == 0) ? 0u : 1u;
+          const uint64_t o = (uint64_t)(2 * q);    // 16 K per step inside the 128-byte swizzle row
+          tc_mma(tbase, xd + o, xd + o, id1, acc);                                 // G: planes 0..7 x all
+          tc_mma(tbase + kColsJob, xd + o, yd + o, id1, acc);                      // S
+          if (S == 9) {
+            tc_mma(tbase + kRows, xd8 + o, xd + o, id2, acc);                      // G: plane 8 x plane 0
+            tc_mma(tbase + kColsJob + kRows, xd8 + o, yd + o, id2, acc);           // S
+          }
+        }
+        tc_commit(smem_u32(&bars->empty[st]));
+        if (last) tc_commit(smem_u32(&bars->acc_full));
+      }
+      if (!ok) {
+        tc_commit(smem_u32(&bars->drain));
+        mbar_drain(smem_u32(&bars->drain), 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int lg = warp & 3;                     // TMEM lane group
+    const int half = (warp - 2) >> 2;            // which plane columns t of the row
+    const int r = lg * 32 + lane;                // TMEM lane = 16 s + i
+    const int sp = r >> 4;                       // plane s of X this lane holds
+    long long hi[2][16], lo[2][16];
+#pragma unroll
+    for (int jb = 0; jb < 2; ++jb)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) hi[jb][j] = lo[jb][j] = 0;
+    bool ok = true;
+    constexpr int kT0 = (S + 1) / 2;             // half 0 takes planes t < kT0, half 1 the rest (+ plane 8 x 0)
+    for (int c = 0; c < NC && ok; ++c) {
+      int w_ok = 0;
+      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full), (uint32_t)(c & 1), abort_flag);
+      ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+      __syncwarp();
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16);
+#pragma unroll
+      for (int jb = 0; jb < 2; ++jb) {
+#pragma unroll
+        for (int b = 0; b < (S + 2) / 2; ++b) {
+          // which 16 columns: plane t of Y (half 0: t < kT0, half 1: t >= kT0), or
+          // (half 1, S = 9, one slot past the planes) plane 8 of X x plane 0 of Y
+          const int t = half == 0 ? b : kT0 + b;
+          if (half == 0 && t >= kT0) continue;
+          if (half == 1 && t > S - (S == 9 ? 0 : 1)) continue;
+          int w;
+          uint32_t col;
+          if (t == S) {
+            col = (uint32_t)(jb * kColsJob + kRows);
+            w = r < 16 ? 8 : 99;                 // rows >= 16 of the plane-8 instruction are not X's
+          } else {
+            col = (uint32_t)(jb * kColsJob + 16 * t);
+            w = sp + t;
+          }
+          uint32_t v[16];
+          TC_LD16(tl + col, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (w <= S - 1) {
+            if (w < 4) {
+              const int sh = kBits * (3 - w);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) hi[jb][j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+            } else {
+              const int sh = kBits * (S - 1 - w);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) lo[jb][j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty));
+    }
+    // the 16 threads holding row i (4 lane groups x 2 lanes x 2 halves) add their sums
+    asm volatile("bar.sync 1, 256;" ::: "memory");   // every epilogue warp is past its last TMEM read
+    longlong2* red = reinterpret_cast<longlong2*>(smem);   // [16 contributors][16 i][16 j] (the ring is idle now)
+    const int i = r & 15;
+    const int qc = lg * 4 + (lane >> 4) * 2 + half;
+    const int te = threadIdx.x - 64;             // 0..255 over the epilogue warps
+    for (int jb = 0; jb < 2; ++jb) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) red[(qc * 16 + i) * 16 + j] = make_longlong2(hi[jb][j], lo[jb][j]);
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      {
+        const int oi = te & 15, oj = te >> 4;
+        long long h = 0, l = 0;
+        for (int q = 0; q < 16; ++q) {
+          const longlong2 e = red[(q * 16 + oi) * 16 + oj];
+          h += e.x;
+          l += e.y;
+        }
+        if (ok && oi < g.k && oj < g.k)
+          g.part[((int64_t)(jb * g.ksplit + split) * g.k + oj) * g.k + oi] = make_longlong2(h, l);
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (bars->abort && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+    if (g.ctl) {
+      Control* c = const_cast<Control*>(g.ctl);
+      c->status = EIGREF_E_TIMEOUT;
+      c->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+  }
+}
+
+// G (job 0), S (job 1) from the split partials of sgram16: the exact sum over
+// any number of splits (128-bit), then the one FP64 recombination.
+template <int S>
+__global__ void sgram16_reduce_kernel(const longlong2* __restrict__ part, int k, int nsplit,
+                                      const int* __restrict__ xexp, const int* __restrict__ wexp,
+                                      double* __restrict__ out, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  const int64_t kk = (int64_t)k * k;
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < 2 * kk;
+       e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int z = (int)(e / kk);
+    const int64_t o = e % kk;
+    const longlong2* p = part + (int64_t)z * nsplit * kk + o;
+    __int128 hi = 0, lo = 0;
+    for (int c = lane; c < nsplit; c += 32) {
+      const longlong2 v = p[(int64_t)c * kk];
+      hi += v.x;
+      lo += v.y;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      const long long hh = (long long)(hi >> 64), hl = (long long)(unsigned long long)hi;
+      const long long lh = (long long)(lo >> 64), ll = (long long)(unsigned long long)lo;
+      const long long ohh = __shfl_xor_sync(0xffffffffu, hh, m), ohl = __shfl_xor_sync(0xffffffffu, hl, m);
+      const long long olh = __shfl_xor_sync(0xffffffffu, lh, m), oll = __shfl_xor_sync(0xffffffffu, ll, m);
+      hi += ((__int128)ohh << 64) | (__int128)(unsigned long long)ohl;
+      lo += ((__int128)olh << 64) | (__int128)(unsigned long long)oll;
+    }
+    if (lane == 0) {
+      const int row = (int)(o % k), col = (int)(o / k);
+      const int er = xexp[row], fc = z ? wexp[col] : xexp[col];
+      if (er == kNonFinite || fc == kNonFinite) {
+        out[e] = __longlong_as_double(0x7FF8000000000000ll);
+      } else {
+        // a 128-bit sum x = x_h 2^32 + x_l with x_l in [0, 2^32): both parts are
+        // exact doubles (|x| < 2^84), so the sum rounds once, for either sign
+        auto to_double = [](__int128 x) {
+          return (double)(long long)(x >> 32) * 0x1p32 + (double)(unsigned int)(x & 0xFFFFFFFF);
+        };
+        const double hd = to_double(hi);
+        const double ld = to_double(lo);
+        out[e] = ldexp(fma(ld, ldexp(1.0, -kBits * (S + 1)), hd * 0x1p-35), er + fc);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Digit planes.  GB300 runs FP64 at ~1/64 of FP32, so the digits are cut
 // with integer arithmetic: |a| 2^-e (< 1) is rounded once to an integer M of
 // 7S bits (the same information the S digits keep), then M is split into
@@ -662,7 +953,8 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ Y, in
 #pragma unroll
     for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][t]);
     const int64_t rowid = (int64_t)t * kp + cb * 32 + jj;
-    *reinterpret_cast<uint4*>(planes + rowid * K + l0 + r0) = *reinterpret_cast<uint4*>(d);
+    if (cb * 32 + jj < kp)   // kp = 16: half the block's columns are padding
+      *reinterpret_cast<uint4*>(planes + rowid * K + l0 + r0) = *reinterpret_cast<uint4*>(d);
   }
 }
 
@@ -863,7 +1155,7 @@ void launch_slice_cols(const double* Y, int64_t rows, int k, int64_t rs, int64_t
   cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
   const int rpb = 256 / k > 0 ? 256 / k : 1;
   colmax_kernel<<<152 * 4, rpb * k, 0, s>>>(Y, rows, k, rs, cs, cmax, ctl);
-  dim3 gx((unsigned)(K / 64), (unsigned)(kp / 32));
+  dim3 gx((unsigned)(K / 64), (unsigned)((kp + 31) / 32));
   slice_cols_kernel<S><<<gx, 256, 0, s>>>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, ctl);
 }
 
@@ -939,7 +1231,9 @@ cudaError_t init_sliced_attributes() {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_UPDATE>,                                 \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sgram16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16Smem);
   EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
   EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
 #undef EIGREF_SET_ATTR
@@ -1432,6 +1726,122 @@ int SlicedA::update_grid() const { return n_pad_ / sl::kBM; }
 
 int SlicedA::timed_out(cudaStream_t s) const {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  int v = 0;
+  cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// SlicedGram: the tensor-core Gram products for k <= 16 without A (CSR).
+// ---------------------------------------------------------------------------
+struct Gram16Layout {
+  size_t x_planes, x_colexp, x_cmax, p_planes, p_colexp, p_cmax, part, err, total;
+};
+
+static Gram16Layout gram16_layout(int64_t n_pad, int S, int ksplit, int k) {
+  Gram16Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 1023) & ~size_t(1023);
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  L.x_planes = take((size_t)S * 16 * n_pad * 2);
+  L.x_colexp = take(16 * 4);
+  L.x_cmax = take(16 * 8);
+  L.p_planes = take((size_t)S * 16 * n_pad * 2);
+  L.p_colexp = take(16 * 4);
+  L.p_cmax = take(16 * 8);
+  L.part = take((size_t)2 * ksplit * k * k * 16);
+  L.err = take(64);
+  L.total = off + 1024;
+  return L;
+}
+
+int SlicedGram::configure(int64_t n, int k, int slices) {
+  n_ = n;
+  k_ = k;
+  slices_ = slices > 0 ? slices : sl::kDefaultS;
+  if (k < 1 || k > 16) {
+    snprintf(err_, sizeof(err_), "tensor-core Gram products for CSR need k <= 16 (k = %d)", k);
+    return EIGREF_E_UNSUPPORTED;
+  }
+  if (slices_ < 2 || slices_ > sl::kMaxS) {
+    snprintf(err_, sizeof(err_), "slices must be in [2, %d]", sl::kMaxS);
+    return EIGREF_E_INVALID;
+  }
+  if (!sl::encode_fn()) {
+    snprintf(err_, sizeof(err_), "cuTensorMapEncodeTiled unavailable");
+    return EIGREF_E_CUDA;
+  }
+  n_pad_ = (n + 255) / 256 * 256;
+  const int64_t kbt = n_pad_ / sl::kBK;
+  // one CTA per SM, and at most 3500 K blocks per CTA (its int64 sums stay exact)
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  ksplit_ = (int)std::min<int64_t>(kbt, sms);
+  while (kbt / ksplit_ > 3500) ksplit_ += sms;
+  return EIGREF_OK;
+}
+
+size_t SlicedGram::workspace_bytes() const { return gram16_layout(n_pad_, slices_, ksplit_, k_).total; }
+
+void SlicedGram::bind_workspace(char* p) {
+  ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+int SlicedGram::prepare(cudaStream_t s) {
+  const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
+  if (cudaMemsetAsync(ws_ + L.x_planes, 0, L.part - L.x_planes, s) != cudaSuccess ||
+      cudaMemsetAsync(ws_ + L.err, 0, 64, s) != cudaSuccess) {
+    snprintf(err_, sizeof(err_), "memset of slice planes failed");
+    return EIGREF_E_CUDA;
+  }
+  const uint64_t rows = (uint64_t)slices_ * 16;
+  bool ok = sl::make_map(reinterpret_cast<CUtensorMap*>(tmX_), ws_ + L.x_planes, (uint64_t)n_pad_, rows, sl::kBK,
+                         (uint32_t)rows);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmP_), ws_ + L.p_planes, (uint64_t)n_pad_, rows, sl::kBK,
+                          (uint32_t)rows);
+  if (!ok) {
+    snprintf(err_, sizeof(err_), "tensor map encoding failed");
+    return EIGREF_E_CUDA;
+  }
+  return EIGREF_OK;
+}
+
+int SlicedGram::gram(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s) {
+  const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
+  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* xmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
+  auto* pmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
+  int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
+  int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
+  const int K = (int)n_pad_;
+  sl::Gram16Args g;
+  g.kb_total = (int)(n_pad_ / sl::kBK);
+  g.ksplit = ksplit_;
+  g.k = k_;
+  g.part = reinterpret_cast<longlong2*>(ws_ + L.part);
+  g.ctl = ctl;
+  g.err = reinterpret_cast<int*>(ws_ + L.err);
+  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
+  const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
+  const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
+#define EIGREF_CALL_G16(S_)                                                                                      \
+  sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, K, 16, xmax, xp, xexp, ctl, s);                                   \
+  sl::launch_slice_cols<S_>(P, n_, k_, k_, 1, K, 16, pmax, pp, pexp, ctl, s);                                   \
+  sl::sgram16_kernel<S_><<<ksplit_, sl::kThreads, sl::kG16Smem, s>>>(mx, mp, g);                                 \
+  sl::sgram16_reduce_kernel<S_><<<rg, 256, 0, s>>>(g.part, k_, ksplit_, xexp, pexp, out, ctl)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_G16)
+#undef EIGREF_CALL_G16
+  return 6;
+}
+
+int SlicedGram::timed_out(cudaStream_t s) const {
+  const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
   int v = 0;
   cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);

@@ -135,4 +135,29 @@ class SlicedA {
   char err_[256] = {0};
 };
 
+// The Gram products G = X^T X, S = X^T P (k <= 16, all n rows) as stacked
+// BF16 digit planes on the tensor cores, without A: the split form of the
+// Gram products for CSR matrices (whose product stays an FP64 SpMM).
+class SlicedGram {
+ public:
+  int configure(int64_t n, int k, int slices);
+  size_t workspace_bytes() const;
+  void bind_workspace(char* p);
+  int prepare(cudaStream_t s);
+  // out[0] = X^T X, out[1] = X^T P (k x k column-major); X, P row-major n x k
+  int gram(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s);
+  int timed_out(cudaStream_t s) const;
+  int ksplit() const { return ksplit_; }
+  int slices() const { return slices_; }
+  const char* error() const { return err_; }
+
+ private:
+  int64_t n_ = 0, n_pad_ = 0;
+  int k_ = 0, slices_ = 0, ksplit_ = 1;
+  char* ws_ = nullptr;
+  alignas(64) unsigned char tmX_[128];
+  alignas(64) unsigned char tmP_[128];
+  char err_[256] = {0};
+};
+
 }  // namespace eigref
