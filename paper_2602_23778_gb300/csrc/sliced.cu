@@ -899,15 +899,34 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
 // as non-negative double bit patterns; NaN survives (fmax would drop it).
 __device__ __forceinline__ void colmax_body(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
                                             unsigned long long* __restrict__ cmax, int bx, int nbx) {
+  __shared__ unsigned long long part[256];
   const int rpb = blockDim.x / k;  // threads beyond rpb k idle
-  if ((int)threadIdx.x >= rpb * k) return;
+  const bool live = (int)threadIdx.x < rpb * k;
   const int j = threadIdx.x % k;
-  double m = 0.0;
-  for (int64_t i = bx * (int64_t)rpb + threadIdx.x / k; i < rows; i += (int64_t)nbx * rpb) {
-    const double v = fabs(Y[i * rs + j * cs]);
-    m = (v > m || v != v) ? v : m;
+  // four independent loads in flight per thread (the max is order-free)
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)nbx * rpb;
+  for (int64_t i = bx * (int64_t)rpb + threadIdx.x / k; live && i < rows; i += 4 * stride) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t iu = i + u * stride;
+      if (iu < rows) {
+        const double v = fabs(Y[iu * rs + j * cs]);
+        m[u] = (v > m[u] || v != v) ? v : m[u];
+      }
+    }
   }
-  atomicMax(cmax + j, (unsigned long long)__double_as_longlong(m));
+  double mm = m[0];
+#pragma unroll
+  for (int u = 1; u < 4; ++u) mm = (m[u] > mm || m[u] != m[u]) ? m[u] : mm;
+  // one atomic per column and block (non-negative doubles order like their bits; NaN is largest)
+  part[threadIdx.x] = live ? (unsigned long long)__double_as_longlong(mm) : 0ull;
+  __syncthreads();
+  if ((int)threadIdx.x < k) {
+    unsigned long long b = 0;
+    for (int r = 0; r < rpb; ++r) b = max(b, part[r * k + threadIdx.x]);
+    atomicMax(cmax + threadIdx.x, b);
+  }
 }
 
 __global__ void colmax_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
@@ -966,6 +985,45 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
                                                          const Control* ctl) {
   if (ctl && ctl->done) return;
   slice_cols_body<S>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, blockIdx.x, blockIdx.y);
+}
+
+// Column digit planes for k <= 16 (planes of 16 rows): planes[(t 16 + j) K + l].
+// A CTA takes 128 rows x 16 columns, so every thread cuts digits of a
+// column that exists in the plane layout.
+template <int S>
+__global__ void __launch_bounds__(256) slice_cols16_kernel(const double* __restrict__ Y, int64_t rows, int k,
+                                                           int64_t rs, int64_t cs, int K,
+                                                           const unsigned long long* __restrict__ cmax,
+                                                           __nv_bfloat16* __restrict__ planes,
+                                                           int* __restrict__ colexp, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  __shared__ double tile[128][17];
+  __shared__ int fexp[16];
+  const int l0 = blockIdx.x * 128;
+  const int tid = threadIdx.x;
+  if (tid < 16) {
+    const double cm = tid < k ? __longlong_as_double((long long)cmax[tid]) : 0.0;
+    const int f = row_exponent(cm);
+    fexp[tid] = isfinite(cm) ? f : 0;
+    if (blockIdx.x == 0 && tid < k) colexp[tid] = isfinite(cm) ? f : kNonFinite;
+  }
+  for (int e = tid; e < 128 * 16; e += 256) {
+    const int rr = e >> 4, jj = e & 15;
+    const int64_t l = l0 + rr;
+    tile[rr][jj] = (l < rows && jj < k) ? Y[l * rs + jj * cs] : 0.0;
+  }
+  __syncthreads();
+  const int jj = tid >> 4, r0 = (tid & 15) * 8;
+  int dg[8][S];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) digits_of<S>(tile[r0 + q][jj], fexp[jj], dg[q]);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    __align__(16) __nv_bfloat16 d[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][t]);
+    *reinterpret_cast<uint4*>(planes + ((int64_t)t * 16 + jj) * K + l0 + r0) = *reinterpret_cast<uint4*>(d);
+  }
 }
 
 // Row digit planes of a row-major n x k operand: planes[(s n_pad + i) K + l],
@@ -1133,13 +1191,40 @@ __global__ void sgram_reduce_kernel(const longlong2* __restrict__ part, int k, i
                        ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
+// Few splits (the batch's small problems): one thread per output, the splits
+// added in order -- the same exact sum as the warp form.
+template <int S>
+__device__ __forceinline__ void sgram_reduce_thread_body(const longlong2* __restrict__ part, int k, int nsplit,
+                                                         const int* __restrict__ xexp, const int* __restrict__ wexp,
+                                                         double* __restrict__ out, int64_t t0, int64_t nt) {
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t e = t0; e < 2 * kk; e += nt) {
+    const int z = (int)(e / kk);
+    const int64_t o = e % kk;
+    const longlong2* p = part + (int64_t)z * nsplit * kk + o;
+    long long hi = 0, lo = 0;
+    for (int c = 0; c < nsplit; ++c) {
+      const longlong2 v = p[(int64_t)c * kk];
+      hi += v.x;
+      lo += v.y;
+    }
+    const int row = (int)(o % k), col = (int)(o / k);
+    out[e] = recombine<S>(hi, lo, xexp[row], z ? wexp[col] : xexp[col]);
+  }
+}
+
 template <int S>
 __global__ void sgram_reduce_grouped_kernel(const GroupItem* __restrict__ items) {
   const GroupItem& it = items[blockIdx.z];
   if (it.b[0].ctl->done) return;
-  sgram_reduce_body<S>(static_cast<const longlong2*>(it.sgpart), it.k, it.ksplit, it.x_colexp, it.p_colexp,
-                       it.b[0].g2, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
-                       ((int64_t)gridDim.x * blockDim.x) >> 5);
+  if (it.ksplit <= 8)
+    sgram_reduce_thread_body<S>(static_cast<const longlong2*>(it.sgpart), it.k, it.ksplit, it.x_colexp, it.p_colexp,
+                                it.b[0].g2, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                (int64_t)gridDim.x * blockDim.x);
+  else
+    sgram_reduce_body<S>(static_cast<const longlong2*>(it.sgpart), it.k, it.ksplit, it.x_colexp, it.p_colexp,
+                         it.b[0].g2, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                         ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 template <int S>
@@ -1154,9 +1239,18 @@ void launch_slice_cols(const double* Y, int64_t rows, int k, int64_t rs, int64_t
                        cudaStream_t s) {
   cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
   const int rpb = 256 / k > 0 ? 256 / k : 1;
-  colmax_kernel<<<152 * 4, rpb * k, 0, s>>>(Y, rows, k, rs, cs, cmax, ctl);
+  colmax_kernel<<<152 * 8, rpb * k, 0, s>>>(Y, rows, k, rs, cs, cmax, ctl);
   dim3 gx((unsigned)(K / 64), (unsigned)((kp + 31) / 32));
   slice_cols_kernel<S><<<gx, 256, 0, s>>>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, ctl);
+}
+
+template <int S>
+void launch_slice_cols16(const double* Y, int64_t rows, int k, int K, unsigned long long* cmax, __nv_bfloat16* planes,
+                         int* colexp, const Control* ctl, cudaStream_t s) {
+  cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
+  const int rpb = 256 / k > 0 ? 256 / k : 1;
+  colmax_kernel<<<152 * 8, rpb * k, 0, s>>>(Y, rows, k, k, 1, cmax, ctl);
+  slice_cols16_kernel<S><<<K / 128, 256, 0, s>>>(Y, rows, k, k, 1, K, cmax, planes, colexp, ctl);
 }
 
 template <int S>
@@ -1831,8 +1925,8 @@ int SlicedGram::gram(const double* X, const double* P, double* out, const Contro
   const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
   const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
 #define EIGREF_CALL_G16(S_)                                                                                      \
-  sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, K, 16, xmax, xp, xexp, ctl, s);                                   \
-  sl::launch_slice_cols<S_>(P, n_, k_, k_, 1, K, 16, pmax, pp, pexp, ctl, s);                                   \
+  sl::launch_slice_cols16<S_>(X, n_, k_, K, xmax, xp, xexp, ctl, s);                                           \
+  sl::launch_slice_cols16<S_>(P, n_, k_, K, pmax, pp, pexp, ctl, s);                                           \
   sl::sgram16_kernel<S_><<<ksplit_, sl::kThreads, sl::kG16Smem, s>>>(mx, mp, g);                                 \
   sl::sgram16_reduce_kernel<S_><<<rg, 256, 0, s>>>(g.part, k_, ksplit_, xexp, pexp, out, ctl)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_G16)
