@@ -233,32 +233,33 @@ __global__ void kk_solve_kernel(const double* __restrict__ LU, const int* __rest
 
 enum { KG_V1 = 0, KG_W2 = 1, KG_YTE = 2, KG_X1 = 3 };
 
-// 16 x 16 output tile per CTA, one output per thread:  s = op(A)(i,:) . Bm(:,j)
-template <int MODE>
+// TT x TT output tile per CTA (TT^2 threads), one output per thread:
+// s = op(A)(i,:) . Bm(:,j), summed in the order l = 0, 1, ... for any TT.
+template <int MODE, int TT = 16>
 __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, int by) {
-  __shared__ double As[16][17];
-  __shared__ double Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = bx * 16 + tx, j = by * 16 + ty;
+  __shared__ double As[TT][TT + 1];
+  __shared__ double Bs[TT][TT + 1];
+  const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
+  const int i = bx * TT + tx, j = by * TT + ty;
   const int64_t kk = (int64_t)k * k;
   const double* A = (MODE == KG_W2) ? b.g2 : b.y1;   // G2 = b.g2[0 .. k*k)
   const double* Bm = (MODE == KG_YTE) ? b.e11 : (MODE == KG_X1 ? b.nmat : b.m);
   const bool transA = (MODE == KG_YTE);
   double s = 0.0;
-  for (int l0 = 0; l0 < k; l0 += 16) {
-    // As[r][c] = op(A)(blockIdx.x*16 + r, l0 + c); Bs[r][c] = Bm(l0 + r, blockIdx.y*16 + c)
+  for (int l0 = 0; l0 < k; l0 += TT) {
+    // As[r][c] = op(A)(bx TT + r, l0 + c); Bs[r][c] = Bm(l0 + r, by TT + c)
     {
       const int r = ty, c = tx;  // each thread loads one element of each tile
-      const int ai = bx * 16 + r, al = l0 + c;
+      const int ai = bx * TT + r, al = l0 + c;
       double av = 0.0;
       if (ai < k && al < k) av = transA ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k];
       As[r][c] = av;
-      const int bl = l0 + r, bj = by * 16 + c;
+      const int bl = l0 + r, bj = by * TT + c;
       Bs[r][c] = (bl < k && bj < k) ? Bm[bl + (int64_t)bj * k] : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < 16; ++c) s = fma(As[tx][c], Bs[c][ty], s);
+    for (int c = 0; c < TT; ++c) s = fma(As[tx][c], Bs[c][ty], s);
     __syncthreads();
   }
   if (i >= k || j >= k) return;
@@ -276,10 +277,10 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
   (void)kk;
 }
 
-template <int MODE>
+template <int MODE, int TT>
 __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
   if (b.ctl->done) return;
-  kk_gemm_body<MODE>(b, k, blockIdx.x, blockIdx.y);
+  kk_gemm_body<MODE, TT>(b, k, blockIdx.x, blockIdx.y);
 }
 
 // E11 by the cases of line 6 of Algorithm 4, one block per column j, plus the
@@ -334,24 +335,24 @@ __global__ void kk_e11_kernel(SweepBufs b, int k, double delta, int beta_zero) {
 
 // C = add_i I + beta C0 + alpha op(A) B  (k x k, column-major).  check > 0:
 // flags Y1 as singular when an entry of C exceeds it (Newton-Schulz diverging).
-template <int TRANS>
+template <int TRANS, int TT = 16>
 __device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ A, const double* __restrict__ B,
                                                      const double* __restrict__ C0, double* __restrict__ C, int k,
                                                      double alpha, double beta, int add_i, double check, Control* ctl,
                                                      int bx, int by) {
-  __shared__ double As[16][17];
-  __shared__ double Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = bx * 16 + tx, j = by * 16 + ty;
+  __shared__ double As[TT][TT + 1];
+  __shared__ double Bs[TT][TT + 1];
+  const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
+  const int i = bx * TT + tx, j = by * TT + ty;
   double acc = 0.0;
-  for (int l0 = 0; l0 < k; l0 += 16) {
-    const int ai = bx * 16 + ty, al = l0 + tx;
+  for (int l0 = 0; l0 < k; l0 += TT) {
+    const int ai = bx * TT + ty, al = l0 + tx;
     As[ty][tx] = (ai < k && al < k) ? (TRANS ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k]) : 0.0;
-    const int bl = l0 + ty, bj = by * 16 + tx;
+    const int bl = l0 + ty, bj = by * TT + tx;
     Bs[ty][tx] = (bl < k && bj < k) ? B[bl + (int64_t)bj * k] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc = fma(As[tx][c], Bs[c][ty], acc);
+    for (int c = 0; c < TT; ++c) acc = fma(As[tx][c], Bs[c][ty], acc);
     __syncthreads();
   }
   if (i < k && j < k) {
@@ -368,22 +369,39 @@ __device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ 
   }
 }
 
-template <int TRANS>
+template <int TRANS, int TT>
 __global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                               const double* __restrict__ C0, double* __restrict__ C,
                                                               int k, double alpha, double beta, int add_i,
                                                               double check, Control* ctl) {
   if (ctl->done) return;
-  kk_gemm_generic_body<TRANS>(A, B, C0, C, k, alpha, beta, add_i, check, ctl, blockIdx.x, blockIdx.y);
+  kk_gemm_generic_body<TRANS, TT>(A, B, C0, C, k, alpha, beta, add_i, check, ctl, blockIdx.x, blockIdx.y);
 }
 
+// Tiles of 8 for k >= 64 (a k x k product then spreads over 64+ SMs), else 16.
 static void kk_gemm_generic(const double* A, bool transA, const double* B, const double* C0, double* C, int k,
                             double alpha, double beta, int add_i, double check, Control* ctl, cudaStream_t s) {
-  dim3 g((k + 15) / 16, (k + 15) / 16);
-  if (transA)
-    kk_gemm_generic_kernel<1><<<g, 256, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+  if (k >= 64) {
+    dim3 g((k + 7) / 8, (k + 7) / 8);
+    if (transA)
+      kk_gemm_generic_kernel<1, 8><<<g, 64, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+    else
+      kk_gemm_generic_kernel<0, 8><<<g, 64, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+  } else {
+    dim3 g((k + 15) / 16, (k + 15) / 16);
+    if (transA)
+      kk_gemm_generic_kernel<1, 16><<<g, 256, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+    else
+      kk_gemm_generic_kernel<0, 16><<<g, 256, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+  }
+}
+
+template <int MODE>
+static void kk_gemm(const SweepBufs& b, int k, cudaStream_t s) {
+  if (k >= 64)
+    kk_gemm_kernel<MODE, 8><<<dim3((k + 7) / 8, (k + 7) / 8), 64, 0, s>>>(b, k);
   else
-    kk_gemm_generic_kernel<0><<<g, 256, 0, s>>>(A, B, C0, C, k, alpha, beta, add_i, check, ctl);
+    kk_gemm_kernel<MODE, 16><<<dim3((k + 15) / 16, (k + 15) / 16), 256, 0, s>>>(b, k);
 }
 
 // Y1 = X1 - I from the row-major X, and rhs = -I (so that the LU solve gives Y1^{-1}).
@@ -417,16 +435,15 @@ void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cu
     kk_lu_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(b, k);
     kk_solve_kernel<0><<<k, tpb, 0, s>>>(b.lu, b.piv, b.t1, b.m, k, b.ctl);
   }
-  dim3 g((k + 15) / 16, (k + 15) / 16);
-  kk_gemm_kernel<KG_V1><<<g, 256, 0, s>>>(b, k);
-  kk_gemm_kernel<KG_W2><<<g, 256, 0, s>>>(b, k);
+  kk_gemm<KG_V1>(b, k, s);
+  kk_gemm<KG_W2>(b, k, s);
   kk_e11_kernel<<<k, tpb, 0, s>>>(b, k, delta, beta_zero);
-  kk_gemm_kernel<KG_YTE><<<g, 256, 0, s>>>(b, k);
+  kk_gemm<KG_YTE>(b, k, s);
   if (b.mixed)
     kk_gemm_generic(b.zinv, true, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, s);     // N = -Z^T (Y^T E)
   else
     kk_solve_kernel<1><<<k, tpb, 0, s>>>(b.lu, b.piv, b.yte, b.nmat, k, b.ctl);
-  kk_gemm_kernel<KG_X1><<<g, 256, 0, s>>>(b, k);
+  kk_gemm<KG_X1>(b, k, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -929,6 +929,58 @@ __device__ __forceinline__ void colmax_body(const double* __restrict__ Y, int64_
   }
 }
 
+// Column maxima of a contiguous row-major rows x k operand, read as a flat
+// array of 16-byte pairs (half the load instructions of the strided form).
+// The grid is sized so that 2 x (threads) is a multiple of k: each thread
+// then meets the same two columns on every step.
+__global__ void __launch_bounds__(256) colmax_flat_kernel(const double* __restrict__ Y, int64_t total, int k,
+                                                          unsigned long long* __restrict__ cmax, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  __shared__ unsigned long long colm[kMaxK];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) colm[j] = 0ull;
+  __syncthreads();
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const double2* Y2 = reinterpret_cast<const double2*>(Y);
+  const int64_t pairs = total / 2;
+  double m0[2] = {0.0, 0.0}, m1[2] = {0.0, 0.0};
+  for (int64_t q = t; q < pairs; q += 2 * T) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t qu = q + u * T;
+      if (qu < pairs) {
+        const double2 v = Y2[qu];
+        const double a = fabs(v.x), b = fabs(v.y);
+        m0[u] = (a > m0[u] || a != a) ? a : m0[u];
+        m1[u] = (b > m1[u] || b != b) ? b : m1[u];
+      }
+    }
+  }
+  const double a = (m0[1] > m0[0] || m0[1] != m0[1]) ? m0[1] : m0[0];
+  const double b = (m1[1] > m1[0] || m1[1] != m1[1]) ? m1[1] : m1[0];
+  if (t < pairs) {
+    atomicMax(&colm[(2 * t) % k], (unsigned long long)__double_as_longlong(a));
+    atomicMax(&colm[(2 * t + 1) % k], (unsigned long long)__double_as_longlong(b));
+  }
+  if (t == 0 && (total & 1)) {   // odd total: the last element
+    const double c = fabs(Y[total - 1]);
+    atomicMax(&colm[(total - 1) % k], (unsigned long long)__double_as_longlong(c));
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    if (colm[j]) atomicMax(cmax + j, colm[j]);
+}
+
+static void launch_colmax_rowmajor(const double* Y, int64_t rows, int k, unsigned long long* cmax, const Control* ctl,
+                                   cudaStream_t s) {
+  // blocks: about 8 per SM, a multiple of k / gcd(k, 512) so that 2 x threads is a multiple of k
+  int g = 512, kk = k;
+  while (kk % 2 == 0 && g % 2 == 0) { kk /= 2; g /= 2; }
+  const int unit = kk;                                  // k / gcd(k, 512)
+  const int blocks = ((152 * 8 + unit - 1) / unit) * unit;
+  colmax_flat_kernel<<<blocks, 256, 0, s>>>(Y, rows * (int64_t)k, k, cmax, ctl);
+}
+
 __global__ void colmax_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs, int64_t cs,
                               unsigned long long* __restrict__ cmax, const Control* ctl) {
   if (ctl && ctl->done) return;
@@ -1238,8 +1290,12 @@ void launch_slice_cols(const double* Y, int64_t rows, int k, int64_t rs, int64_t
                        unsigned long long* cmax, __nv_bfloat16* planes, int* colexp, const Control* ctl,
                        cudaStream_t s) {
   cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
-  const int rpb = 256 / k > 0 ? 256 / k : 1;
-  colmax_kernel<<<152 * 8, rpb * k, 0, s>>>(Y, rows, k, rs, cs, cmax, ctl);
+  if (rs == k && cs == 1) {
+    launch_colmax_rowmajor(Y, rows, k, cmax, ctl, s);
+  } else {
+    const int rpb = 256 / k > 0 ? 256 / k : 1;
+    colmax_kernel<<<152 * 8, rpb * k, 0, s>>>(Y, rows, k, rs, cs, cmax, ctl);
+  }
   dim3 gx((unsigned)(K / 64), (unsigned)((kp + 31) / 32));
   slice_cols_kernel<S><<<gx, 256, 0, s>>>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, ctl);
 }
@@ -1248,8 +1304,7 @@ template <int S>
 void launch_slice_cols16(const double* Y, int64_t rows, int k, int K, unsigned long long* cmax, __nv_bfloat16* planes,
                          int* colexp, const Control* ctl, cudaStream_t s) {
   cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
-  const int rpb = 256 / k > 0 ? 256 / k : 1;
-  colmax_kernel<<<152 * 8, rpb * k, 0, s>>>(Y, rows, k, k, 1, cmax, ctl);
+  launch_colmax_rowmajor(Y, rows, k, cmax, ctl, s);
   slice_cols16_kernel<S><<<K / 128, 256, 0, s>>>(Y, rows, k, k, 1, K, cmax, planes, colexp, ctl);
 }
 
