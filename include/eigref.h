@@ -68,7 +68,10 @@ enum eigref_target {
 enum eigref_precision {
   EIGREF_FP64 = 0,         /* plain FP64 on the CUDA cores */
   EIGREF_BF16_SLICES = 1,  /* error-free BF16 slices on the tensor cores, FP32 accumulation */
-  EIGREF_INT8_SLICES = 2   /* error-free INT8 slices on the tensor cores, INT32 accumulation */
+  EIGREF_INT8_SLICES = 2,  /* error-free INT8 slices on the tensor cores, INT32 accumulation (not
+                              built: GB300's INT8 tensor rate is far below its BF16 rate) */
+  EIGREF_AUTO = 3          /* the faster form the build offers for the call: BF16 slices for dense
+                              1024 <= n <= 2^18 and for CSR k <= 16, FP64 otherwise */
 };
 
 enum eigref_stop {

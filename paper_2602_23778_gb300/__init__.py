@@ -19,7 +19,7 @@ _LIB = None
 OK, E_INVALID, E_CUDA, E_NOMEM, E_SINGULAR_WY, E_DIVERGED, E_NOT_CONVERGED, E_NONFINITE, E_TIMEOUT, \
     E_UNSUPPORTED = range(10)
 TARGETS = {"largest_mag": 0, "largest": 1, "smallest": 2, "shift": 3, "smallest_mag": 4}
-PRECISIONS = {"fp64": 0, "bf16": 1, "int8": 2}
+PRECISIONS = {"fp64": 0, "bf16": 1, "int8": 2, "auto": 3}
 STOPS = {"correction": 0, "residual": 1}
 BETAS = {"cluster": 0, "zero": 1}
 

@@ -140,7 +140,7 @@ int read_params(eigref_ctx* h, const eigref_params* p, Params* q) {
     return set_err(h, EIGREF_E_INVALID, "stop %d out of range", q->stop);
   if (q->beta != EIGREF_BETA_CLUSTER && q->beta != EIGREF_BETA_ZERO)
     return set_err(h, EIGREF_E_INVALID, "beta %d out of range", q->beta);
-  if (q->precision < EIGREF_FP64 || q->precision > EIGREF_INT8_SLICES)
+  if (q->precision < EIGREF_FP64 || q->precision > EIGREF_AUTO)
     return set_err(h, EIGREF_E_INVALID, "precision %d out of range", q->precision);
   if (!isfinite(q->shift) || !isfinite(q->norm_a)) return set_err(h, EIGREF_E_INVALID, "shift/norm_a not finite");
   return EIGREF_OK;
@@ -695,6 +695,13 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   return status;
 }
 
+// EIGREF_AUTO: the split form where this build has one that pays off.
+int resolve_precision(int precision, bool csr, int64_t n, int k) {
+  if (precision != EIGREF_AUTO) return precision;
+  if (csr) return k <= 16 ? EIGREF_BF16_SLICES : EIGREF_FP64;
+  return (n >= 1024 && n <= ((int64_t)1 << 18)) ? EIGREF_BF16_SLICES : EIGREF_FP64;
+}
+
 int check_dims(eigref_ctx* h, int64_t n, int k, int64_t ldx, const double* X) {
   if (!X) return set_err(h, EIGREF_E_INVALID, "X is NULL");
   if (n < 2 || n > (int64_t)INT32_MAX) return set_err(h, EIGREF_E_INVALID, "n = %lld out of range", (long long)n);
@@ -806,7 +813,9 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
   if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
   eigref_params dp;
   eigref_params_default(&dp);
-  const eigref_params* pp = p ? p : &dp;
+  if (p) dp = *p;
+  dp.precision = resolve_precision(dp.precision, false, n, k);
+  const eigref_params* pp = &dp;
   Problem pr;
   pr.n = n;
   pr.k = k;
@@ -876,17 +885,21 @@ int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* co
   pr.ci = static_cast<const int32_t*>(bufs[1] ? bufs[1] : col_idx);
   pr.val = static_cast<const double*>(bufs[2] ? bufs[2] : val);
   SlicedGram sg;
-  if (p && p->precision == EIGREF_BF16_SLICES) {
-    st = sg.configure(n, k, p->slices);
+  eigref_params cp;
+  eigref_params_default(&cp);
+  if (p) cp = *p;
+  cp.precision = resolve_precision(cp.precision, true, n, k);
+  if (cp.precision == EIGREF_BF16_SLICES) {
+    st = sg.configure(n, k, cp.slices);
     if (st) {
       set_err(h, st, "%s", sg.error());
     } else {
       pr.sgram = &sg;
     }
-  } else if (p && p->precision != EIGREF_FP64) {
-    st = set_err(h, EIGREF_E_UNSUPPORTED, "CSR: precision %d not built (FP64 or BF16 slices)", p->precision);
+  } else if (cp.precision != EIGREF_FP64) {
+    st = set_err(h, EIGREF_E_UNSUPPORTED, "CSR: precision %d not built (FP64 or BF16 slices)", cp.precision);
   }
-  if (st == EIGREF_OK) st = refine_common(h, pr, X, ldx, p, rep);
+  if (st == EIGREF_OK) st = refine_common(h, pr, X, ldx, &cp, rep);
   cudaStreamSynchronize(h->stream);
   for (void* q : bufs)
     if (q) cudaFree(q);
@@ -908,6 +921,11 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
   Params q;
   int st = read_params(h, p, &q);
   if (st) return st;
+  if (q.precision == EIGREF_AUTO) {
+    int64_t nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, probs[i].n);
+    q.precision = nmax <= ((int64_t)1 << 18) ? EIGREF_BF16_SLICES : EIGREF_FP64;
+  }
   std::vector<Run> runs(count);
   std::unique_ptr<SlicedA[]> sls(new SlicedA[count]);
   for (int i = 0; i < count; ++i) {
@@ -1211,6 +1229,7 @@ int eigref_gram(eigref_handle h, const double* X, int64_t ldx, const double* P, 
   if (!X || !P || !G || !S) return set_err(h, EIGREF_E_INVALID, "NULL argument");
   if (n < 1 || k < 1 || k > kMaxK || ldx < n || ldp < n) return set_err(h, EIGREF_E_INVALID, "bad sizes");
   if (!is_device_ptr(X) || !is_device_ptr(P)) return set_err(h, EIGREF_E_INVALID, "gram needs X and P in device memory");
+  if (precision == EIGREF_AUTO) precision = k <= 16 ? EIGREF_BF16_SLICES : EIGREF_FP64;
   if (precision != EIGREF_FP64 && precision != EIGREF_BF16_SLICES)
     return set_err(h, EIGREF_E_UNSUPPORTED, "precision %d not built for the Gram products", precision);
   if (cudaSetDevice(h->device) != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "cudaSetDevice");
@@ -1319,6 +1338,7 @@ int eigref_product_dense(eigref_handle h, const double* A, int64_t n, int64_t ld
   pr.A = A;
   pr.lda = lda;
   SlicedA sl;
+  precision = resolve_precision(precision, false, n, k);
   if (precision != EIGREF_FP64) {
     int st = sl.configure(A, n, lda, k, precision, slices);
     if (st) return set_err(h, st, "%s", sl.error());
