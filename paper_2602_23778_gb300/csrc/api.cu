@@ -160,6 +160,10 @@ struct Problem {
   int k = 0;
   SlicedA* sliced = nullptr;  // split-precision dense product, or null
   SlicedGram* sgram = nullptr;  // CSR split form: tensor-core Gram products (k <= 16), or null
+  // CSR split form with even k: the SpMM and the normalisation also form the
+  // column maxima the slicing of P and X needs (no separate passes over them)
+  unsigned long long* p_cmax = nullptr;
+  bool fused_max = false;
   bool square = false;        // B = A^2 - alpha I (Section 5.2): W = A (A X) - alpha X
   double* tbuf = nullptr;     // A X of the shifted square (workspace)
 };
@@ -174,7 +178,7 @@ int launch_product(const Problem& pr, const double* X, double* P, double shift, 
     if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
     if (pr.csr) {
       launch_spmm_csr(pr.rp, pr.ci, pr.val, X, pr.tbuf, pr.n, pr.k, 0.0, ctl, s);
-      launch_spmm_csr(pr.rp, pr.ci, pr.val, pr.tbuf, P, pr.n, pr.k, shift, ctl, s, X);
+      launch_spmm_csr(pr.rp, pr.ci, pr.val, pr.tbuf, P, pr.n, pr.k, shift, ctl, s, X, pr.p_cmax);
     } else {
       launch_gemm_fp64(pr.A, pr.lda, X, pr.tbuf, pr.n, pr.k, 0.0, ctl, s);
       launch_gemm_fp64(pr.A, pr.lda, pr.tbuf, P, pr.n, pr.k, shift, ctl, s, X);
@@ -186,9 +190,9 @@ int launch_product(const Problem& pr, const double* X, double* P, double shift, 
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
   if (pr.csr) {
     if (pr.folded)
-      launch_spmm_csr(pr.rp, pr.ci, pr.val_folded, X, P, pr.n, pr.k, 0.0, ctl, s);
+      launch_spmm_csr(pr.rp, pr.ci, pr.val_folded, X, P, pr.n, pr.k, 0.0, ctl, s, nullptr, pr.p_cmax);
     else
-      launch_spmm_csr(pr.rp, pr.ci, pr.val, X, P, pr.n, pr.k, shift, ctl, s);
+      launch_spmm_csr(pr.rp, pr.ci, pr.val, X, P, pr.n, pr.k, shift, ctl, s, nullptr, pr.p_cmax);
   } else
     launch_gemm_fp64(pr.A, pr.lda, X, P, pr.n, pr.k, shift, ctl, s);
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
@@ -203,12 +207,21 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   if (pr.sgram) {
     // CSR split form: Gram products over all rows on the tensor cores, the
     // leading block in FP64 (the k x k stage forms G2 = G - G1); FP64 update
-    launches += pr.sgram->gram(b.x, b.p, b.g2, b.ctl, s);
+    if (pr.fused_max)
+      launches += pr.sgram->gram_ready(b.x, b.p, b.g2, b.ctl, s);
+    else
+      launches += pr.sgram->gram(b.x, b.p, b.g2, b.ctl, s);
     launch_top_gram(b.x, b.p, k, b.gtop, b.ctl, s);
     launch_kxk_stage(b, k, delta, beta_zero, s);
-    launch_update_rows(b, n, k, s);
+    // the row update on the tensor cores where this k has it, else in FP64
+    if (pr.sgram->update(b.x, b.p, b.f, b.d, b.dinv, b.xn, b.upart, b.ctl, s) > 0) {
+      b.ugrid = pr.sgram->update_grid();
+    } else {
+      launch_update_rows(b, n, k, s);
+      b.ugrid = update_rows_grid();
+    }
     launch_finalize(b, k, delta, s);
-    launch_normalize(b, n, k, s);
+    launch_normalize(b, n, k, s, pr.fused_max ? pr.sgram->x_cmax() : nullptr);
     return launches + 1 + 12 + 1 + 2;
   }
   if (pr.sliced) {
@@ -267,6 +280,7 @@ void run_plan(Run& r) {
   while ((n - k + r.chunk_rows - 1) / r.chunk_rows > 1024) r.chunk_rows *= 2;
   r.nchunks = (int)std::max<int64_t>(1, (n - k + r.chunk_rows - 1) / r.chunk_rows);
   r.ugrid = r.pr.sliced ? r.pr.sliced->update_grid() : update_rows_grid();
+  if (r.pr.sgram) r.ugrid = std::max(r.ugrid, r.pr.sgram->update_grid());   // either row update may run
   r.hist_len = std::max(1, r.q.max_iters);
 }
 
@@ -317,7 +331,10 @@ void run_bind(Run& r, char* base, Control* ctl) {
   c.base = base;
   run_layout(r, c, ctl);
   if (r.pr.sliced) r.pr.sliced->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
-  if (r.pr.sgram) r.pr.sgram->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
+  if (r.pr.sgram) {
+    r.pr.sgram->bind_workspace(base + ((c.off + 255) & ~size_t(255)));
+    if (r.pr.fused_max) r.pr.p_cmax = r.pr.sgram->p_cmax();
+  }
 }
 
 // Shift and delta from ||A|| and the target (Sections 3.1.3, 5.1 and 5.2).
@@ -346,6 +363,14 @@ Control run_control(const Run& r) {
   c.status = EIGREF_OK;
   c.done = r.q.max_iters == 0;
   return c;
+}
+
+// Column maxima the first sweep's slicing reads when the producers form them:
+// those of the starting X, and none yet for P.
+void run_setup_maxima(const Run& r, cudaStream_t s) {
+  if (!r.pr.fused_max) return;
+  cudaMemsetAsync(r.pr.p_cmax, 0, (size_t)r.pr.k * 8, s);
+  r.pr.sgram->colmax_x(r.xbuf[0], s);
 }
 
 // Device half of the set-up after ||A|| and the shift are known: the internal
@@ -393,6 +418,7 @@ int run_setup_device(eigref_ctx* h, Run& r, cudaStream_t s) {
       r.sg = r.sigma;
     }
   }
+  run_setup_maxima(r, s);
   return EIGREF_OK;
 }
 
@@ -641,6 +667,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
       *h->host_ctl = c;
       CUDA_TRY(h, cudaMemcpyAsync(b.ctl, h->host_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
       run_setup_inverse(r, s);
+      run_setup_maxima(r, s);
       ++resigned;
       launched = it;
       it_before = it;
@@ -895,6 +922,7 @@ int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* co
       set_err(h, st, "%s", sg.error());
     } else {
       pr.sgram = &sg;
+      pr.fused_max = (k % 2) == 0;
     }
   } else if (cp.precision != EIGREF_FP64) {
     st = set_err(h, EIGREF_E_UNSUPPORTED, "CSR: precision %d not built (FP64 or BF16 slices)", cp.precision);

@@ -96,7 +96,8 @@ void launch_gram_reduce(const double* part, int k, int nchunks, double* out, con
 void launch_top_gram(const double* X, const double* P, int k, double* out, const Control* ctl, cudaStream_t s);
 void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s);
 void launch_finalize(const SweepBufs& b, int k, double delta_unused, cudaStream_t s);
-void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s);
+// cmax (optional): also the column maxima of the normalised |X| (ordered bits, atomicMax).
+void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s, unsigned long long* cmax = nullptr);
 void launch_copy_in(const double* Xu, int64_t ldx, double* X, int64_t n, int k, const double* sigma,
                     cudaStream_t s);
 void launch_copy_out(const double* X, double* Xu, int64_t ldx, int64_t n, int k, const double* sigma,
@@ -108,8 +109,10 @@ int update_rows_grid();
 cudaError_t init_fp64_attributes();
 cudaError_t init_kxk_attributes();
 // spmm.cu
+// cmax (optional, even k only): also the column maxima of |P| (ordered bits, atomicMax).
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
-                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s, const double* Xs = nullptr);
+                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s, const double* Xs = nullptr,
+                     unsigned long long* cmax = nullptr);
 void launch_csr_fold_diag(const int32_t* rp, const int32_t* ci, const double* val, int64_t n, double shift,
                           double* val_out, int* missing, cudaStream_t s);
 // kxk.cu

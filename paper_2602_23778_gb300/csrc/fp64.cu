@@ -514,8 +514,42 @@ void launch_normalize_grouped(const GroupItem* items, const GroupDims& gd, int p
   normalize_grouped_kernel<<<dim3(grid, 1, gd.count), 256, 0, s>>>(items, parity);
 }
 
-void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {
+// The same, also forming the column maxima of the normalised |X| (the next
+// sweep's slicing of X needs them).  The grid makes the thread count a
+// multiple of k, so every thread stays on one column.
+__global__ void __launch_bounds__(256) normalize_max_kernel(double* __restrict__ X, int64_t n, int k,
+                                                            const double* __restrict__ nu, const Control* ctl,
+                                                            unsigned long long* __restrict__ cmax) {
+  if (!ctl->pending_norm) return;
+  __shared__ unsigned long long colm[kMaxK];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) colm[j] = 0ull;
+  __syncthreads();
+  const int64_t total = n * k;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const double sc = nu[t % k];
+  unsigned long long m = 0ull;   // max |X| as an ordered bit pattern (integer compares)
+  for (int64_t e = t; e < total; e += T) {
+    const double v = X[e] * sc;
+    X[e] = v;
+    m = max(m, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+  }
+  if (t < total) atomicMax(&colm[t % k], m);
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    if (colm[j]) atomicMax(cmax + j, colm[j]);
+}
+
+void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s, unsigned long long* cmax) {
   int64_t total = n * k;
+  if (cmax) {
+    // blocks: about 8 per SM, a multiple of k / gcd(k, 256)
+    int g = 256, kk = k;
+    while (kk % 2 == 0 && g % 2 == 0) { kk /= 2; g /= 2; }
+    const int blocks = ((152 * 8 + kk - 1) / kk) * kk;
+    normalize_max_kernel<<<blocks, 256, 0, s>>>(b.xn, n, k, b.nu, b.ctl, cmax);
+    return;
+  }
   int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   normalize_kernel<<<grid, 256, 0, s>>>(b.xn, n, k, b.nu, b.ctl);
 }

@@ -112,6 +112,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
   }
 }
+// The same with a short sleep between polls after the first few: for waits
+// that are long against the work of the other warps on the SM (the spinning
+// lanes would take their issue slots).
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 8) __nanosleep(128);
+    if ((it & 15) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
 // Bounded wait used while leaving after an abort: lets work already issued
 // complete, gives up after 100 ms.
 __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
@@ -821,8 +839,8 @@ __global__ void sgram16_reduce_kernel(const longlong2* __restrict__ part, int k,
 // Digit planes.  GB300 runs FP64 at ~1/64 of FP32, so the digits are cut
 // with integer arithmetic: |a| 2^-e (< 1) is rounded once to an integer M of
 // 7S bits (the same information the S digits keep), then M is split into
-// base-128 digits with round-half-up, the first in [0, 128], the others in
-// [-64, 64]; the sign of a is applied to all of them.
+// balanced base-128 digits, the first in [0, 128], the others in [-64, 63];
+// the sign of a is applied to all of them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int row_exponent(double amax) {
   if (!(amax > 0.0) || !isfinite(amax)) return 0;
@@ -831,29 +849,68 @@ __device__ __forceinline__ int row_exponent(double amax) {
   return e;
 }
 
+// |a| as its bit pattern: non-negative doubles order like these integers, and
+// integer compares stay off the FP64 pipe (a small fraction of the integer
+// rate on this part).  Inf is 0x7FF0..., NaN above it.
+__device__ __forceinline__ unsigned long long abs_bits(double a) {
+  return (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+}
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+// A small integer (|v| <= 256) as FP32 bits with the low 16 bits zero (so
+// the upper half is its BF16), and an integer-valued FP32 (|x| < 2^22) as an
+// int: one add at the 1.5 x 2^23 offset each, no conversion instructions.
+__device__ __forceinline__ uint32_t f32_bits_of_small_int(int v) {
+  return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f);
+}
+__device__ __forceinline__ int int_of_f32(uint32_t u) {
+  return __float_as_int(__uint_as_float(u) + 12582912.0f) - 0x4B400000;
+}
+__device__ __forceinline__ uint32_t bf16_bits_of_int(int v) { return f32_bits_of_small_int(v) >> 16; }
+
+// round(|a| 2^(7S - e)) (half up) for |a| < 2^e: the 7S-bit magnitude the
+// digits represent.
+template <int S>
+__device__ __forceinline__ unsigned long long magnitude_bits(unsigned long long bits, int e) {
+  const int exr = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (exr ? (1ull << 52) : 0ull);
+  const int sh = (exr ? exr : 1) - 1075 - e + kBits * S;   // |a| 2^(7S - e) = mant 2^sh, sh <= 7S - 53
+  const int rs = -sh;
+  const unsigned long long up = mant << (sh > 0 ? sh : 0);
+  const unsigned long long dn = rs > 0 && rs < 64 ? (mant + (1ull << (rs - 1))) >> rs : 0ull;
+  return sh >= 0 ? up : dn;
+}
+
+// Balanced digits by one offset: with B = 64 (1 + 128 + ... + 128^(S-2)),
+// the base-128 fields g_s of M + B (most significant first) give
+// M = g_0 128^(S-1) + sum_(s>=1) (g_s - 64) 128^(S-1-s): digit 0 is g_0 in
+// [0, 128], digit s >= 1 is g_s - 64 in [-64, 63].  Carries are the one
+// 64-bit addition; each digit is a shift and a mask.
+template <int S>
+struct DigitBias {
+  static constexpr unsigned long long value = 64ull + 128ull * DigitBias<S - 1>::value;
+};
+template <>
+struct DigitBias<1> {
+  static constexpr unsigned long long value = 0ull;
+};
+template <int S>
+__device__ __forceinline__ unsigned long long biased_magnitude(unsigned long long bits, int e) {
+  return magnitude_bits<S>(bits, e) + DigitBias<S>::value;
+}
+template <int S>
+__device__ __forceinline__ int bal_digit(unsigned long long Mb, int s) {
+  const int sh = kBits * (S - 1 - s);
+  return s == 0 ? (int)(Mb >> sh) : (int)((Mb >> sh) & 127ull) - 64;
+}
+
 template <int S>
 __device__ __forceinline__ void digits_of(double a, int e, int* d) {
-  const long long bits = __double_as_longlong(a);
-  int ex = (int)((bits >> 52) & 0x7FF);
-  unsigned long long mant = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
-  if (ex) mant |= 1ull << 52; else ex = 1;
-  // |a| 2^(7S - e) = mant 2^sh; |a| < 2^e and mant < 2^53 give M < 2^(7S) <= 2^63
-  const int sh = ex - 1075 - e + 7 * S;
-  unsigned long long M;
-  if (sh >= 0) M = sh < 64 ? mant << sh : 0ull;
-  else M = -sh < 64 ? (mant + (1ull << (-sh - 1))) >> (-sh) : 0ull;
-  const int k0 = 7 * (S - 1);
-  const unsigned long long q0 = k0 ? (M + (1ull << (k0 - 1))) >> k0 : M;
-  long long R = (long long)(M - (q0 << k0));
-  const int sg = bits < 0 ? -1 : 1;
-  d[0] = sg * (int)q0;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long Mb = biased_magnitude<S>(bits, e);
+  const int sg = (long long)bits < 0 ? -1 : 1;
 #pragma unroll
-  for (int s = 1; s < S; ++s) {
-    const int k = 7 * (S - 1 - s);
-    const long long q = k ? (R + (1ll << (k - 1))) >> k : R;
-    R -= q << k;
-    d[s] = sg * (int)q;
-  }
+  for (int s = 0; s < S; ++s) d[s] = sg * bal_digit<S>(Mb, s);
 }
 
 template <int S>
@@ -864,17 +921,12 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t plane = (int64_t)n_pad * n_pad;
   for (int64_t i = wid; i < n_pad; i += nw) {
-    double amax = 0.0;
-    bool finite = true;
+    unsigned long long amax = 0ull;
     if (i < n)
-      for (int64_t l = lane; l < n; l += 32) {
-        const double v = A[i * lda + l];
-        finite = finite && isfinite(v);
-        amax = fmax(amax, fabs(v));
-      }
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    finite = __all_sync(0xffffffffu, finite);
-    const int e = row_exponent(amax);
+      for (int64_t l = lane; l < n; l += 32) amax = max(amax, abs_bits(A[i * lda + l]));
+    for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const bool finite = amax < kInfBits;
+    const int e = row_exponent(__longlong_as_double((long long)amax));
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int64_t l0 = (int64_t)lane * 8; l0 < n_pad; l0 += 32 * 8) {
       int dg[8][S];
@@ -904,23 +956,18 @@ __device__ __forceinline__ void colmax_body(const double* __restrict__ Y, int64_
   const bool live = (int)threadIdx.x < rpb * k;
   const int j = threadIdx.x % k;
   // four independent loads in flight per thread (the max is order-free)
-  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
   const int64_t stride = (int64_t)nbx * rpb;
   for (int64_t i = bx * (int64_t)rpb + threadIdx.x / k; live && i < rows; i += 4 * stride) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t iu = i + u * stride;
-      if (iu < rows) {
-        const double v = fabs(Y[iu * rs + j * cs]);
-        m[u] = (v > m[u] || v != v) ? v : m[u];
-      }
+      if (iu < rows) m[u] = max(m[u], abs_bits(Y[iu * rs + j * cs]));
     }
   }
-  double mm = m[0];
-#pragma unroll
-  for (int u = 1; u < 4; ++u) mm = (m[u] > mm || m[u] != m[u]) ? m[u] : mm;
-  // one atomic per column and block (non-negative doubles order like their bits; NaN is largest)
-  part[threadIdx.x] = live ? (unsigned long long)__double_as_longlong(mm) : 0ull;
+  const unsigned long long mm = max(max(m[0], m[1]), max(m[2], m[3]));
+  // one atomic per column and block
+  part[threadIdx.x] = live ? mm : 0ull;
   __syncthreads();
   if ((int)threadIdx.x < k) {
     unsigned long long b = 0;
@@ -943,36 +990,31 @@ __global__ void __launch_bounds__(256) colmax_flat_kernel(const double* __restri
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const double2* Y2 = reinterpret_cast<const double2*>(Y);
   const int64_t pairs = total / 2;
-  double m0[2] = {0.0, 0.0}, m1[2] = {0.0, 0.0};
+  unsigned long long m0[2] = {0ull, 0ull}, m1[2] = {0ull, 0ull};
   for (int64_t q = t; q < pairs; q += 2 * T) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int64_t qu = q + u * T;
       if (qu < pairs) {
         const double2 v = Y2[qu];
-        const double a = fabs(v.x), b = fabs(v.y);
-        m0[u] = (a > m0[u] || a != a) ? a : m0[u];
-        m1[u] = (b > m1[u] || b != b) ? b : m1[u];
+        m0[u] = max(m0[u], abs_bits(v.x));
+        m1[u] = max(m1[u], abs_bits(v.y));
       }
     }
   }
-  const double a = (m0[1] > m0[0] || m0[1] != m0[1]) ? m0[1] : m0[0];
-  const double b = (m1[1] > m1[0] || m1[1] != m1[1]) ? m1[1] : m1[0];
   if (t < pairs) {
-    atomicMax(&colm[(2 * t) % k], (unsigned long long)__double_as_longlong(a));
-    atomicMax(&colm[(2 * t + 1) % k], (unsigned long long)__double_as_longlong(b));
+    atomicMax(&colm[(2 * t) % k], max(m0[0], m0[1]));
+    atomicMax(&colm[(2 * t + 1) % k], max(m1[0], m1[1]));
   }
-  if (t == 0 && (total & 1)) {   // odd total: the last element
-    const double c = fabs(Y[total - 1]);
-    atomicMax(&colm[(total - 1) % k], (unsigned long long)__double_as_longlong(c));
-  }
+  if (t == 0 && (total & 1))   // odd total: the last element
+    atomicMax(&colm[(total - 1) % k], abs_bits(Y[total - 1]));
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x)
     if (colm[j]) atomicMax(cmax + j, colm[j]);
 }
 
-static void launch_colmax_rowmajor(const double* Y, int64_t rows, int k, unsigned long long* cmax, const Control* ctl,
-                                   cudaStream_t s) {
+void launch_colmax_rowmajor(const double* Y, int64_t rows, int k, unsigned long long* cmax, const Control* ctl,
+                            cudaStream_t s) {
   // blocks: about 8 per SM, a multiple of k / gcd(k, 512) so that 2 x threads is a multiple of k
   int g = 512, kk = k;
   while (kk % 2 == 0 && g % 2 == 0) { kk /= 2; g /= 2; }
@@ -1054,10 +1096,10 @@ __global__ void __launch_bounds__(256) slice_cols16_kernel(const double* __restr
   const int l0 = blockIdx.x * 128;
   const int tid = threadIdx.x;
   if (tid < 16) {
-    const double cm = tid < k ? __longlong_as_double((long long)cmax[tid]) : 0.0;
-    const int f = row_exponent(cm);
-    fexp[tid] = isfinite(cm) ? f : 0;
-    if (blockIdx.x == 0 && tid < k) colexp[tid] = isfinite(cm) ? f : kNonFinite;
+    const unsigned long long cm = tid < k ? cmax[tid] : 0ull;
+    const int f = row_exponent(__longlong_as_double((long long)cm));
+    fexp[tid] = cm < kInfBits ? f : kNonFinite;
+    if (blockIdx.x == 0 && tid < k) colexp[tid] = cm < kInfBits ? f : kNonFinite;
   }
   for (int e = tid; e < 128 * 16; e += 256) {
     const int rr = e >> 4, jj = e & 15;
@@ -1065,16 +1107,28 @@ __global__ void __launch_bounds__(256) slice_cols16_kernel(const double* __restr
     tile[rr][jj] = (l < rows && jj < k) ? Y[l * rs + jj * cs] : 0.0;
   }
   __syncthreads();
+  // balanced digits of the rounded 7S-bit magnitudes, the sign flipped into
+  // each BF16's sign bit
   const int jj = tid >> 4, r0 = (tid & 15) * 8;
-  int dg[8][S];
+  const int fe = fexp[jj];
+  unsigned long long M[8];
+  uint32_t sgn[4];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) digits_of<S>(tile[r0 + q][jj], fexp[jj], dg[q]);
+  for (int q = 0; q < 8; ++q) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(tile[r0 + q][jj]);
+    M[q] = biased_magnitude<S>(fe != kNonFinite ? b : 0ull, fe != kNonFinite ? fe : 0);
+    if (q & 1) sgn[q >> 1] |= (uint32_t)(b >> 63) << 31;
+    else sgn[q >> 1] = (uint32_t)(b >> 63) << 15;
+  }
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    __align__(16) __nv_bfloat16 d[8];
+    uint32_t w4[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][t]);
-    *reinterpret_cast<uint4*>(planes + ((int64_t)t * 16 + jj) * K + l0 + r0) = *reinterpret_cast<uint4*>(d);
+    for (int q = 0; q < 4; ++q)
+      w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], t)),
+                          f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], t)), 0x7632) ^
+              sgn[q];
+    *reinterpret_cast<uint4*>(planes + ((int64_t)t * 16 + jj) * K + l0 + r0) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
   }
 }
 
@@ -1087,17 +1141,12 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ Y, in
   const int lane = threadIdx.x & 31;
   const int64_t plane = (int64_t)n_pad * K;
   for (int64_t i = wid; i < n_pad; i += nw) {
-    double amax = 0.0;
-    bool finite = true;
+    unsigned long long amax = 0ull;
     if (i < n)
-      for (int l = lane; l < k; l += 32) {
-        const double v = Y[i * k + l];
-        finite = finite && isfinite(v);
-        amax = fmax(amax, fabs(v));
-      }
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    finite = __all_sync(0xffffffffu, finite);
-    const int e = row_exponent(amax);
+      for (int l = lane; l < k; l += 32) amax = max(amax, abs_bits(Y[i * k + l]));
+    for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const bool finite = amax < kInfBits;
+    const int e = row_exponent(__longlong_as_double((long long)amax));
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int c = lane; c < K / 8; c += 32) {
       int dg[8][S];
@@ -1314,6 +1363,453 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __nv
   slice_rows_kernel<S><<<152 * 8, 256, 0, s>>>(Y, n, k, n_pad, K, planes, rowexp, ctl);
 }
 
+// ---------------------------------------------------------------------------
+// Row update X' = X + (W - X D) D^-1 - X F on the tensor cores, for an even
+// k <= 16 over very many rows (the sparse workloads).  One CTA per SM,
+// persistent over 128-row tiles; rows k.. are updated (the leading block is
+// the k x k stage's).
+//   warp 0     TMA loads of the X and W tiles: FP64, 128-byte rows (16
+//              columns; those past k and rows past n read as zero), 128-byte
+//              swizzle.
+//   warp 1     tcgen05.mma.  A = the S row digit planes of the X tile stacked
+//              along K (plane s at K = 16 s .. 16 s + 15, exponent e_i per
+//              row); B = the S column digit planes of F stacked along N
+//              (plane t at N = 16 t .., exponent f_j per column).  The
+//              instruction for plane s takes B rows 0 .. 16 (S - s) - 1 and
+//              writes TMEM columns 16 s ..: column 16 w + j then holds the sum
+//              of every pair (s, t) with s + t = w, the pairs of one weight
+//              only, exact in FP32 (at most 16 x 45056 < 2^20).
+//   warps 2-9  two threads per tile row (warps w and w + 4 share a TMEM lane
+//              group), eight columns each: cut the next tile's X row into the
+//              A operand; drain the accumulators, rebuild each (X F)_ij with
+//              integer arithmetic up to its bit pattern, form
+//              x' = x + (w - x d_j) / d_j - (X F)_ij in FP64, write it over the
+//              X tile in shared memory and store it with TMA (32 rows per lane
+//              group), keeping the column sums of x'^2 and (w - x d_j)^2.
+// Accumulators and A operands are double-
+// buffered, the X / W tiles triple-buffered.  Every wait is bounded; on expiry
+// the CTA records a timeout.  No FP64 instruction outside the update formula
+// and its sums: this part runs FP64 at a small fraction of its integer rate.
+// ---------------------------------------------------------------------------
+constexpr int kU16Stages = 3;
+constexpr int kU16Tile = 128 * 128;                // 128 rows x 16 FP64: 16 KiB
+constexpr int kU16Stage = 2 * kU16Tile;           // X tile, W tile
+constexpr int kU16ABlock = kBM * kBK * 2;         // 128 rows x 64 K BF16 (four planes)
+constexpr int kU16ABuf = 3 * kU16ABlock;          // planes 0..8
+constexpr int kU16BBytes = 16 * kMaxS * 128;      // 144 rows (t, j) of 128 B; K = l in the first 32 B
+constexpr int kU16RowWarps = 8;
+constexpr int kU16Threads = 64 + 32 * kU16RowWarps;
+constexpr int kU16Smem = kU16Stages * kU16Stage + 2 * kU16ABuf + kU16BBytes + 1024 + 1024;
+
+struct Upd16Args {
+  int64_t n;
+  int k;
+  int row_begin;        // rows below it (the leading block) are left alone
+  int tiles;            // ceil(n / 128); the grid is at most this
+  const double* F;      // k x k column-major
+  const double* d;
+  const double* dinv;
+  double* Xn;           // plain stores of the one tile that holds rows below row_begin
+  double* upart;        // [gridDim.x][2k]: column sums of x'^2, then of (w - x d)^2
+  const Control* ctl;
+  int* err;
+};
+
+struct __align__(8) BarsU16 {
+  uint64_t full[kU16Stages], empty[kU16Stages], a_full[2], a_empty[2], acc_full[2], acc_empty[2], sub[4], drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// Byte offset of 16-byte chunk c of row r in a tile of 128-byte rows with the
+// 128-byte swizzle (the layout TMA writes and the MMA descriptors describe).
+__device__ __forceinline__ uint32_t swz128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map), "r"(src),
+               "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+#define TC_LD8(taddr, r)                                                                             \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"               \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+                 "=r"(r[7])                                                                          \
+               : "r"(taddr))
+
+// 2^(er + fc) (hi 2^-35 + lo 2^-7(S+1)) rounded once to nearest-even, like
+// recombine<S>, with 64-bit integer arithmetic up to the bit pattern.
+// |hi| < 2^42, |lo| < 2^50 (the sums of the update's nine weights).
+template <int S>
+__device__ __forceinline__ double recombine_int(long long hi, long long lo, int er, int fc) {
+  if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);
+  constexpr int m = (kBits * (S + 1) > 35) ? kBits * (S + 1) : 35;   // V = hi 2^(m-35) + lo, value V 2^-m
+  constexpr int K = m - 35;
+  // V as a 128-bit two's complement (vh, vl)
+  const unsigned long long a = K ? ((unsigned long long)hi << K) : (unsigned long long)hi;
+  const long long ah = K ? (hi >> (64 - K)) : (hi >> 63);
+  const unsigned long long vl0 = a + (unsigned long long)lo;
+  long long vh = ah + (lo >> 63) + (vl0 < a ? 1 : 0);
+  unsigned long long vl = vl0;
+  const bool neg = vh < 0;
+  if (neg) {
+    vl = 0ull - vl0;
+    vh = ~vh + (vl0 == 0ull ? 1 : 0);
+  }
+  if ((vh | (long long)vl) == 0) return 0.0;
+  const unsigned long long uh = (unsigned long long)vh;   // < 2^14
+  const int nb = uh ? 128 - __clzll((long long)uh) : 64 - __clzll((long long)vl);
+  unsigned long long mant;
+  int e2 = nb - 53;
+  if (nb <= 53) {
+    mant = vl << (53 - nb);
+  } else {
+    const int sh = nb - 53;                                 // 1 .. 25
+    mant = (vl >> sh) | (uh << (64 - sh));
+    const unsigned long long rem = vl & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mant += (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e2;
+    }
+  }
+  const int ex = e2 - m + er + fc;
+  const int be = ex + 52 + 1023;
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
+                                            (mant & 0xFFFFFFFFFFFFFull)));
+  const double v = ldexp((double)mant, ex);   // outside the normal range (not met in practice)
+  return neg ? -v : v;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                                  const __grid_constant__ CUtensorMap tmW,
+                                                                  const __grid_constant__ CUtensorMap tmXn,
+                                                                  Upd16Args g) {
+  if (g.ctl && g.ctl->done) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stage0 = smem;
+  unsigned char* abuf0 = smem + kU16Stages * kU16Stage;
+  unsigned char* bop = abuf0 + 2 * kU16ABuf;
+  BarsU16* bars = reinterpret_cast<BarsU16*>(bop + kU16BBytes);
+  __shared__ int fexp_s[16];
+  __shared__ double d_s[16], dinv_s[16];
+  __shared__ double colsum[2][4][16];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  const int cnt = (g.tiles - (int)blockIdx.x + G - 1) / G;   // this CTA's tiles: blockIdx.x + i G
+  volatile int* abort_flag = &bars->abort;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kU16Stages; ++i) {
+      mbar_init(smem_u32(&bars->full[i]), 1);
+      mbar_init(smem_u32(&bars->empty[i]), 4);                  // the four lane-group leaders
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bars->a_full[i]), kU16RowWarps);
+      mbar_init(smem_u32(&bars->a_empty[i]), 1);
+      mbar_init(smem_u32(&bars->acc_full[i]), 1);
+      mbar_init(smem_u32(&bars->acc_empty[i]), kU16RowWarps);
+    }
+    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars->sub[i]), 2);   // both halves of a lane group written
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x < 16) {
+    // column exponents of F, and d, 1/d (zero past k)
+    const int j = threadIdx.x;
+    int fe = 0;
+    double dj = 0.0, dij = 0.0;
+    if (j < g.k) {
+      unsigned long long m = 0ull;
+      for (int l = 0; l < g.k; ++l) m = max(m, abs_bits(g.F[(int64_t)j * g.k + l]));
+      fe = m < kInfBits ? row_exponent(__longlong_as_double((long long)m)) : kNonFinite;
+      dj = g.d[j];
+      dij = g.dinv[j];
+    }
+    fexp_s[j] = fe;
+    d_s[j] = dj;
+    dinv_s[j] = dij;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmW) : "memory");
+      bool ok = true;
+      int issued = 0;
+      for (int i = 0; i < cnt && ok; ++i) {
+        const int st = i % kU16Stages, lap = i / kU16Stages;
+        ok = mbar_wait_sleep(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), abort_flag);
+        if (!ok) break;
+        const int row0 = ((int)blockIdx.x + i * G) * 128;
+        unsigned char* sx = stage0 + st * kU16Stage;
+        mbar_expect_tx(smem_u32(&bars->full[st]), (uint32_t)kU16Stage);
+        tma_load_2d(smem_u32(sx), &tmX, smem_u32(&bars->full[st]), 0, row0);
+        tma_load_2d(smem_u32(sx + kU16Tile), &tmW, smem_u32(&bars->full[st]), 0, row0);
+        ++issued;
+      }
+      if (!ok)
+        for (int i = (issued > kU16Stages ? issued - kU16Stages : 0); i < issued; ++i)
+          mbar_drain(smem_u32(&bars->full[i % kU16Stages]), (uint32_t)((i / kU16Stages) & 1));
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = true;
+      const uint64_t bd = smem_desc(smem_u32(bop));
+      for (int i = 0; i < cnt && ok; ++i) {
+        const int a = i & 1, u = i >> 1;
+        ok = mbar_wait_sleep(smem_u32(&bars->a_full[a]), (uint32_t)(u & 1), abort_flag);
+        if (ok) ok = mbar_wait_sleep(smem_u32(&bars->acc_empty[a]), (uint32_t)((u & 1) ^ 1), abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t ab = smem_u32(abuf0 + a * kU16ABuf);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const uint64_t ad = smem_desc(ab + (uint32_t)((s >> 2) * kU16ABlock)) + (uint64_t)(2 * (s & 3));
+          tc_mma(tbase + (uint32_t)(a * 256 + 16 * s), ad, bd, idesc_bf16(kBM, 16 * (S - s)), s == 0 ? 0u : 1u);
+        }
+        tc_commit(smem_u32(&bars->a_empty[a]));
+        tc_commit(smem_u32(&bars->acc_full[a]));
+      }
+      if (!ok) {
+        tc_commit(smem_u32(&bars->drain));
+        mbar_drain(smem_u32(&bars->drain), 0);
+      }
+    }
+  } else {
+    // ---------------- rows: slicing and epilogue ----------------
+    const int lg = warp & 3;                 // TMEM lane group: tile rows 32 lg .. 32 lg + 31
+    const int half = (warp - 2) >> 2;        // columns 8 half .. 8 half + 7
+    const bool leader = half == 0;           // stores the lane group's 32 rows
+    const int r = lg * 32 + lane;
+    // B operand: digit t of F(l, j) at row 16 t + j, K = l
+    {
+      const int e = threadIdx.x - 64;        // 0..255: one (j, l) each
+      const int j = e >> 4, l = e & 15;
+      const int fe = fexp_s[j];
+      const double v = (j < g.k && l < g.k && fe != kNonFinite) ? g.F[(int64_t)j * g.k + l] : 0.0;
+      int dg[S];
+      digits_of<S>(v, fe == kNonFinite ? 0 : fe, dg);
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+        *reinterpret_cast<uint16_t*>(bop + swz128(16 * t + j, l >> 3) + (l & 7) * 2) =
+            (uint16_t)bf16_bits_of_int(dg[t]);
+    }
+    double sq[8], rq[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sq[j] = rq[j] = 0.0;
+
+    // this thread's eight values of the X row of local tile i as S digit
+    // planes in A buffer i & 1; e_out = the row's exponent
+    auto slice = [&](int i, int& e_out) -> bool {
+      const int st = i % kU16Stages, lap = i / kU16Stages;
+      int w_ok = 1;
+      if (lane == 0) {
+        w_ok = mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);
+        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[i & 1]), (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag);
+      }
+      if (!__shfl_sync(0xffffffffu, w_ok, 0)) return false;
+      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);   // complete: each lane acquires
+      const unsigned char* xt = stage0 + st * kU16Stage;
+      unsigned long long b[8];
+      unsigned long long am = 0ull;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const double2 v = *reinterpret_cast<const double2*>(xt + swz128(r, c));
+        const unsigned long long b0 = (unsigned long long)__double_as_longlong(v.x);
+        const unsigned long long b1 = (unsigned long long)__double_as_longlong(v.y);
+        am = max(am, max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull));
+        if ((c >> 2) == half) {
+          b[2 * (c & 3)] = b0;
+          b[2 * (c & 3) + 1] = b1;
+        }
+      }
+      const bool fin = am < kInfBits;
+      const int e = fin ? row_exponent(__longlong_as_double((long long)am)) : 0;
+      e_out = fin ? e : kNonFinite;
+      unsigned long long M[8];
+      uint32_t sgn[4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) M[q] = biased_magnitude<S>(fin ? b[q] : 0ull, e);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        sgn[q] = (uint32_t)(b[2 * q] >> 63) << 15 | (uint32_t)(b[2 * q + 1] >> 63) << 31;
+      unsigned char* ab = abuf0 + (i & 1) * kU16ABuf;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], s)),
+                              f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], s)), 0x7632) ^
+                  sgn[q];
+        *reinterpret_cast<uint4*>(ab + (s >> 2) * kU16ABlock + swz128(r, 2 * (s & 3) + half)) =
+            make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->a_full[i & 1]));
+      return true;
+    };
+
+    int prev_st = -1;   // stage whose TMA store may still be reading shared memory (leaders)
+    auto epilogue = [&](int i, int e_row) -> bool {
+      const int a = i & 1, u = i >> 1;
+      int w_ok = 1;
+      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[a]), (uint32_t)(u & 1), abort_flag);
+      if (!__shfl_sync(0xffffffffu, w_ok, 0)) return false;
+      __syncwarp();
+      tc_fence_after();
+      long long hi[8], lo[8];
+      const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * 256 + 8 * half);
+      {
+        // weights in pairs: C_w 2^7 + C_(w+1) stays below 2^28
+        int c[S][8];
+#pragma unroll
+        for (int w = 0; w < S; ++w) {
+          uint32_t v[8];
+          TC_LD8(tl + 16 * w, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 8; ++j) c[w][j] = int_of_f32(v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          long long h = 0, l = 0;
+#pragma unroll
+          for (int w = 0; w < S && w < 4; w += 2) {
+            const int pr = (w + 1 < 4 && w + 1 < S) ? c[w][j] * 128 + c[w + 1][j] : c[w][j];
+            const int sh = (w + 1 < 4 && w + 1 < S) ? kBits * (2 - w) : kBits * (3 - w);
+            h += (long long)pr << sh;
+          }
+#pragma unroll
+          for (int w = 4; w < S; w += 2) {
+            const int pr = (w + 1 < S) ? c[w][j] * 128 + c[w + 1][j] : c[w][j];
+            const int sh = (w + 1 < S) ? kBits * (S - 2 - w) : kBits * (S - 1 - w);
+            l += (long long)pr << sh;
+          }
+          hi[j] = h;
+          lo[j] = l;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[a]));
+      const int st = i % kU16Stages;
+      unsigned char* xt = stage0 + st * kU16Stage;
+      const unsigned char* wt = xt + kU16Tile;
+      const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)i * G) * 128;
+      const int64_t row = row0 + r;
+      const bool live = row >= g.row_begin && row < g.n;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int cc = 4 * half + q;          // 16-byte chunk: columns 2 cc, 2 cc + 1
+        double2 xv = *reinterpret_cast<const double2*>(xt + swz128(r, cc));
+        const double2 wv = *reinterpret_cast<const double2*>(wt + swz128(r, cc));
+        const int j0 = 2 * cc, j1 = 2 * cc + 1;
+        const double f0 = recombine_int<S>(hi[2 * q], lo[2 * q], e_row, fexp_s[j0]);
+        const double f1 = recombine_int<S>(hi[2 * q + 1], lo[2 * q + 1], e_row, fexp_s[j1]);
+        const double r0 = fma(-xv.x, d_s[j0], wv.x), r1 = fma(-xv.y, d_s[j1], wv.y);
+        const double n0 = fma(r0, dinv_s[j0], xv.x) - f0, n1 = fma(r1, dinv_s[j1], xv.y) - f1;
+        if (live) {
+          sq[2 * q] = fma(n0, n0, sq[2 * q]);
+          sq[2 * q + 1] = fma(n1, n1, sq[2 * q + 1]);
+          rq[2 * q] = fma(r0, r0, rq[2 * q]);
+          rq[2 * q + 1] = fma(r1, r1, rq[2 * q + 1]);
+        }
+        xv.x = n0;
+        xv.y = n1;
+        *reinterpret_cast<double2*>(xt + swz128(r, cc)) = xv;
+      }
+      const bool plain = row0 < g.row_begin;   // the tile with the leading block
+      if (plain && live)
+        for (int j = 8 * half; j < 8 * half + 8 && j < g.k; ++j)
+          g.Xn[row * g.k + j] = reinterpret_cast<const double*>(xt + swz128(r, j >> 1))[j & 1];
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->sub[lg]));
+      if (leader) {
+        int s_ok = 1;
+        if (lane == 0) {
+          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg]), (uint32_t)(i & 1), abort_flag);
+          if (s_ok) {
+            bulk_wait_read_all();   // the previous tile's store has read its shared memory
+            if (prev_st >= 0) mbar_arrive(smem_u32(&bars->empty[prev_st]));
+            if (plain) {
+              mbar_arrive(smem_u32(&bars->empty[st]));
+            } else if (row0 + 32 * lg < g.n) {
+              tma_store_2d(&tmXn, smem_u32(xt + lg * 32 * 128), 0, (int)(row0 + 32 * lg));
+              bulk_commit();
+            }
+          }
+        }
+        prev_st = plain ? -1 : st;
+        if (!__shfl_sync(0xffffffffu, s_ok, 0)) return false;
+      }
+      return true;
+    };
+
+    int e_cur = 0, e_next = 0;
+    bool ok = slice(0, e_cur);
+    for (int i = 0; i < cnt && ok; ++i) {
+      if (i + 1 < cnt) ok = slice(i + 1, e_next);
+      if (ok) ok = epilogue(i, e_cur);
+      e_cur = e_next;
+    }
+    if (lane == 0) bulk_wait_all();
+    // column sums over this warp's rows, in a fixed order
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      for (int o = 16; o > 0; o >>= 1) {
+        sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], o);
+        rq[j] += __shfl_xor_sync(0xffffffffu, rq[j], o);
+      }
+      if (lane == 0) {
+        colsum[0][lg][8 * half + j] = sq[j];
+        colsum[1][lg][8 * half + j] = rq[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if ((int)threadIdx.x < 2 * g.k) {
+    const int which = threadIdx.x / g.k, j = threadIdx.x % g.k;
+    g.upart[(int64_t)blockIdx.x * 2 * g.k + which * g.k + j] =
+        colsum[which][0][j] + colsum[which][1][j] + colsum[which][2][j] + colsum[which][3][j];
+  }
+  if (bars->abort && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+    if (g.ctl) {
+      Control* c = const_cast<Control*>(g.ctl);
+      c->status = EIGREF_E_TIMEOUT;
+      c->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+  }
+}
+
 #define EIGREF_SLICE_DISPATCH(S_, CALL) \
   switch (S_) {                         \
     case 2: CALL(2); break;             \
@@ -1358,6 +1854,20 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Row-major rows x k FP64 operand in tiles of 16 columns (past k: zero) by
+// box_rows rows, 128-byte swizzle (k even: rows are 16-byte multiples).
+bool make_map_f64(CUtensorMap* m, const void* base, int k, int64_t rows, uint32_t box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)k * 8};
+  cuuint32_t box[2] = {16, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace sl
 
 cudaError_t init_sliced_attributes() {
@@ -1382,7 +1892,9 @@ cudaError_t init_sliced_attributes() {
     e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_UPDATE>,                                 \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
   if (e == cudaSuccess)                                                                                            \
-    e = cudaFuncSetAttribute(sl::sgram16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16Smem);
+    e = cudaFuncSetAttribute(sl::sgram16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16Smem); \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::update16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kU16Smem);
   EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
   EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
 #undef EIGREF_SET_ATTR
@@ -1932,7 +2444,42 @@ int SlicedGram::configure(int64_t n, int k, int slices) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   ksplit_ = (int)std::min<int64_t>(kbt, sms);
   while (kbt / ksplit_ > 3500) ksplit_ += sms;
+  // the row update on the tensor cores: even k (16-byte rows for TMA), one
+  // CTA per SM or per 128-row tile
+  upd_grid_ = (int)std::min<int64_t>((n + 127) / 128, sms);
+  upd_ok_ = false;
+  if (k % 2 == 0) {
+    alignas(64) CUtensorMap probe;
+    const void* aligned = reinterpret_cast<const void*>(uintptr_t(1) << 20);
+    upd_ok_ = sl::make_map_f64(&probe, aligned, k, n, 128) && sl::make_map_f64(&probe, aligned, k, n, 32);
+  }
   return EIGREF_OK;
+}
+
+int SlicedGram::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
+                       double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
+  if (!upd_ok_) return -1;
+  alignas(64) CUtensorMap mx, mw, mn;
+  if (!sl::make_map_f64(&mx, X, k_, n_, 128) || !sl::make_map_f64(&mw, W, k_, n_, 128) ||
+      !sl::make_map_f64(&mn, Xn, k_, n_, 32))
+    return -1;
+  const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
+  sl::Upd16Args a;
+  a.n = n_;
+  a.k = k_;
+  a.row_begin = k_;
+  a.tiles = (int)((n_ + 127) / 128);
+  a.F = F;
+  a.d = d;
+  a.dinv = dinv;
+  a.Xn = Xn;
+  a.upart = upart;
+  a.ctl = ctl;
+  a.err = reinterpret_cast<int*>(ws_ + L.err);
+#define EIGREF_CALL_U16(S_) sl::update16_kernel<S_><<<upd_grid_, sl::kU16Threads, sl::kU16Smem, s>>>(mx, mw, mn, a)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_U16)
+#undef EIGREF_CALL_U16
+  return 1;
 }
 
 size_t SlicedGram::workspace_bytes() const { return gram16_layout(n_pad_, slices_, ksplit_, k_).total; }
@@ -1987,6 +2534,50 @@ int SlicedGram::gram(const double* X, const double* P, double* out, const Contro
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_G16)
 #undef EIGREF_CALL_G16
   return 6;
+}
+
+unsigned long long* SlicedGram::x_cmax() const {
+  return reinterpret_cast<unsigned long long*>(ws_ + gram16_layout(n_pad_, slices_, ksplit_, k_).x_cmax);
+}
+
+unsigned long long* SlicedGram::p_cmax() const {
+  return reinterpret_cast<unsigned long long*>(ws_ + gram16_layout(n_pad_, slices_, ksplit_, k_).p_cmax);
+}
+
+void SlicedGram::colmax_x(const double* X, cudaStream_t s) {
+  cudaMemsetAsync(x_cmax(), 0, (size_t)k_ * 8, s);
+  sl::launch_colmax_rowmajor(X, n_, k_, x_cmax(), nullptr, s);
+}
+
+int SlicedGram::gram_ready(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s) {
+  const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
+  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
+  int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
+  const int K = (int)n_pad_;
+  sl::Gram16Args g;
+  g.kb_total = (int)(n_pad_ / sl::kBK);
+  g.ksplit = ksplit_;
+  g.k = k_;
+  g.part = reinterpret_cast<longlong2*>(ws_ + L.part);
+  g.ctl = ctl;
+  g.err = reinterpret_cast<int*>(ws_ + L.err);
+  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
+  const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
+  const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
+  // the maxima come from the kernels that wrote X and P; once sliced, they are
+  // cleared for those kernels' next run (both arrays are k entries, adjacent layout not assumed)
+#define EIGREF_CALL_G16R(S_)                                                                                     \
+  sl::slice_cols16_kernel<S_><<<K / 128, 256, 0, s>>>(X, n_, k_, k_, 1, K, x_cmax(), xp, xexp, ctl);            \
+  sl::slice_cols16_kernel<S_><<<K / 128, 256, 0, s>>>(P, n_, k_, k_, 1, K, p_cmax(), pp, pexp, ctl);            \
+  cudaMemsetAsync(x_cmax(), 0, (size_t)k_ * 8, s);                                                              \
+  cudaMemsetAsync(p_cmax(), 0, (size_t)k_ * 8, s);                                                              \
+  sl::sgram16_kernel<S_><<<ksplit_, sl::kThreads, sl::kG16Smem, s>>>(mx, mp, g);                                 \
+  sl::sgram16_reduce_kernel<S_><<<rg, 256, 0, s>>>(g.part, k_, ksplit_, xexp, pexp, out, ctl)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_G16R)
+#undef EIGREF_CALL_G16R
+  return 4;
 }
 
 int SlicedGram::timed_out(cudaStream_t s) const {

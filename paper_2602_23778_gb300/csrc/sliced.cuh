@@ -146,6 +146,19 @@ class SlicedGram {
   int prepare(cudaStream_t s);
   // out[0] = X^T X, out[1] = X^T P (k x k column-major); X, P row-major n x k
   int gram(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s);
+  // The same with the column maxima of X and P already in x_cmax() / p_cmax()
+  // (formed by the kernels that wrote X and P); clears them after use.
+  int gram_ready(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s);
+  void colmax_x(const double* X, cudaStream_t s);   // x_cmax() = column maxima of X
+  // X' = X + (W - X D) D^-1 - X F for rows k .. n - 1 on the tensor cores
+  // (even k); upart gets update_grid() x 2k column sums (x'^2, (w - x d)^2).
+  // Returns the launch count, or -1 when this k has no such kernel.
+  bool update_ready() const { return upd_ok_; }
+  int update_grid() const { return upd_grid_; }
+  int update(const double* X, const double* W, const double* F, const double* d, const double* dinv, double* Xn,
+             double* upart, const Control* ctl, cudaStream_t s);
+  unsigned long long* x_cmax() const;
+  unsigned long long* p_cmax() const;
   int timed_out(cudaStream_t s) const;
   int ksplit() const { return ksplit_; }
   int slices() const { return slices_; }
@@ -154,6 +167,8 @@ class SlicedGram {
  private:
   int64_t n_ = 0, n_pad_ = 0;
   int k_ = 0, slices_ = 0, ksplit_ = 1;
+  int upd_grid_ = 0;
+  bool upd_ok_ = false;
   char* ws_ = nullptr;
   alignas(64) unsigned char tmX_[128];
   alignas(64) unsigned char tmP_[128];

@@ -30,14 +30,21 @@ __device__ __forceinline__ double ld_stream_f64(const double* p) {
 // HBM (~48 us for its 328 MB): it is kept lean -- one X row load and two DFMA
 // per nonzero and lane.  With the shift folded into the stored diagonal
 // (SHIFT = false, see csr_fold_diag) there is no separate shift term.
+// cmax (optional): column maxima of |P| as ordered bit patterns (atomicMax),
+// for the slicing of P that follows in the split form.
 template <int LPR, bool SHIFT>
 __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ ci,
                                                             const double* __restrict__ val,
                                                             const double* __restrict__ X, double* __restrict__ P,
                                                             int64_t n, int k, double shift,
-                                                            const double* __restrict__ Xs, const Control* ctl) {
+                                                            const double* __restrict__ Xs, const Control* ctl,
+                                                            unsigned long long* __restrict__ cmax) {
   if (ctl && ctl->done) return;
+  __shared__ unsigned long long colm[kMaxK];
+  // this lane's column pairs (at most two): max |P| as ordered bit patterns,
+  // compared as integers (the FP64 pipe is the kernel's bottleneck)
+  unsigned long long mx[2][2] = {{0ull, 0ull}, {0ull, 0ull}};
   const int lane = threadIdx.x % LPR;
   const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR;
   const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / LPR;
@@ -62,7 +69,33 @@ __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __res
         ay = fma(-shift, xi.y, ay);
       }
       P2[i * k2 + c2] = make_double2(ax, ay);
+      if (cmax) {
+        const unsigned long long a = (unsigned long long)__double_as_longlong(ax) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(ay) & 0x7FFFFFFFFFFFFFFFull;
+        if (c2 < lane + LPR) {
+          mx[0][0] = max(mx[0][0], a);
+          mx[0][1] = max(mx[0][1], b);
+        } else {
+          mx[1][0] = max(mx[1][0], a);
+          mx[1][1] = max(mx[1][1], b);
+        }
+      }
     }
+  }
+  if (cmax) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) colm[j] = 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c2 = lane + q * LPR;
+      if (c2 < k2) {
+        atomicMax(&colm[2 * c2], mx[q][0]);
+        atomicMax(&colm[2 * c2 + 1], mx[q][1]);
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+      if (colm[j]) atomicMax(cmax + j, colm[j]);
   }
 }
 
@@ -110,16 +143,18 @@ __global__ void __launch_bounds__(256) spmm_csr_scalar_kernel(const int32_t* __r
 }
 
 void launch_spmm_csr(const int32_t* rp, const int32_t* ci, const double* val, const double* X, double* P,
-                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s, const double* Xs) {
+                     int64_t n, int k, double shift, const Control* ctl, cudaStream_t s, const double* Xs,
+                     unsigned long long* cmax) {
   if (!Xs) Xs = X;
+  if ((k & 1) || k > 2 * 2 * 32) cmax = nullptr;   // maxima only from the paired-column kernel
   const int grid = 152 * 8;  // 8 resident CTAs of 256 threads per SM, grid-stride over rows
   if ((k & 1) == 0) {
     const int k2 = k >> 1;
 #define EIGREF_SPMM(L)                                                                                       \
   if (shift != 0.0)                                                                                         \
-    spmm_csr_vec2_kernel<L, true><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl);             \
+    spmm_csr_vec2_kernel<L, true><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl, cmax);       \
   else                                                                                                      \
-    spmm_csr_vec2_kernel<L, false><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl);
+    spmm_csr_vec2_kernel<L, false><<<grid, 256, 0, s>>>(rp, ci, val, X, P, n, k, shift, Xs, ctl, cmax);
     if (k2 <= 2) {
       EIGREF_SPMM(2)
     } else if (k2 <= 4) {

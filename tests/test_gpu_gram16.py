@@ -98,7 +98,7 @@ def split_tol(p):
                      gaps.min() if gaps.size else np.inf)
 
 
-@pytest.mark.parametrize("nx,ny,k", [(40, 30, 16), (33, 17, 5), (64, 64, 1)])
+@pytest.mark.parametrize("nx,ny,k", [(40, 30, 16), (33, 17, 5), (64, 64, 1), (50, 41, 12), (37, 29, 2)])
 def test_csr_split_sweeps_match_oracle(eig, nx, ny, k):
     p = laplace_case(nx, ny, k)
     X = dev(np.asfortranarray(p.X0))
