@@ -1379,13 +1379,15 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __nv
 //              writes TMEM columns 16 s ..: column 16 w + j then holds the sum
 //              of every pair (s, t) with s + t = w, the pairs of one weight
 //              only, exact in FP32 (at most 16 x 45056 < 2^20).
-//   warps 2-9  two threads per tile row (warps w and w + 4 share a TMEM lane
-//              group), eight columns each: cut the next tile's X row into the
-//              A operand; drain the accumulators, rebuild each (X F)_ij with
-//              integer arithmetic up to its bit pattern, form
-//              x' = x + (w - x d_j) / d_j - (X F)_ij in FP64, write it over the
-//              X tile in shared memory and store it with TMA (32 rows per lane
-//              group), keeping the column sums of x'^2 and (w - x d_j)^2.
+//   warps 2-5  one thread per tile row: cut the X row into the A operand
+//              (running up to two tiles ahead of the epilogue).
+//   warps 6-13 two threads per tile row (warps w and w + 4 share a TMEM lane
+//              group), eight columns each: drain the accumulators, rebuild
+//              each (X F)_ij with integer arithmetic up to its bit pattern,
+//              form x' = x + (w - x d_j) / d_j - (X F)_ij in FP64, write it
+//              over the X tile in shared memory and store it with TMA (32 rows
+//              per lane group), keeping the column sums of x'^2 and
+//              (w - x d_j)^2.
 // Accumulators and A operands are double-
 // buffered, the X / W tiles triple-buffered.  Every wait is bounded; on expiry
 // the CTA records a timeout.  No FP64 instruction outside the update formula
@@ -1397,8 +1399,9 @@ constexpr int kU16Stage = 2 * kU16Tile;           // X tile, W tile
 constexpr int kU16ABlock = kBM * kBK * 2;         // 128 rows x 64 K BF16 (four planes)
 constexpr int kU16ABuf = 3 * kU16ABlock;          // planes 0..8
 constexpr int kU16BBytes = 16 * kMaxS * 128;      // 144 rows (t, j) of 128 B; K = l in the first 32 B
-constexpr int kU16RowWarps = 8;
-constexpr int kU16Threads = 64 + 32 * kU16RowWarps;
+constexpr int kU16SliceWarps = 4;                 // one thread per tile row
+constexpr int kU16EpiWarps = 8;                   // two threads per tile row
+constexpr int kU16Threads = 64 + 32 * (kU16SliceWarps + kU16EpiWarps);
 constexpr int kU16Smem = kU16Stages * kU16Stage + 2 * kU16ABuf + kU16BBytes + 1024 + 1024;
 
 struct Upd16Args {
@@ -1416,7 +1419,9 @@ struct Upd16Args {
 };
 
 struct __align__(8) BarsU16 {
-  uint64_t full[kU16Stages], empty[kU16Stages], a_full[2], a_empty[2], acc_full[2], acc_empty[2], sub[4], drain;
+  // sub[g][i & 3]: both warps of lane group g have written tile i (a ring of
+  // four: the second warp of a group can run up to two tiles ahead)
+  uint64_t full[kU16Stages], empty[kU16Stages], a_full[2], a_empty[2], acc_full[2], acc_empty[2], sub[4][4], drain;
   uint32_t tmem_base;
   int abort;
 };
@@ -1511,12 +1516,12 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       mbar_init(smem_u32(&bars->empty[i]), 4);                  // the four lane-group leaders
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(&bars->a_full[i]), kU16RowWarps);
+      mbar_init(smem_u32(&bars->a_full[i]), kU16SliceWarps);
       mbar_init(smem_u32(&bars->a_empty[i]), 1);
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
-      mbar_init(smem_u32(&bars->acc_empty[i]), kU16RowWarps);
+      mbar_init(smem_u32(&bars->acc_empty[i]), kU16EpiWarps);
     }
-    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars->sub[i]), 2);   // both halves of a lane group written
+    for (int i = 0; i < 16; ++i) mbar_init(smem_u32(&bars->sub[i >> 2][i & 3]), 2);
     mbar_init(smem_u32(&bars->drain), 1);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1595,15 +1600,11 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         mbar_drain(smem_u32(&bars->drain), 0);
       }
     }
-  } else {
-    // ---------------- rows: slicing and epilogue ----------------
-    const int lg = warp & 3;                 // TMEM lane group: tile rows 32 lg .. 32 lg + 31
-    const int half = (warp - 2) >> 2;        // columns 8 half .. 8 half + 7
-    const bool leader = half == 0;           // stores the lane group's 32 rows
-    const int r = lg * 32 + lane;
-    // B operand: digit t of F(l, j) at row 16 t + j, K = l
-    {
-      const int e = threadIdx.x - 64;        // 0..255: one (j, l) each
+  } else if (warp < 2 + kU16SliceWarps) {
+    // ---------------- slicers: one thread per tile row, all 16 columns ----------------
+    const int r = (warp - 2) * 32 + lane;
+    // B operand first: digit t of F(l, j) at row 16 t + j, K = l (two (j, l) a thread)
+    for (int e = r; e < 256; e += 128) {
       const int j = e >> 4, l = e & 15;
       const int fe = fexp_s[j];
       const double v = (j < g.k && l < g.k && fe != kNonFinite) ? g.F[(int64_t)j * g.k + l] : 0.0;
@@ -1614,131 +1615,147 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         *reinterpret_cast<uint16_t*>(bop + swz128(16 * t + j, l >> 3) + (l & 7) * 2) =
             (uint16_t)bf16_bits_of_int(dg[t]);
     }
-    double sq[8], rq[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) sq[j] = rq[j] = 0.0;
-
-    // this thread's eight values of the X row of local tile i as S digit
-    // planes in A buffer i & 1; e_out = the row's exponent
-    auto slice = [&](int i, int& e_out) -> bool {
-      const int st = i % kU16Stages, lap = i / kU16Stages;
+    bool ok = true;
+    for (int i = 0; i < cnt && ok; ++i) {
+      const int st = i % kU16Stages, lap = i / kU16Stages, a = i & 1;
       int w_ok = 1;
       if (lane == 0) {
         w_ok = mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);
-        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[i & 1]), (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag);
+        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[a]), (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag);
       }
-      if (!__shfl_sync(0xffffffffu, w_ok, 0)) return false;
+      ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+      if (!ok) break;
       mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);   // complete: each lane acquires
       const unsigned char* xt = stage0 + st * kU16Stage;
-      unsigned long long b[8];
+      unsigned long long b[16];
       unsigned long long am = 0ull;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const double2 v = *reinterpret_cast<const double2*>(xt + swz128(r, c));
-        const unsigned long long b0 = (unsigned long long)__double_as_longlong(v.x);
-        const unsigned long long b1 = (unsigned long long)__double_as_longlong(v.y);
-        am = max(am, max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull));
-        if ((c >> 2) == half) {
-          b[2 * (c & 3)] = b0;
-          b[2 * (c & 3) + 1] = b1;
-        }
+        b[2 * c] = (unsigned long long)__double_as_longlong(v.x);
+        b[2 * c + 1] = (unsigned long long)__double_as_longlong(v.y);
+        am = max(am, max(b[2 * c] & 0x7FFFFFFFFFFFFFFFull, b[2 * c + 1] & 0x7FFFFFFFFFFFFFFFull));
       }
       const bool fin = am < kInfBits;
       const int e = fin ? row_exponent(__longlong_as_double((long long)am)) : 0;
-      e_out = fin ? e : kNonFinite;
-      unsigned long long M[8];
-      uint32_t sgn[4];
+      unsigned char* ab = abuf0 + a * kU16ABuf;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) M[q] = biased_magnitude<S>(fin ? b[q] : 0ull, e);
+      for (int h = 0; h < 2; ++h) {   // columns 8 h .. 8 h + 7: one 16-byte chunk per plane
+        unsigned long long M[8];
+        uint32_t sgn[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        sgn[q] = (uint32_t)(b[2 * q] >> 63) << 15 | (uint32_t)(b[2 * q + 1] >> 63) << 31;
-      unsigned char* ab = abuf0 + (i & 1) * kU16ABuf;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        uint32_t w4[4];
+        for (int q = 0; q < 8; ++q) M[q] = biased_magnitude<S>(fin ? b[8 * h + q] : 0ull, e);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], s)),
-                              f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], s)), 0x7632) ^
-                  sgn[q];
-        *reinterpret_cast<uint4*>(ab + (s >> 2) * kU16ABlock + swz128(r, 2 * (s & 3) + half)) =
-            make_uint4(w4[0], w4[1], w4[2], w4[3]);
+          sgn[q] = (uint32_t)(b[8 * h + 2 * q] >> 63) << 15 | (uint32_t)(b[8 * h + 2 * q + 1] >> 63) << 31;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          uint32_t w4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], s)),
+                                f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], s)), 0x7632) ^
+                    sgn[q];
+          *reinterpret_cast<uint4*>(ab + (s >> 2) * kU16ABlock + swz128(r, 2 * (s & 3) + h)) =
+              make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
       }
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars->a_full[i & 1]));
-      return true;
-    };
-
-    int prev_st = -1;   // stage whose TMA store may still be reading shared memory (leaders)
-    auto epilogue = [&](int i, int e_row) -> bool {
+      if (lane == 0) mbar_arrive(smem_u32(&bars->a_full[a]));
+    }
+  } else {
+    // ---------------- epilogue: two threads per tile row, eight columns each ----------------
+    const int ew = warp - 2 - kU16SliceWarps;   // 0..7
+    const int lg = warp & 3;                     // TMEM lane group: tile rows 32 lg .. 32 lg + 31
+    const int half = ew >> 2;                    // columns 8 half .. 8 half + 7
+    const bool leader = half == 0;               // stores the lane group's 32 rows
+    const int r = lg * 32 + lane;
+    double sq[8], rq[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sq[j] = rq[j] = 0.0;
+    bool ok = true;
+    for (int i = 0; i < cnt && ok; ++i) {
       const int a = i & 1, u = i >> 1;
       int w_ok = 1;
       if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[a]), (uint32_t)(u & 1), abort_flag);
-      if (!__shfl_sync(0xffffffffu, w_ok, 0)) return false;
+      ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+      if (!ok) break;
       __syncwarp();
       tc_fence_after();
+      // the X and W tiles of this tile: loaded (the slicers waited for them)
+      // and not refilled before this warp's leader releases the stage
+      const int st = i % kU16Stages;
+      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)((i / kU16Stages) & 1), abort_flag);
+      unsigned char* xt = stage0 + st * kU16Stage;
+      const unsigned char* wt = xt + kU16Tile;
+      // the row's exponent (as the slicers took it) and this thread's X values
+      double2 xv[4];
+      int e_row;
+      {
+        unsigned long long am = 0ull;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const double2 v = *reinterpret_cast<const double2*>(xt + swz128(r, c));
+          am = max(am, max(abs_bits(v.x), abs_bits(v.y)));
+          if ((c >> 2) == half) xv[c & 3] = v;
+        }
+        e_row = am < kInfBits ? row_exponent(__longlong_as_double((long long)am)) : kNonFinite;
+      }
       long long hi[8], lo[8];
       const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * 256 + 8 * half);
       {
-        // weights in pairs: C_w 2^7 + C_(w+1) stays below 2^28
-        int c[S][8];
+        // weights in pairs (w, w + 1) within each group: C_w 2^7 + C_(w+1) stays below 2^28
+#pragma unroll
+        for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
+        int pend[8];
 #pragma unroll
         for (int w = 0; w < S; ++w) {
           uint32_t v[8];
           TC_LD8(tl + 16 * w, v);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int base = w < 4 ? 0 : 4;                       // first weight of its group
+          const int end = w < 4 ? (S < 4 ? S : 4) : S;           // one past its group's last
+          const bool first = ((w - base) & 1) == 0;
+          const bool paired = first ? (w + 1 < end) : true;
+          const int last_w = first ? (paired ? w + 1 : w) : w;   // weight of the pair's low digit
+          const int sh = w < 4 ? kBits * (3 - last_w) : kBits * (S - 1 - last_w);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) c[w][j] = int_of_f32(v[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          long long h = 0, l = 0;
-#pragma unroll
-          for (int w = 0; w < S && w < 4; w += 2) {
-            const int pr = (w + 1 < 4 && w + 1 < S) ? c[w][j] * 128 + c[w + 1][j] : c[w][j];
-            const int sh = (w + 1 < 4 && w + 1 < S) ? kBits * (2 - w) : kBits * (3 - w);
-            h += (long long)pr << sh;
+          for (int j = 0; j < 8; ++j) {
+            const int cw = int_of_f32(v[j]);
+            if (first && paired) {
+              pend[j] = cw;
+            } else {
+              const int pr = first ? cw : pend[j] * 128 + cw;
+              if (w < 4) hi[j] += (long long)pr << sh;
+              else lo[j] += (long long)pr << sh;
+            }
           }
-#pragma unroll
-          for (int w = 4; w < S; w += 2) {
-            const int pr = (w + 1 < S) ? c[w][j] * 128 + c[w + 1][j] : c[w][j];
-            const int sh = (w + 1 < S) ? kBits * (S - 2 - w) : kBits * (S - 1 - w);
-            l += (long long)pr << sh;
-          }
-          hi[j] = h;
-          lo[j] = l;
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[a]));
-      const int st = i % kU16Stages;
-      unsigned char* xt = stage0 + st * kU16Stage;
-      const unsigned char* wt = xt + kU16Tile;
       const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)i * G) * 128;
       const int64_t row = row0 + r;
       const bool live = row >= g.row_begin && row < g.n;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int cc = 4 * half + q;          // 16-byte chunk: columns 2 cc, 2 cc + 1
-        double2 xv = *reinterpret_cast<const double2*>(xt + swz128(r, cc));
+        const double2 x2 = xv[q];
         const double2 wv = *reinterpret_cast<const double2*>(wt + swz128(r, cc));
         const int j0 = 2 * cc, j1 = 2 * cc + 1;
         const double f0 = recombine_int<S>(hi[2 * q], lo[2 * q], e_row, fexp_s[j0]);
         const double f1 = recombine_int<S>(hi[2 * q + 1], lo[2 * q + 1], e_row, fexp_s[j1]);
-        const double r0 = fma(-xv.x, d_s[j0], wv.x), r1 = fma(-xv.y, d_s[j1], wv.y);
-        const double n0 = fma(r0, dinv_s[j0], xv.x) - f0, n1 = fma(r1, dinv_s[j1], xv.y) - f1;
+        const double r0 = fma(-x2.x, d_s[j0], wv.x), r1 = fma(-x2.y, d_s[j1], wv.y);
+        const double n0 = fma(r0, dinv_s[j0], x2.x) - f0, n1 = fma(r1, dinv_s[j1], x2.y) - f1;
         if (live) {
           sq[2 * q] = fma(n0, n0, sq[2 * q]);
           sq[2 * q + 1] = fma(n1, n1, sq[2 * q + 1]);
           rq[2 * q] = fma(r0, r0, rq[2 * q]);
           rq[2 * q + 1] = fma(r1, r1, rq[2 * q + 1]);
         }
-        xv.x = n0;
-        xv.y = n1;
-        *reinterpret_cast<double2*>(xt + swz128(r, cc)) = xv;
+        *reinterpret_cast<double2*>(xt + swz128(r, cc)) = make_double2(n0, n1);
       }
       const bool plain = row0 < g.row_begin;   // the tile with the leading block
       if (plain && live)
@@ -1746,34 +1763,22 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
           g.Xn[row * g.k + j] = reinterpret_cast<const double*>(xt + swz128(r, j >> 1))[j & 1];
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars->sub[lg]));
+      if (lane == 0) mbar_arrive(smem_u32(&bars->sub[lg][i & 3]));
       if (leader) {
         int s_ok = 1;
         if (lane == 0) {
-          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg]), (uint32_t)(i & 1), abort_flag);
+          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg][i & 3]), (uint32_t)((i >> 2) & 1), abort_flag);
           if (s_ok) {
-            bulk_wait_read_all();   // the previous tile's store has read its shared memory
-            if (prev_st >= 0) mbar_arrive(smem_u32(&bars->empty[prev_st]));
-            if (plain) {
-              mbar_arrive(smem_u32(&bars->empty[st]));
-            } else if (row0 + 32 * lg < g.n) {
+            if (!plain && row0 + 32 * lg < g.n) {
               tma_store_2d(&tmXn, smem_u32(xt + lg * 32 * 128), 0, (int)(row0 + 32 * lg));
               bulk_commit();
+              bulk_wait_read_all();   // the store has read the tile: the stage may be refilled
             }
+            mbar_arrive(smem_u32(&bars->empty[st]));
           }
         }
-        prev_st = plain ? -1 : st;
-        if (!__shfl_sync(0xffffffffu, s_ok, 0)) return false;
+        ok = __shfl_sync(0xffffffffu, s_ok, 0) != 0;
       }
-      return true;
-    };
-
-    int e_cur = 0, e_next = 0;
-    bool ok = slice(0, e_cur);
-    for (int i = 0; i < cnt && ok; ++i) {
-      if (i + 1 < cnt) ok = slice(i + 1, e_next);
-      if (ok) ok = epilogue(i, e_cur);
-      e_cur = e_next;
     }
     if (lane == 0) bulk_wait_all();
     // column sums over this warp's rows, in a fixed order
