@@ -1304,6 +1304,7 @@ __device__ __forceinline__ void sgram_reduce_thread_body(const longlong2* __rest
     const int64_t o = e % kk;
     const longlong2* p = part + (int64_t)z * nsplit * kk + o;
     long long hi = 0, lo = 0;
+#pragma unroll 4
     for (int c = 0; c < nsplit; ++c) {
       const longlong2 v = p[(int64_t)c * kk];
       hi += v.x;
@@ -1312,6 +1313,17 @@ __device__ __forceinline__ void sgram_reduce_thread_body(const longlong2* __rest
     const int row = (int)(o % k), col = (int)(o / k);
     out[e] = recombine<S>(hi, lo, xexp[row], z ? wexp[col] : xexp[col]);
   }
+}
+
+// The thread form for one problem with many outputs: consecutive threads read
+// consecutive partials of a split (the warp form reads one sector per lane).
+template <int S>
+__global__ void sgram_reduce_thread_kernel(const longlong2* __restrict__ part, int k, int nsplit,
+                                           const int* __restrict__ xexp, const int* __restrict__ wexp,
+                                           double* __restrict__ out, const Control* ctl) {
+  if (ctl && ctl->done) return;
+  sgram_reduce_thread_body<S>(part, k, nsplit, xexp, wexp, out, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                              (int64_t)gridDim.x * blockDim.x);
 }
 
 template <int S>
@@ -1815,6 +1827,294 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same Gram products for an even k <= 16, cutting the digit planes in the
+// kernel: each 64-row K block of X and W arrives by TMA as FP64 rows (128-byte
+// swizzle, rows past n read as zero), the eight worker warps cut both into
+// the stacked-plane tiles the MMA reads (one 16-byte chunk of 8 rows per
+// thread, plane and operand), and the same warps drain the accumulators after
+// the last K block of each exact chunk.  The column exponents come from
+// column maxima formed before the launch.  HBM traffic is the FP64 operands,
+// read once; the planes never leave shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kG16FRaw = 4;                          // FP64 tile ring
+constexpr int kG16FRawTile = 64 * 128;               // 64 rows x 16 FP64: 8 KiB
+constexpr int kG16FPlanes = 3;                       // plane-tile ring (X planes, W planes)
+constexpr int kG16FSmem = kG16FRaw * 2 * kG16FRawTile + kG16FPlanes * kG16Stage + 1024 + 1024;
+
+struct Gram16FArgs {
+  Gram16Args g;
+  const unsigned long long* xmax;   // column maxima of |X|, |W| (ordered bits)
+  const unsigned long long* wmax;
+  int* xexp;                        // column exponents for the reduction (written by CTA 0)
+  int* wexp;
+};
+
+struct __align__(8) Bars16F {
+  uint64_t raw_full[kG16FRaw], raw_empty[kG16FRaw], pl_full[kG16FPlanes], pl_empty[kG16FPlanes], acc_full,
+      acc_empty, drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                              const __grid_constant__ CUtensorMap tmW,
+                                                              Gram16FArgs fa) {
+  const Gram16Args& g = fa.g;
+  __shared__ int s_skip;
+  __shared__ int fexp_s[2][16];
+  if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
+  if (threadIdx.x < 32) {
+    // column exponents of X (0..15) and W (16..31); non-finite columns give NaN
+    const int op = threadIdx.x >> 4, j = threadIdx.x & 15;
+    const unsigned long long cm = j < g.k ? (op ? fa.wmax[j] : fa.xmax[j]) : 0ull;
+    const int f = row_exponent(__longlong_as_double((long long)cm));
+    const int fe = cm < kInfBits ? f : kNonFinite;
+    fexp_s[op][j] = fe;
+    if (blockIdx.x == 0 && j < g.k) (op ? fa.wexp : fa.xexp)[j] = fe;
+  }
+  __syncthreads();
+  if (s_skip) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* raw0 = smem;                                        // [kG16FRaw][X tile, W tile]
+  unsigned char* pl0 = smem + kG16FRaw * 2 * kG16FRawTile;           // [kG16FPlanes][X planes, W planes]
+  Bars16F* bars = reinterpret_cast<Bars16F*>(pl0 + kG16FPlanes * kG16Stage);
+  constexpr int kRows = 16 * S;                      // rows of a stacked tile
+  constexpr int kColsJob = kRows + (S == 9 ? 16 : 0);   // TMEM columns per product
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int split = blockIdx.x;
+  const int kb_lo = (int)((int64_t)g.kb_total * split / g.ksplit);
+  const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / g.ksplit);
+  const int KB = kb_hi - kb_lo;
+  volatile int* abort_flag = &bars->abort;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kG16FRaw; ++i) {
+      mbar_init(smem_u32(&bars->raw_full[i]), 1);
+      mbar_init(smem_u32(&bars->raw_empty[i]), kEpiWarps);
+    }
+    for (int i = 0; i < kG16FPlanes; ++i) {
+      mbar_init(smem_u32(&bars->pl_full[i]), kEpiWarps);
+      mbar_init(smem_u32(&bars->pl_empty[i]), 1);
+    }
+    mbar_init(smem_u32(&bars->acc_full), 1);
+    mbar_init(smem_u32(&bars->acc_empty), kEpiWarps);
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: the FP64 X and W rows of each K block ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmW) : "memory");
+      bool ok = true;
+      int issued = 0;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int st = kb % kG16FRaw, lap = kb / kG16FRaw;
+        ok = mbar_wait_sleep(smem_u32(&bars->raw_empty[st]), (uint32_t)((lap & 1) ^ 1), abort_flag);
+        if (!ok) break;
+        const int row = (kb_lo + kb) * kBK;
+        unsigned char* rt = raw0 + st * 2 * kG16FRawTile;
+        mbar_expect_tx(smem_u32(&bars->raw_full[st]), (uint32_t)(2 * kG16FRawTile));
+        tma_load_2d(smem_u32(rt), &tmX, smem_u32(&bars->raw_full[st]), 0, row);
+        tma_load_2d(smem_u32(rt + kG16FRawTile), &tmW, smem_u32(&bars->raw_full[st]), 0, row);
+        ++issued;
+      }
+      if (!ok)
+        for (int i = (issued > kG16FRaw ? issued - kG16FRaw : 0); i < issued; ++i)
+          mbar_drain(smem_u32(&bars->raw_full[i % kG16FRaw]), (uint32_t)((i / kG16FRaw) & 1));
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = true;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int c = kb / kG16Chunk;
+        const bool first = (kb % kG16Chunk) == 0;
+        const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
+        if (first && c > 0) {   // one accumulator set: the previous chunk must be drained
+          ok = mbar_wait_sleep(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+        }
+        const int pb = kb % kG16FPlanes;
+        ok = mbar_wait_sleep(smem_u32(&bars->pl_full[pb]), (uint32_t)((kb / kG16FPlanes) & 1), abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        unsigned char* pt = pl0 + pb * kG16Stage;
+        const uint64_t xd = smem_desc(smem_u32(pt));
+        const uint64_t xd8 = smem_desc(smem_u32(pt + 128 * kBK * 2));   // X rows 128.. (plane 8)
+        const uint64_t yd = smem_desc(smem_u32(pt + kG16Tile));
+        constexpr uint32_t id1 = idesc_bf16(kBM, kRows);
+        constexpr uint32_t id2 = idesc_bf16(kBM, 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t acc = (first && q == 0) ? 0u : 1u;
+          const uint64_t o = (uint64_t)(2 * q);    // 16 K per step inside the 128-byte swizzle row
+          tc_mma(tbase, xd + o, xd + o, id1, acc);                                 // G: planes 0..7 x all
+          tc_mma(tbase + kColsJob, xd + o, yd + o, id1, acc);                      // S
+          if (S == 9) {
+            tc_mma(tbase + kRows, xd8 + o, xd + o, id2, acc);                      // G: plane 8 x plane 0
+            tc_mma(tbase + kColsJob + kRows, xd8 + o, yd + o, id2, acc);           // S
+          }
+        }
+        tc_commit(smem_u32(&bars->pl_empty[pb]));
+        if (last) tc_commit(smem_u32(&bars->acc_full));
+      }
+      if (!ok) {
+        tc_commit(smem_u32(&bars->drain));
+        mbar_drain(smem_u32(&bars->drain), 0);
+      }
+    }
+  } else {
+    // ---------------- workers: cut the planes of every K block, drain every chunk ----------------
+    const int te = threadIdx.x - 64;             // 0..255
+    const int op = te >> 7;                      // slicing: 0 = X, 1 = W
+    const int sj = te & 15, sig = (te >> 4) & 7; // column j, rows 8 sig .. 8 sig + 7 of the K block
+    const int fe = fexp_s[op][sj];
+    const int lg = warp & 3;                     // TMEM lane group
+    const int job = (warp - 2) >> 2;             // 0: G = X^T X, 1: S = X^T W
+    const int r = lg * 32 + lane;                // TMEM lane = 16 s + i
+    const int sp = r >> 4;                       // plane s of X this lane holds
+    long long hi[16], lo[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+    bool ok = true;
+    for (int kb = 0; kb < KB && ok; ++kb) {
+      const int st = kb % kG16FRaw, pb = kb % kG16FPlanes;
+      int w_ok = 1;
+      if (lane == 0) {
+        w_ok = mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), abort_flag);
+        if (w_ok)
+          w_ok = mbar_wait_sleep(smem_u32(&bars->pl_empty[pb]), (uint32_t)(((kb / kG16FPlanes) & 1) ^ 1), abort_flag);
+      }
+      ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+      if (!ok) break;
+      mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), abort_flag);   // each lane acquires
+      {
+        const unsigned char* rt = raw0 + (st * 2 + op) * kG16FRawTile;
+        unsigned long long M[8];
+        uint32_t sgn[4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = 8 * sig + q;
+          const unsigned long long b =
+              (unsigned long long)__double_as_longlong(*reinterpret_cast<const double*>(rt + swz128(i, sj >> 1) + (sj & 1) * 8));
+          M[q] = biased_magnitude<S>(fe != kNonFinite ? b : 0ull, fe != kNonFinite ? fe : 0);
+          if (q & 1) sgn[q >> 1] |= (uint32_t)(b >> 63) << 31;
+          else sgn[q >> 1] = (uint32_t)(b >> 63) << 15;
+        }
+        unsigned char* pt = pl0 + pb * kG16Stage + op * kG16Tile;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          uint32_t w4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], t)),
+                                f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], t)), 0x7632) ^
+                    sgn[q];
+          *reinterpret_cast<uint4*>(pt + swz128(16 * t + sj, sig)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bars->pl_full[pb]));
+        mbar_arrive(smem_u32(&bars->raw_empty[st]));
+      }
+      const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
+      if (last) {
+        const int c = kb / kG16Chunk;
+        int a_ok = 1;
+        if (lane == 0) a_ok = mbar_wait_sleep(smem_u32(&bars->acc_full), (uint32_t)(c & 1), abort_flag);
+        ok = __shfl_sync(0xffffffffu, a_ok, 0) != 0;
+        __syncwarp();
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(job * kColsJob);
+#pragma unroll
+        for (int t = 0; t <= S - (S == 9 ? 0 : 1); ++t) {
+          // plane t of the right operand, or (S = 9, one slot past the planes)
+          // plane 8 of X x plane 0 of the right operand
+          int w;
+          uint32_t col;
+          if (t == S) {
+            col = (uint32_t)kRows;
+            w = r < 16 ? 8 : 99;                 // rows >= 16 of the plane-8 instruction are not X's
+          } else {
+            col = (uint32_t)(16 * t);
+            w = sp + t;
+          }
+          uint32_t v[16];
+          TC_LD16(tl + col, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (w <= S - 1) {
+            if (w < 4) {
+              const int sh = kBits * (3 - w);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+            } else {
+              const int sh = kBits * (S - 1 - w);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty));
+      }
+    }
+    // the 8 threads of a job holding row i (4 lane groups x 2 lanes) add their sums
+    asm volatile("bar.sync 1, 256;" ::: "memory");   // every worker is past its last shared-memory use
+    longlong2* red = reinterpret_cast<longlong2*>(pl0);   // [2 jobs][8 contributors][16 i][16 j]
+    const int i = r & 15;
+    const int qc = lg * 2 + (lane >> 4);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) red[((job * 8 + qc) * 16 + i) * 16 + j] = make_longlong2(hi[j], lo[j]);
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    const int oi = te & 15, oj = (te >> 4) & 15;
+#pragma unroll
+    for (int jb = 0; jb < 2; ++jb) {
+      long long h = 0, l = 0;
+      for (int q = 0; q < 8; ++q) {
+        const longlong2 e = red[((jb * 8 + q) * 16 + oi) * 16 + oj];
+        h += e.x;
+        l += e.y;
+      }
+      if (ok && oi < g.k && oj < g.k)
+        g.part[((int64_t)(jb * g.ksplit + split) * g.k + oj) * g.k + oi] = make_longlong2(h, l);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (bars->abort && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+    if (g.ctl) {
+      Control* c = const_cast<Control*>(g.ctl);
+      c->status = EIGREF_E_TIMEOUT;
+      c->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+  }
+}
+
 #define EIGREF_SLICE_DISPATCH(S_, CALL) \
   switch (S_) {                         \
     case 2: CALL(2); break;             \
@@ -1899,7 +2199,9 @@ cudaError_t init_sliced_attributes() {
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sgram16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16Smem); \
   if (e == cudaSuccess)                                                                                            \
-    e = cudaFuncSetAttribute(sl::update16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kU16Smem);
+    e = cudaFuncSetAttribute(sl::update16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kU16Smem); \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sgram16f_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16FSmem);
   EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
   EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
 #undef EIGREF_SET_ATTR
@@ -2269,9 +2571,15 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
 #undef EIGREF_CALL_SLICE_P
   const MmaTask t = gram_task(part, ctl);
   launch_task(slices_, sl::MODE_GRAM, t, s);
-#define EIGREF_CALL_SGR(S_)                                                                                   \
-  sl::sgram_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.gpart, k_, ksplit_, t.g.colexp, t.g.colexp2, out, ctl)
-  const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
+  // many outputs (k >= 32): a thread per output, coalesced over the splits;
+  // otherwise a warp per output.  Both add the exact int64 partials.
+  const bool per_thread = 2LL * k_ * k_ >= 2048;
+  const int rg = per_thread ? (int)((2LL * k_ * k_ + 255) / 256) : (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
+#define EIGREF_CALL_SGR(S_)                                                                                          \
+  if (per_thread)                                                                                                  \
+    sl::sgram_reduce_thread_kernel<S_><<<rg, 256, 0, s>>>(t.g.gpart, k_, ksplit_, t.g.colexp, t.g.colexp2, out, ctl); \
+  else                                                                                                             \
+    sl::sgram_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.gpart, k_, ksplit_, t.g.colexp, t.g.colexp2, out, ctl)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SGR)
 #undef EIGREF_CALL_SGR
   return 6;
@@ -2512,7 +2820,46 @@ int SlicedGram::prepare(cudaStream_t s) {
   return EIGREF_OK;
 }
 
+// Even k: the fused kernel (planes cut in shared memory) from the column
+// maxima in x_cmax() / p_cmax(), then the reduction.  Returns the launch
+// count, or -1 when the operands cannot be mapped (then the plane path runs).
+int SlicedGram::gram_fused(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s) {
+  if (!upd_ok_) return -1;
+  alignas(64) CUtensorMap mx, mp;
+  if (!sl::make_map_f64(&mx, X, k_, n_, 64) || !sl::make_map_f64(&mp, P, k_, n_, 64)) return -1;
+  const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
+  int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
+  int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
+  sl::Gram16FArgs fa;
+  fa.g.kb_total = (int)((n_ + sl::kBK - 1) / sl::kBK);
+  fa.g.ksplit = ksplit_;
+  fa.g.k = k_;
+  fa.g.part = reinterpret_cast<longlong2*>(ws_ + L.part);
+  fa.g.ctl = ctl;
+  fa.g.err = reinterpret_cast<int*>(ws_ + L.err);
+  fa.xmax = x_cmax();
+  fa.wmax = p_cmax();
+  fa.xexp = xexp;
+  fa.wexp = pexp;
+  const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
+#define EIGREF_CALL_G16F(S_)                                                                                     \
+  sl::sgram16f_kernel<S_><<<ksplit_, sl::kThreads, sl::kG16FSmem, s>>>(mx, mp, fa);                               \
+  sl::sgram16_reduce_kernel<S_><<<rg, 256, 0, s>>>(fa.g.part, k_, ksplit_, xexp, pexp, out, ctl)
+  EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_G16F)
+#undef EIGREF_CALL_G16F
+  return 2;
+}
+
 int SlicedGram::gram(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s) {
+  if (upd_ok_) {
+    // column maxima, then the fused kernel
+    cudaMemsetAsync(x_cmax(), 0, (size_t)k_ * 8, s);
+    cudaMemsetAsync(p_cmax(), 0, (size_t)k_ * 8, s);
+    sl::launch_colmax_rowmajor(X, n_, k_, x_cmax(), ctl, s);
+    sl::launch_colmax_rowmajor(P, n_, k_, p_cmax(), ctl, s);
+    const int nl = gram_fused(X, P, out, ctl, s);
+    if (nl > 0) return nl + 2;
+  }
   const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
   auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
   auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
@@ -2555,6 +2902,15 @@ void SlicedGram::colmax_x(const double* X, cudaStream_t s) {
 }
 
 int SlicedGram::gram_ready(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s) {
+  {
+    const int nl = gram_fused(X, P, out, ctl, s);
+    if (nl > 0) {
+      // the maxima are read: clear them for the kernels that form the next ones
+      cudaMemsetAsync(x_cmax(), 0, (size_t)k_ * 8, s);
+      cudaMemsetAsync(p_cmax(), 0, (size_t)k_ * 8, s);
+      return nl;
+    }
+  }
   const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
   auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
   auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);

@@ -150,6 +150,7 @@ class SlicedGram {
   // (formed by the kernels that wrote X and P); clears them after use.
   int gram_ready(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s);
   void colmax_x(const double* X, cudaStream_t s);   // x_cmax() = column maxima of X
+  int gram_fused(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s);
   // X' = X + (W - X D) D^-1 - X F for rows k .. n - 1 on the tensor cores
   // (even k); upart gets update_grid() x 2k column sums (x'^2, (w - x d)^2).
   // Returns the launch count, or -1 when this k has no such kernel.
