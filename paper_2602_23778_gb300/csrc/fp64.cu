@@ -385,23 +385,32 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
     return;
   }
   if (tid == 0) bad = 0;
-  // column sums: one warp per column, lanes over the update partials and the
-  // leading-block rows; fixed order, so the result is reproducible
-  for (int j = warp; j < k; j += nwarp) {
-    double xsq = 0.0, r2 = 0.0;
-    for (int i = lane; i < k; i += 32) {
-      const double v = b.xn[(int64_t)i * k + j];
-      xsq += v * v;
+  // column sums of the update partials [ugrid][2k]: thread (grp, c) adds
+  // partials grp, grp + groups, ... of column c (consecutive threads read
+  // consecutive addresses), then the groups are added in order; fixed order,
+  // so the result is reproducible
+  __shared__ double part_s[1024];
+  {
+    const int w2 = 2 * k, groups = (int)blockDim.x / w2;
+    if (tid < groups * w2) {
+      const int c = tid % w2, grp = tid / w2;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int g = grp; g < b.ugrid; g += groups) acc += b.upart[(int64_t)g * w2 + c];
+      part_s[grp * w2 + c] = acc;
     }
-    for (int g = lane; g < b.ugrid; g += 32) {
-      xsq += b.upart[(int64_t)g * 2 * k + j];
-      r2 += b.upart[(int64_t)g * 2 * k + k + j];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      xsq += __shfl_xor_sync(0xffffffffu, xsq, o);
-      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-    }
-    if (lane == 0) {
+    __syncthreads();
+    if (tid < k) {
+      const int j = tid;
+      double xsq = 0.0, r2 = 0.0;
+      for (int grp = 0; grp < groups; ++grp) {
+        xsq += part_s[grp * w2 + j];
+        r2 += part_s[grp * w2 + k + j];
+      }
+      for (int i = 0; i < k; ++i) {   // the leading block
+        const double v = b.xn[(int64_t)i * k + j];
+        xsq += v * v;
+      }
       xsq_s[j] = xsq;
       r2_s[j] = r2;
     }

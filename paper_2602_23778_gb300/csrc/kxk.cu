@@ -233,35 +233,49 @@ __global__ void kk_solve_kernel(const double* __restrict__ LU, const int* __rest
 
 enum { KG_V1 = 0, KG_W2 = 1, KG_YTE = 2, KG_X1 = 3 };
 
+// The TT rows of op(A) and TT columns of B a tile needs, whole (every load in
+// flight at once: these products are latency-bound), into As[r][l] = op(A)(i0
+// + r, l) and Bs[l][c] = B(l, j0 + c); zero outside k.
+template <int TT>
+__device__ __forceinline__ void kk_load_panels(const double* __restrict__ A, bool transA, const double* __restrict__ B,
+                                               int k, int i0, int j0, double (*As)[kMaxK + 1],
+                                               double (*Bs)[TT + 1]) {
+  const int nt = blockDim.x;
+  for (int e = threadIdx.x; e < TT * k; e += nt) {
+    int r, l;
+    if (transA) {   // op(A)(i, l) = A(l, i): l runs along memory
+      l = e % k;
+      r = e / k;
+    } else {
+      r = e % TT;
+      l = e / TT;
+    }
+    const int ai = i0 + r;
+    As[r][l] = ai < k ? (transA ? A[l + (int64_t)ai * k] : A[ai + (int64_t)l * k]) : 0.0;
+  }
+  for (int e = threadIdx.x; e < TT * k; e += nt) {
+    const int l = e % k, c = e / k;
+    const int bj = j0 + c;
+    Bs[l][c] = bj < k ? B[l + (int64_t)bj * k] : 0.0;
+  }
+}
+
 // TT x TT output tile per CTA (TT^2 threads), one output per thread:
 // s = op(A)(i,:) . Bm(:,j), summed in the order l = 0, 1, ... for any TT.
 template <int MODE, int TT = 16>
 __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, int by) {
-  __shared__ double As[TT][TT + 1];
-  __shared__ double Bs[TT][TT + 1];
+  __shared__ double As[TT][kMaxK + 1];
+  __shared__ double Bs[kMaxK][TT + 1];
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
   const int i = bx * TT + tx, j = by * TT + ty;
   const int64_t kk = (int64_t)k * k;
   const double* A = (MODE == KG_W2) ? b.g2 : b.y1;   // G2 = b.g2[0 .. k*k)
   const double* Bm = (MODE == KG_YTE) ? b.e11 : (MODE == KG_X1 ? b.nmat : b.m);
   const bool transA = (MODE == KG_YTE);
+  kk_load_panels<TT>(A, transA, Bm, k, bx * TT, by * TT, As, Bs);
+  __syncthreads();
   double s = 0.0;
-  for (int l0 = 0; l0 < k; l0 += TT) {
-    // As[r][c] = op(A)(bx TT + r, l0 + c); Bs[r][c] = Bm(l0 + r, by TT + c)
-    {
-      const int r = ty, c = tx;  // each thread loads one element of each tile
-      const int ai = bx * TT + r, al = l0 + c;
-      double av = 0.0;
-      if (ai < k && al < k) av = transA ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k];
-      As[r][c] = av;
-      const int bl = l0 + r, bj = by * TT + c;
-      Bs[r][c] = (bl < k && bj < k) ? Bm[bl + (int64_t)bj * k] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < TT; ++c) s = fma(As[tx][c], Bs[c][ty], s);
-    __syncthreads();
-  }
+  for (int l = 0; l < k; ++l) s = fma(As[tx][l], Bs[l][ty], s);
   if (i >= k || j >= k) return;
   const int64_t e = i + (int64_t)j * k;
   if (MODE == KG_V1) {
@@ -340,21 +354,14 @@ __device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ 
                                                      const double* __restrict__ C0, double* __restrict__ C, int k,
                                                      double alpha, double beta, int add_i, double check, Control* ctl,
                                                      int bx, int by) {
-  __shared__ double As[TT][TT + 1];
-  __shared__ double Bs[TT][TT + 1];
+  __shared__ double As[TT][kMaxK + 1];
+  __shared__ double Bs[kMaxK][TT + 1];
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
   const int i = bx * TT + tx, j = by * TT + ty;
+  kk_load_panels<TT>(A, TRANS != 0, B, k, bx * TT, by * TT, As, Bs);
+  __syncthreads();
   double acc = 0.0;
-  for (int l0 = 0; l0 < k; l0 += TT) {
-    const int ai = bx * TT + ty, al = l0 + tx;
-    As[ty][tx] = (ai < k && al < k) ? (TRANS ? A[al + (int64_t)ai * k] : A[ai + (int64_t)al * k]) : 0.0;
-    const int bl = l0 + ty, bj = by * TT + tx;
-    Bs[ty][tx] = (bl < k && bj < k) ? B[bl + (int64_t)bj * k] : 0.0;
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < TT; ++c) acc = fma(As[tx][c], Bs[c][ty], acc);
-    __syncthreads();
-  }
+  for (int l = 0; l < k; ++l) acc = fma(As[tx][l], Bs[l][ty], acc);
   if (i < k && j < k) {
     const int64_t e = i + (int64_t)j * k;
     double v = alpha * acc;
