@@ -510,7 +510,7 @@ def main():
         kfile = "fp64.cu"
     else:
         from paper_2602_23778_gb300 import sliced_info
-        info = sliced_info(precision, n, k, slices=args.slices or 9)
+        info = sliced_info(precision, n, k, slices=args.slices or 8)
         flops = info["executed_flops"]
         peak = pk["bf16_tflops_sustained"] if precision == "bf16" else \
             pk["bf16_tflops_sustained"] * NOMINAL["int8"] / NOMINAL["bf16"]
@@ -526,7 +526,7 @@ def main():
            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision + "-slices+f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": n, "k": k, "form": precision, "seed": 3000,
-                      "slices": (args.slices or 9) if precision != "fp64" else None,
+                      "slices": (args.slices or 8) if precision != "fp64" else None,
                       "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
                       "parallelism": "replicas" if world > 1 else "single",
                       "split_k": {"product": rep["psplit"], "gram": rep["ksplit"]} if precision != "fp64" else None},

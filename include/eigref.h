@@ -93,7 +93,8 @@ typedef struct eigref_params {
   double tol;          /* stopping tolerance; 0 = run exactly max_iters sweeps */
   int stop;            /* enum eigref_stop */
   int precision;       /* enum eigref_precision (dense only; CSR is always FP64) */
-  int slices;          /* split forms: slices per operand, 0 = default */
+  int slices;          /* split forms: 8-bit digit planes per operand, 2..8; 0 = default (8:
+                          63 bits, FP64-level products) */
   int beta;            /* enum eigref_beta */
   double delta_c;      /* c of delta = c ||B|| u (Section 3.1.3); <= 0: 10 */
   double div_factor;   /* diverged when ||E_t||_F > div_factor * min_{s<t} ||E_s||_F and

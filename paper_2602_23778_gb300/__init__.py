@@ -105,7 +105,7 @@ def status_string(s):
 
 # ---- array marshalling ------------------------------------------------------
 
-def sliced_info(precision, n, k, slices=9):
+def sliced_info(precision, n, k, slices=8):
     """Work of one split-precision product W = B X as the library pads it:
     S (S + 1) / 2 digit-plane pairs, each a 2 n_pad^2 k_pad-flop BF16 GEMM
     (n_pad = n rounded up to 256, k_pad = k rounded up to 32)."""

@@ -3,35 +3,36 @@
 //
 // Slicing (Ozaki, Ogita, Oishi and Rump's error-free splitting, BIT 2012):
 // every row i of A is scaled by 2^-e_i (e_i = exponent of the row's largest
-// |a_il|, so |a_il 2^-e_i| < 1) and written as a sum of S signed 7-bit digit
-// planes, a_il 2^-e_i = sum_s d_s 2^-7s + r with |d_1| <= 128, |d_s| <= 64
-// (s >= 2), |r| <= 2^-7S / 2.  Every column j of X gets the same treatment
-// with its own exponent f_j.  Each digit is an integer of at most 8
-// significant bits, hence exact in BF16, and a digit product is exact in
-// FP32.  The product keeps the S(S+1)/2 digit pairs with s + t <= S + 1
-// (triangular truncation):
-//     W_ij = 2^(e_i + f_j) sum_w 2^-7(w+2) C_w,   C_w = sum_{s+t=w} A_s X_t
-// (0-based s, t, w).  C_w is accumulated in FP32 over K chunks of 320:
-// the largest partial sum is bounded by 320 (2 * 128 * 64 + (S - 2) * 64 * 64)
-// <= 320 * 45056 = 14417920 < 2^24 (S <= 9), so every FP32 addition is exact.  After
+// |a_il|, so |a_il 2^-e_i| < 1), rounded to a 63-bit integer M (at S = 8) and
+// written as S balanced base-256 digits, a_il 2^-e_i = sum_s d_s 2^-(8s+7) + r
+// with d_0 in [0, 128], d_s in [-128, 127] (s >= 1), |r| <= 2^-(8S) .  Every
+// column j of X gets the same treatment with its own exponent f_j.  Each
+// digit has at most 8 significant bits, hence is exact in BF16, and a digit
+// product (at most 2^14) is exact in FP32.  The product keeps the S(S+1)/2
+// digit pairs with s + t <= S - 1 (triangular truncation):
+//     W_ij = 2^(e_i + f_j) sum_w 2^-(8w+14) C_w,   C_w = sum_{s+t=w} A_s X_t
+// (0-based s, t, w).  C_w is accumulated in FP32 over K chunks of 128: a
+// weight group has at most S = 8 pairs, so every partial sum is at most
+// 8 x 2^14 x 128 = 2^24 in magnitude and every FP32 addition is exact.  After
 // each chunk the epilogue warps move C_w into two int64 registers per output
-// (hi = sum_{w<4} C_w 2^7(3-w), lo = sum_{w>=4} C_w 2^7(S-1-w)), exact
-// integer arithmetic; at the end W_ij = 2^(e_i+f_j) (hi 2^-35 + lo
-// 2^-7(S+1)) with one rounding.  The only errors are the truncated digits:
-// per product term about 2^-(7S+1) of the scaled operands.
+// (hi = sum_{w<4} C_w 2^8(3-w), lo = sum_{w>=4} C_w 2^8(S-1-w)), exact
+// integer arithmetic; at the end W_ij = 2^(e_i+f_j) (hi 2^-38 + lo
+// 2^-(8S+6)) with one rounding.  The only errors are the rounding of M and
+// the truncated digit pairs: per product term about (S + 2) 2^-8S of the
+// scaled operands.  (Eight-bit digits: 36 plane pairs for 63 bits, against
+// 45 with seven-bit digits.)
 //
 // Kernel: one CTA per 128 rows x 32 columns of W.  Warp 0 issues TMA loads
 // (A digit tiles 128 x 64 per plane, X digit tiles of all S planes stacked:
 // 32 S rows x 64), warp 1 issues tcgen05.mma (M = 128, N = 32 (S - s) for A
 // plane s: one instruction covers every X plane that pairs with it, writing
 // the accumulators of weights s..S-1, which sit side by side in TMEM),
-// warps 2-9 drain TMEM (two per lane group, 16 columns each).  (At S = 9 the plane-0 stack is 288 rows and goes
-// out as two instructions, N = 256 and N = 32.)  The accumulators are double-buffered when they fit
-// (2 x S x 32 FP32 columns <= 512, S <= 8) so draining overlaps the next
-// chunk; at S = 9 consecutive chunks alternate between columns [0, 288) and
-// [224, 512) and share only the two weight groups the epilogue drains first.
-// All waits are bounded (globaltimer); on expiry the CTA records a timeout,
-// drains what it started and returns.
+// warps 2-9 drain TMEM (two per lane group, 16 columns each).  The
+// accumulators are double-buffered (2 x S x 32 FP32 columns <= 512) so
+// draining overlaps the next chunk.  (A rotating layout for S x 32 > 256,
+// sharing two weight groups between consecutive chunks, stays in the code
+// for that case.)  All waits are bounded (globaltimer); on expiry the CTA
+// records a timeout, drains what it started and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -47,14 +48,22 @@ namespace eigref {
 
 namespace sl {
 
-constexpr int kBits = 7;           // bits per digit plane
-constexpr int kMaxS = 9;           // digit planes per operand (at most)
-constexpr int kDefaultS = 9;       // default digit planes (63 bits: FP64-level accuracy at n = 16384)
+constexpr int kBits = 8;           // bits per digit plane (BF16 holds 8 significant bits)
+constexpr int kMaxS = 8;           // digit planes per operand (at most)
+constexpr int kDefaultS = 8;       // default digit planes (63 bits: FP64-level accuracy at n = 16384)
 constexpr int kBM = 128;           // rows of W per CTA
 constexpr int kBN = 32;            // columns of W per CTA
 constexpr int kBK = 64;            // K per pipeline stage (128 bytes of BF16)
-constexpr int kChunkBlocks = 5;    // K blocks per exact accumulation chunk (320: 320 x 45056 < 2^24)
-constexpr int kRA = 9;             // A ring stages (a whole K block of planes at S = 9)
+constexpr int kChunkBlocks = 2;    // K blocks per exact accumulation chunk (128: 8 pairs x 2^14 x 128 <= 2^24)
+constexpr int kRA = 9;             // A ring stages (a K block of planes and one more)
+// Digit weights: a = 2^e sum_s d_s 2^-(kBits s + 7), so the pairs of weight
+// group w = s + t carry 2^-(kBits w + 14); the epilogue keeps
+// hi = sum_(w<4) C_w 2^(kBits (3 - w)) and lo = sum_(w>=4) C_w 2^(kBits (S-1-w)).
+constexpr int kHiExp = 3 * kBits + 14;                  // hi carries 2^-kHiExp
+template <int S>
+struct LoExp {
+  static constexpr int value = kBits * (S - 1) + 14;    // lo carries 2^-value
+};
 constexpr int kRX = 2;             // X ring stages
 constexpr int kATile = kBM * kBK * 2;                // 16 KiB
 constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 36 KiB (all planes of a K block)
@@ -197,12 +206,52 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 
 
 // The value of one output from its two exact int64 sums (digit-pair groups
-// w < 4 and w >= 4, see the epilogue) and the row / column exponents.
+// w < 4 and w >= 4, see the epilogue) and the row / column exponents:
+// 2^(er + fc) (hi 2^-kHiExp + lo 2^-LoExp), rounded once to nearest-even.  The
+// exact sum V = hi 2^(m-kHiExp) + lo (value V 2^-m) is formed as a 128-bit
+// integer and rounded to 53 bits with integer arithmetic up to the bit
+// pattern: no FP64 instruction (FP64 runs at a small fraction of the integer
+// rate on this part), and the same value as rounding the exact sum once.
 template <int S>
 __device__ __forceinline__ double recombine(long long hi, long long lo, int er, int fc) {
   if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);  // Inf / NaN operand
-  const double v = fma((double)lo, ldexp(1.0, -kBits * (S + 1)), (double)hi * 0x1p-35);
-  return ldexp(v, er + fc);
+  constexpr int m = LoExp<S>::value > kHiExp ? LoExp<S>::value : kHiExp;
+  constexpr int K = m - kHiExp;                 // lo = 0 when S < 4 (no weight group >= 4)
+  // V as a 128-bit two's complement (vh, vl); |V| < 2^98
+  const unsigned long long a = K ? ((unsigned long long)hi << K) : (unsigned long long)hi;
+  const long long ah = K ? (hi >> (64 - K)) : (hi >> 63);
+  const unsigned long long vl0 = a + (unsigned long long)lo;
+  long long vh = ah + (lo >> 63) + (vl0 < a ? 1 : 0);
+  unsigned long long vl = vl0;
+  const bool neg = vh < 0;
+  if (neg) {
+    vl = 0ull - vl0;
+    vh = ~vh + (vl0 == 0ull ? 1 : 0);
+  }
+  if ((vh | (long long)vl) == 0) return 0.0;
+  const unsigned long long uh = (unsigned long long)vh;
+  const int nb = uh ? 128 - __clzll((long long)uh) : 64 - __clzll((long long)vl);   // bit length, <= 98
+  unsigned long long mant;
+  int e2 = nb - 53;
+  if (nb <= 53) {
+    mant = vl << (53 - nb);
+  } else {
+    const int sh = nb - 53;                                 // 1 .. 45
+    mant = (vl >> sh) | (uh << (64 - sh));
+    const unsigned long long rem = vl & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mant += (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e2;
+    }
+  }
+  const int ex = e2 - m + er + fc;
+  const int be = ex + 52 + 1023;
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
+                                            (mant & 0xFFFFFFFFFFFFFull)));
+  const double v = ldexp((double)mant, ex);   // outside the normal range (not met in practice)
+  return neg ? -v : v;
 }
 
 // One CTA's tile: output column block nb, row tile mb, K split / job zb.
@@ -564,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const _
 // ---------------------------------------------------------------------------
 constexpr int kG16Stages = 5;
 constexpr int kG16Chunk = 15;                       // K blocks per exact chunk (960)
-constexpr int kG16Tile = 144 * kBK * 2;             // 16 S rows x 64 K, BF16 (S = 9: 18 KiB)
+constexpr int kG16Tile = 16 * kMaxS * kBK * 2;      // 16 S rows x 64 K, BF16 (S = 8: 16 KiB)
 constexpr int kG16Stage = 2 * kG16Tile;             // X tile + Y tile
 constexpr int kG16Smem = kG16Stages * kG16Stage + 1024 + 1024;
 
@@ -829,7 +878,7 @@ __global__ void sgram16_reduce_kernel(const longlong2* __restrict__ part, int k,
         };
         const double hd = to_double(hi);
         const double ld = to_double(lo);
-        out[e] = ldexp(fma(ld, ldexp(1.0, -kBits * (S + 1)), hd * 0x1p-35), er + fc);
+        out[e] = ldexp(fma(ld, ldexp(1.0, -LoExp<S>::value), hd * ldexp(1.0, -kHiExp)), er + fc);
       }
     }
   }
@@ -847,6 +896,15 @@ __device__ __forceinline__ int row_exponent(double amax) {
   int e;
   frexp(amax, &e);       // amax = m 2^e, m in [0.5, 1): |a| < 2^e
   return e;
+}
+
+// The same from the bit pattern of a non-negative double (integer work only):
+// a normal value 1.f 2^(x - 1023) has e = x - 1022, a subnormal m 2^-1074
+// with m of L bits has e = L - 1074; zero, Inf and NaN give 0.
+__device__ __forceinline__ int exponent_of_bits(unsigned long long u) {
+  if (u == 0ull || u >= 0x7FF0000000000000ull) return 0;
+  const int x = (int)(u >> 52);
+  return x ? x - 1022 : (64 - __clzll((long long)u)) - 1074;
 }
 
 // |a| as its bit pattern: non-negative doubles order like these integers, and
@@ -868,27 +926,31 @@ __device__ __forceinline__ int int_of_f32(uint32_t u) {
 }
 __device__ __forceinline__ uint32_t bf16_bits_of_int(int v) { return f32_bits_of_small_int(v) >> 16; }
 
-// round(|a| 2^(7S - e)) (half up) for |a| < 2^e: the 7S-bit magnitude the
-// digits represent.
+// round(|a| 2^(kBits (S - 1) + 7 - e)) (half up) for |a| < 2^e: the
+// magnitude the digits represent (63 bits at S = 8).
 template <int S>
 __device__ __forceinline__ unsigned long long magnitude_bits(unsigned long long bits, int e) {
   const int exr = (int)((bits >> 52) & 0x7FF);
   const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (exr ? (1ull << 52) : 0ull);
-  const int sh = (exr ? exr : 1) - 1075 - e + kBits * S;   // |a| 2^(7S - e) = mant 2^sh, sh <= 7S - 53
+  // |a| 2^(kBits (S - 1) + 7 - e) = mant 2^sh; below 2^(kBits (S - 1) + 7) <= 2^63
+  const int sh = (exr ? exr : 1) - 1075 - e + kBits * (S - 1) + 7;
   const int rs = -sh;
   const unsigned long long up = mant << (sh > 0 ? sh : 0);
   const unsigned long long dn = rs > 0 && rs < 64 ? (mant + (1ull << (rs - 1))) >> rs : 0ull;
   return sh >= 0 ? up : dn;
 }
 
-// Balanced digits by one offset: with B = 64 (1 + 128 + ... + 128^(S-2)),
-// the base-128 fields g_s of M + B (most significant first) give
-// M = g_0 128^(S-1) + sum_(s>=1) (g_s - 64) 128^(S-1-s): digit 0 is g_0 in
-// [0, 128], digit s >= 1 is g_s - 64 in [-64, 63].  Carries are the one
-// 64-bit addition; each digit is a shift and a mask.
+// Balanced digits by one offset: with b = 2^kBits (256) and
+// B = (b/2)(1 + b + ... + b^(S-2)), the base-b fields g_s of M + B (most
+// significant first) give M = g_0 b^(S-1) + sum_(s>=1) (g_s - b/2) b^(S-1-s):
+// digit 0 is g_0 in [0, 128] (M <= 2^63), digit s >= 1 is g_s - 128 in
+// [-128, 127].  Every digit has at most 8 significant bits, so it is exact
+// in BF16, and a product of two is at most 2^14.  Carries are the one 64-bit
+// addition; each digit is a shift and a mask.
 template <int S>
 struct DigitBias {
-  static constexpr unsigned long long value = 64ull + 128ull * DigitBias<S - 1>::value;
+  static constexpr unsigned long long value =
+      (1ull << (kBits - 1)) + (1ull << kBits) * DigitBias<S - 1>::value;
 };
 template <>
 struct DigitBias<1> {
@@ -901,7 +963,7 @@ __device__ __forceinline__ unsigned long long biased_magnitude(unsigned long lon
 template <int S>
 __device__ __forceinline__ int bal_digit(unsigned long long Mb, int s) {
   const int sh = kBits * (S - 1 - s);
-  return s == 0 ? (int)(Mb >> sh) : (int)((Mb >> sh) & 127ull) - 64;
+  return s == 0 ? (int)(Mb >> sh) : (int)((Mb >> sh) & ((1ull << kBits) - 1ull)) - (1 << (kBits - 1));
 }
 
 template <int S>
@@ -926,7 +988,7 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
       for (int64_t l = lane; l < n; l += 32) amax = max(amax, abs_bits(A[i * lda + l]));
     for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     const bool finite = amax < kInfBits;
-    const int e = row_exponent(__longlong_as_double((long long)amax));
+    const int e = exponent_of_bits(amax);
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int64_t l0 = (int64_t)lane * 8; l0 < n_pad; l0 += 32 * 8) {
       int dg[8][S];
@@ -1097,7 +1159,7 @@ __global__ void __launch_bounds__(256) slice_cols16_kernel(const double* __restr
   const int tid = threadIdx.x;
   if (tid < 16) {
     const unsigned long long cm = tid < k ? cmax[tid] : 0ull;
-    const int f = row_exponent(__longlong_as_double((long long)cm));
+    const int f = exponent_of_bits(cm);
     fexp[tid] = cm < kInfBits ? f : kNonFinite;
     if (blockIdx.x == 0 && tid < k) colexp[tid] = cm < kInfBits ? f : kNonFinite;
   }
@@ -1146,7 +1208,7 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ Y, in
       for (int l = lane; l < k; l += 32) amax = max(amax, abs_bits(Y[i * k + l]));
     for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     const bool finite = amax < kInfBits;
-    const int e = row_exponent(__longlong_as_double((long long)amax));
+    const int e = exponent_of_bits(amax);
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int c = lane; c < K / 8; c += 32) {
       int dg[8][S];
@@ -1390,7 +1452,7 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __nv
 //              instruction for plane s takes B rows 0 .. 16 (S - s) - 1 and
 //              writes TMEM columns 16 s ..: column 16 w + j then holds the sum
 //              of every pair (s, t) with s + t = w, the pairs of one weight
-//              only, exact in FP32 (at most 16 x 45056 < 2^20).
+//              only, exact in FP32 (at most 8 pairs x 16 x 2^14 = 2^21).
 //   warps 2-5  one thread per tile row: cut the X row into the A operand
 //              (running up to two tiles ahead of the epilogue).
 //   warps 6-13 two threads per tile row (warps w and w + 4 share a TMEM lane
@@ -1409,8 +1471,8 @@ constexpr int kU16Stages = 3;
 constexpr int kU16Tile = 128 * 128;                // 128 rows x 16 FP64: 16 KiB
 constexpr int kU16Stage = 2 * kU16Tile;           // X tile, W tile
 constexpr int kU16ABlock = kBM * kBK * 2;         // 128 rows x 64 K BF16 (four planes)
-constexpr int kU16ABuf = 3 * kU16ABlock;          // planes 0..8
-constexpr int kU16BBytes = 16 * kMaxS * 128;      // 144 rows (t, j) of 128 B; K = l in the first 32 B
+constexpr int kU16ABuf = ((kMaxS + 3) / 4) * kU16ABlock;   // planes 0..7, four per block
+constexpr int kU16BBytes = 16 * kMaxS * 128;      // 128 rows (t, j) of 128 B; K = l in the first 32 B
 constexpr int kU16SliceWarps = 4;                 // one thread per tile row
 constexpr int kU16EpiWarps = 8;                   // two threads per tile row
 constexpr int kU16Threads = 64 + 32 * (kU16SliceWarps + kU16EpiWarps);
@@ -1457,51 +1519,6 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
                  "=r"(r[7])                                                                          \
                : "r"(taddr))
-
-// 2^(er + fc) (hi 2^-35 + lo 2^-7(S+1)) rounded once to nearest-even, like
-// recombine<S>, with 64-bit integer arithmetic up to the bit pattern.
-// |hi| < 2^42, |lo| < 2^50 (the sums of the update's nine weights).
-template <int S>
-__device__ __forceinline__ double recombine_int(long long hi, long long lo, int er, int fc) {
-  if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);
-  constexpr int m = (kBits * (S + 1) > 35) ? kBits * (S + 1) : 35;   // V = hi 2^(m-35) + lo, value V 2^-m
-  constexpr int K = m - 35;
-  // V as a 128-bit two's complement (vh, vl)
-  const unsigned long long a = K ? ((unsigned long long)hi << K) : (unsigned long long)hi;
-  const long long ah = K ? (hi >> (64 - K)) : (hi >> 63);
-  const unsigned long long vl0 = a + (unsigned long long)lo;
-  long long vh = ah + (lo >> 63) + (vl0 < a ? 1 : 0);
-  unsigned long long vl = vl0;
-  const bool neg = vh < 0;
-  if (neg) {
-    vl = 0ull - vl0;
-    vh = ~vh + (vl0 == 0ull ? 1 : 0);
-  }
-  if ((vh | (long long)vl) == 0) return 0.0;
-  const unsigned long long uh = (unsigned long long)vh;   // < 2^14
-  const int nb = uh ? 128 - __clzll((long long)uh) : 64 - __clzll((long long)vl);
-  unsigned long long mant;
-  int e2 = nb - 53;
-  if (nb <= 53) {
-    mant = vl << (53 - nb);
-  } else {
-    const int sh = nb - 53;                                 // 1 .. 25
-    mant = (vl >> sh) | (uh << (64 - sh));
-    const unsigned long long rem = vl & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    mant += (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++e2;
-    }
-  }
-  const int ex = e2 - m + er + fc;
-  const int be = ex + 52 + 1023;
-  if (be >= 1 && be <= 2046)
-    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
-                                            (mant & 0xFFFFFFFFFFFFFull)));
-  const double v = ldexp((double)mant, ex);   // outside the normal range (not met in practice)
-  return neg ? -v : v;
-}
 
 template <int S>
 __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_constant__ CUtensorMap tmX,
@@ -1552,7 +1569,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     if (j < g.k) {
       unsigned long long m = 0ull;
       for (int l = 0; l < g.k; ++l) m = max(m, abs_bits(g.F[(int64_t)j * g.k + l]));
-      fe = m < kInfBits ? row_exponent(__longlong_as_double((long long)m)) : kNonFinite;
+      fe = m < kInfBits ? exponent_of_bits(m) : kNonFinite;
       dj = g.d[j];
       dij = g.dinv[j];
     }
@@ -1649,7 +1666,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         am = max(am, max(b[2 * c] & 0x7FFFFFFFFFFFFFFFull, b[2 * c + 1] & 0x7FFFFFFFFFFFFFFFull));
       }
       const bool fin = am < kInfBits;
-      const int e = fin ? row_exponent(__longlong_as_double((long long)am)) : 0;
+      const int e = fin ? exponent_of_bits(am) : 0;
       unsigned char* ab = abuf0 + a * kU16ABuf;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {   // columns 8 h .. 8 h + 7: one 16-byte chunk per plane
@@ -1712,12 +1729,12 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
           am = max(am, max(abs_bits(v.x), abs_bits(v.y)));
           if ((c >> 2) == half) xv[c & 3] = v;
         }
-        e_row = am < kInfBits ? row_exponent(__longlong_as_double((long long)am)) : kNonFinite;
+        e_row = am < kInfBits ? exponent_of_bits(am) : kNonFinite;
       }
       long long hi[8], lo[8];
       const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * 256 + 8 * half);
       {
-        // weights in pairs (w, w + 1) within each group: C_w 2^7 + C_(w+1) stays below 2^28
+        // weights in pairs (w, w + 1) within each group: C_w 2^8 + C_(w+1) stays below 2^30
 #pragma unroll
         for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
         int pend[8];
@@ -1738,7 +1755,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
             if (first && paired) {
               pend[j] = cw;
             } else {
-              const int pr = first ? cw : pend[j] * 128 + cw;
+              const int pr = first ? cw : pend[j] * (1 << kBits) + cw;
               if (w < 4) hi[j] += (long long)pr << sh;
               else lo[j] += (long long)pr << sh;
             }
@@ -1757,8 +1774,8 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         const double2 x2 = xv[q];
         const double2 wv = *reinterpret_cast<const double2*>(wt + swz128(r, cc));
         const int j0 = 2 * cc, j1 = 2 * cc + 1;
-        const double f0 = recombine_int<S>(hi[2 * q], lo[2 * q], e_row, fexp_s[j0]);
-        const double f1 = recombine_int<S>(hi[2 * q + 1], lo[2 * q + 1], e_row, fexp_s[j1]);
+        const double f0 = recombine<S>(hi[2 * q], lo[2 * q], e_row, fexp_s[j0]);
+        const double f1 = recombine<S>(hi[2 * q + 1], lo[2 * q + 1], e_row, fexp_s[j1]);
         const double r0 = fma(-x2.x, d_s[j0], wv.x), r1 = fma(-x2.y, d_s[j1], wv.y);
         const double n0 = fma(r0, dinv_s[j0], x2.x) - f0, n1 = fma(r1, dinv_s[j1], x2.y) - f1;
         if (live) {
@@ -1869,7 +1886,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
     // column exponents of X (0..15) and W (16..31); non-finite columns give NaN
     const int op = threadIdx.x >> 4, j = threadIdx.x & 15;
     const unsigned long long cm = j < g.k ? (op ? fa.wmax[j] : fa.xmax[j]) : 0ull;
-    const int f = row_exponent(__longlong_as_double((long long)cm));
+    const int f = exponent_of_bits(cm);
     const int fe = cm < kInfBits ? f : kNonFinite;
     fexp_s[op][j] = fe;
     if (blockIdx.x == 0 && j < g.k) (op ? fa.wexp : fa.xexp)[j] = fe;
@@ -2123,8 +2140,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
     case 5: CALL(5); break;             \
     case 6: CALL(6); break;             \
     case 7: CALL(7); break;             \
-    case 8: CALL(8); break;             \
-    default: CALL(9); break;            \
+    default: CALL(8); break;            \
   }
 
 // ---------------------------------------------------------------------------
@@ -2203,7 +2219,7 @@ cudaError_t init_sliced_attributes() {
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sgram16f_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16FSmem);
   EIGREF_SET_ATTR(2) EIGREF_SET_ATTR(3) EIGREF_SET_ATTR(4) EIGREF_SET_ATTR(5) EIGREF_SET_ATTR(6)
-  EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8) EIGREF_SET_ATTR(9)
+  EIGREF_SET_ATTR(7) EIGREF_SET_ATTR(8)
 #undef EIGREF_SET_ATTR
   return e;
 }

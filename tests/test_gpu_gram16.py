@@ -11,7 +11,7 @@ from workloads import configs as C
 
 pytestmark = pytest.mark.gpu
 
-SLICES = 9
+SLICES = 8
 
 
 @pytest.fixture(scope="module")
@@ -31,12 +31,13 @@ def gram(eig, X, P, precision="bf16"):
 
 
 def bound(X, Y):
-    """|error| of entry (i, j) of X^T Y: the truncated digits (n 2^(e_i + f_j)
-    2^-7S per term sum, exponents of the column maxima) plus one FP64 rounding."""
+    """|error| of entry (i, j) of X^T Y: the rounded magnitudes and the
+    truncated digit pairs (n (S + 2) 2^(e_i + f_j) 2^-8S over the sum,
+    exponents of the column maxima) plus one FP64 rounding."""
     n = X.shape[0]
     e = np.frexp(np.abs(X).max(axis=0))[1]
     f = np.frexp(np.abs(Y).max(axis=0))[1]
-    trunc = n * np.ldexp(1.0, e[:, None] + f[None, :] - 7 * SLICES) * 2
+    trunc = n * (SLICES + 2) * np.ldexp(1.0, e[:, None] + f[None, :] - 8 * SLICES)
     return trunc + 2 * U * (np.abs(X).T @ np.abs(Y))
 
 
@@ -94,7 +95,7 @@ def laplace_case(nx, ny, k, seed=4000):
 
 def split_tol(p):
     gaps = np.diff(np.sort(p.lam))
-    return sweep_tol((1 + p.n ** 0.5 * 2.0 ** -(7 * 8) / U) * (p.normA + abs(p.shift)),
+    return sweep_tol((1 + p.n ** 0.5 * 2.0 ** -(8 * SLICES - 8) / U) * (p.normA + abs(p.shift)),
                      gaps.min() if gaps.size else np.inf)
 
 

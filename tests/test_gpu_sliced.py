@@ -11,7 +11,7 @@ from workloads import configs as C
 
 pytestmark = pytest.mark.gpu
 
-SLICE_BITS = 7
+SLICE_BITS = 8
 
 
 @pytest.fixture(scope="module")
@@ -33,13 +33,15 @@ def scale_exponents(M, axis):
 
 
 def slice_bound(A, X, shift, slices):
-    """|W_sliced - W| <= 2^(e_i + f_j) n 2^-(7 S) + 2 u (|A||X| + |shift x|)_ij:
-    each product term loses at most ~2^-7S of its scaled size to the dropped
-    digit pairs, and the FP64 recombination rounds once."""
+    """|W_sliced - W| <= 2^(e_i + f_j) n (S + 2) 2^-(8 S) + 2 u (|A||X| + |shift x|)_ij:
+    each product term loses at most 2 x 2^-8S of its scaled size to the
+    rounding of the two 63-bit magnitudes and (S - 1) x 2^-8S to the dropped
+    digit pairs (|d| <= 128), and the recombination rounds once."""
     n = A.shape[0]
     e = scale_exponents(A, 1)
     f = scale_exponents(X, 0)
-    trunc = np.ldexp(np.ones((n, X.shape[1])), e[:, None] + f[None, :]) * n * 2.0 ** (-SLICE_BITS * slices)
+    trunc = (np.ldexp(np.ones((n, X.shape[1])), e[:, None] + f[None, :]) * n * (slices + 2)
+             * 2.0 ** (-SLICE_BITS * slices))
     return trunc + 2 * U * (np.abs(A) @ np.abs(X) + abs(shift) * np.abs(X))
 
 
@@ -80,7 +82,7 @@ def test_sliced_exact_on_adversarial_signs(eig):
     assert (err / np.abs(hi)).max() < 64 * U
 
 
-@pytest.mark.parametrize("slices", [6, 7, 8, 9])
+@pytest.mark.parametrize("slices", [5, 6, 7, 8])
 def test_slice_count_sets_accuracy(eig, slices):
     p = dense_case(700, 16, seed=31)
     Pb = product(eig, p.A, p.X0, 0.0, "bf16", slices=slices)
@@ -123,21 +125,27 @@ def test_sliced_trajectory_n512(eig):
     assert rel_diff(Xg, Xo) <= 1e-12
 
 
-@pytest.mark.parametrize("slices", [8, 9])
+@pytest.mark.parametrize("slices", [7, 8])
 def test_sliced_converges_like_fp64(eig, slices):
-    """Both forms run to the same residual level; the split form's final angle
-    (double-double, against the construction's eigenvectors) stays within the
-    1e-13 target and close to the FP64 form's."""
+    """Both forms run to the same residual level; with the default 8 planes
+    the split form's final angle (double-double, against the construction's
+    eigenvectors) stays within the 1e-13 target and close to the FP64 form's."""
     p = dense_case(1200, 24, seed=41)
-    Xb, rb = run_gpu(eig, p, max_iters=400, tol=1e-14, stop="residual", slices=slices)
+    # 8 planes keep 63 bits of each operand; 7 keep 55, whose products settle
+    # the residual near 1.2e-14 at this size: that run stops at 4e-14
+    tol = 1e-14 if slices == 8 else 4e-14
+    Xb, rb = run_gpu(eig, p, max_iters=400, tol=tol, stop="residual", slices=slices)
     assert rb["status"] == 0, rb
     sb = dd.sin_angles(Xb, p.Xtrue).max()
     Xf = dev(np.asfortranarray(p.X0))
-    rf = eig.refine_dense(dev(p.A), Xf, norm_a=p.normA, max_iters=400, tol=1e-14, stop="residual")
+    rf = eig.refine_dense(dev(p.A), Xf, norm_a=p.normA, max_iters=400, tol=tol, stop="residual")
     sf = dd.sin_angles(host(Xf), p.Xtrue).max()
     orth = np.abs(dd.orth_error(Xb)).max()
-    assert sb < 1e-13 and orth < 1e-13, (sb, sf, orth)
-    if slices == 9:      # 63 bits: as accurate as the FP64 form
+    # 63 bits meet the 1e-13 target; 55 bits land near 1.4e-13 (one bit more
+    # truncation than seven-bit digits at S = 8 kept: the error tracks the bits)
+    lim = 1e-13 if slices == 8 else 4e-13
+    assert sb < lim and orth < lim, (sb, sf, orth)
+    if slices == 8:      # 63 bits: as accurate as the FP64 form
         assert sb <= 4 * sf + 2e-15 and orth < 1e-14, (sb, sf, orth)
     assert abs(rb["iterations"] - rf["iterations"]) <= 3
 
