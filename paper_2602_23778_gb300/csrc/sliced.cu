@@ -440,12 +440,20 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
     long long hi[kC], lo[kC];
 #pragma unroll
     for (int j = 0; j < kC; ++j) hi[j] = lo[j] = 0;
+    if (MODE == MODE_UPDATE && row < g.m_valid && row >= g.row_begin) {
+      // the row's X and W values the update reads after the drain: into L1
+      // while the MMAs run (128 contiguous bytes each)
+      const int64_t e0 = row * g.k + nb * kBN + half * kC;
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.X + e0));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.W + e0));
+    }
     bool ok = true;
     for (int c = 0; c < NC && ok; ++c) {
       const int buf = NBUF == 2 ? (c & 1) : 0;
-      // one lane waits, the warp follows (the TMEM loads below are warp-collective)
+      // one lane waits, the warp follows (the TMEM loads below are warp-collective);
+      // it sleeps between polls, leaving issue slots to the MMA warp
       int w_ok = 0;
-      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
+      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       __syncwarp();
       if (!ok) break;
@@ -522,19 +530,30 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       }
     }
     if (MODE == MODE_UPDATE) {
-      // column sums over this CTA's rows, in a fixed order
+      // column sums over the warp's 32 rows, in a fixed order, by a butterfly
+      // that halves the values a lane holds at each step (16 + 16 FP64 adds a
+      // lane instead of 5 x 32): lane L ends with column
+      // 8 b4 + 4 b3 + 2 b2 + b1 of its half (b = the bits of L), twice
+      static_assert(kC == 16, "the butterfly below is written for 16 columns");
 #pragma unroll
-      for (int j = 0; j < kC; ++j)
-        for (int o = 16; o > 0; o >>= 1) {
-          sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], o);
-          rq[j] += __shfl_xor_sync(0xffffffffu, rq[j], o);
-        }
-      if (lane == 0)
+      for (int step = 0; step < 4; ++step) {
+        const int o = 16 >> step, m = 8 >> step;     // partner distance, values kept
+        const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int j = 0; j < kC; ++j) {
-          s_colsum[0][lg][half * kC + j] = sq[j];
-          s_colsum[1][lg][half * kC + j] = rq[j];
+        for (int i = 0; i < m; ++i) {
+          const double ks = upper ? sq[m + i] : sq[i], ss = upper ? sq[i] : sq[m + i];
+          const double kr = upper ? rq[m + i] : rq[i], sr = upper ? rq[i] : rq[m + i];
+          sq[i] = ks + __shfl_xor_sync(0xffffffffu, ss, o);
+          rq[i] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
         }
+      }
+      sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
+      rq[0] += __shfl_xor_sync(0xffffffffu, rq[0], 1);
+      if ((lane & 1) == 0) {
+        const int c = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        s_colsum[0][lg][half * kC + c] = sq[0];
+        s_colsum[1][lg][half * kC + c] = rq[0];
+      }
     }
   }
   tc_fence_before();
