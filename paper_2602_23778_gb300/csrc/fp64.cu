@@ -407,9 +407,12 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
         xsq += part_s[grp * w2 + j];
         r2 += part_s[grp * w2 + k + j];
       }
-      for (int i = 0; i < k; ++i) {   // the leading block
-        const double v = b.xn[(int64_t)i * k + j];
-        xsq += v * v;
+      for (int i0 = 0; i0 < k; i0 += 16) {   // the leading block: 16 loads in flight, then in order
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = i0 + u < k ? b.xn[(int64_t)(i0 + u) * k + j] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) xsq += v[u] * v[u];
       }
       xsq_s[j] = xsq;
       r2_s[j] = r2;
