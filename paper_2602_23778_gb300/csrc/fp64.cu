@@ -390,6 +390,7 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
   // consecutive addresses), then the groups are added in order; fixed order,
   // so the result is reproducible
   __shared__ double part_s[1024];
+  __shared__ double top_s[1024];
   {
     const int w2 = 2 * k, groups = (int)blockDim.x / w2;
     if (tid < groups * w2) {
@@ -399,6 +400,19 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
       for (int g = grp; g < b.ugrid; g += groups) acc += b.upart[(int64_t)g * w2 + c];
       part_s[grp * w2 + c] = acc;
     }
+    // the leading block's column sums of squares the same way: thread
+    // (grp, j) takes rows grp, grp + g2, ...
+    const int g2 = (int)blockDim.x / k;
+    if (tid < g2 * k) {
+      const int j = tid % k, grp = tid / k;
+      double acc = 0.0;
+#pragma unroll 4
+      for (int i = grp; i < k; i += g2) {
+        const double v = b.xn[(int64_t)i * k + j];
+        acc += v * v;
+      }
+      top_s[grp * k + j] = acc;
+    }
     __syncthreads();
     if (tid < k) {
       const int j = tid;
@@ -407,13 +421,7 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
         xsq += part_s[grp * w2 + j];
         r2 += part_s[grp * w2 + k + j];
       }
-      for (int i0 = 0; i0 < k; i0 += 16) {   // the leading block: 16 loads in flight, then in order
-        double v[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = i0 + u < k ? b.xn[(int64_t)(i0 + u) * k + j] : 0.0;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) xsq += v[u] * v[u];
-      }
+      for (int grp = 0; grp < g2; ++grp) xsq += top_s[grp * k + j];
       xsq_s[j] = xsq;
       r2_s[j] = r2;
     }

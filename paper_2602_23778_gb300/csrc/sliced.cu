@@ -29,10 +29,8 @@
 // the accumulators of weights s..S-1, which sit side by side in TMEM),
 // warps 2-9 drain TMEM (two per lane group, 16 columns each).  The
 // accumulators are double-buffered (2 x S x 32 FP32 columns <= 512) so
-// draining overlaps the next chunk.  (A rotating layout for S x 32 > 256,
-// sharing two weight groups between consecutive chunks, stays in the code
-// for that case.)  All waits are bounded (globaltimer); on expiry the CTA
-// records a timeout, drains what it started and returns.
+// draining overlaps the next chunk.  All waits are bounded (globaltimer); on
+// expiry the CTA records a timeout, drains what it started and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -75,7 +73,6 @@ constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 102
 
 struct __align__(8) Bars {
   uint64_t a_full[kRA], a_empty[kRA], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
-  uint64_t g01;                      // rotating accumulators: weight groups 0, 1 of a chunk drained
   uint32_t tmem_base;
   int abort;
 };
@@ -279,15 +276,8 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / nsplit);
   const int KB = kb_hi - kb_lo;                      // K blocks of this CTA
   const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
-  constexpr int NBUF = (2 * S * kBN <= 512) ? 2 : 1; // TMEM accumulator sets (double-buffered if they fit)
-  // When two sets do not fit (S = 9: 288 of 512 columns each), even chunks
-  // sit at columns [0, 288) and odd chunks at [224, 512): consecutive chunks
-  // share 64 columns, weight groups 7, 8 of an even chunk and 0, 1 of an odd
-  // one.  The epilogue drains those two groups first (even chunks from w = 8
-  // down, odd chunks from w = 0 up), so the next chunk's MMAs wait for two
-  // groups instead of the whole drain.
-  constexpr bool ROT = NBUF == 1;
-  constexpr uint32_t kOddBase = 512u - (uint32_t)(S * kBN);
+  constexpr int NBUF = 2;                            // TMEM accumulator sets: 2 x S x 32 <= 512 columns
+  static_assert(2 * kMaxS * kBN <= 512, "two accumulator sets must fit in TMEM");
   const CUtensorMap* tB = job ? tmB2 : tmB;
   volatile int* abort_flag = &bars->abort;
 
@@ -305,7 +295,6 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       mbar_init(smem_u32(&bars->acc_empty[i]), kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bars->drain), 1);
-    mbar_init(smem_u32(&bars->g01), kEpiWarps);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -375,11 +364,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         const bool first = (kb % kChunkBlocks) == 0;
         const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
         if (first) {
-          if (ROT) {
-            if (c > 0) ok = mbar_wait(smem_u32(&bars->g01), (uint32_t)((c - 1) & 1), abort_flag);
-          } else {
-            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
-          }
+          ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
           if (!ok) break;
           tc_fence_after();
         }
@@ -388,7 +373,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         if (!ok) break;
         tc_fence_after();
         const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
-        const uint32_t cbase = ROT ? ((c & 1) ? kOddBase : 0u) : (uint32_t)(buf * S * kBN);
+        const uint32_t cbase = (uint32_t)(buf * S * kBN);
         const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -458,23 +443,21 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-      const uint32_t cbase = ROT ? ((c & 1) ? kOddBase : 0u) : (uint32_t)(buf * S * kBN);
-      const bool down = ROT && (c & 1) == 0;            // even chunks drain from w = S-1 down
+      const uint32_t cbase = (uint32_t)(buf * S * kBN);
       const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + cbase + (uint32_t)(half * kC);
       // several weights per round trip to TMEM (two at S >= 8, within the register budget)
       constexpr int GW = S >= 8 ? 2 : 3;
-      static_assert(!ROT || GW >= 2, "the next chunk may only wait for weight groups 0 and 1");
 #pragma unroll
       for (int w0 = 0; w0 < S; w0 += GW) {
         uint32_t r[GW][kC];
 #pragma unroll
         for (int q = 0; q < GW; ++q)
-          if (w0 + q < S) TC_LD16(tw + (uint32_t)((down ? S - 1 - (w0 + q) : w0 + q) * kBN), r[q]);
+          if (w0 + q < S) TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < GW; ++q) {
           if (w0 + q >= S) continue;
-          const int w = down ? S - 1 - (w0 + q) : w0 + q;
+          const int w = w0 + q;
           if (w < 4) {
             const int sh = kBits * (3 - w);
 #pragma unroll
@@ -484,12 +467,6 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
 #pragma unroll
             for (int j = 0; j < kC; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
           }
-        }
-        if (ROT && w0 == 0) {
-          // the two shared weight groups are in registers: the next chunk may overwrite them
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&bars->g01));
         }
       }
       tc_fence_before();
@@ -620,9 +597,8 @@ __global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const _
 // stack into one tile of 16 S rows: the MMA takes A = planes 0..7 of X
 // (128 rows) and B = all S planes of Y (N = 16 S), so one instruction forms
 // every plane pair (s, t) -- each TMEM element holds exactly one pair, at
-// lane 16 s + i, column 16 t + j.  Plane 8 of X (S = 9) is a second M = 128
-// instruction whose rows 16..127 read past the plane and are ignored, paired
-// with plane 0 of Y (N = 16).  One CTA per K split forms both products from
+// lane 16 s + i, column 16 t + j (S < 8: lanes past the planes read zeros or
+// stale rows and are never drained).  One CTA per K split forms both products from
 // one load of each tile.  A single pair's sum stays below 2^24 for 960 K
 // (960 x 128 x 128 < 2^24), so chunks are 15 K blocks long.  The epilogue
 // keeps, per thread, the int64 (hi, lo) sums of its plane row s for 16
@@ -664,7 +640,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
   Bars16* bars = reinterpret_cast<Bars16*>(smem + kG16Stages * kG16Stage);
   constexpr int kRows = 16 * S;                      // rows of a stacked tile
   constexpr int kTileBytes = kRows * kBK * 2;
-  constexpr int kColsJob = kRows + (S == 9 ? 16 : 0);   // TMEM columns per product
+  constexpr int kColsJob = kRows;                    // TMEM columns per product
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int split = blockIdx.x;
   const int kb_lo = (int)((int64_t)g.kb_total * split / g.ksplit);
@@ -733,20 +709,14 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
         if (!ok) break;
         tc_fence_after();
         const uint64_t xd = smem_desc(smem_u32(smem + st * kG16Stage));
-        const uint64_t xd8 = smem_desc(smem_u32(smem + st * kG16Stage + 128 * kBK * 2));   // X rows 128.. (plane 8)
         const uint64_t yd = smem_desc(smem_u32(smem + st * kG16Stage + kG16Tile));
         constexpr uint32_t id1 = idesc_bf16(kBM, kRows);
-        constexpr uint32_t id2 = idesc_bf16(kBM, 16);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t acc = (first && q == 0) ? 0u : 1u;
           const uint64_t o = (uint64_t)(2 * q);    // 16 K per step inside the 128-byte swizzle row
-          tc_mma(tbase, xd + o, xd + o, id1, acc);                                 // G: planes 0..7 x all
-          tc_mma(tbase + kColsJob, xd + o, yd + o, id1, acc);                      // S
-          if (S == 9) {
-            tc_mma(tbase + kRows, xd8 + o, xd + o, id2, acc);                      // G: plane 8 x plane 0
-            tc_mma(tbase + kColsJob + kRows, xd8 + o, yd + o, id2, acc);           // S
-          }
+          tc_mma(tbase, xd + o, xd + o, id1, acc);                                 // G: X planes x X planes
+          tc_mma(tbase + kColsJob, xd + o, yd + o, id1, acc);                      // S: X planes x Y planes
         }
         tc_commit(smem_u32(&bars->empty[st]));
         if (last) tc_commit(smem_u32(&bars->acc_full));
@@ -768,7 +738,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
 #pragma unroll
       for (int j = 0; j < 16; ++j) hi[jb][j] = lo[jb][j] = 0;
     bool ok = true;
-    constexpr int kT0 = (S + 1) / 2;             // half 0 takes planes t < kT0, half 1 the rest (+ plane 8 x 0)
+    constexpr int kT0 = (S + 1) / 2;             // half 0 takes planes t < kT0, half 1 the rest
     for (int c = 0; c < NC && ok; ++c) {
       int w_ok = 0;
       if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full), (uint32_t)(c & 1), abort_flag);
@@ -781,20 +751,12 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
       for (int jb = 0; jb < 2; ++jb) {
 #pragma unroll
         for (int b = 0; b < (S + 2) / 2; ++b) {
-          // which 16 columns: plane t of Y (half 0: t < kT0, half 1: t >= kT0), or
-          // (half 1, S = 9, one slot past the planes) plane 8 of X x plane 0 of Y
+          // which 16 columns: plane t of Y (half 0: t < kT0, half 1: t >= kT0)
           const int t = half == 0 ? b : kT0 + b;
           if (half == 0 && t >= kT0) continue;
-          if (half == 1 && t > S - (S == 9 ? 0 : 1)) continue;
-          int w;
-          uint32_t col;
-          if (t == S) {
-            col = (uint32_t)(jb * kColsJob + kRows);
-            w = r < 16 ? 8 : 99;                 // rows >= 16 of the plane-8 instruction are not X's
-          } else {
-            col = (uint32_t)(jb * kColsJob + 16 * t);
-            w = sp + t;
-          }
+          if (half == 1 && t > S - 1) continue;
+          const uint32_t col = (uint32_t)(jb * kColsJob + 16 * t);
+          const int w = sp + t;
           uint32_t v[16];
           TC_LD16(tl + col, v);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -1918,7 +1880,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
   unsigned char* pl0 = smem + kG16FRaw * 2 * kG16FRawTile;           // [kG16FPlanes][X planes, W planes]
   Bars16F* bars = reinterpret_cast<Bars16F*>(pl0 + kG16FPlanes * kG16Stage);
   constexpr int kRows = 16 * S;                      // rows of a stacked tile
-  constexpr int kColsJob = kRows + (S == 9 ? 16 : 0);   // TMEM columns per product
+  constexpr int kColsJob = kRows;                    // TMEM columns per product
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int split = blockIdx.x;
   const int kb_lo = (int)((int64_t)g.kb_total * split / g.ksplit);
@@ -1992,20 +1954,14 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
         tc_fence_after();
         unsigned char* pt = pl0 + pb * kG16Stage;
         const uint64_t xd = smem_desc(smem_u32(pt));
-        const uint64_t xd8 = smem_desc(smem_u32(pt + 128 * kBK * 2));   // X rows 128.. (plane 8)
         const uint64_t yd = smem_desc(smem_u32(pt + kG16Tile));
         constexpr uint32_t id1 = idesc_bf16(kBM, kRows);
-        constexpr uint32_t id2 = idesc_bf16(kBM, 16);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t acc = (first && q == 0) ? 0u : 1u;
           const uint64_t o = (uint64_t)(2 * q);    // 16 K per step inside the 128-byte swizzle row
-          tc_mma(tbase, xd + o, xd + o, id1, acc);                                 // G: planes 0..7 x all
-          tc_mma(tbase + kColsJob, xd + o, yd + o, id1, acc);                      // S
-          if (S == 9) {
-            tc_mma(tbase + kRows, xd8 + o, xd + o, id2, acc);                      // G: plane 8 x plane 0
-            tc_mma(tbase + kColsJob + kRows, xd8 + o, yd + o, id2, acc);           // S
-          }
+          tc_mma(tbase, xd + o, xd + o, id1, acc);                                 // G: X planes x X planes
+          tc_mma(tbase + kColsJob, xd + o, yd + o, id1, acc);                      // S: X planes x W planes
         }
         tc_commit(smem_u32(&bars->pl_empty[pb]));
         if (last) tc_commit(smem_u32(&bars->acc_full));
@@ -2082,18 +2038,10 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
         tc_fence_after();
         const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(job * kColsJob);
 #pragma unroll
-        for (int t = 0; t <= S - (S == 9 ? 0 : 1); ++t) {
-          // plane t of the right operand, or (S = 9, one slot past the planes)
-          // plane 8 of X x plane 0 of the right operand
-          int w;
-          uint32_t col;
-          if (t == S) {
-            col = (uint32_t)kRows;
-            w = r < 16 ? 8 : 99;                 // rows >= 16 of the plane-8 instruction are not X's
-          } else {
-            col = (uint32_t)(16 * t);
-            w = sp + t;
-          }
+        for (int t = 0; t < S; ++t) {
+          // plane t of the right operand
+          const uint32_t col = (uint32_t)(16 * t);
+          const int w = sp + t;
           uint32_t v[16];
           TC_LD16(tl + col, v);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
