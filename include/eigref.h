@@ -67,7 +67,8 @@ enum eigref_target {
 /* How W = B X and the Gram products are evaluated. */
 enum eigref_precision {
   EIGREF_FP64 = 0,         /* plain FP64 on the CUDA cores */
-  EIGREF_BF16_SLICES = 1,  /* error-free BF16 slices on the tensor cores, FP32 accumulation */
+  EIGREF_BF16_SLICES = 1,  /* error-free digit slices on the tensor cores, FP32 accumulation (8-bit
+                              digits, exact in BF16 and F16; the planes are stored as F16) */
   EIGREF_INT8_SLICES = 2,  /* error-free INT8 slices on the tensor cores, INT32 accumulation (not
                               built: GB300's INT8 tensor rate is far below its BF16 rate) */
   EIGREF_AUTO = 3          /* the faster form the build offers for the call: BF16 slices for dense

@@ -1,5 +1,5 @@
 // Split-precision (error-free sliced) product W = (A - shift I) X on the
-// tcgen05 tensor cores, BF16 operands, FP32 accumulation in TMEM.
+// tcgen05 tensor cores, F16 operands, FP32 accumulation in TMEM.
 //
 // Slicing (Ozaki, Ogita, Oishi and Rump's error-free splitting, BIT 2012):
 // every row i of A is scaled by 2^-e_i (e_i = exponent of the row's largest
@@ -7,7 +7,7 @@
 // written as S balanced base-256 digits, a_il 2^-e_i = sum_s d_s 2^-(8s+7) + r
 // with d_0 in [0, 128], d_s in [-128, 127] (s >= 1), |r| <= 2^-(8S) .  Every
 // column j of X gets the same treatment with its own exponent f_j.  Each
-// digit has at most 8 significant bits, hence is exact in BF16, and a digit
+// digit has at most 8 significant bits, hence is exact in F16, and a digit
 // product (at most 2^14) is exact in FP32.  The product keeps the S(S+1)/2
 // digit pairs with s + t <= S - 1 (triangular truncation):
 //     W_ij = 2^(e_i + f_j) sum_w 2^-(8w+14) C_w,   C_w = sum_{s+t=w} A_s X_t
@@ -32,7 +32,7 @@
 // draining overlaps the next chunk.  All waits are bounded (globaltimer); on
 // expiry the CTA records a timeout, drains what it started and returns.
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -46,12 +46,12 @@ namespace eigref {
 
 namespace sl {
 
-constexpr int kBits = 8;           // bits per digit plane (BF16 holds 8 significant bits)
+constexpr int kBits = 8;           // bits per digit plane (a digit has at most 8 significant bits)
 constexpr int kMaxS = 8;           // digit planes per operand (at most)
 constexpr int kDefaultS = 8;       // default digit planes (63 bits: FP64-level accuracy at n = 16384)
 constexpr int kBM = 128;           // rows of W per CTA
 constexpr int kBN = 32;            // columns of W per CTA
-constexpr int kBK = 64;            // K per pipeline stage (128 bytes of BF16)
+constexpr int kBK = 64;            // K per pipeline stage (128 bytes of F16)
 constexpr int kChunkBlocks = 2;    // K blocks per exact accumulation chunk (128: 8 pairs x 2^14 x 128 <= 2^24)
 constexpr int kRA = 9;             // A ring stages (a K block of planes and one more)
 // Digit weights: a = 2^e sum_s d_s 2^-(kBits s + 7), so the pairs of weight
@@ -167,9 +167,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// kind::f16 instruction descriptor: D = F32, A = B = F16, both K-major.
+// (Every digit is an integer of at most 8 significant bits, exact in F16.)
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 #define TC_LD16(taddr, r)                                                                                   \
@@ -388,13 +389,13 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           const int N = kBN * (S - s);
           const int N1 = N < 256 ? N : 256;
           const uint32_t dt = tbase + cbase + (uint32_t)(s * kBN);
-          tc_mma(dt, ad, xd, idesc_bf16(kBM, N1), s == 0 ? acc0 : 1u);
-          tc_mma(dt, ad + 2, xd + 2, idesc_bf16(kBM, N1), 1u);
-          tc_mma(dt, ad + 4, xd + 4, idesc_bf16(kBM, N1), 1u);
-          tc_mma(dt, ad + 6, xd + 6, idesc_bf16(kBM, N1), 1u);
+          tc_mma(dt, ad, xd, idesc_f16(kBM, N1), s == 0 ? acc0 : 1u);
+          tc_mma(dt, ad + 2, xd + 2, idesc_f16(kBM, N1), 1u);
+          tc_mma(dt, ad + 4, xd + 4, idesc_f16(kBM, N1), 1u);
+          tc_mma(dt, ad + 6, xd + 6, idesc_f16(kBM, N1), 1u);
           if (N > 256) {
             const uint64_t xd2 = xd + (uint64_t)((256 * kBK * 2) >> 4);
-            const uint32_t id2 = idesc_bf16(kBM, N - 256);
+            const uint32_t id2 = idesc_f16(kBM, N - 256);
             tc_mma(dt + 256u, ad, xd2, id2, s == 0 ? acc0 : 1u);
             tc_mma(dt + 256u, ad + 2, xd2 + 2, id2, 1u);
             tc_mma(dt + 256u, ad + 4, xd2 + 4, id2, 1u);
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const _
 // ---------------------------------------------------------------------------
 constexpr int kG16Stages = 5;
 constexpr int kG16Chunk = 15;                       // K blocks per exact chunk (960)
-constexpr int kG16Tile = 16 * kMaxS * kBK * 2;      // 16 S rows x 64 K, BF16 (S = 8: 16 KiB)
+constexpr int kG16Tile = 16 * kMaxS * kBK * 2;      // 16 S rows x 64 K, F16 (S = 8: 16 KiB)
 constexpr int kG16Stage = 2 * kG16Tile;             // X tile + Y tile
 constexpr int kG16Smem = kG16Stages * kG16Stage + 1024 + 1024;
 
@@ -710,7 +711,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
         tc_fence_after();
         const uint64_t xd = smem_desc(smem_u32(smem + st * kG16Stage));
         const uint64_t yd = smem_desc(smem_u32(smem + st * kG16Stage + kG16Tile));
-        constexpr uint32_t id1 = idesc_bf16(kBM, kRows);
+        constexpr uint32_t id1 = idesc_f16(kBM, kRows);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t acc = (first && q == 0) ? 0u : 1u;
@@ -868,8 +869,8 @@ __global__ void sgram16_reduce_kernel(const longlong2* __restrict__ part, int k,
 // ---------------------------------------------------------------------------
 // Digit planes.  GB300 runs FP64 at ~1/64 of FP32, so the digits are cut
 // with integer arithmetic: |a| 2^-e (< 1) is rounded once to an integer M of
-// 7S bits (the same information the S digits keep), then M is split into
-// balanced base-128 digits, the first in [0, 128], the others in [-64, 63];
+// 8S - 1 bits (the same information the S digits keep), then M is split into
+// balanced base-256 digits, the first in [0, 128], the others in [-128, 127];
 // the sign of a is applied to all of them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int row_exponent(double amax) {
@@ -896,16 +897,11 @@ __device__ __forceinline__ unsigned long long abs_bits(double a) {
 }
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
-// A small integer (|v| <= 256) as FP32 bits with the low 16 bits zero (so
-// the upper half is its BF16), and an integer-valued FP32 (|x| < 2^22) as an
-// int: one add at the 1.5 x 2^23 offset each, no conversion instructions.
-__device__ __forceinline__ uint32_t f32_bits_of_small_int(int v) {
-  return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f);
-}
+// An integer-valued FP32 (|x| < 2^22) as an int: one add at the 1.5 x 2^23
+// offset, no conversion instruction.
 __device__ __forceinline__ int int_of_f32(uint32_t u) {
   return __float_as_int(__uint_as_float(u) + 12582912.0f) - 0x4B400000;
 }
-__device__ __forceinline__ uint32_t bf16_bits_of_int(int v) { return f32_bits_of_small_int(v) >> 16; }
 
 // round(|a| 2^(kBits (S - 1) + 7 - e)) (half up) for |a| < 2^e: the
 // magnitude the digits represent (63 bits at S = 8).
@@ -926,7 +922,7 @@ __device__ __forceinline__ unsigned long long magnitude_bits(unsigned long long 
 // significant first) give M = g_0 b^(S-1) + sum_(s>=1) (g_s - b/2) b^(S-1-s):
 // digit 0 is g_0 in [0, 128] (M <= 2^63), digit s >= 1 is g_s - 128 in
 // [-128, 127].  Every digit has at most 8 significant bits, so it is exact
-// in BF16, and a product of two is at most 2^14.  Carries are the one 64-bit
+// in F16 (and in BF16), and a product of two is at most 2^14.  Carries are the one 64-bit
 // addition; each digit is a shift and a mask.
 template <int S>
 struct DigitBias {
@@ -956,9 +952,47 @@ __device__ __forceinline__ void digits_of(double a, int e, int* d) {
   for (int s = 0; s < S; ++s) d[s] = sg * bal_digit<S>(Mb, s);
 }
 
+// Eight values' S digit planes as F16, one 16-byte chunk (eight values) per
+// plane: out[s] holds digit s of values 0..7, all scaled by 2^-e.  The
+// digits come straight from the bytes of the biased magnitudes: for a pair
+// of values, one byte permute gathers byte s of both, a mask and an offset
+// make them the F16 numbers 1024 + g, and one F16 fused multiply-add with
+// (+-1, -+1152) (-+1024 for the first digit, which has no offset) gives the
+// signed digits exactly.
+template <int S>
+__device__ __forceinline__ void planes_of8(const unsigned long long (&bits)[8], int e, uint4 (&out)[S]) {
+  unsigned long long M[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) M[q] = biased_magnitude<S>(bits[q], e);
+  uint32_t sg[4], ctop[4], clow[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool n0 = (long long)bits[2 * q] < 0, n1 = (long long)bits[2 * q + 1] < 0;
+    sg[q] = (n0 ? 0xBC00u : 0x3C00u) | ((n1 ? 0xBC00u : 0x3C00u) << 16);     // +-1
+    ctop[q] = (n0 ? 0x6400u : 0xE400u) | ((n1 ? 0x6400u : 0xE400u) << 16);   // -+1024
+    clow[q] = (n0 ? 0x6480u : 0xE480u) | ((n1 ? 0x6480u : 0xE480u) << 16);   // -+1152
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int bi = S - 1 - s;                          // byte of the magnitude holding digit s
+    const uint32_t sel = (uint32_t)(bi & 3) | ((uint32_t)((bi & 3) + 4) << 8);
+    uint32_t w4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t a = bi < 4 ? (uint32_t)M[2 * q] : (uint32_t)(M[2 * q] >> 32);
+      const uint32_t b = bi < 4 ? (uint32_t)M[2 * q + 1] : (uint32_t)(M[2 * q + 1] >> 32);
+      const uint32_t w = (__byte_perm(a, b, sel) & 0x00FF00FFu) | 0x64006400u;
+      const __half2 h = __hfma2(*reinterpret_cast<const __half2*>(&w), *reinterpret_cast<const __half2*>(&sg[q]),
+                                *reinterpret_cast<const __half2*>(s == 0 ? &ctop[q] : &clow[q]));
+      w4[q] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    out[s] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+  }
+}
+
 template <int S>
 __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t lda, int n_pad,
-                               __nv_bfloat16* __restrict__ As, int* __restrict__ rowexp) {
+                               __half* __restrict__ As, int* __restrict__ rowexp) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -972,20 +1006,16 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
     const int e = exponent_of_bits(amax);
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int64_t l0 = (int64_t)lane * 8; l0 < n_pad; l0 += 32 * 8) {
-      int dg[8][S];
+      unsigned long long b[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int64_t l = l0 + q;
-        const double v = (i < n && l < n && finite) ? A[i * lda + l] : 0.0;
-        digits_of<S>(v, e, dg[q]);
+        b[q] = (i < n && l < n && finite) ? (unsigned long long)__double_as_longlong(A[i * lda + l]) : 0ull;
       }
+      uint4 pl[S];
+      planes_of8<S>(b, e, pl);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        __align__(16) __nv_bfloat16 d[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][s]);
-        *reinterpret_cast<uint4*>(As + s * plane + i * n_pad + l0) = *reinterpret_cast<uint4*>(d);
-      }
+      for (int s = 0; s < S; ++s) *reinterpret_cast<uint4*>(As + s * plane + i * n_pad + l0) = pl[s];
     }
   }
 }
@@ -1072,13 +1102,13 @@ __global__ void colmax_kernel(const double* __restrict__ Y, int64_t rows, int k,
   colmax_body(Y, rows, k, rs, cs, cmax, blockIdx.x, gridDim.x);
 }
 
-// Column digit planes: planes[(t kp + j) K + l] (BF16) for column j of the
+// Column digit planes: planes[(t kp + j) K + l] (F16) for column j of the
 // strided operand, scaled by its column exponent.  A CTA takes 64 rows x 32
-// columns through shared memory, so the BF16 writes are contiguous.
+// columns through shared memory, so the plane writes are contiguous.
 template <int S>
 __device__ __forceinline__ void slice_cols_body(const double* __restrict__ Y, int64_t rows, int k, int64_t rs,
                                                 int64_t cs, int K, int kp, const unsigned long long* __restrict__ cmax,
-                                                __nv_bfloat16* __restrict__ planes, int* __restrict__ colexp, int bx,
+                                                __half* __restrict__ planes, int* __restrict__ colexp, int bx,
                                                 int cb) {
   __shared__ double tile[64][33];
   __shared__ int fexp[32];
@@ -1100,17 +1130,16 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ Y, in
   __syncthreads();
   // thread -> (jj, 8 consecutive rows); writes 16 bytes per plane
   const int jj = tid >> 3, r0 = (tid & 7) * 8;
-  int dg[8][S];
+  unsigned long long b[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) digits_of<S>(tile[r0 + q][jj], fexp[jj], dg[q]);
+  for (int q = 0; q < 8; ++q) b[q] = (unsigned long long)__double_as_longlong(tile[r0 + q][jj]);
+  uint4 pl[S];
+  planes_of8<S>(b, fexp[jj], pl);
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    __align__(16) __nv_bfloat16 d[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][t]);
     const int64_t rowid = (int64_t)t * kp + cb * 32 + jj;
     if (cb * 32 + jj < kp)   // kp = 16: half the block's columns are padding
-      *reinterpret_cast<uint4*>(planes + rowid * K + l0 + r0) = *reinterpret_cast<uint4*>(d);
+      *reinterpret_cast<uint4*>(planes + rowid * K + l0 + r0) = pl[t];
   }
 }
 
@@ -1118,7 +1147,7 @@ template <int S>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int k, int64_t rs,
                                                          int64_t cs, int K, int kp,
                                                          const unsigned long long* __restrict__ cmax,
-                                                         __nv_bfloat16* __restrict__ planes, int* __restrict__ colexp,
+                                                         __half* __restrict__ planes, int* __restrict__ colexp,
                                                          const Control* ctl) {
   if (ctl && ctl->done) return;
   slice_cols_body<S>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, blockIdx.x, blockIdx.y);
@@ -1131,7 +1160,7 @@ template <int S>
 __global__ void __launch_bounds__(256) slice_cols16_kernel(const double* __restrict__ Y, int64_t rows, int k,
                                                            int64_t rs, int64_t cs, int K,
                                                            const unsigned long long* __restrict__ cmax,
-                                                           __nv_bfloat16* __restrict__ planes,
+                                                           __half* __restrict__ planes,
                                                            int* __restrict__ colexp, const Control* ctl) {
   if (ctl && ctl->done) return;
   __shared__ double tile[128][17];
@@ -1150,36 +1179,24 @@ __global__ void __launch_bounds__(256) slice_cols16_kernel(const double* __restr
     tile[rr][jj] = (l < rows && jj < k) ? Y[l * rs + jj * cs] : 0.0;
   }
   __syncthreads();
-  // balanced digits of the rounded 7S-bit magnitudes, the sign flipped into
-  // each BF16's sign bit
+  // the digit planes of eight rows of column jj
   const int jj = tid >> 4, r0 = (tid & 15) * 8;
   const int fe = fexp[jj];
-  unsigned long long M[8];
-  uint32_t sgn[4];
+  unsigned long long b[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(tile[r0 + q][jj]);
-    M[q] = biased_magnitude<S>(fe != kNonFinite ? b : 0ull, fe != kNonFinite ? fe : 0);
-    if (q & 1) sgn[q >> 1] |= (uint32_t)(b >> 63) << 31;
-    else sgn[q >> 1] = (uint32_t)(b >> 63) << 15;
-  }
+  for (int q = 0; q < 8; ++q)
+    b[q] = fe != kNonFinite ? (unsigned long long)__double_as_longlong(tile[r0 + q][jj]) : 0ull;
+  uint4 pl[S];
+  planes_of8<S>(b, fe != kNonFinite ? fe : 0, pl);
 #pragma unroll
-  for (int t = 0; t < S; ++t) {
-    uint32_t w4[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], t)),
-                          f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], t)), 0x7632) ^
-              sgn[q];
-    *reinterpret_cast<uint4*>(planes + ((int64_t)t * 16 + jj) * K + l0 + r0) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-  }
+  for (int t = 0; t < S; ++t) *reinterpret_cast<uint4*>(planes + ((int64_t)t * 16 + jj) * K + l0 + r0) = pl[t];
 }
 
 // Row digit planes of a row-major n x k operand: planes[(s n_pad + i) K + l],
 // one exponent per row.  One warp per row; lane c takes elements 8c..8c+7.
 template <int S>
 __device__ __forceinline__ void slice_rows_body(const double* __restrict__ Y, int64_t n, int k, int n_pad, int K,
-                                                __nv_bfloat16* __restrict__ planes, int* __restrict__ rowexp,
+                                                __half* __restrict__ planes, int* __restrict__ rowexp,
                                                 int64_t wid, int64_t nw) {
   const int lane = threadIdx.x & 31;
   const int64_t plane = (int64_t)n_pad * K;
@@ -1192,27 +1209,23 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ Y, in
     const int e = exponent_of_bits(amax);
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
     for (int c = lane; c < K / 8; c += 32) {
-      int dg[8][S];
+      unsigned long long b[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int l = c * 8 + q;
-        const double v = (i < n && l < k && finite) ? Y[i * k + l] : 0.0;
-        digits_of<S>(v, e, dg[q]);
+        b[q] = (i < n && l < k && finite) ? (unsigned long long)__double_as_longlong(Y[i * k + l]) : 0ull;
       }
+      uint4 pl[S];
+      planes_of8<S>(b, e, pl);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        __align__(16) __nv_bfloat16 d[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) d[q] = __int2bfloat16_rn(dg[q][s]);
-        *reinterpret_cast<uint4*>(planes + s * plane + i * K + c * 8) = *reinterpret_cast<uint4*>(d);
-      }
+      for (int s = 0; s < S; ++s) *reinterpret_cast<uint4*>(planes + s * plane + i * K + c * 8) = pl[s];
     }
   }
 }
 
 template <int S>
 __global__ void slice_rows_kernel(const double* __restrict__ Y, int64_t n, int k, int n_pad, int K,
-                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ rowexp, const Control* ctl) {
+                                  __half* __restrict__ planes, int* __restrict__ rowexp, const Control* ctl) {
   if (ctl && ctl->done) return;
   slice_rows_body<S>(Y, n, k, n_pad, K, planes, rowexp, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
                      ((int64_t)gridDim.x * blockDim.x) >> 5);
@@ -1230,20 +1243,20 @@ __global__ void zero_cmax_grouped_kernel(const GroupItem* __restrict__ items) {
 // Operand OP of problem `it` in sweep parity `parity`: rows, row / column strides.
 __device__ __forceinline__ const double* grouped_operand(const GroupItem& it, int parity, int op, int64_t* rows,
                                                         int64_t* rs, int64_t* cs, unsigned long long** cmax,
-                                                        __nv_bfloat16** planes, int** colexp, int* K) {
+                                                        __half** planes, int** colexp, int* K) {
   const SweepBufs& b = it.b[parity];
   if (op == OPD_FCOLS) {   // F is k x k column-major: element (l, j) at F[l + j k]
     *rows = it.k; *rs = 1; *cs = it.k; *cmax = it.f_cmax;
-    *planes = static_cast<__nv_bfloat16*>(it.f_planes); *colexp = it.f_colexp; *K = it.kr;
+    *planes = static_cast<__half*>(it.f_planes); *colexp = it.f_colexp; *K = it.kr;
     return b.f;
   }
   *rows = it.n; *rs = it.k; *cs = 1;
   *K = it.n_pad;
   if (op == OPD_XCOLS) {
-    *cmax = it.x_cmax; *planes = static_cast<__nv_bfloat16*>(it.x_planes); *colexp = it.x_colexp;
+    *cmax = it.x_cmax; *planes = static_cast<__half*>(it.x_planes); *colexp = it.x_colexp;
     return b.x;
   }
-  *cmax = it.p_cmax; *planes = static_cast<__nv_bfloat16*>(it.p_planes); *colexp = it.p_colexp;
+  *cmax = it.p_cmax; *planes = static_cast<__half*>(it.p_planes); *colexp = it.p_colexp;
   return b.p;
 }
 
@@ -1253,7 +1266,7 @@ __global__ void colmax_grouped_kernel(const GroupItem* __restrict__ items, int p
   if (it.b[0].ctl->done) return;
   int64_t rows, rs, cs;
   unsigned long long* cmax;
-  __nv_bfloat16* planes;
+  __half* planes;
   int* colexp;
   int K;
   const double* Y = grouped_operand(it, parity, OP, &rows, &rs, &cs, &cmax, &planes, &colexp, &K);
@@ -1265,7 +1278,7 @@ __global__ void __launch_bounds__(256) slice_cols_grouped_kernel(const GroupItem
   const GroupItem& it = items[blockIdx.z];
   int64_t rows, rs, cs;
   unsigned long long* cmax;
-  __nv_bfloat16* planes;
+  __half* planes;
   int* colexp;
   int K;
   const double* Y = grouped_operand(it, parity, OP, &rows, &rs, &cs, &cmax, &planes, &colexp, &K);
@@ -1277,7 +1290,7 @@ template <int S>
 __global__ void slice_rows_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
   const GroupItem& it = items[blockIdx.z];
   if (it.b[0].ctl->done) return;
-  slice_rows_body<S>(it.b[parity].x, it.n, it.k, it.n_pad, it.kr, static_cast<__nv_bfloat16*>(it.xr_planes),
+  slice_rows_body<S>(it.b[parity].x, it.n, it.k, it.n_pad, it.kr, static_cast<__half*>(it.xr_planes),
                      it.xr_rowexp, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
                      ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
@@ -1384,14 +1397,14 @@ __global__ void sgram_reduce_grouped_kernel(const GroupItem* __restrict__ items)
 }
 
 template <int S>
-void launch_slice_a(const double* A, int64_t n, int64_t lda, int n_pad, __nv_bfloat16* As, int* rowexp,
+void launch_slice_a(const double* A, int64_t n, int64_t lda, int n_pad, __half* As, int* rowexp,
                     cudaStream_t s) {
   slice_a_kernel<S><<<152 * 8, 256, 0, s>>>(A, n, lda, n_pad, As, rowexp);
 }
 
 template <int S>
 void launch_slice_cols(const double* Y, int64_t rows, int k, int64_t rs, int64_t cs, int K, int kp,
-                       unsigned long long* cmax, __nv_bfloat16* planes, int* colexp, const Control* ctl,
+                       unsigned long long* cmax, __half* planes, int* colexp, const Control* ctl,
                        cudaStream_t s) {
   cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
   if (rs == k && cs == 1) {
@@ -1405,7 +1418,7 @@ void launch_slice_cols(const double* Y, int64_t rows, int k, int64_t rs, int64_t
 }
 
 template <int S>
-void launch_slice_cols16(const double* Y, int64_t rows, int k, int K, unsigned long long* cmax, __nv_bfloat16* planes,
+void launch_slice_cols16(const double* Y, int64_t rows, int k, int K, unsigned long long* cmax, __half* planes,
                          int* colexp, const Control* ctl, cudaStream_t s) {
   cudaMemsetAsync(cmax, 0, (size_t)k * 8, s);
   launch_colmax_rowmajor(Y, rows, k, cmax, ctl, s);
@@ -1413,7 +1426,7 @@ void launch_slice_cols16(const double* Y, int64_t rows, int k, int K, unsigned l
 }
 
 template <int S>
-void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __nv_bfloat16* planes, int* rowexp,
+void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __half* planes, int* rowexp,
                        const Control* ctl, cudaStream_t s) {
   slice_rows_kernel<S><<<152 * 8, 256, 0, s>>>(Y, n, k, n_pad, K, planes, rowexp, ctl);
 }
@@ -1451,7 +1464,7 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __nv
 constexpr int kU16Stages = 3;
 constexpr int kU16Tile = 128 * 128;                // 128 rows x 16 FP64: 16 KiB
 constexpr int kU16Stage = 2 * kU16Tile;           // X tile, W tile
-constexpr int kU16ABlock = kBM * kBK * 2;         // 128 rows x 64 K BF16 (four planes)
+constexpr int kU16ABlock = kBM * kBK * 2;         // 128 rows x 64 K F16 (four planes)
 constexpr int kU16ABuf = ((kMaxS + 3) / 4) * kU16ABlock;   // planes 0..7, four per block
 constexpr int kU16BBytes = 16 * kMaxS * 128;      // 128 rows (t, j) of 128 B; K = l in the first 32 B
 constexpr int kU16SliceWarps = 4;                 // one thread per tile row
@@ -1600,7 +1613,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const uint64_t ad = smem_desc(ab + (uint32_t)((s >> 2) * kU16ABlock)) + (uint64_t)(2 * (s & 3));
-          tc_mma(tbase + (uint32_t)(a * 256 + 16 * s), ad, bd, idesc_bf16(kBM, 16 * (S - s)), s == 0 ? 0u : 1u);
+          tc_mma(tbase + (uint32_t)(a * 256 + 16 * s), ad, bd, idesc_f16(kBM, 16 * (S - s)), s == 0 ? 0u : 1u);
         }
         tc_commit(smem_u32(&bars->a_empty[a]));
         tc_commit(smem_u32(&bars->acc_full[a]));
@@ -1623,7 +1636,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
 #pragma unroll
       for (int t = 0; t < S; ++t)
         *reinterpret_cast<uint16_t*>(bop + swz128(16 * t + j, l >> 3) + (l & 7) * 2) =
-            (uint16_t)bf16_bits_of_int(dg[t]);
+            __half_as_ushort(__int2half_rn(dg[t]));
     }
     bool ok = true;
     for (int i = 0; i < cnt && ok; ++i) {
@@ -1651,24 +1664,14 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       unsigned char* ab = abuf0 + a * kU16ABuf;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {   // columns 8 h .. 8 h + 7: one 16-byte chunk per plane
-        unsigned long long M[8];
-        uint32_t sgn[4];
+        unsigned long long bh[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) M[q] = biased_magnitude<S>(fin ? b[8 * h + q] : 0ull, e);
+        for (int q = 0; q < 8; ++q) bh[q] = fin ? b[8 * h + q] : 0ull;
+        uint4 pl[S];
+        planes_of8<S>(bh, e, pl);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          sgn[q] = (uint32_t)(b[8 * h + 2 * q] >> 63) << 15 | (uint32_t)(b[8 * h + 2 * q + 1] >> 63) << 31;
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-          uint32_t w4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], s)),
-                                f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], s)), 0x7632) ^
-                    sgn[q];
-          *reinterpret_cast<uint4*>(ab + (s >> 2) * kU16ABlock + swz128(r, 2 * (s & 3) + h)) =
-              make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        }
+        for (int s = 0; s < S; ++s)
+          *reinterpret_cast<uint4*>(ab + (s >> 2) * kU16ABlock + swz128(r, 2 * (s & 3) + h)) = pl[s];
       }
       fence_async_smem();
       __syncwarp();
@@ -1955,7 +1958,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
         unsigned char* pt = pl0 + pb * kG16Stage;
         const uint64_t xd = smem_desc(smem_u32(pt));
         const uint64_t yd = smem_desc(smem_u32(pt + kG16Tile));
-        constexpr uint32_t id1 = idesc_bf16(kBM, kRows);
+        constexpr uint32_t id1 = idesc_f16(kBM, kRows);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t acc = (first && q == 0) ? 0u : 1u;
@@ -1998,28 +2001,19 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), abort_flag);   // each lane acquires
       {
         const unsigned char* rt = raw0 + (st * 2 + op) * kG16FRawTile;
-        unsigned long long M[8];
-        uint32_t sgn[4];
+        unsigned long long b[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int i = 8 * sig + q;
-          const unsigned long long b =
-              (unsigned long long)__double_as_longlong(*reinterpret_cast<const double*>(rt + swz128(i, sj >> 1) + (sj & 1) * 8));
-          M[q] = biased_magnitude<S>(fe != kNonFinite ? b : 0ull, fe != kNonFinite ? fe : 0);
-          if (q & 1) sgn[q >> 1] |= (uint32_t)(b >> 63) << 31;
-          else sgn[q >> 1] = (uint32_t)(b >> 63) << 15;
+          b[q] = fe != kNonFinite ? (unsigned long long)__double_as_longlong(
+                                        *reinterpret_cast<const double*>(rt + swz128(i, sj >> 1) + (sj & 1) * 8))
+                                  : 0ull;
         }
+        uint4 pl[S];
+        planes_of8<S>(b, fe != kNonFinite ? fe : 0, pl);
         unsigned char* pt = pl0 + pb * kG16Stage + op * kG16Tile;
 #pragma unroll
-        for (int t = 0; t < S; ++t) {
-          uint32_t w4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            w4[q] = __byte_perm(f32_bits_of_small_int(bal_digit<S>(M[2 * q], t)),
-                                f32_bits_of_small_int(bal_digit<S>(M[2 * q + 1], t)), 0x7632) ^
-                    sgn[q];
-          *reinterpret_cast<uint4*>(pt + swz128(16 * t + sj, sig)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        }
+        for (int t = 0; t < S; ++t) *reinterpret_cast<uint4*>(pt + swz128(16 * t + sj, sig)) = pl[t];
       }
       fence_async_smem();
       __syncwarp();
@@ -2137,7 +2131,7 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
   cuuint64_t strides[1] = {inner * 2};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -2320,7 +2314,7 @@ void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpr
 
 int SlicedA::prepare(cudaStream_t s) {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
-  auto* ap = reinterpret_cast<__nv_bfloat16*>(ws_ + L.a_planes);
+  auto* ap = reinterpret_cast<__half*>(ws_ + L.a_planes);
   // B-side and row planes: zero once, so padding rows and columns stay zero
   if (cudaMemsetAsync(ws_ + L.x_planes, 0, L.xr_rowexp - L.x_planes, s) != cudaSuccess ||
       cudaMemsetAsync(ws_ + L.f_planes, 0, L.f_colexp - L.f_planes, s) != cudaSuccess ||
@@ -2492,7 +2486,7 @@ void SlicedA::fill_group_item(GroupItem* it) const {
 int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
                      cudaEvent_t ev1, unsigned ev_flags) {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
-  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  auto* xp = reinterpret_cast<__half*>(ws_ + L.x_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   int* colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
 #define EIGREF_CALL_SLICE_X(S_) \
@@ -2517,7 +2511,7 @@ int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, con
   const int64_t total = n_ * k_;
   const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   // T = A X: X's column planes in the X slot (kept for gram())
-  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
+  auto* xp = reinterpret_cast<__half*>(ws_ + L.x_planes);
   auto* xmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
 #define EIGREF_CALL_SLICE_X2(S_) \
@@ -2529,7 +2523,7 @@ int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, con
   launch_task(slices_, sl::MODE_PRODUCT, t1, s);
   if (psplit_ > 1) launch_product_reduce(slices_, t1, psplit_, X, T, total, 0.0, ctl, s);
   // P = A T - alpha X: T's column planes in the W slot (gram() re-slices W there)
-  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* pp = reinterpret_cast<__half*>(ws_ + L.p_planes);
   auto* pmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
 #define EIGREF_CALL_SLICE_T(S_) \
@@ -2545,7 +2539,7 @@ int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, con
 
 int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s) {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
-  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* pp = reinterpret_cast<__half*>(ws_ + L.p_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
 #define EIGREF_CALL_SLICE_P(S_) \
@@ -2571,8 +2565,8 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
 int SlicedA::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
                     double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
-  auto* xr = reinterpret_cast<__nv_bfloat16*>(ws_ + L.xr_planes);
-  auto* fp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.f_planes);
+  auto* xr = reinterpret_cast<__half*>(ws_ + L.xr_planes);
+  auto* fp = reinterpret_cast<__half*>(ws_ + L.f_planes);
   int* xrexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
   int* fexp = reinterpret_cast<int*>(ws_ + L.f_colexp);
   auto* fmax_ = reinterpret_cast<unsigned long long*>(ws_ + L.f_cmax);
@@ -2844,8 +2838,8 @@ int SlicedGram::gram(const double* X, const double* P, double* out, const Contro
     if (nl > 0) return nl + 2;
   }
   const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
-  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
-  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* xp = reinterpret_cast<__half*>(ws_ + L.x_planes);
+  auto* pp = reinterpret_cast<__half*>(ws_ + L.p_planes);
   auto* xmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   auto* pmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
@@ -2895,8 +2889,8 @@ int SlicedGram::gram_ready(const double* X, const double* P, double* out, const 
     }
   }
   const Gram16Layout L = gram16_layout(n_pad_, slices_, ksplit_, k_);
-  auto* xp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.x_planes);
-  auto* pp = reinterpret_cast<__nv_bfloat16*>(ws_ + L.p_planes);
+  auto* xp = reinterpret_cast<__half*>(ws_ + L.x_planes);
+  auto* pp = reinterpret_cast<__half*>(ws_ + L.p_planes);
   int* xexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
   const int K = (int)n_pad_;
