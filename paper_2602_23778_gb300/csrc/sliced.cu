@@ -54,6 +54,7 @@ constexpr int kBN = 32;            // columns of W per CTA
 constexpr int kBK = 64;            // K per pipeline stage (128 bytes of F16)
 constexpr int kChunkBlocks = 2;    // K blocks per exact accumulation chunk (128: 8 pairs x 2^14 x 128 <= 2^24)
 constexpr int kRA = 9;             // A ring stages (a K block of planes and one more)
+constexpr int kRAProduct = 10;     // the product's ring: one stage deeper (its epilogue keeps no sums in shared memory)
 // Digit weights: a = 2^e sum_s d_s 2^-(kBits s + 7), so the pairs of weight
 // group w = s + t carry 2^-(kBits w + 14); the epilogue keeps
 // hi = sum_(w<4) C_w 2^(kBits (3 - w)) and lo = sum_(w>=4) C_w 2^(kBits (S-1-w)).
@@ -70,9 +71,12 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kNonFinite = -100000;  // exponent marking a row / column holding Inf or NaN
 constexpr uint64_t kTimeoutNs = 2000000000ull;       // 2 s: no legitimate wait comes close
 constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kSmemBytesProduct = kRAProduct * kATile + kRX * kXTile + 1024 + 1024;
+__host__ __device__ constexpr int ring_a(int mode) { return mode == 0 ? kRAProduct : kRA; }
+__host__ __device__ constexpr int smem_bytes(int mode) { return mode == 0 ? kSmemBytesProduct : kSmemBytes; }
 
 struct __align__(8) Bars {
-  uint64_t a_full[kRA], a_empty[kRA], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
+  uint64_t a_full[kRAProduct], a_empty[kRAProduct], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
   int abort;
 };
@@ -264,8 +268,9 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   if (s_skip) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sa = smem;                          // kRA x 16 KiB
-  unsigned char* sx = smem + kRA * kATile;           // kRX x 36 KiB
+  constexpr int RA = ring_a(MODE);                   // A ring stages
+  unsigned char* sa = smem;                          // RA x 16 KiB
+  unsigned char* sx = smem + RA * kATile;            // kRX x 32 KiB
   Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column blocks vary fastest, so the CTAs sharing A-side rows run together
@@ -283,7 +288,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   volatile int* abort_flag = &bars->abort;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kRA; ++i) {
+    for (int i = 0; i < RA; ++i) {
       mbar_init(smem_u32(&bars->a_full[i]), 1);
       mbar_init(smem_u32(&bars->a_empty[i]), 1);
     }
@@ -337,7 +342,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
           tma_load_2d(smem_u32(sa + as * kATile), tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
           ++issued_a;
-          if (++as == kRA) {
+          if (++as == RA) {
             as = 0;
             aph ^= 1;
           }
@@ -345,8 +350,8 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       }
       if (!ok) {
         // let the copies this thread started land before the CTA leaves
-        for (int i = (issued_a > kRA ? issued_a - kRA : 0); i < issued_a; ++i)
-          mbar_drain(smem_u32(&bars->a_full[i % kRA]), (i / kRA) & 1);
+        for (int i = (issued_a > RA ? issued_a - RA : 0); i < issued_a; ++i)
+          mbar_drain(smem_u32(&bars->a_full[i % RA]), (i / RA) & 1);
         for (int i = (issued_x > kRX ? issued_x - kRX : 0); i < issued_x; ++i)
           mbar_drain(smem_u32(&bars->x_full[i % kRX]), (i / kRX) & 1);
       }
@@ -402,7 +407,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
             tc_mma(dt + 256u, ad + 6, xd2 + 6, id2, 1u);
           }
           tc_commit(smem_u32(&bars->a_empty[as]));
-          if (++as == kRA) {
+          if (++as == RA) {
             as = 0;
             aph ^= 1;
           }
@@ -2157,7 +2162,7 @@ cudaError_t init_sliced_attributes() {
 #define EIGREF_SET_ATTR(S_)                                                                                        \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_PRODUCT>,                                        \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytesProduct);                  \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              sl::kSmemBytes);                                                                      \
@@ -2166,7 +2171,7 @@ cudaError_t init_sliced_attributes() {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_PRODUCT>,                                \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytesProduct);                  \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_GRAM>,                                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
@@ -2361,7 +2366,8 @@ static sl::MmaArgs base_args(const Control* ctl, int* err) {
 template <int MODE>
 static void launch_mma(int S, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b2,
                        const sl::MmaArgs& g, cudaStream_t s) {
-#define EIGREF_CALL_MMA(S_) sl::sliced_mma_kernel<S_, MODE><<<grid, sl::kThreads, sl::kSmemBytes, s>>>(a, b, b2, g)
+#define EIGREF_CALL_MMA(S_) \
+  sl::sliced_mma_kernel<S_, MODE><<<grid, sl::kThreads, sl::smem_bytes(MODE), s>>>(a, b, b2, g)
   EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_MMA)
 #undef EIGREF_CALL_MMA
 }
@@ -2585,7 +2591,7 @@ int SlicedA::update(const double* X, const double* W, const double* F, const dou
 template <int MODE>
 static void launch_mma_group(int S, const sl::GroupMma& p, int ctas, cudaStream_t s) {
 #define EIGREF_CALL_MMA_G(S_) \
-  sl::sliced_mma_grouped_kernel<S_, MODE><<<ctas, sl::kThreads, sl::kSmemBytes, s>>>(p)
+  sl::sliced_mma_grouped_kernel<S_, MODE><<<ctas, sl::kThreads, sl::smem_bytes(MODE), s>>>(p)
   EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_MMA_G)
 #undef EIGREF_CALL_MMA_G
 }
