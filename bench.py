@@ -302,7 +302,7 @@ def run_laplacian(args, world, rank, local):
            "data": "synthetic",
            "config": {"workload": LAPLACE, "n": n, "k": k, "nnz": nnz,
                       "form": "FP64 SpMM, " + ("FP64 Gram products" if precision == "fp64" else
-                                               "Gram products as BF16 digit planes on the tensor cores"),
+                                               "Gram products and row update as digit planes on the tensor cores"),
                       "split_k_gram": rep["ksplit"] or None,
                       "l2": "inputs larger than L2 (CSR 65 MB + X 131 MB + P 131 MB per SpMM); no flush"},
            "roofline": {"bound": "alu", "kernel": "spmm_csr_vec2_kernel", "achieved": tfs, "peak": fp64_peak,

@@ -172,7 +172,7 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
 
 /* Same for CSR A.  The product is an FP64 SpMM.  p->precision EIGREF_FP64:
  * FP64 Gram products; EIGREF_BF16_SLICES: the Gram products X^T X and X^T W
- * as error-free BF16 digit planes on the tensor cores (k <= 16, else
+ * as error-free digit planes on the tensor cores (k <= 16, else
  * EIGREF_E_UNSUPPORTED); the k x k stage and the row update stay FP64. */
 int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx,
                       const double* val, int64_t n, int64_t nnz,
@@ -214,7 +214,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
 /* Lines 3-4 of Algorithm 4 on their own: G = X^T X and S = X^T P over all n
  * rows, k x k column-major (ld k) into caller-owned G and S (host or device).
  * X (ldx) and P (ldp) are n x k column-major in device memory.  precision
- * EIGREF_FP64: FP64 dot products; EIGREF_BF16_SLICES: error-free BF16 digit
+ * EIGREF_FP64: FP64 dot products; EIGREF_BF16_SLICES: error-free digit
  * planes on the tensor cores (the split form used by eigref_refine_csr),
  * k <= 16, each entry exact up to the slice truncation and one rounding.
  * Errors: EIGREF_E_INVALID (NULL, sizes, host X/P), EIGREF_E_UNSUPPORTED

@@ -136,7 +136,7 @@ class SlicedA {
 };
 
 // The Gram products G = X^T X, S = X^T P (k <= 16, all n rows) as stacked
-// BF16 digit planes on the tensor cores, without A: the split form of the
+// F16 digit planes on the tensor cores, without A: the split form of the
 // Gram products for CSR matrices (whose product stays an FP64 SpMM).
 class SlicedGram {
  public:

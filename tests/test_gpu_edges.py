@@ -103,3 +103,26 @@ def test_auto_precision_picks_the_form(eig):
         assert (rg["psplit"] > 0) == split
         Xo, _ = R.refine(R.dense_operator(A), X0, normA, max_iters=2)
         assert rel_diff(host(X), Xo) <= 2 * sweep_tol((1 + n ** 0.5 * 2.0 ** -56 / U) * normA, gap)
+
+
+def as_csr(A):
+    rows, cols = np.nonzero(A)
+    row_ptr = np.zeros(A.shape[0] + 1, dtype=np.int32)
+    np.add.at(row_ptr, rows + 1, 1)
+    return np.cumsum(row_ptr).astype(np.int32), cols.astype(np.int32), A[rows, cols].astype(np.float64)
+
+
+@pytest.mark.parametrize("n,k", [(3, 2), (17, 16), (40, 4), (70, 10), (200, 14)])
+def test_small_csr_split_form_matches_oracle(eig, n, k):
+    """The CSR split form's kernels at sizes below one tile (n < 64 rows of a
+    Gram block, n < 128 rows of an update tile) and with ragged last tiles,
+    for even k (the Gram planes cut in shared memory, the tensor-core row
+    update) -- against the oracle."""
+    A, X0, Xt, normA, gap = small_problem(n, k, seed=20 * n + k)
+    rp, ci, val = as_csr(A)
+    X = dev(np.asfortranarray(X0))
+    rg = eig.refine_csr(dev(rp), dev(ci), dev(val), X, max_iters=3, norm_a=normA, precision="bf16")
+    Xo, ro = R.refine(R.dense_operator(A), X0, normA, max_iters=3)
+    assert rg["status"] == 0 and rg["iterations"] == 3
+    tol = sweep_tol((1 + n ** 0.5 * 2.0 ** -56 / U) * normA, gap)
+    assert rel_diff(host(X), Xo) <= 3 * tol

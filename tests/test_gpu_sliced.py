@@ -1,4 +1,4 @@
-"""The split-precision (BF16 digit-plane) tensor-core product and sweeps:
+"""The split-precision (digit-plane) tensor-core product and sweeps:
 the product against double-double at sampled entries within the bound the
 slicing gives, adversarial inputs for the exactness of the FP32 chunks, sweep
 parity with the FP64 oracle and the final accuracy of a converged run."""
