@@ -55,6 +55,7 @@ constexpr int kBK = 64;            // K per pipeline stage (128 bytes of F16)
 constexpr int kChunkBlocks = 2;    // K blocks per exact accumulation chunk (128: 8 pairs x 2^14 x 128 <= 2^24)
 constexpr int kRA = 9;             // A ring stages (a K block of planes and one more)
 constexpr int kRAProduct = 10;     // the product's ring: one stage deeper (its epilogue keeps no sums in shared memory)
+constexpr int kRAUpdate = 7;       // the update's ring: two stages give way to the epilogue's transpose blocks
 // Digit weights: a = 2^e sum_s d_s 2^-(kBits s + 7), so the pairs of weight
 // group w = s + t carry 2^-(kBits w + 14); the epilogue keeps
 // hi = sum_(w<4) C_w 2^(kBits (3 - w)) and lo = sum_(w>=4) C_w 2^(kBits (S-1-w)).
@@ -72,8 +73,13 @@ constexpr int kNonFinite = -100000;  // exponent marking a row / column holding 
 constexpr uint64_t kTimeoutNs = 2000000000ull;       // 2 s: no legitimate wait comes close
 constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
 constexpr int kSmemBytesProduct = kRAProduct * kATile + kRX * kXTile + 1024 + 1024;
-__host__ __device__ constexpr int ring_a(int mode) { return mode == 0 ? kRAProduct : kRA; }
-__host__ __device__ constexpr int smem_bytes(int mode) { return mode == 0 ? kSmemBytesProduct : kSmemBytes; }
+constexpr int kTrStride = kBN / 2 + 1;               // doubles a row of a warp's 32 x 16 transpose block (no bank conflicts)
+constexpr int kTrBytes = kEpiWarps * 32 * kTrStride * 8;   // 34 KiB
+constexpr int kSmemBytesUpdate = kRAUpdate * kATile + kRX * kXTile + 1024 + kTrBytes + 1024;
+__host__ __device__ constexpr int ring_a(int mode) { return mode == 0 ? kRAProduct : (mode == 2 ? kRAUpdate : kRA); }
+__host__ __device__ constexpr int smem_bytes(int mode) {
+  return mode == 0 ? kSmemBytesProduct : (mode == 2 ? kSmemBytesUpdate : kSmemBytes);
+}
 
 struct __align__(8) Bars {
   uint64_t a_full[kRAProduct], a_empty[kRAProduct], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
@@ -257,12 +263,18 @@ __device__ __forceinline__ double recombine(long long hi, long long lo, int er, 
 }
 
 // One CTA's tile: output column block nb, row tile mb, K split / job zb.
+// tiles > 0 (UPDATE only): persistent, the CTA takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... of tiles (column block fastest, tgx of them;
+// nb and mb unused).  Ring, stage and accumulator counters run on across
+// the CTA's tiles, so the MMAs of one tile fill the second accumulator set
+// while the epilogue warps finish the previous one.
 template <int S, int MODE>
 __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CUtensorMap* tmB,
-                                                const CUtensorMap* tmB2, const MmaArgs& g, int nb, int mb, int zb) {
+                                                const CUtensorMap* tmB2, const MmaArgs& g, int nb, int mb, int zb,
+                                                int tgx = 0, int tiles = 0) {
   // one read of the stop flag per CTA: an aborting CTA of this grid may set it
   __shared__ int s_skip;
-  __shared__ double s_colsum[2][4][kBN];            // UPDATE: per lane-group column sums
+  __shared__ double s_colsum[2][2][4][kBN];         // UPDATE: per lane-group column sums, by tile parity
   if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
   __syncthreads();
   if (s_skip) return;
@@ -272,9 +284,14 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   unsigned char* sa = smem;                          // RA x 16 KiB
   unsigned char* sx = smem + RA * kATile;            // kRX x 32 KiB
   Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
+  static_assert(sizeof(Bars) <= 1024, "barrier block");
+  double* s_tr = reinterpret_cast<double*>(sx + kRX * kXTile + 1024);   // UPDATE: 8 warps x 32 x kTrStride
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column blocks vary fastest, so the CTAs sharing A-side rows run together
-  const int m0 = mb * kBM;                           // output row tile
+  const bool persist = MODE == MODE_UPDATE && tiles > 0;
+  const int t_first = persist ? (int)blockIdx.x : 0;
+  const int t_end = persist ? tiles : 1;
+  const int t_step = persist ? (int)gridDim.x : 1;
   const int job = MODE == MODE_GRAM ? (zb & 1) : 0;
   const int split = MODE == MODE_GRAM ? (zb >> 1) : (MODE == MODE_PRODUCT ? zb : 0);
   const int nsplit = MODE == MODE_UPDATE ? 1 : g.ksplit;
@@ -324,27 +341,32 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       bool ok = true;
       int as = 0;
       uint32_t aph = 0;                              // lap parity of the A ring
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        const int kx = (kb_lo + kb) * kBK;           // K coordinate (elements)
-        const int xs = kb & 1;
-        ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((kb >> 1) & 1) ^ 1, abort_flag);
-        if (!ok) break;
-        mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
-#pragma unroll
-        for (int t = 0; t < S; ++t)
-          tma_load_2d(smem_u32(sx + xs * kXTile + t * kBN * kBK * 2), tB, smem_u32(&bars->x_full[xs]), kx,
-                      t * g.b_plane_rows + nb * kBN);
-        ++issued_x;
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-          ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, abort_flag);
+      int gkb = 0;                                   // K blocks over the CTA's tiles (X stage and parity)
+      for (int ti = t_first; ti < t_end && ok; ti += t_step) {
+        const int nbt = persist ? ti % tgx : nb;
+        const int m0 = (persist ? ti / tgx : mb) * kBM;
+        for (int kb = 0; kb < KB && ok; ++kb, ++gkb) {
+          const int kx = (kb_lo + kb) * kBK;         // K coordinate (elements)
+          const int xs = gkb & 1;
+          ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb >> 1) & 1) ^ 1, abort_flag);
           if (!ok) break;
-          mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
-          tma_load_2d(smem_u32(sa + as * kATile), tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
-          ++issued_a;
-          if (++as == RA) {
-            as = 0;
-            aph ^= 1;
+          mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
+#pragma unroll
+          for (int t = 0; t < S; ++t)
+            tma_load_2d(smem_u32(sx + xs * kXTile + t * kBN * kBK * 2), tB, smem_u32(&bars->x_full[xs]), kx,
+                        t * g.b_plane_rows + nbt * kBN);
+          ++issued_x;
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, abort_flag);
+            if (!ok) break;
+            mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
+            tma_load_2d(smem_u32(sa + as * kATile), tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
+            ++issued_a;
+            if (++as == RA) {
+              as = 0;
+              aph ^= 1;
+            }
           }
         }
       }
@@ -364,57 +386,60 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       bool ok = true;
       int as = 0;
       uint32_t aph = 0;
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        const int c = kb / kChunkBlocks;
-        const int buf = NBUF == 2 ? (c & 1) : 0;
-        const bool first = (kb % kChunkBlocks) == 0;
-        const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
-        if (first) {
-          ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
+      int gkb = 0, gc = 0;                           // K blocks and chunks over the CTA's tiles
+      for (int ti = t_first; ti < t_end && ok; ti += t_step, gc += NC) {
+        for (int kb = 0; kb < KB && ok; ++kb, ++gkb) {
+          const int c = gc + kb / kChunkBlocks;
+          const int buf = NBUF == 2 ? (c & 1) : 0;
+          const bool first = (kb % kChunkBlocks) == 0;
+          const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
+          if (first) {
+            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+          }
+          const int xs = gkb & 1;
+          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb >> 1) & 1, abort_flag);
           if (!ok) break;
           tc_fence_after();
-        }
-        const int xs = kb & 1;
-        ok = mbar_wait(smem_u32(&bars->x_full[xs]), (kb >> 1) & 1, abort_flag);
-        if (!ok) break;
-        tc_fence_after();
-        const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
-        const uint32_t cbase = (uint32_t)(buf * S * kBN);
-        const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
+          const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
+          const uint32_t cbase = (uint32_t)(buf * S * kBN);
+          const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, abort_flag);
+          for (int s = 0; s < S; ++s) {
+            ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
+            // B = B-side planes 0 .. S-1-s stacked: N = 32 (S - s) rows (weight
+            // groups w = s .. S-1 at columns cbase + 32 w), issued as pieces of
+            // at most 256 (the M = 128 limit); +2 in the address field steps 32
+            // bytes (16 K) inside the 128-byte swizzle row
+            const int N = kBN * (S - s);
+            const int N1 = N < 256 ? N : 256;
+            const uint32_t dt = tbase + cbase + (uint32_t)(s * kBN);
+            tc_mma(dt, ad, xd, idesc_f16(kBM, N1), s == 0 ? acc0 : 1u);
+            tc_mma(dt, ad + 2, xd + 2, idesc_f16(kBM, N1), 1u);
+            tc_mma(dt, ad + 4, xd + 4, idesc_f16(kBM, N1), 1u);
+            tc_mma(dt, ad + 6, xd + 6, idesc_f16(kBM, N1), 1u);
+            if (N > 256) {
+              const uint64_t xd2 = xd + (uint64_t)((256 * kBK * 2) >> 4);
+              const uint32_t id2 = idesc_f16(kBM, N - 256);
+              tc_mma(dt + 256u, ad, xd2, id2, s == 0 ? acc0 : 1u);
+              tc_mma(dt + 256u, ad + 2, xd2 + 2, id2, 1u);
+              tc_mma(dt + 256u, ad + 4, xd2 + 4, id2, 1u);
+              tc_mma(dt + 256u, ad + 6, xd2 + 6, id2, 1u);
+            }
+            tc_commit(smem_u32(&bars->a_empty[as]));
+            if (++as == RA) {
+              as = 0;
+              aph ^= 1;
+            }
+          }
           if (!ok) break;
-          tc_fence_after();
-          const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
-          // B = B-side planes 0 .. S-1-s stacked: N = 32 (S - s) rows (weight
-          // groups w = s .. S-1 at columns cbase + 32 w), issued as pieces of
-          // at most 256 (the M = 128 limit); +2 in the address field steps 32
-          // bytes (16 K) inside the 128-byte swizzle row
-          const int N = kBN * (S - s);
-          const int N1 = N < 256 ? N : 256;
-          const uint32_t dt = tbase + cbase + (uint32_t)(s * kBN);
-          tc_mma(dt, ad, xd, idesc_f16(kBM, N1), s == 0 ? acc0 : 1u);
-          tc_mma(dt, ad + 2, xd + 2, idesc_f16(kBM, N1), 1u);
-          tc_mma(dt, ad + 4, xd + 4, idesc_f16(kBM, N1), 1u);
-          tc_mma(dt, ad + 6, xd + 6, idesc_f16(kBM, N1), 1u);
-          if (N > 256) {
-            const uint64_t xd2 = xd + (uint64_t)((256 * kBK * 2) >> 4);
-            const uint32_t id2 = idesc_f16(kBM, N - 256);
-            tc_mma(dt + 256u, ad, xd2, id2, s == 0 ? acc0 : 1u);
-            tc_mma(dt + 256u, ad + 2, xd2 + 2, id2, 1u);
-            tc_mma(dt + 256u, ad + 4, xd2 + 4, id2, 1u);
-            tc_mma(dt + 256u, ad + 6, xd2 + 6, id2, 1u);
-          }
-          tc_commit(smem_u32(&bars->a_empty[as]));
-          if (++as == RA) {
-            as = 0;
-            aph ^= 1;
-          }
+          tc_commit(smem_u32(&bars->x_empty[xs]));
+          if (last) tc_commit(smem_u32(&bars->acc_full[buf]));
         }
-        if (!ok) break;
-        tc_commit(smem_u32(&bars->x_empty[xs]));
-        if (last) tc_commit(smem_u32(&bars->acc_full[buf]));
       }
       if (!ok) {
         // wait for the MMAs already issued before the CTA releases TMEM
@@ -426,130 +451,156 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
     // ---------------- epilogue: drain chunks into exact int64 sums ----------------
     const int lg = warp & 3;                           // TMEM lane group of this warp
     const int half = (warp - 2) >> 2;                  // which 16 of the 32 columns
-    const int64_t row = m0 + lg * 32 + lane;
     constexpr int kC = kBN / 2;
-    long long hi[kC], lo[kC];
-#pragma unroll
-    for (int j = 0; j < kC; ++j) hi[j] = lo[j] = 0;
-    if (MODE == MODE_UPDATE && row < g.m_valid && row >= g.row_begin) {
-      // the row's X and W values the update reads after the drain: into L1
-      // while the MMAs run (128 contiguous bytes each)
-      const int64_t e0 = row * g.k + nb * kBN + half * kC;
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.X + e0));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.W + e0));
-    }
     bool ok = true;
-    for (int c = 0; c < NC && ok; ++c) {
-      const int buf = NBUF == 2 ? (c & 1) : 0;
-      // one lane waits, the warp follows (the TMEM loads below are warp-collective);
-      // it sleeps between polls, leaving issue slots to the MMA warp
-      int w_ok = 0;
-      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
-      ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
-      __syncwarp();
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t cbase = (uint32_t)(buf * S * kBN);
-      const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + cbase + (uint32_t)(half * kC);
-      // several weights per round trip to TMEM (two at S >= 8, within the register budget)
-      constexpr int GW = S >= 8 ? 2 : 3;
+    int gc = 0;                                        // chunks over the CTA's tiles
+    for (int ti = t_first; ti < t_end; ti += t_step, gc += NC) {
+      const int nbt = persist ? ti % tgx : nb;
+      const int mbt = persist ? ti / tgx : mb;
+      const int64_t row = (int64_t)mbt * kBM + lg * 32 + lane;
+      long long hi[kC], lo[kC];
 #pragma unroll
-      for (int w0 = 0; w0 < S; w0 += GW) {
-        uint32_t r[GW][kC];
+      for (int j = 0; j < kC; ++j) hi[j] = lo[j] = 0;
+      if (MODE == MODE_UPDATE && row < g.m_valid && row >= g.row_begin) {
+        // the row's X and W values the update reads after the drain: into L1
+        // while the MMAs run (128 contiguous bytes each)
+        const int64_t e0 = row * g.k + nbt * kBN + half * kC;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(g.X + e0));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(g.W + e0));
+      }
+      for (int cl = 0; cl < NC && ok; ++cl) {
+        const int c = gc + cl;
+        const int buf = NBUF == 2 ? (c & 1) : 0;
+        // one lane waits, the warp follows (the TMEM loads below are warp-collective);
+        // it sleeps between polls, leaving issue slots to the MMA warp
+        int w_ok = 0;
+        if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
+        ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+        __syncwarp();
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t cbase = (uint32_t)(buf * S * kBN);
+        const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + cbase + (uint32_t)(half * kC);
+        // several weights per round trip to TMEM (two at S >= 8, within the register budget)
+        constexpr int GW = S >= 8 ? 2 : 3;
 #pragma unroll
-        for (int q = 0; q < GW; ++q)
-          if (w0 + q < S) TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int w0 = 0; w0 < S; w0 += GW) {
+          uint32_t r[GW][kC];
 #pragma unroll
-        for (int q = 0; q < GW; ++q) {
-          if (w0 + q >= S) continue;
-          const int w = w0 + q;
-          if (w < 4) {
-            const int sh = kBits * (3 - w);
+          for (int q = 0; q < GW; ++q)
+            if (w0 + q < S) TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < kC; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
-          } else {
-            const int sh = kBits * (S - 1 - w);
+          for (int q = 0; q < GW; ++q) {
+            if (w0 + q >= S) continue;
+            const int w = w0 + q;
+            if (w < 4) {
+              const int sh = kBits * (3 - w);
 #pragma unroll
-            for (int j = 0; j < kC; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
+              for (int j = 0; j < kC; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
+            } else {
+              const int sh = kBits * (S - 1 - w);
+#pragma unroll
+              for (int j = 0; j < kC; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[q][j])) << sh;
+            }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[buf]));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[buf]));
-    }
-    const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
-    const int* cexp = job ? g.colexp2 : g.colexp;
-    double sq[kC], rq[kC];
+      const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
+      const int* cexp = job ? g.colexp2 : g.colexp;
+      if constexpr (MODE == MODE_UPDATE) {
+        // X' = X + (W - X D) D^-1 - X F.  Each lane recombines its row of
+        // X F (16 columns); the warp's 32 x 16 block then turns through
+        // shared memory, so that a half-warp holds 16 consecutive columns
+        // of one row and every global load and store of X, W and X' moves
+        // 128-byte rows (one row per lane would touch 32 rows an access).
+        // X, W, d and 1/d are read-only in this launch (X' is another buffer).
+        const int c0 = nbt * kBN + half * kC;
+        const int cl = c0 + (lane & (kC - 1));           // this lane's column after the turn
+        const bool cok = cl < g.k;
+        const int e_l = cok ? __ldg(cexp + cl) : 0;
+        double* tr = s_tr + (warp - 2) * 32 * kTrStride;
+        __syncwarp();                                    // the last tile's reads of tr are done
 #pragma unroll
-    for (int j = 0; j < kC; ++j) {
-      const int col = nb * kBN + half * kC + j;
-      const bool live = ok && row < g.m_valid && col < g.k;
-      // split-K partials stay exact int64 pairs: the sum over splits is exact,
-      // so the result does not depend on how K was split
-      const bool raw = (MODE == MODE_GRAM) || (MODE == MODE_PRODUCT && nsplit > 1);
-      const double w = (live && !raw) ? recombine<S>(hi[j], lo[j], er, cexp[col]) : 0.0;
-      sq[j] = rq[j] = 0.0;
-      if (MODE == MODE_PRODUCT) {
-        if (live) {
-          if (nsplit == 1)
-            g.P[row * g.k + col] = w - g.shift * g.Xs[row * g.k + col];
-          else
-            g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
+        for (int j = 0; j < kC; ++j) {
+          const int ej = __shfl_sync(0xffffffffu, e_l, j);
+          const bool lv = ok && row < g.m_valid && row >= g.row_begin && c0 + j < g.k;
+          tr[lane * kTrStride + j] = lv ? recombine<S>(hi[j], lo[j], er, ej) : 0.0;
         }
-      } else if (MODE == MODE_GRAM) {
-        if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = make_longlong2(hi[j], lo[j]);
+        __syncwarp();
+        // lane L: column cl of rows r0 + 2i, i = 0 .. 15
+        const int64_t r0 = (int64_t)mbt * kBM + lg * 32 + (lane >> 4);
+        const double dj = cok ? __ldg(g.d + cl) : 0.0, dij = cok ? __ldg(g.dinv + cl) : 0.0;
+        double xv[kC], wv[kC];
+#pragma unroll
+        for (int i = 0; i < kC; ++i) {
+          const int64_t r = r0 + 2 * i;
+          const bool lv = ok && cok && r < g.m_valid && r >= g.row_begin;
+          xv[i] = lv ? __ldg(g.X + r * g.k + cl) : 0.0;
+          wv[i] = lv ? __ldg(g.W + r * g.k + cl) : 0.0;
+        }
+        double ssq = 0.0, srq = 0.0;                     // column sums of X'^2 and (W - X D)^2, rows in order
+#pragma unroll
+        for (int i = 0; i < kC; ++i) {
+          const int64_t r = r0 + 2 * i;
+          if (ok && cok && r < g.m_valid && r >= g.row_begin) {
+            const double rr = wv[i] - xv[i] * dj;
+            const double xn = xv[i] + rr * dij - tr[(2 * i + (lane >> 4)) * kTrStride + (lane & (kC - 1))];
+            g.Xn[r * g.k + cl] = xn;
+            ssq = fma(xn, xn, ssq);
+            srq = fma(rr, rr, srq);
+          }
+        }
+        ssq += __shfl_xor_sync(0xffffffffu, ssq, 16);   // the two half-warps share the columns
+        srq += __shfl_xor_sync(0xffffffffu, srq, 16);
+        const int tp = ((ti - t_first) / t_step) & 1;   // tile parity: the buffer of this tile's sums
+        if (lane < kC) {
+          s_colsum[tp][0][lg][half * kC + lane] = ssq;
+          s_colsum[tp][1][lg][half * kC + lane] = srq;
+        }
+        // the eight epilogue warps meet; the first two add the four lane
+        // groups' sums of the tile.  A warp writes buffer tp again two tiles
+        // later, after the next meeting, which every reader of this one has
+        // passed.
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+        const int et = (int)threadIdx.x - 64;
+        if (et < 2 * kBN) {
+          const int which = et / kBN, cc = et % kBN;
+          const int col = nbt * kBN + cc;
+          if (col < g.k) {
+            const double v = s_colsum[tp][which][0][cc] + s_colsum[tp][which][1][cc] + s_colsum[tp][which][2][cc] +
+                             s_colsum[tp][which][3][cc];
+            g.upart[(int64_t)mbt * 2 * g.k + which * g.k + col] = v;
+          }
+        }
       } else {
-        if (live && row >= g.row_begin) {
-          const int64_t e = row * g.k + col;
-          const double x = g.X[e], dj = g.d[col];
-          const double rr = g.W[e] - x * dj;
-          const double xn = x + rr * g.dinv[col] - w;
-          g.Xn[e] = xn;
-          sq[j] = xn * xn;
-          rq[j] = rr * rr;
-        }
-      }
-    }
-    if (MODE == MODE_UPDATE) {
-      // column sums over the warp's 32 rows, in a fixed order, by a butterfly
-      // that halves the values a lane holds at each step (16 + 16 FP64 adds a
-      // lane instead of 5 x 32): lane L ends with column
-      // 8 b4 + 4 b3 + 2 b2 + b1 of its half (b = the bits of L), twice
-      static_assert(kC == 16, "the butterfly below is written for 16 columns");
 #pragma unroll
-      for (int step = 0; step < 4; ++step) {
-        const int o = 16 >> step, m = 8 >> step;     // partner distance, values kept
-        const bool upper = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < m; ++i) {
-          const double ks = upper ? sq[m + i] : sq[i], ss = upper ? sq[i] : sq[m + i];
-          const double kr = upper ? rq[m + i] : rq[i], sr = upper ? rq[i] : rq[m + i];
-          sq[i] = ks + __shfl_xor_sync(0xffffffffu, ss, o);
-          rq[i] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
+        for (int j = 0; j < kC; ++j) {
+          const int col = nbt * kBN + half * kC + j;
+          const bool live = ok && row < g.m_valid && col < g.k;
+          // split-K partials stay exact int64 pairs: the sum over splits is exact,
+          // so the result does not depend on how K was split
+          const bool raw = (MODE == MODE_GRAM) || (MODE == MODE_PRODUCT && nsplit > 1);
+          const double w = (live && !raw) ? recombine<S>(hi[j], lo[j], er, cexp[col]) : 0.0;
+          if (MODE == MODE_PRODUCT) {
+            if (live) {
+              if (nsplit == 1)
+                g.P[row * g.k + col] = w - g.shift * g.Xs[row * g.k + col];
+              else
+                g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
+            }
+          } else {
+            if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = make_longlong2(hi[j], lo[j]);
+          }
         }
-      }
-      sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
-      rq[0] += __shfl_xor_sync(0xffffffffu, rq[0], 1);
-      if ((lane & 1) == 0) {
-        const int c = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-        s_colsum[0][lg][half * kC + c] = sq[0];
-        s_colsum[1][lg][half * kC + c] = rq[0];
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (MODE == MODE_UPDATE && threadIdx.x < 2 * kBN) {
-    const int which = threadIdx.x / kBN, cc = threadIdx.x % kBN;
-    const int col = nb * kBN + cc;
-    if (col < g.k) {
-      const double v = s_colsum[which][0][cc] + s_colsum[which][1][cc] + s_colsum[which][2][cc] +
-                       s_colsum[which][3][cc];
-      g.upart[(int64_t)mb * 2 * g.k + which * g.k + col] = v;
-    }
-  }
   if (bars->abort && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     if (g.ctl) {
@@ -569,6 +620,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     sliced_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ CUtensorMap tmB2, MmaArgs g) {
   sliced_mma_body<S, MODE>(&tmA, &tmB, &tmB2, g, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The row update over a persistent grid (one CTA per SM): tiles = gx column
+// blocks x row tiles, column block fastest.  With one tile a CTA, load, MMAs
+// and the FP64 epilogue of a CTA run one after another and nothing else
+// shares the SM; here the MMAs of a CTA's next tile overlap the epilogue of
+// its current one.
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+    sliced_update_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                                    MmaArgs g, int gx, int tiles) {
+  sliced_mma_body<S, MODE_UPDATE>(&tmA, &tmB, &tmB, g, 0, 0, 0, gx, tiles);
 }
 
 // Many problems' tiles in one launch (a batch).  The tensor maps travel in
@@ -2167,8 +2230,8 @@ cudaError_t init_sliced_attributes() {
     e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              sl::kSmemBytes);                                                                      \
   if (e == cudaSuccess)                                                                                            \
-    e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_UPDATE>,                                         \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+    e = cudaFuncSetAttribute(sl::sliced_update_persistent_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             sl::kSmemBytesUpdate);                                                                \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_PRODUCT>,                                \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytesProduct);                  \
@@ -2177,7 +2240,7 @@ cudaError_t init_sliced_attributes() {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_grouped_kernel<S_, sl::MODE_UPDATE>,                                 \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytes);                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytesUpdate);                   \
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sgram16_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kG16Smem); \
   if (e == cudaSuccess)                                                                                            \
@@ -2384,9 +2447,21 @@ static void launch_product_reduce(int S, const MmaTask& t, int psplit, const dou
 
 static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
   const dim3 grid((unsigned)t.gx, (unsigned)t.gy, (unsigned)t.gz);
-  if (mode == sl::MODE_PRODUCT) launch_mma<sl::MODE_PRODUCT>(S, grid, t.a, t.b, t.b2, t.g, s);
-  else if (mode == sl::MODE_GRAM) launch_mma<sl::MODE_GRAM>(S, grid, t.a, t.b, t.b2, t.g, s);
-  else launch_mma<sl::MODE_UPDATE>(S, grid, t.a, t.b, t.b2, t.g, s);
+  if (mode == sl::MODE_PRODUCT) {
+    launch_mma<sl::MODE_PRODUCT>(S, grid, t.a, t.b, t.b2, t.g, s);
+  } else if (mode == sl::MODE_GRAM) {
+    launch_mma<sl::MODE_GRAM>(S, grid, t.a, t.b, t.b2, t.g, s);
+  } else {
+    // persistent: one CTA per SM (the kernel's shared memory allows one), at most one per tile
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = t.gx * t.gy;
+    const int ctas = std::max(1, std::min(tiles, sms));
+#define EIGREF_CALL_UPD(S_)                                                                                   \
+  sl::sliced_update_persistent_kernel<S_><<<ctas, sl::kThreads, sl::kSmemBytesUpdate, s>>>(t.a, t.b, t.g, t.gx, tiles)
+    EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_UPD)
+#undef EIGREF_CALL_UPD
+  }
 }
 
 MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Control* ctl, const double* Xs,

@@ -37,7 +37,7 @@ struct MmaArgs {
   const double* W;       // UPDATE: row-major n x k
   const double* d;       // UPDATE: Rayleigh quotients [k]
   const double* dinv;    // UPDATE: 1 / d
-  double* Xn;            // UPDATE: row-major n x k
+  double* Xn;            // UPDATE: row-major n x k (overlaps none of X, W, d, dinv)
   double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
   const Control* ctl;
   int* err;              // set to 1 on a timed-out wait
