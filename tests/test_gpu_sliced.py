@@ -108,7 +108,9 @@ def split_tol(p):
     return sweep_tol((1 + p.n ** 0.5 * 2.0 ** -(SLICE_BITS * 8) / U) * (p.normA + abs(p.shift)), p.min_gap)
 
 
-@pytest.mark.parametrize("n,k", [(300, 8), (1000, 128), (517, 17)])
+# (10000, 65): 80 row tiles x 3 column blocks (the last one 1 column of 32)
+# = 240 tiles, more than one per CTA of the persistent row update
+@pytest.mark.parametrize("n,k", [(300, 8), (1000, 128), (517, 17), (10000, 65)])
 def test_sliced_sweep_parity(eig, n, k):
     p = dense_case(n, k, seed=400 + n)
     Xg, rg = run_gpu(eig, p, max_iters=1)
