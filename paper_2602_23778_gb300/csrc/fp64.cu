@@ -380,11 +380,23 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
   __shared__ double red[3][32];
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  if (ctl->done) {
-    if (tid == 0) ctl->pending_norm = 0;
-    return;
+  // The kernel is a chain of latencies, so every control field it needs is
+  // loaded here, together with the partials below; the stop flag is acted on
+  // once they are in (reading partials of a finished run writes nothing).
+  const int done = ctl->done, judge = ctl->judge;
+  int it = 0, stop = 0, max_iters = 0;
+  double tol = 0.0, norm_a = 1.0, div_factor = 0.0, div_floor = 0.0, emin = 0.0;
+  if (tid == 0) {
+    it = ctl->iterations;
+    stop = ctl->stop;
+    max_iters = ctl->max_iters;
+    tol = ctl->tol;
+    norm_a = ctl->norm_a;
+    div_factor = ctl->div_factor;
+    div_floor = ctl->div_floor;
+    emin = ctl->emin;
+    bad = 0;
   }
-  if (tid == 0) bad = 0;
   // column sums of the update partials [ugrid][2k]: thread (grp, c) adds
   // partials grp, grp + groups, ... of column c (consecutive threads read
   // consecutive addresses), then the groups are added in order; fixed order,
@@ -426,6 +438,10 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
       r2_s[j] = r2;
     }
   }
+  if (done) {
+    if (tid == 0) ctl->pending_norm = 0;
+    return;
+  }
   __syncthreads();
   double rsum = 0.0, esum = 0.0, e11 = 0.0;
   if (tid < k) {
@@ -433,9 +449,9 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
     const double xsq = xsq_s[j], r2 = r2_s[j], dj = b.d[j];
     const double e21 = (r2 - 2.0 * b.cz[j] + b.cw[j]) / (dj * dj);
     // the correction of the judged leading columns decides stop and divergence
-    esum = (j < ctl->judge && e21 > 0.0) ? e21 : 0.0;
+    esum = (j < judge && e21 > 0.0) ? e21 : 0.0;
     rsum = b.r1sq[j] + r2;
-    e11 = j < ctl->judge ? b.e11sq[j] : 0.0;
+    e11 = j < judge ? b.e11sq[j] : 0.0;
     b.nu[j] = 1.0 / sqrt(xsq);
     if (!isfinite(xsq) || !(xsq > 0.0)) atomicExch(&bad, 1);
   }
@@ -450,16 +466,18 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
     red[2][warp] = e11;
   }
   __syncthreads();
-  if (tid != 0) return;
-  double rs = 0.0, es = 0.0, ee = 0.0;
-  for (int w = 0; w < nwarp; ++w) {
-    rs += red[0][w];
-    es += red[1][w];
-    ee += red[2][w];
+  // the warps' sums by a shuffle tree in warp 0 (fixed order)
+  if (warp != 0) return;
+  double rs = lane < nwarp ? red[0][lane] : 0.0, es = lane < nwarp ? red[1][lane] : 0.0,
+         ee = lane < nwarp ? red[2][lane] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    es += __shfl_xor_sync(0xffffffffu, es, o);
+    ee += __shfl_xor_sync(0xffffffffu, ee, o);
   }
-  const double res = sqrt(rs) / ctl->norm_a;
+  if (tid != 0) return;
+  const double res = sqrt(rs) / norm_a;
   const double corr = sqrt(es + ee);
-  const int it = ctl->iterations;
   if (bad || !isfinite(res) || !isfinite(corr)) {
     ctl->status = EIGREF_E_NONFINITE;
     ctl->nonfinite = 1;
@@ -473,18 +491,18 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
   ctl->last_corr = corr;
   ctl->iterations = it + 1;
   ctl->pending_norm = 1;
-  const double crit = ctl->stop == EIGREF_STOP_CORRECTION ? corr : res;
-  if (ctl->tol > 0.0 && crit <= ctl->tol) {
+  const double crit = stop == EIGREF_STOP_CORRECTION ? corr : res;
+  if (tol > 0.0 && crit <= tol) {
     ctl->status = EIGREF_OK;
     ctl->done = 1;
-  } else if (corr >= 1.0 || (corr > ctl->div_factor * ctl->emin && corr > ctl->div_floor)) {
+  } else if (corr >= 1.0 || (corr > div_factor * emin && corr > div_floor)) {
     ctl->status = EIGREF_E_DIVERGED;
     ctl->done = 1;
-  } else if (it + 1 >= ctl->max_iters) {
-    ctl->status = ctl->tol > 0.0 ? EIGREF_E_NOT_CONVERGED : EIGREF_OK;
+  } else if (it + 1 >= max_iters) {
+    ctl->status = tol > 0.0 ? EIGREF_E_NOT_CONVERGED : EIGREF_OK;
     ctl->done = 1;
   }
-  if (corr < ctl->emin) ctl->emin = corr;
+  if (corr < emin) ctl->emin = corr;
 }
 
 __global__ void __launch_bounds__(1024) finalize_kernel(SweepBufs b, int k) { finalize_body(b, k); }

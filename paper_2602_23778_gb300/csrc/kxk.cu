@@ -263,7 +263,7 @@ __device__ __forceinline__ void kk_load_panels(const double* __restrict__ A, boo
 // TT x TT output tile per CTA (TT^2 threads), one output per thread:
 // s = op(A)(i,:) . Bm(:,j), summed in the order l = 0, 1, ... for any TT.
 template <int MODE, int TT = 16>
-__device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, int by) {
+__device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, int by, int done = 0) {
   __shared__ double As[TT][kMaxK + 1];
   __shared__ double Bs[kMaxK][TT + 1];
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
@@ -274,6 +274,7 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
   const bool transA = (MODE == KG_YTE);
   kk_load_panels<TT>(A, transA, Bm, k, bx * TT, by * TT, As, Bs);
   __syncthreads();
+  if (done) return;
   double s = 0.0;
   for (int l = 0; l < k; ++l) s = fma(As[tx][l], Bs[l][ty], s);
   if (i >= k || j >= k) return;
@@ -291,10 +292,12 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
   (void)kk;
 }
 
+// The stop flag is loaded first and acted on after the panel loads, so the
+// two latencies overlap (reading the inputs of a finished run writes nothing).
 template <int MODE, int TT>
 __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
-  if (b.ctl->done) return;
-  kk_gemm_body<MODE, TT>(b, k, blockIdx.x, blockIdx.y);
+  const int done = b.ctl->done;
+  kk_gemm_body<MODE, TT>(b, k, blockIdx.x, blockIdx.y, done);
 }
 
 // E11 by the cases of line 6 of Algorithm 4, one block per column j, plus the
@@ -353,13 +356,14 @@ template <int TRANS, int TT = 16>
 __device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ A, const double* __restrict__ B,
                                                      const double* __restrict__ C0, double* __restrict__ C, int k,
                                                      double alpha, double beta, int add_i, double check, Control* ctl,
-                                                     int bx, int by) {
+                                                     int bx, int by, int done = 0) {
   __shared__ double As[TT][kMaxK + 1];
   __shared__ double Bs[kMaxK][TT + 1];
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
   const int i = bx * TT + tx, j = by * TT + ty;
   kk_load_panels<TT>(A, TRANS != 0, B, k, bx * TT, by * TT, As, Bs);
   __syncthreads();
+  if (done) return;
   double acc = 0.0;
   for (int l = 0; l < k; ++l) acc = fma(As[tx][l], Bs[l][ty], acc);
   if (i < k && j < k) {
@@ -381,8 +385,8 @@ __global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __re
                                                               const double* __restrict__ C0, double* __restrict__ C,
                                                               int k, double alpha, double beta, int add_i,
                                                               double check, Control* ctl) {
-  if (ctl->done) return;
-  kk_gemm_generic_body<TRANS, TT>(A, B, C0, C, k, alpha, beta, add_i, check, ctl, blockIdx.x, blockIdx.y);
+  const int done = ctl->done;   // acted on after the panel loads (see kk_gemm_kernel)
+  kk_gemm_generic_body<TRANS, TT>(A, B, C0, C, k, alpha, beta, add_i, check, ctl, blockIdx.x, blockIdx.y, done);
 }
 
 // Tiles of 8 for k >= 64 (a k x k product then spreads over 64+ SMs), else 16.
@@ -476,8 +480,8 @@ template <int MODE>
 __global__ void __launch_bounds__(256) kk_gemm_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
   const GroupItem& it = items[blockIdx.z];
   const SweepBufs& b = it.b[parity];
-  if ((int)blockIdx.x * 16 >= it.k || (int)blockIdx.y * 16 >= it.k || b.ctl->done) return;
-  kk_gemm_body<MODE>(b, it.k, blockIdx.x, blockIdx.y);
+  if ((int)blockIdx.x * 16 >= it.k || (int)blockIdx.y * 16 >= it.k) return;
+  kk_gemm_body<MODE>(b, it.k, blockIdx.x, blockIdx.y, b.ctl->done);   // the flag is acted on after the loads
 }
 
 // The products of the Newton-Schulz refresh and of M, N (see launch_kxk_stage).
@@ -488,13 +492,15 @@ __global__ void __launch_bounds__(256) kk_ns_grouped_kernel(const GroupItem* __r
   const GroupItem& it = items[blockIdx.z];
   const SweepBufs& b = it.b[parity];
   const int k = it.k;
-  if ((int)blockIdx.x * 16 >= k || (int)blockIdx.y * 16 >= k || b.ctl->done) return;
-  if (OP == NS_T1) kk_gemm_generic_body<0>(b.y1, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, blockIdx.x, blockIdx.y);
-  if (OP == NS_Z1) kk_gemm_generic_body<0>(b.zinv, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
-  if (OP == NS_T2) kk_gemm_generic_body<0>(b.y1, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, blockIdx.x, blockIdx.y);
-  if (OP == NS_Z2) kk_gemm_generic_body<0>(b.zinv2, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
-  if (OP == NS_M) kk_gemm_generic_body<0>(b.zinv, b.t1, nullptr, b.m, k, -1.0, 0.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
-  if (OP == NS_N) kk_gemm_generic_body<1>(b.zinv, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, blockIdx.x, blockIdx.y);
+  if ((int)blockIdx.x * 16 >= k || (int)blockIdx.y * 16 >= k) return;
+  const int done = b.ctl->done;   // acted on after the panel loads
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (OP == NS_T1) kk_gemm_generic_body<0>(b.y1, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, bx, by, done);
+  if (OP == NS_Z1) kk_gemm_generic_body<0>(b.zinv, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, bx, by, done);
+  if (OP == NS_T2) kk_gemm_generic_body<0>(b.y1, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, bx, by, done);
+  if (OP == NS_Z2) kk_gemm_generic_body<0>(b.zinv2, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, bx, by, done);
+  if (OP == NS_M) kk_gemm_generic_body<0>(b.zinv, b.t1, nullptr, b.m, k, -1.0, 0.0, 0, 0.0, b.ctl, bx, by, done);
+  if (OP == NS_N) kk_gemm_generic_body<1>(b.zinv, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, bx, by, done);
 }
 
 void launch_kxk_stage_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
