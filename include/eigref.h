@@ -144,7 +144,9 @@ typedef struct eigref_report {
                                  (W = B X) over the sweeps applied; else 0 */
   int64_t kernel_launches;    /* kernels launched by the call (graph replays included) */
   int product_launches;       /* product kernels timed in product_ms */
-  int psplit;                 /* split form: split-K of the product used (0: FP64 form) */
+  int psplit;                 /* split form: the product's K decomposition: 1..4 equal K splits a tile,
+                                 8 equal-work ranges of (row tile, K block) units, whole rounds of one
+                                 CTA per SM (0: FP64 form) */
   int ksplit;                 /* split form: split-K of the Gram products used */
 } eigref_report;
 

@@ -268,7 +268,9 @@ __device__ __forceinline__ double recombine(long long hi, long long lo, int er, 
 // nb and mb unused).  Ring, stage and accumulator counters run on across
 // the CTA's tiles, so the MMAs of one tile fill the second accumulator set
 // while the epilogue warps finish the previous one.
-template <int S, int MODE>
+// ITEMS false (the grouped kernels): one tile a CTA only, the code for the
+// persistent and equal-work item lists left out (it costs registers).
+template <int S, int MODE, bool ITEMS = true>
 __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CUtensorMap* tmB,
                                                 const CUtensorMap* tmB2, const MmaArgs& g, int nb, int mb, int zb,
                                                 int tgx = 0, int tiles = 0) {
@@ -288,17 +290,43 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   double* s_tr = reinterpret_cast<double*>(sx + kRX * kXTile + 1024);   // UPDATE: 8 warps x 32 x kTrStride
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column blocks vary fastest, so the CTAs sharing A-side rows run together
-  const bool persist = MODE == MODE_UPDATE && tiles > 0;
-  const int t_first = persist ? (int)blockIdx.x : 0;
-  const int t_end = persist ? tiles : 1;
-  const int t_step = persist ? (int)gridDim.x : 1;
   const int job = MODE == MODE_GRAM ? (zb & 1) : 0;
   const int split = MODE == MODE_GRAM ? (zb >> 1) : (MODE == MODE_PRODUCT ? zb : 0);
   const int nsplit = MODE == MODE_UPDATE ? 1 : g.ksplit;
-  const int kb_lo = (int)((int64_t)g.kb_total * split / nsplit);
-  const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / nsplit);
-  const int KB = kb_hi - kb_lo;                      // K blocks of this CTA
-  const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
+  const bool persist = ITEMS && MODE == MODE_UPDATE && tiles > 0;
+  const bool ranged = ITEMS && MODE == MODE_PRODUCT && g.sk_ranges > 0;
+  // Work items of this CTA in order: column block, row tile, first K block,
+  // K blocks and the slot of its exact partial.  By default one item: the
+  // CTA's tile, K split `split` of nsplit.  Persistent update: tiles
+  // blockIdx.x, blockIdx.x + gridDim.x, ...  Equal-work product: range mb
+  // (of sk_ranges equal ranges) of the (row tile, K block) units of column
+  // block nb, cut at row-tile boundaries (at most two items); an item's slot
+  // is mb less the range holding its tile's first unit.
+  struct Item {
+    int nb, mb, kb_lo, kb, slot;
+  };
+  auto item = [&](int w, Item& it) -> bool {
+    if (persist) {
+      const int t = (int)blockIdx.x + w * (int)gridDim.x;
+      if (t >= tiles) return false;
+      it = Item{t % tgx, t / tgx, 0, g.kb_total, 0};
+      return true;
+    }
+    if (ranged) {
+      const int64_t U = g.sk_units, R = g.sk_ranges, KBt = g.kb_total;
+      const int64_t u0 = (int64_t)mb * U / R, u1 = ((int64_t)mb + 1) * U / R;
+      const int64_t s0 = w == 0 ? u0 : (u0 / KBt + w) * KBt;
+      if (s0 >= u1) return false;
+      const int64_t e0 = min((s0 / KBt + 1) * KBt, u1);
+      const int64_t first = (((s0 / KBt) * KBt + 1) * R - 1) / U;
+      it = Item{nb, (int)(s0 / KBt), (int)(s0 % KBt), (int)(e0 - s0), (int)(mb - first)};
+      return true;
+    }
+    if (w > 0) return false;
+    const int lo = (int)((int64_t)g.kb_total * split / nsplit);
+    it = Item{nb, mb, lo, (int)((int64_t)g.kb_total * (split + 1) / nsplit) - lo, split};
+    return true;
+  };
   constexpr int NBUF = 2;                            // TMEM accumulator sets: 2 x S x 32 <= 512 columns
   static_assert(2 * kMaxS * kBN <= 512, "two accumulator sets must fit in TMEM");
   const CUtensorMap* tB = job ? tmB2 : tmB;
@@ -342,11 +370,12 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       int as = 0;
       uint32_t aph = 0;                              // lap parity of the A ring
       int gkb = 0;                                   // K blocks over the CTA's tiles (X stage and parity)
-      for (int ti = t_first; ti < t_end && ok; ti += t_step) {
-        const int nbt = persist ? ti % tgx : nb;
-        const int m0 = (persist ? ti / tgx : mb) * kBM;
-        for (int kb = 0; kb < KB && ok; ++kb, ++gkb) {
-          const int kx = (kb_lo + kb) * kBK;         // K coordinate (elements)
+      Item it;
+      for (int w = 0; ok && item(w, it); ++w) {
+        const int nbt = it.nb;
+        const int m0 = it.mb * kBM;
+        for (int kb = 0; kb < it.kb && ok; ++kb, ++gkb) {
+          const int kx = (it.kb_lo + kb) * kBK;      // K coordinate (elements)
           const int xs = gkb & 1;
           ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb >> 1) & 1) ^ 1, abort_flag);
           if (!ok) break;
@@ -387,7 +416,10 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       int as = 0;
       uint32_t aph = 0;
       int gkb = 0, gc = 0;                           // K blocks and chunks over the CTA's tiles
-      for (int ti = t_first; ti < t_end && ok; ti += t_step, gc += NC) {
+      Item it;
+      for (int w = 0; ok && item(w, it); ++w) {
+        const int KB = it.kb;
+        const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
         for (int kb = 0; kb < KB && ok; ++kb, ++gkb) {
           const int c = gc + kb / kChunkBlocks;
           const int buf = NBUF == 2 ? (c & 1) : 0;
@@ -440,6 +472,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           tc_commit(smem_u32(&bars->x_empty[xs]));
           if (last) tc_commit(smem_u32(&bars->acc_full[buf]));
         }
+        gc += NC;
       }
       if (!ok) {
         // wait for the MMAs already issued before the CTA releases TMEM
@@ -454,9 +487,11 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
     constexpr int kC = kBN / 2;
     bool ok = true;
     int gc = 0;                                        // chunks over the CTA's tiles
-    for (int ti = t_first; ti < t_end; ti += t_step, gc += NC) {
-      const int nbt = persist ? ti % tgx : nb;
-      const int mbt = persist ? ti / tgx : mb;
+    Item it;
+    for (int w = 0; item(w, it); ++w) {
+      const int nbt = it.nb;
+      const int mbt = it.mb;
+      const int NC = (it.kb + kChunkBlocks - 1) / kChunkBlocks;
       const int64_t row = (int64_t)mbt * kBM + lg * 32 + lane;
       long long hi[kC], lo[kC];
 #pragma unroll
@@ -509,6 +544,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[buf]));
       }
+      gc += NC;
       const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
       const int* cexp = job ? g.colexp2 : g.colexp;
       if constexpr (MODE == MODE_UPDATE) {
@@ -556,7 +592,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         }
         ssq += __shfl_xor_sync(0xffffffffu, ssq, 16);   // the two half-warps share the columns
         srq += __shfl_xor_sync(0xffffffffu, srq, 16);
-        const int tp = ((ti - t_first) / t_step) & 1;   // tile parity: the buffer of this tile's sums
+        const int tp = w & 1;                            // tile parity: the buffer of this tile's sums
         if (lane < kC) {
           s_colsum[tp][0][lg][half * kC + lane] = ssq;
           s_colsum[tp][1][lg][half * kC + lane] = srq;
@@ -583,14 +619,14 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           const bool live = ok && row < g.m_valid && col < g.k;
           // split-K partials stay exact int64 pairs: the sum over splits is exact,
           // so the result does not depend on how K was split
-          const bool raw = (MODE == MODE_GRAM) || (MODE == MODE_PRODUCT && nsplit > 1);
+          const bool raw = (MODE == MODE_GRAM) || (MODE == MODE_PRODUCT && (nsplit > 1 || ranged));
           const double w = (live && !raw) ? recombine<S>(hi[j], lo[j], er, cexp[col]) : 0.0;
           if (MODE == MODE_PRODUCT) {
             if (live) {
-              if (nsplit == 1)
+              if (nsplit == 1 && !ranged)
                 g.P[row * g.k + col] = w - g.shift * g.Xs[row * g.k + col];
               else
-                g.ppart[(int64_t)split * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
+                g.ppart[(int64_t)it.slot * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
             }
           } else {
             if (live) g.gpart[((int64_t)(job * nsplit + split) * g.k + col) * g.k + row] = make_longlong2(hi[j], lo[j]);
@@ -656,8 +692,8 @@ __global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const _
   while (t + 1 < p.count && c >= p.cta_begin[t + 1]) ++t;
   const int local = c - p.cta_begin[t];
   const int gx = p.gx[t], gy = p.gy[t];
-  sliced_mma_body<S, MODE>(&p.tmA[t], &p.tmB[t], &p.tmB2[t], p.args[t], local % gx, (local / gx) % gy,
-                           local / (gx * gy));
+  sliced_mma_body<S, MODE, false>(&p.tmA[t], &p.tmB[t], &p.tmB2[t], p.args[t], local % gx, (local / gx) % gy,
+                                  local / (gx * gy));
 }
 
 // ---------------------------------------------------------------------------
@@ -1363,15 +1399,23 @@ __global__ void slice_rows_grouped_kernel(const GroupItem* __restrict__ items, i
                      ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
-// P = (exact sum of the split partial products) - shift Xs.
+// P = (exact sum of the split partial products) - shift Xs.  Fixed splits:
+// ksplit partials an element.  Equal-work ranges (R > 0): the ranges that
+// touch the element's row tile (U units of kbt K blocks a column block).
 template <int S>
 __global__ void product_reduce_kernel(const longlong2* __restrict__ part, int ksplit, const int* __restrict__ rowexp,
                                       const int* __restrict__ colexp, int k, const double* __restrict__ Xs,
-                                      double* __restrict__ P, int64_t total, double shift, const Control* ctl) {
+                                      double* __restrict__ P, int64_t total, double shift, const Control* ctl,
+                                      int64_t R, int64_t U, int64_t kbt) {
   if (ctl && ctl->done) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     long long hi = 0, lo = 0;
-    for (int q = 0; q < ksplit; ++q) {
+    int nq = ksplit;
+    if (R > 0) {
+      const int64_t u = (e / k) / kBM * kbt;   // first unit of the row tile
+      nq = (int)(((u + kbt) * R - 1) / U - ((u + 1) * R - 1) / U) + 1;
+    }
+    for (int q = 0; q < nq; ++q) {
       const longlong2 v = part[(int64_t)q * total + e];
       hi += v.x;
       lo += v.y;
@@ -2290,7 +2334,7 @@ static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int k
 }
 
 size_t SlicedA::layout_total() const {
-  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_).total;
+  return sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_).total;
 }
 
 int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int precision, int slices) {
@@ -2322,21 +2366,8 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
   k_pad_ = (k + 31) / 32 * 32;
   kr_ = (k + 63) / 64 * 64;
   // Gram split-K: about two CTAs per SM in total (2 jobs x k_pad/32 column blocks)
-  // product split-K: the count of CTA rounds (one CTA per SM) wastes least
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t ctas = (int64_t)(k_pad_ / 32) * (n_pad_ / 128);
-  double best = 0.0;
-  psplit_ = 1;
-  for (int p = 1; p <= 4; ++p) {
-    if ((n_pad_ / 64) / p < 8) break;                  // keep at least two chunks per CTA
-    const int64_t c = ctas * p;
-    const double eff = (double)c / (double)(sms * ((c + sms - 1) / sms));
-    if (eff > best + 0.02) {
-      best = eff;
-      psplit_ = p;
-    }
-  }
   const int per_split = 2 * (k_pad_ / 32);
   ksplit_ = (304 + per_split - 1) / per_split;
   const int kbt = n_pad_ / sl::kBK;
@@ -2347,11 +2378,25 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
   for (int p = 2; p <= 4; ++p)
     if ((n_pad_ / 64) / p >= 8) psplit_max_ = p;
   ksplit_max_ = std::min(kbt, 2 * ksplit_);
+  // Equal-work product: each column block's gy x kbt (row tile, K block)
+  // units cut into R equal ranges, R a whole number of rounds of one CTA per
+  // SM with ranges no longer than a row tile (a range then covers at most two
+  // tiles); small problems take at most 3 gy ranges, so that a tile meets at
+  // most 4 ranges (the workspace's partial slots).
+  {
+    const int gx = k_pad_ / 32, gy = n_pad_ / sl::kBM;
+    const int q = std::max(1, sms / gx);
+    sk_units_ = (long long)gy * kbt;
+    sk_ranges_ = gy < q ? std::min<long long>(q, 3LL * gy) : (long long)q * ((gy + q - 1) / q);
+  }
+  pslots_ = 4;
+  psplit_ = kPsplitBalanced;
   return EIGREF_OK;
 }
 
 std::vector<int> SlicedA::psplit_candidates() const {
   std::vector<int> v;
+  if (pslots_ >= 4) v.push_back(kPsplitBalanced);
   for (int p = 1; p <= psplit_max_; ++p) v.push_back(p);
   return v;
 }
@@ -2365,7 +2410,7 @@ std::vector<int> SlicedA::ksplit_candidates() const {
 }
 
 void SlicedA::set_splits(int psplit, int ksplit) {
-  psplit_ = std::max(1, std::min(psplit, psplit_max_));
+  psplit_ = (psplit == kPsplitBalanced && pslots_ >= 4) ? kPsplitBalanced : std::max(1, std::min(psplit, psplit_max_));
   ksplit_ = std::max(1, std::min(ksplit, ksplit_max_));
 }
 
@@ -2373,7 +2418,7 @@ size_t SlicedA::workspace_bytes() const { return layout_total(); }
 
 void SlicedA::share_gpu(int problems) {
   if (problems <= 1) return;
-  psplit_ = psplit_max_ = 1;
+  psplit_ = psplit_max_ = pslots_ = 1;
   const int kbt = n_pad_ / sl::kBK;
   ksplit_ = ksplit_max_ = std::max(1, std::min(kbt, n_pad_ / 4096));
 }
@@ -2381,7 +2426,7 @@ void SlicedA::share_gpu(int problems) {
 void SlicedA::bind_workspace(char* p) { ws_ = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023)); }
 
 int SlicedA::prepare(cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   auto* ap = reinterpret_cast<__half*>(ws_ + L.a_planes);
   // B-side and row planes: zero once, so padding rows and columns stay zero
   if (cudaMemsetAsync(ws_ + L.x_planes, 0, L.xr_rowexp - L.x_planes, s) != cudaSuccess ||
@@ -2440,7 +2485,7 @@ static void launch_product_reduce(int S, const MmaTask& t, int psplit, const dou
   const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
 #define EIGREF_CALL_PR(S_)                                                                                   \
   sl::product_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.ppart, psplit, t.g.rowexp, t.g.colexp, t.g.k, Xs, P, total, \
-                                                   shift, ctl)
+                                                   shift, ctl, t.g.sk_ranges, t.g.sk_units, t.g.kb_total)
   EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_PR)
 #undef EIGREF_CALL_PR
 }
@@ -2466,7 +2511,7 @@ static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
 
 MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Control* ctl, const double* Xs,
                               bool b_from_p) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   MmaTask t;
   t.a = *reinterpret_cast<const CUtensorMap*>(tmA_);
   t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(b_from_p ? tmP_ : tmX_);
@@ -2483,16 +2528,25 @@ MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Co
   g.Xs = Xs ? Xs : X;
   g.P = P;
   g.shift = shift;
-  g.ksplit = psplit_;
   g.ppart = reinterpret_cast<longlong2*>(ws_ + L.ppart);
   t.gx = k_pad_ / sl::kBN;
-  t.gy = n_pad_ / sl::kBM;
-  t.gz = psplit_;
+  if (psplit_ == kPsplitBalanced) {
+    // grid (column blocks, ranges): range blockIdx.y of column block blockIdx.x
+    g.ksplit = 1;
+    g.sk_ranges = (int)sk_ranges_;
+    g.sk_units = sk_units_;
+    t.gy = (int)sk_ranges_;
+    t.gz = 1;
+  } else {
+    g.ksplit = psplit_;
+    t.gy = n_pad_ / sl::kBM;
+    t.gz = psplit_;
+  }
   return t;
 }
 
 MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   MmaTask t;
   t.a = *reinterpret_cast<const CUtensorMap*>(tmXA_);
   t.b = *reinterpret_cast<const CUtensorMap*>(tmX_);
@@ -2518,7 +2572,7 @@ MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
 
 MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, const double* dinv, double* Xn,
                              double* upart, const Control* ctl) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   MmaTask t;
   t.a = *reinterpret_cast<const CUtensorMap*>(tmXR_);
   t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(tmF_);
@@ -2545,7 +2599,7 @@ MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, 
 }
 
 void SlicedA::fill_group_item(GroupItem* it) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   it->n_pad = n_pad_;
   it->k_pad = k_pad_;
   it->kr = kr_;
@@ -2566,7 +2620,7 @@ void SlicedA::fill_group_item(GroupItem* it) const {
 
 int SlicedA::product(const double* X, double* P, double shift, const Control* ctl, cudaStream_t s, cudaEvent_t ev0,
                      cudaEvent_t ev1, unsigned ev_flags) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   auto* xp = reinterpret_cast<__half*>(ws_ + L.x_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
   int* colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
@@ -2588,7 +2642,7 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
 
 int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, const Control* ctl, cudaStream_t s,
                         cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   const int64_t total = n_ * k_;
   const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   // T = A X: X's column planes in the X slot (kept for gram())
@@ -2619,7 +2673,7 @@ int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, con
 }
 
 int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   auto* pp = reinterpret_cast<__half*>(ws_ + L.p_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
@@ -2645,7 +2699,7 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
 
 int SlicedA::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
                     double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   auto* xr = reinterpret_cast<__half*>(ws_ + L.xr_planes);
   auto* fp = reinterpret_cast<__half*>(ws_ + L.f_planes);
   int* xrexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
@@ -2757,7 +2811,7 @@ void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims
 int SlicedA::update_grid() const { return n_pad_ / sl::kBM; }
 
 int SlicedA::timed_out(cudaStream_t s) const {
-  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, psplit_max_, n_);
+  const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   int v = 0;
   cudaMemcpyAsync(&v, ws_ + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);

@@ -41,6 +41,8 @@ struct MmaArgs {
   double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
   const Control* ctl;
   int* err;              // set to 1 on a timed-out wait
+  int sk_ranges;         // PRODUCT: > 0: equal-work ranges of (row tile, K block) units per column block
+  long long sk_units;    // PRODUCT with sk_ranges: units per column block (row tiles x K blocks)
 };
 }  // namespace sl
 
@@ -109,9 +111,13 @@ class SlicedA {
   // Tensor-core flops one product executes (all digit pairs, padded sizes).
   double executed_flops() const;
   int slices() const { return slices_; }
-  // Split-K of the product (psplit) and of the Gram products (ksplit).  The
-  // split partials are exact, so any choice gives the same results bitwise;
-  // only the time differs (what the autotuner measures).
+  // K decomposition of the product (psplit) and split-K of the Gram products
+  // (ksplit).  psplit 1..4: that many equal K splits a tile; kPsplitBalanced:
+  // equal-work ranges over (row tile, K block) units, as many as make whole
+  // rounds of one CTA per SM.  The partials are exact, so any choice gives
+  // the same results bitwise; only the time differs (what the autotuner
+  // measures).
+  static constexpr int kPsplitBalanced = 8;
   std::vector<int> psplit_candidates() const;
   std::vector<int> ksplit_candidates() const;
   void set_splits(int psplit, int ksplit);
@@ -125,6 +131,8 @@ class SlicedA {
   int64_t n_ = 0, lda_ = 0;
   int k_ = 0, precision_ = 0, slices_ = 0;
   int n_pad_ = 0, k_pad_ = 0, kr_ = 0, ksplit_ = 1, psplit_ = 1, ksplit_max_ = 1, psplit_max_ = 1;
+  int pslots_ = 4;                      // product partial slots a tile in the workspace
+  long long sk_ranges_ = 0, sk_units_ = 0;   // the equal-work plan (ranges and units a column block)
   char* ws_ = nullptr;
   alignas(64) unsigned char tmA_[128];
   alignas(64) unsigned char tmX_[128];
