@@ -22,7 +22,9 @@
 // scaled operands.  (Eight-bit digits: 36 plane pairs for 63 bits, against
 // 45 with seven-bit digits.)
 //
-// Kernel: one CTA per 128 rows x 32 columns of W.  Warp 0 issues TMA loads
+// Kernel: a CTA owns 128 rows x 32 columns of W over a range of K (the
+// product's equal-work plan: a range of (row tile, K block) units, at most
+// two tiles; the row update: a persistent list of tiles).  Warp 0 issues TMA loads
 // (A digit tiles 128 x 64 per plane, X digit tiles of all S planes stacked:
 // 32 S rows x 64), warp 1 issues tcgen05.mma (M = 128, N = 32 (S - s) for A
 // plane s: one instruction covers every X plane that pairs with it, writing
