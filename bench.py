@@ -529,6 +529,7 @@ def main():
                       "slices": (args.slices or 8) if precision != "fp64" else None,
                       "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
                       "parallelism": "replicas" if world > 1 else "single",
+                      # product: 1..4 equal K splits a tile, 8 the equal-work plan (whole CTA rounds)
                       "split_k": {"product": rep["psplit"], "gram": rep["ksplit"]} if precision != "fp64" else None},
            "setup_ms": rep["setup_ms"], "call_s": call_s, "roofline": roof,
            "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary()}
