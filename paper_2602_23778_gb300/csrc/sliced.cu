@@ -68,7 +68,7 @@ struct LoExp {
 };
 constexpr int kRX = 2;             // X ring stages
 constexpr int kATile = kBM * kBK * 2;                // 16 KiB
-constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 36 KiB (all planes of a K block)
+constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 32 KiB (all planes of a K block)
 constexpr int kEpiWarps = 8;       // two warps per TMEM lane group, 16 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kNonFinite = -100000;  // exponent marking a row / column holding Inf or NaN
