@@ -123,6 +123,11 @@ typedef struct eigref_params {
                           candidates of its tensor-core product and Gram products and keeps the
                           fastest on the handle (results are identical for every choice: the split
                           partials are exact).  0: the built-in choice. */
+  double wait_limit_s; /* limit, in seconds, of every bounded wait inside the tensor-core kernels
+                          (a pipeline stage that never arrives); <= 0: 2 s.  A wait that runs out
+                          ends its kernel early and the call returns EIGREF_E_TIMEOUT with X at
+                          the last completed iterate; the handle stays usable.  A tiny limit
+                          (1e-9) gives up at the first wait that is not already complete. */
 } eigref_params;
 
 /* Report of one refinement call.  The three array pointers are optional,
@@ -152,7 +157,8 @@ typedef struct eigref_report {
 
 /* Defaults: LARGEST_MAG, norm_a computed, max_iters 100, tol 0, correction
  * criterion, FP64, beta cluster, delta_c 10, div 10 / 1e-4, check 32,
- * sign_fix 1, use_graph 1, profile 0, rayleigh_ritz 0, judge_cols 0, reorth 0, resign 0, autotune 1. */
+ * sign_fix 1, use_graph 1, profile 0, rayleigh_ritz 0, judge_cols 0, reorth 0, resign 0, autotune 1,
+ * wait_limit_s 0 (2 s). */
 void eigref_params_default(eigref_params* p);
 
 /* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -243,10 +249,9 @@ int eigref_product_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* c
 /* P = (A - shift I) X in FP64, like eigref_product_dense with precision
  * EIGREF_FP64, but without allocating any device memory.  The paper has no
  * counterpart: this is for callers that cannot call cudaMalloc at the point
- * they need the product -- code running while a CUDA graph is being captured
- * on its stream (an allocation there would break or invalidate the capture),
- * or code inside a framework or plugin whose memory pool owns the device and
- * forbids allocations behind its back.
+ * they need the product -- code inside a framework or plugin whose memory
+ * pool owns the device and forbids allocations behind its back, or code on a
+ * path where an allocation's implicit device synchronisation is not allowed.
  *
  * A, X, P: device pointers on the current CUDA device (host memory is
  * rejected), layouts as in eigref_product_dense, n * k <= 2^20.  Work is
@@ -255,14 +260,17 @@ int eigref_product_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* c
  *
  * Scratch: a fixed 16 MiB array of device memory inside the library, which
  * every GPU that loads the library holds until the process exits.  The first
- * call on a device looks up that array's address (cudaGetSymbolAddress), so
- * make one call on each device before any stream capture.  All calls share
- * the array and it keeps the last call's contents; calls whose work overlaps
- * on the GPU (different streams, or different host threads) race on it, so
- * serialise them.  Nothing in it needs to start at zero: each call writes
- * every entry it reads.
+ * call on a device looks up that array's address (cudaGetSymbolAddress) and
+ * keeps it, so make one call on each device before any stream capture; a
+ * cudaDeviceReset of that device makes the kept address stale.  All calls
+ * share the array and it keeps the last call's contents; calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it, so serialise them.  Nothing in it needs to start at zero: each call
+ * writes every entry it reads.
  * Errors: EIGREF_E_INVALID (NULL or foreign pointers, sizes out of range,
- * n * k above the limit), EIGREF_E_CUDA (address look-up or launch failed). */
+ * n * k above the limit), EIGREF_E_CUDA (a CUDA error was already pending on
+ * the calling thread -- left pending for its owner --, or the address look-up
+ * or a launch of this call failed). */
 int eigref_product_dense_noalloc(const double* A, int64_t n, int64_t lda,
                                  const double* X, int64_t ldx, int k, double shift,
                                  double* P, int64_t ldp, void* cuda_stream);

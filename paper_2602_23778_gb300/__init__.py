@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
                 ("delta_c", ctypes.c_double), ("div_factor", ctypes.c_double), ("div_floor", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("sign_fix", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("rayleigh_ritz", ctypes.c_int), ("judge_cols", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("resign", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("resign", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("wait_limit_s", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -116,6 +117,13 @@ def sliced_info(precision, n, k, slices=8):
             "executed_flops": 2.0 * n_pad * n_pad * k_pad * pairs,
             "a_plane_bytes": 2.0 * slices * n_pad * n_pad}
 
+def _same_shape(name, got, want):
+    """Refuse an output or operand whose shape does not match before anything
+    reaches the library (a narrow P would be written past its end)."""
+    if tuple(got) != tuple(want):
+        raise ValueError("%s is %s, expected %s" % (name, "x".join(map(str, got)), "x".join(map(str, want))))
+
+
 def product_dense_noalloc(A, X, P, shift=0.0, stream=None):
     """P = (A - shift I) X through eigref_product_dense_noalloc: FP64, device
     arrays only, queued on ``stream`` (torch stream, raw handle or None) with
@@ -123,6 +131,8 @@ def product_dense_noalloc(A, X, P, shift=0.0, stream=None):
     pa, n, lda, ka = _dense_a(A)
     px, nx, k, ldx, kx = _colmajor(X)
     pp, np_, kp, ldp, kpp = _colmajor(P, "P")
+    _same_shape("X", (nx, k), (n, k))
+    _same_shape("P", (np_, kp), (n, k))
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
@@ -312,10 +322,11 @@ class Handle:
         G, S k x k column-major, written in place."""
         px, n, k, ldx, kx = _colmajor(X)
         pp, n2, k2, ldp, kp = _colmajor(P, "P")
-        pg, _, _, _, kg = _colmajor(G, "G")
-        ps, _, _, _, ks = _colmajor(S, "S")
-        if n2 != n or k2 != k:
-            raise ValueError("X and P shapes differ")
+        pg, ng, kg_, _, kg = _colmajor(G, "G")
+        ps, ns, ks_, _, ks = _colmajor(S, "S")
+        _same_shape("P", (n2, k2), (n, k))
+        _same_shape("G", (ng, kg_), (k, k))
+        _same_shape("S", (ns, ks_), (k, k))
         prec = PRECISIONS[precision] if isinstance(precision, str) else precision
         st = lib().eigref_gram(self._h, px, ldx, pp, ldp, n, k, prec, int(slices), pg, ps)
         if st != OK:
@@ -326,6 +337,8 @@ class Handle:
         pa, n, lda, ka = _dense_a(A)
         px, nx, k, ldx, kx = _colmajor(X)
         pp, np_, kp, ldp, kpp = _colmajor(P, "P")
+        _same_shape("X", (nx, k), (n, k))
+        _same_shape("P", (np_, kp), (n, k))
         prec = PRECISIONS[precision] if isinstance(precision, str) else precision
         st = lib().eigref_product_dense(self._h, pa, n, lda, px, ldx, k, float(shift), prec, int(slices), pp, ldp)
         if st != OK:
@@ -338,6 +351,9 @@ class Handle:
         pv, nnz2, k3 = _f64vec(val, "val")
         px, n, k, ldx, kx = _colmajor(X)
         pp, np_, kp, ldp, kpp = _colmajor(P, "P")
+        if n1 != n + 1 or nnz2 != nnz:
+            raise ValueError("inconsistent CSR sizes")
+        _same_shape("P", (np_, kp), (n, k))
         st = lib().eigref_product_csr(self._h, prp, pci, pv, n, nnz, px, ldx, k, float(shift), pp, ldp)
         if st != OK:
             raise EigrefError(st, self.last_error())

@@ -103,6 +103,7 @@ struct Params {
   int target, max_iters, stop, precision, slices, beta, check_every, sign_fix, use_graph, profile, rayleigh_ritz,
       judge_cols, reorth, resign, autotune;
   double shift, norm_a, tol, delta_c, div_factor, div_floor;
+  unsigned long long wait_ns;  // bounded waits of the tensor-core kernels (0: their default)
 };
 
 int read_params(eigref_ctx* h, const eigref_params* p, Params* q) {
@@ -131,6 +132,9 @@ int read_params(eigref_ctx* h, const eigref_params* p, Params* q) {
   q->reorth = p->reorth;
   q->resign = p->resign;
   q->autotune = p->autotune;
+  q->wait_ns = p->wait_limit_s > 0.0 && isfinite(p->wait_limit_s)
+                   ? (unsigned long long)std::max(1.0, std::min(p->wait_limit_s, 3600.0) * 1e9)
+                   : 0ull;
   if (q->judge_cols < 0) return set_err(h, EIGREF_E_INVALID, "judge_cols < 0");
   if (q->target < EIGREF_LARGEST_MAG || q->target > EIGREF_SMALLEST_MAG)
     return set_err(h, EIGREF_E_INVALID, "target %d out of range", q->target);
@@ -214,7 +218,7 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
     launch_top_gram(b.x, b.p, k, b.gtop, b.ctl, s);
     launch_kxk_stage(b, k, delta, beta_zero, s);
     // the row update on the tensor cores where this k has it, else in FP64
-    if (pr.sgram->update(b.x, b.p, b.f, b.d, b.dinv, b.xn, b.upart, b.ctl, s) > 0) {
+    if (pr.sgram->update(b.x, b.p, b.f, b.m, b.d, b.dinv, b.xn, b.upart, b.ctl, s) > 0) {
       b.ugrid = pr.sgram->update_grid();
     } else {
       launch_update_rows(b, n, k, s);
@@ -239,7 +243,7 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   launch_kxk_stage(b, k, delta, beta_zero, s);
   launches += b.mixed ? 12 : 9;
   if (pr.sliced) {
-    pr.sliced->update(b.x, b.p, b.f, b.d, b.dinv, b.xn, b.upart, b.ctl, s);
+    pr.sliced->update(b.x, b.p, b.fm, b.d, b.dinv, b.xn, b.upart, b.ctl, s);
     launches += 4;
   } else {
     launch_update_rows(b, n, k, s);
@@ -301,11 +305,13 @@ void run_layout(Run& r, Carve& c, Control* ctl) {
   double** mats[] = {&b.r1, &b.t1, &b.z, &b.y1, &b.lu, &b.m, &b.v1, &b.w2, &b.e11, &b.yte, &b.nmat, &b.f, &b.res,
                      &b.zinv, &b.zinv2};
   for (double** m : mats) *m = c.take<double>(kk);
+  // the dense split form's row update reads F and M as one interleaved panel
+  b.fm = (r.pr.sliced != nullptr) ? c.take<double>((int64_t)k * kfm_cols(k)) : nullptr;
   b.piv = c.take<int>(k);
-  double** vecs[] = {&b.alpha, &b.d, &b.dinv, &b.cz, &b.cw, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
+  double** vecs[] = {&b.alpha, &b.d, &b.dinv, &b.nu, &b.r1sq, &b.e11sq, &b.x1sq};
   for (double** v : vecs) *v = c.take<double>(k);
   r.sigma = c.take<double>(k);
-  b.upart = c.take<double>((int64_t)r.ugrid * 2 * k);
+  b.upart = c.take<double>((int64_t)r.ugrid * 3 * k);
   b.hist_res = c.take<double>(r.hist_len);
   b.hist_corr = c.take<double>(r.hist_len);
   b.ctl = ctl ? ctl : c.take<Control>(1);
@@ -386,6 +392,8 @@ int run_setup_device(eigref_ctx* h, Run& r, cudaStream_t s) {
   }
   const int64_t ldu = r.x_dev ? r.ldx : n;
   r.sg = nullptr;
+  // the [F | M] panel's padding columns (past k in its last block) stay zero
+  if (r.b.fm) CUDA_TRY(h, cudaMemsetAsync(r.b.fm, 0, sizeof(double) * (size_t)k * kfm_cols(k), s));
   if (!r.q.rayleigh_ritz) {
     if (r.q.sign_fix) {
       launch_sign_fix(xu, ldu, k, r.sigma, nullptr, s);
@@ -546,6 +554,8 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   const int64_t n = pr.n;
   const int k = pr.k;
   cudaStream_t s = h->stream;
+  if (r.pr.sliced) r.pr.sliced->set_wait_ns(q.wait_ns);
+  if (r.pr.sgram) r.pr.sgram->set_wait_ns(q.wait_ns);
   r.X = X;
   r.ldx = ldx;
   r.x_dev = is_device_ptr(X);
@@ -988,6 +998,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
       st = sls[i].configure(pb.A, pb.n, pb.lda, pb.k, q.precision, q.slices);
       if (st) return set_err(h, st, "problem %d: %s", i, sls[i].error());
       sls[i].share_gpu(count);
+      sls[i].set_wait_ns(q.wait_ns);
       r.pr.sliced = &sls[i];
     }
     run_plan(r);

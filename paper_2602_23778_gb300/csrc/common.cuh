@@ -48,10 +48,12 @@ struct SweepBufs {
   double* g2;         // [2][k*k]: G2 = X2^T X2, S2 = X2^T P2 (rows >= k)
   double *r1, *t1, *z, *y1, *lu, *m, *v1, *w2, *e11, *yte, *nmat, *f, *res;  // k x k
   double *zinv, *zinv2;  // k x k: Y1^{-1} kept across sweeps (split form) and a scratch copy
+  double* fm;         // split form, dense: k x kfm(k) column-major, F and M interleaved in blocks of 16
+                      // columns (block q: F(:, 16q .. 16q+15), then M(:, 16q .. 16q+15)), or null
   int mixed;          // 1: Y1^{-1} by Newton-Schulz updates instead of an LU per sweep
   int* piv;           // [k]
-  double *alpha, *d, *dinv, *cz, *cw, *nu, *r1sq, *e11sq, *x1sq;  // [k]
-  double* upart;      // update partials [ugrid][2k]
+  double *alpha, *d, *dinv, *nu, *r1sq, *e11sq, *x1sq;  // [k]
+  double* upart;      // update partials [ugrid][3k]: column sums of x'^2, r^2, v2^2
   double *hist_res, *hist_corr;  // [max_iters]
   Control* ctl;
   int nchunks;
@@ -78,6 +80,11 @@ struct GroupItem {
   unsigned long long *x_cmax, *p_cmax, *f_cmax;
   void* sgpart;              // tensor-core Gram partials: [2][ksplit][k k] exact (hi, lo) int64 pairs
 };
+
+// Columns of the interleaved [F | M] panel: 32 per 16 columns of k.
+__host__ __device__ inline int kfm_cols(int k) { return 32 * ((k + 15) / 16); }
+// Column of the panel that holds F(:, j) (M(:, j) is 16 further).
+__host__ __device__ inline int kfm_col(int j) { return 32 * (j >> 4) + (j & 15); }
 
 // Extent of a grouped launch: blockIdx.z = problem, x/y sized for the largest.
 struct GroupDims {

@@ -268,7 +268,11 @@ void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1
 // ---------------------------------------------------------------------------
 // Row update below the leading block (rows k..n-1), folded form of line 7:
 //   x' = x + (w - x o d) / d - x F,   F = M D^-1 + N
-// with per-CTA partial column sums of x'^2 and of the residual r = w - x o d.
+// with per-CTA partial column sums of x'^2, of the residual r = w - x o d and
+// of the rows of V2 = R2 - X2 M (E21 = V2 D^-1, the lower block of E-tilde_L
+// in line 6): ||E21||_F is formed from explicit rows, as the stopping test of
+// Section 3.1.3 reads it, not from k x k Gram quantities (whose difference
+// cancels once the correction falls below sqrt(u)).
 // ---------------------------------------------------------------------------
 constexpr int UPD_ROWS = 16;     // rows per step at k = 128; smaller k takes UPD_ROWS * 128 / k
 constexpr int UPD_GRID = 2 * 152;
@@ -276,101 +280,131 @@ constexpr int UPD_GRID = 2 * 152;
 int update_rows_grid() { return UPD_GRID; }
 
 __host__ __device__ inline int update_rows_per_step(int k) { return (UPD_ROWS * kMaxK) / k > 0 ? (UPD_ROWS * kMaxK) / k : 1; }
+// Column parts: above 64 columns a CTA takes half of them, so that its panels
+// of F and M (k x columns each) fit in shared memory together.
+__host__ __device__ inline int update_rows_parts(int k) { return k > 64 ? 2 : 1; }
+__host__ __device__ inline int update_rows_cols(int k) { return (k + update_rows_parts(k) - 1) / update_rows_parts(k); }
 
+// CTA (g, h): row blocks g, g + gridDim.x, ... and columns h kc .. h kc + kc - 1.
 // Column sums are formed in a fixed order (no atomics), so results are
-// bitwise reproducible run to run.
+// bitwise reproducible run to run.  upart[g][3k]: sums of x'^2, r^2, v2^2.
 __global__ void __launch_bounds__(256) update_rows_kernel(const double* __restrict__ X,
                                                           const double* __restrict__ P,
                                                           double* __restrict__ Xn, int64_t n, int k,
                                                           const double* __restrict__ F,
+                                                          const double* __restrict__ M,
                                                           const double* __restrict__ d,
                                                           double* __restrict__ upart, const Control* ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ double sm[];
-  const int rb = update_rows_per_step(k);   // rows per step: rb k ~ 2048 outputs
-  double* Fs = sm;                          // Fs[l * k + j] = F(l, j)
-  double* xs = Fs + k * k;                  // [rb][k]
-  double* sq = xs + rb * k;                 // [rb][k]: x'^2
-  double* rq = sq + rb * k;                 // [rb][k]: r^2
-  double* dinv = rq + rb * k;               // [k]
-  double* dv = dinv + k;                    // [k]
+  const int kc = update_rows_cols(k);
+  const int j0 = (int)blockIdx.y * kc;
+  const int jn = min(kc, k - j0);           // columns of this CTA
+  const int rb = update_rows_per_step(k);   // rows per step: rb k ~ 2048 inputs
+  double* Fs = sm;                          // Fs[l * kc + jj] = F(l, j0 + jj)
+  double* Ms = Fs + k * kc;                 // Ms[l * kc + jj] = M(l, j0 + jj)
+  double* xs = Ms + k * kc;                 // [rb][k]: whole rows of X
+  double* sq = xs + rb * k;                 // [rb][jn]: x'^2
+  double* rq = sq + rb * kc;                // [rb][jn]: r^2
+  double* vq = rq + rb * kc;                // [rb][jn]: v2^2
+  double* dinv = vq + rb * kc;              // [jn]
+  double* dv = dinv + kc;                   // [jn]
   const int tid = threadIdx.x;
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    int l = e % k, j = e / k;               // F column-major
-    Fs[l * k + j] = F[e];
+  for (int e = tid; e < k * jn; e += blockDim.x) {
+    const int l = e % k, jj = e / k;        // F, M column-major
+    Fs[l * kc + jj] = F[l + (int64_t)(j0 + jj) * k];
+    Ms[l * kc + jj] = M[l + (int64_t)(j0 + jj) * k];
   }
-  for (int j = tid; j < k; j += blockDim.x) {
-    dv[j] = d[j];
-    dinv[j] = 1.0 / d[j];
+  for (int jj = tid; jj < jn; jj += blockDim.x) {
+    dv[jj] = d[j0 + jj];
+    dinv[jj] = 1.0 / d[j0 + jj];
   }
-  // column sums: thread tid owns column tid % k and rows tid / k, tid / k + gstride, ...
-  const int gstride = blockDim.x / k > 0 ? blockDim.x / k : 1;
-  const int scol = tid % k, srow0 = tid / k;
-  double accx = 0.0, accr = 0.0;
+  // column sums: thread tid owns column tid % jn and rows tid / jn, tid / jn + gstride, ...
+  const int gstride = blockDim.x / jn > 0 ? blockDim.x / jn : 1;
+  const int scol = tid % jn, srow0 = tid / jn;
+  double accx = 0.0, accr = 0.0, accv = 0.0;
   __syncthreads();
   const int64_t rows = n - k;
   const int64_t nblk = (rows + rb - 1) / rb;
-  const int per = rb * k;
+  const int per = rb * jn;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     const int64_t row0 = k + b * rb;
-    for (int e = tid; e < per; e += blockDim.x) {
+    for (int e = tid; e < rb * k; e += blockDim.x) {
       int64_t row = row0 + e / k;
       xs[e] = row < n ? X[row0 * k + e] : 0.0;
     }
     __syncthreads();
     for (int e = tid; e < per; e += blockDim.x) {
-      int r = e / k, j = e % k;
-      int64_t row = row0 + r;
-      double xn = 0.0, rr = 0.0;
+      const int r = e / jn, jj = e % jn, j = j0 + jj;
+      const int64_t row = row0 + r;
+      double xn = 0.0, rr = 0.0, v = 0.0;
       if (row < n) {
         const double* xr = xs + r * k;
-        double x = xr[j];
-        rr = P[row * k + j] - x * dv[j];
-        double s = 0.0;
-        for (int l = 0; l < k; ++l) s = fma(xr[l], Fs[l * k + j], s);
-        xn = x + rr * dinv[j] - s;
+        const double x = xr[j];
+        rr = P[row * k + j] - x * dv[jj];
+        double s = 0.0, sm2 = 0.0;
+        for (int l = 0; l < k; ++l) {
+          s = fma(xr[l], Fs[l * kc + jj], s);
+          sm2 = fma(xr[l], Ms[l * kc + jj], sm2);
+        }
+        xn = x + rr * dinv[jj] - s;
+        v = rr - sm2;                       // row of V2 = R2 - X2 M
         Xn[row * k + j] = xn;
       }
       sq[e] = xn * xn;
       rq[e] = rr * rr;
+      vq[e] = v * v;
     }
     __syncthreads();
-    if (srow0 < gstride && tid < gstride * k)
+    if (srow0 < gstride && tid < gstride * jn)
       for (int r = srow0; r < rb; r += gstride) {
-        accx += sq[r * k + scol];
-        accr += rq[r * k + scol];
+        accx += sq[r * jn + scol];
+        accr += rq[r * jn + scol];
+        accv += vq[r * jn + scol];
       }
     __syncthreads();
   }
   // combine the gstride partial sums of each column in a fixed order
-  __shared__ double cs[2][256];
+  __shared__ double cs[3][256];
   cs[0][tid] = accx;
   cs[1][tid] = accr;
+  cs[2][tid] = accv;
   __syncthreads();
-  if (tid < k) {
-    double sx = 0.0, sr = 0.0;
+  if (tid < jn) {
+    double sx = 0.0, sr = 0.0, sv = 0.0;
     for (int g = 0; g < gstride; ++g) {
-      sx += cs[0][g * k + tid];
-      sr += cs[1][g * k + tid];
+      sx += cs[0][g * jn + tid];
+      sr += cs[1][g * jn + tid];
+      sv += cs[2][g * jn + tid];
     }
-    upart[(int64_t)blockIdx.x * 2 * k + tid] = sx;
-    upart[(int64_t)blockIdx.x * 2 * k + k + tid] = sr;
+    double* up = upart + (int64_t)blockIdx.x * 3 * k + j0 + tid;
+    up[0] = sx;
+    up[k] = sr;
+    up[2 * k] = sv;
   }
 }
 
 static size_t update_smem(int k) {
-  return sizeof(double) * ((size_t)k * k + 3 * (size_t)update_rows_per_step(k) * k + 2 * (size_t)k);
+  const size_t kc = (size_t)update_rows_cols(k), rb = (size_t)update_rows_per_step(k);
+  return sizeof(double) * (2 * (size_t)k * kc + rb * (size_t)k + 3 * rb * kc + 2 * kc);
+}
+
+static size_t update_smem_max() {
+  size_t m = 0;
+  for (int k = 1; k <= kMaxK; ++k) m = std::max(m, update_smem(k));
+  return m;
 }
 
 void launch_update_rows(const SweepBufs& b, int64_t n, int k, cudaStream_t s) {
   size_t smem = update_smem(k);
-  update_rows_kernel<<<UPD_GRID, 256, smem, s>>>(b.x, b.p, b.xn, n, k, b.f, b.d, b.upart, b.ctl);
+  update_rows_kernel<<<dim3(UPD_GRID, update_rows_parts(k)), 256, smem, s>>>(b.x, b.p, b.xn, n, k, b.f, b.m, b.d,
+                                                                              b.upart, b.ctl);
 }
 
 // ---------------------------------------------------------------------------
 // Per-sweep statistics and control (one CTA).
 //   ||R||_F^2  = sum_j r1sq_j + sum_blocks r^2
-//   ||E||_F^2  = ||E11||_F^2 + sum_j (||r2_j||^2 - 2 (M^T Z)_jj + (M^T G2 M)_jj) / d_j^2
+//   ||E||_F^2  = ||E11||_F^2 + sum_j ||v2_j||^2 / d_j^2   (E21 = V2 D^-1, rows of V2 summed by the update)
 //   nu_j = 1 / ||x'_j||
 // Stopping, divergence and non-finite tests of Section 3.1.3 / Section 4.3.1.
 // ---------------------------------------------------------------------------
@@ -397,14 +431,15 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
     emin = ctl->emin;
     bad = 0;
   }
-  // column sums of the update partials [ugrid][2k]: thread (grp, c) adds
+  // column sums of the update partials [ugrid][3k]: thread (grp, c) adds
   // partials grp, grp + groups, ... of column c (consecutive threads read
   // consecutive addresses), then the groups are added in order; fixed order,
   // so the result is reproducible
   __shared__ double part_s[1024];
   __shared__ double top_s[1024];
+  __shared__ double v2_s[kMaxK];
   {
-    const int w2 = 2 * k, groups = (int)blockDim.x / w2;
+    const int w2 = 3 * k, groups = (int)blockDim.x / w2;
     if (tid < groups * w2) {
       const int c = tid % w2, grp = tid / w2;
       double acc = 0.0;
@@ -428,14 +463,16 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
     __syncthreads();
     if (tid < k) {
       const int j = tid;
-      double xsq = 0.0, r2 = 0.0;
+      double xsq = 0.0, r2 = 0.0, v2 = 0.0;
       for (int grp = 0; grp < groups; ++grp) {
         xsq += part_s[grp * w2 + j];
         r2 += part_s[grp * w2 + k + j];
+        v2 += part_s[grp * w2 + 2 * k + j];
       }
       for (int grp = 0; grp < g2; ++grp) xsq += top_s[grp * k + j];
       xsq_s[j] = xsq;
       r2_s[j] = r2;
+      v2_s[j] = v2;
     }
   }
   if (done) {
@@ -447,9 +484,9 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
   if (tid < k) {
     const int j = tid;
     const double xsq = xsq_s[j], r2 = r2_s[j], dj = b.d[j];
-    const double e21 = (r2 - 2.0 * b.cz[j] + b.cw[j]) / (dj * dj);
+    const double e21 = v2_s[j] / (dj * dj);   // ||E21(:, j)||^2 from the explicit rows of V2
     // the correction of the judged leading columns decides stop and divergence
-    esum = (j < judge && e21 > 0.0) ? e21 : 0.0;
+    esum = j < judge ? e21 : 0.0;
     rsum = b.r1sq[j] + r2;
     e11 = j < judge ? b.e11sq[j] : 0.0;
     b.nu[j] = 1.0 / sqrt(xsq);
@@ -519,7 +556,7 @@ void launch_finalize_grouped(const GroupItem* items, const GroupDims& gd, int pa
 
 cudaError_t init_fp64_attributes() {
   return cudaFuncSetAttribute(update_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)update_smem(kMaxK));
+                              (int)update_smem_max());
 }
 
 void launch_finalize(const SweepBufs& b, int k, double, cudaStream_t s) {

@@ -287,7 +287,13 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
     b.yte[e] = s + (b.z[e] - b.w2[e]) / b.d[j];
   } else {
     b.xn[(int64_t)i * k + j] = b.x[(int64_t)i * k + j] + b.e11[e] - s;
-    b.f[e] = b.m[e] / b.d[j] + b.nmat[e];
+    const double f = b.m[e] / b.d[j] + b.nmat[e];
+    b.f[e] = f;
+    if (b.fm) {   // the tensor-core update's operand: F and M side by side (X2 F and X2 M in one pass)
+      const int64_t c = kfm_col(j);
+      b.fm[i + c * k] = f;
+      b.fm[i + (c + 16) * k] = b.m[e];
+    }
   }
   (void)kk;
 }
@@ -301,12 +307,12 @@ __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
 }
 
 // E11 by the cases of line 6 of Algorithm 4, one block per column j, plus the
-// column sums the finalize step needs: ||E11(:,j)||^2, (M^T Z)_jj, (M^T G2 M)_jj.
+// column sum the finalize step needs: ||E11(:,j)||^2.
 __device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double delta, int beta_zero, int j, int vb) {
   __shared__ double sh[32];
   const int64_t kk = (int64_t)k * k;
   const double dj = b.d[j];
-  double es = 0.0, cz = 0.0, cw = 0.0;
+  double es = 0.0;
   for (int i = threadIdx.x; i < k && (int)threadIdx.x < vb; i += vb) {
     const int64_t e = i + (int64_t)j * k;
     const double di = b.d[i];
@@ -320,18 +326,9 @@ __device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double de
     }
     b.e11[e] = v;
     es += v * v;
-    const double mij = b.m[e];
-    cz += mij * b.z[e];
-    cw += mij * b.w2[e];
   }
   es = block_sum(es, sh, vb);
-  cz = block_sum(cz, sh, vb);
-  cw = block_sum(cw, sh, vb);
-  if (threadIdx.x == 0) {
-    b.e11sq[j] = es;
-    b.cz[j] = cz;
-    b.cw[j] = cw;
-  }
+  if (threadIdx.x == 0) b.e11sq[j] = es;
   (void)kk;
 }
 

@@ -21,15 +21,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in,
-// never a device address.
-int scratch_for_current_device(double** out) {
+// Device address of g_noalloc_scratch on the current device (returned in
+// *dev), looked up once per device and cached.  In host code the array's name
+// is only a host-side stand-in, never a device address.  A cudaDeviceReset of
+// the device makes the cached address stale; the library does not detect it.
+int scratch_for_current_device(double** out, int* dev_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return EIGREF_E_CUDA;
   }
+  *dev_out = dev;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
@@ -63,11 +65,14 @@ extern "C" int eigref_product_dense_noalloc(const double* A, int64_t n, int64_t 
   if (!A || !X || !P) return EIGREF_E_INVALID;
   if (n < 1 || k < 1 || lda < n || ldx < n || ldp < n) return EIGREF_E_INVALID;
   if (n * (int64_t)k > kNoAllocMaxElems) return EIGREF_E_INVALID;  // beyond the fixed scratch
+  // An error already pending on this thread belongs to the caller's earlier
+  // work: report it without consuming it, so that the check after the
+  // launches below sees only this call's own launches.
+  if (cudaPeekAtLastError() != cudaSuccess) return EIGREF_E_CUDA;
   double* scratch = nullptr;
-  int st = scratch_for_current_device(&scratch);
-  if (st) return st;
   int dev = 0;
-  cudaGetDevice(&dev);
+  int st = scratch_for_current_device(&scratch, &dev);
+  if (st) return st;
   if (!on_device(A, dev) || !on_device(X, dev) || !on_device(P, dev)) return EIGREF_E_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* xi = scratch;                     // every entry written by copy_in before it is read

@@ -83,10 +83,19 @@ __host__ __device__ constexpr int smem_bytes(int mode) {
   return mode == 0 ? kSmemBytesProduct : (mode == 2 ? kSmemBytesUpdate : kSmemBytes);
 }
 
+// A CTA's abort flag and the limit of each of its bounded waits (shared
+// memory).  The limit comes from the launch's arguments (0: kTimeoutNs); a
+// limit below 100 us is checked on every poll, so that a tiny one gives up at
+// the first wait that is not already complete.
+struct WaitState {
+  volatile int abort;
+  unsigned long long limit_ns;
+};
+
 struct __align__(8) Bars {
   uint64_t a_full[kRAProduct], a_empty[kRAProduct], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
-  int abort;
+  WaitState wait;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -115,16 +124,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ void wait_state_init(WaitState* w, unsigned long long limit_ns) {
+  w->abort = 0;
+  w->limit_ns = limit_ns ? limit_ns : kTimeoutNs;
+}
 // Bounded wait: false when the CTA is aborting or the wait ran past the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, WaitState* w) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
+  const uint64_t lim = w->limit_ns;
+  const uint32_t mask = lim < 100000ull ? 0u : 63u;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 0) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > kTimeoutNs) {
-        *abort_flag = 1;
+    if ((it & mask) == 0) {
+      if (w->abort) return false;
+      if (globaltimer() - t0 > lim) {
+        w->abort = 1;
         return false;
       }
     }
@@ -133,16 +148,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // The same with a short sleep between polls after the first few: for waits
 // that are long against the work of the other warps on the SM (the spinning
 // lanes would take their issue slots).
-__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, WaitState* w) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
+  const uint64_t lim = w->limit_ns;
+  const uint32_t mask = lim < 100000ull ? 0u : 15u;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (it > 8) __nanosleep(128);
-    if ((it & 15) == 0) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > kTimeoutNs) {
-        *abort_flag = 1;
+    if (it > 8 && mask) __nanosleep(128);
+    if ((it & mask) == 0) {
+      if (w->abort) return false;
+      if (globaltimer() - t0 > lim) {
+        w->abort = 1;
         return false;
       }
     }
@@ -278,7 +295,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
                                                 int tgx = 0, int tiles = 0) {
   // one read of the stop flag per CTA: an aborting CTA of this grid may set it
   __shared__ int s_skip;
-  __shared__ double s_colsum[2][2][4][kBN];         // UPDATE: per lane-group column sums, by tile parity
+  __shared__ double s_colsum[2][3][4][kBN / 2];     // UPDATE: per lane-group column sums, by tile parity
   if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
   __syncthreads();
   if (s_skip) return;
@@ -332,7 +349,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   constexpr int NBUF = 2;                            // TMEM accumulator sets: 2 x S x 32 <= 512 columns
   static_assert(2 * kMaxS * kBN <= 512, "two accumulator sets must fit in TMEM");
   const CUtensorMap* tB = job ? tmB2 : tmB;
-  volatile int* abort_flag = &bars->abort;
+  WaitState* wst = &bars->wait;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < RA; ++i) {
@@ -348,7 +365,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       mbar_init(smem_u32(&bars->acc_empty[i]), kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bars->drain), 1);
-    bars->abort = 0;
+    wait_state_init(&bars->wait, g.wait_ns);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -379,7 +396,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         for (int kb = 0; kb < it.kb && ok; ++kb, ++gkb) {
           const int kx = (it.kb_lo + kb) * kBK;      // K coordinate (elements)
           const int xs = gkb & 1;
-          ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb >> 1) & 1) ^ 1, abort_flag);
+          ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb >> 1) & 1) ^ 1, wst);
           if (!ok) break;
           mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
 #pragma unroll
@@ -389,7 +406,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           ++issued_x;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, abort_flag);
+            ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, wst);
             if (!ok) break;
             mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
             tma_load_2d(smem_u32(sa + as * kATile), tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
@@ -428,12 +445,12 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           const bool first = (kb % kChunkBlocks) == 0;
           const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
           if (first) {
-            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, abort_flag);
+            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, wst);
             if (!ok) break;
             tc_fence_after();
           }
           const int xs = gkb & 1;
-          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb >> 1) & 1, abort_flag);
+          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb >> 1) & 1, wst);
           if (!ok) break;
           tc_fence_after();
           const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
@@ -441,7 +458,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, abort_flag);
+            ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, wst);
             if (!ok) break;
             tc_fence_after();
             const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
@@ -501,7 +518,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       if (MODE == MODE_UPDATE && row < g.m_valid && row >= g.row_begin) {
         // the row's X and W values the update reads after the drain: into L1
         // while the MMAs run (128 contiguous bytes each)
-        const int64_t e0 = row * g.k + nbt * kBN + half * kC;
+        const int64_t e0 = row * g.k + nbt * kC;
         asm volatile("prefetch.global.L1 [%0];" ::"l"(g.X + e0));
         asm volatile("prefetch.global.L1 [%0];" ::"l"(g.W + e0));
       }
@@ -511,7 +528,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         // one lane waits, the warp follows (the TMEM loads below are warp-collective);
         // it sleeps between polls, leaving issue slots to the MMA warp
         int w_ok = 0;
-        if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, abort_flag);
+        if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, wst);
         ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
         __syncwarp();
         if (!ok) break;
@@ -550,16 +567,21 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
       const int* cexp = job ? g.colexp2 : g.colexp;
       if constexpr (MODE == MODE_UPDATE) {
-        // X' = X + (W - X D) D^-1 - X F.  Each lane recombines its row of
-        // X F (16 columns); the warp's 32 x 16 block then turns through
-        // shared memory, so that a half-warp holds 16 consecutive columns
-        // of one row and every global load and store of X, W and X' moves
-        // 128-byte rows (one row per lane would touch 32 rows an access).
-        // X, W, d and 1/d are read-only in this launch (X' is another buffer).
-        const int c0 = nbt * kBN + half * kC;
+        // The B operand interleaves F and M by 16 columns, so column block nbt
+        // covers the real columns c0 .. c0 + 15 with X F in the first half of
+        // the tile (warps of half 0) and X M in the second (half 1).
+        //   half 0:  X' = X + (W - X D) D^-1 - X F   (written), sums of X'^2 and R^2
+        //   half 1:  V2 = R2 - X2 M                  (the rows of E21 D), sums of V2^2
+        // Each lane recombines its row of X F or X M (16 columns); the warp's
+        // 32 x 16 block then turns through shared memory, so that a half-warp
+        // holds 16 consecutive columns of one row and every global load and
+        // store of X, W and X' moves 128-byte rows (one row per lane would
+        // touch 32 rows an access).  X, W, d and 1/d are read-only in this
+        // launch (X' is another buffer).
+        const int c0 = nbt * kC;
         const int cl = c0 + (lane & (kC - 1));           // this lane's column after the turn
         const bool cok = cl < g.k;
-        const int e_l = cok ? __ldg(cexp + cl) : 0;
+        const int e_l = cok ? __ldg(cexp + nbt * kBN + half * kC + (lane & (kC - 1))) : 0;
         double* tr = s_tr + (warp - 2) * 32 * kTrStride;
         __syncwarp();                                    // the last tile's reads of tr are done
 #pragma unroll
@@ -580,24 +602,35 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           xv[i] = lv ? __ldg(g.X + r * g.k + cl) : 0.0;
           wv[i] = lv ? __ldg(g.W + r * g.k + cl) : 0.0;
         }
-        double ssq = 0.0, srq = 0.0;                     // column sums of X'^2 and (W - X D)^2, rows in order
+        // column sums, rows in order: half 0 of X'^2 and (W - X D)^2, half 1 of V2^2
+        double s0 = 0.0, s1 = 0.0;
 #pragma unroll
         for (int i = 0; i < kC; ++i) {
           const int64_t r = r0 + 2 * i;
           if (ok && cok && r < g.m_valid && r >= g.row_begin) {
             const double rr = wv[i] - xv[i] * dj;
-            const double xn = xv[i] + rr * dij - tr[(2 * i + (lane >> 4)) * kTrStride + (lane & (kC - 1))];
-            g.Xn[r * g.k + cl] = xn;
-            ssq = fma(xn, xn, ssq);
-            srq = fma(rr, rr, srq);
+            const double t = tr[(2 * i + (lane >> 4)) * kTrStride + (lane & (kC - 1))];
+            if (half == 0) {
+              const double xn = xv[i] + rr * dij - t;
+              g.Xn[r * g.k + cl] = xn;
+              s0 = fma(xn, xn, s0);
+              s1 = fma(rr, rr, s1);
+            } else {
+              const double v = rr - t;
+              s0 = fma(v, v, s0);
+            }
           }
         }
-        ssq += __shfl_xor_sync(0xffffffffu, ssq, 16);   // the two half-warps share the columns
-        srq += __shfl_xor_sync(0xffffffffu, srq, 16);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 16);     // the two half-warps share the columns
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
         const int tp = w & 1;                            // tile parity: the buffer of this tile's sums
         if (lane < kC) {
-          s_colsum[tp][0][lg][half * kC + lane] = ssq;
-          s_colsum[tp][1][lg][half * kC + lane] = srq;
+          if (half == 0) {
+            s_colsum[tp][0][lg][lane] = s0;
+            s_colsum[tp][1][lg][lane] = s1;
+          } else {
+            s_colsum[tp][2][lg][lane] = s0;
+          }
         }
         // the eight epilogue warps meet; the first two add the four lane
         // groups' sums of the tile.  A warp writes buffer tp again two tiles
@@ -605,13 +638,13 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         // passed.
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
         const int et = (int)threadIdx.x - 64;
-        if (et < 2 * kBN) {
-          const int which = et / kBN, cc = et % kBN;
-          const int col = nbt * kBN + cc;
+        if (et < 3 * kC) {
+          const int which = et / kC, cc = et % kC;
+          const int col = c0 + cc;
           if (col < g.k) {
             const double v = s_colsum[tp][which][0][cc] + s_colsum[tp][which][1][cc] + s_colsum[tp][which][2][cc] +
                              s_colsum[tp][which][3][cc];
-            g.upart[(int64_t)mbt * 2 * g.k + which * g.k + col] = v;
+            g.upart[(int64_t)mbt * 3 * g.k + which * g.k + col] = v;
           }
         }
       } else {
@@ -639,7 +672,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   }
   tc_fence_before();
   __syncthreads();
-  if (bars->abort && threadIdx.x == 0) {
+  if (bars->wait.abort && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     if (g.ctl) {
       Control* c = const_cast<Control*>(g.ctl);
@@ -726,12 +759,13 @@ struct Gram16Args {
   longlong2* part;         // [2][ksplit][k k] exact partials, column-major k x k
   const Control* ctl;
   int* err;
+  unsigned long long wait_ns;   // limit of every bounded wait (0: the default)
 };
 
 struct __align__(8) Bars16 {
   uint64_t full[kG16Stages], empty[kG16Stages], acc_full, acc_empty, drain;
   uint32_t tmem_base;
-  int abort;
+  WaitState wait;
 };
 
 template <int S>
@@ -754,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
   const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / g.ksplit);
   const int KB = kb_hi - kb_lo;
   const int NC = (KB + kG16Chunk - 1) / kG16Chunk;
-  volatile int* abort_flag = &bars->abort;
+  WaitState* wst = &bars->wait;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kG16Stages; ++i) {
       mbar_init(smem_u32(&bars->full[i]), 1);
@@ -763,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
     mbar_init(smem_u32(&bars->acc_full), 1);
     mbar_init(smem_u32(&bars->acc_empty), kEpiWarps);
     mbar_init(smem_u32(&bars->drain), 1);
-    bars->abort = 0;
+    wait_state_init(&bars->wait, g.wait_ns);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -786,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
       int issued = 0;
       for (int kb = 0; kb < KB && ok; ++kb) {
         const int st = kb % kG16Stages, lap = kb / kG16Stages;
-        ok = mbar_wait(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), abort_flag);
+        ok = mbar_wait(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), wst);
         if (!ok) break;
         const int kx = (kb_lo + kb) * kBK;
         mbar_expect_tx(smem_u32(&bars->full[st]), (uint32_t)(2 * kTileBytes));
@@ -807,12 +841,12 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
         const bool first = (kb % kG16Chunk) == 0;
         const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
         if (first && c > 0) {   // one accumulator set: the previous chunk must be drained
-          ok = mbar_wait(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), abort_flag);
+          ok = mbar_wait(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), wst);
           if (!ok) break;
           tc_fence_after();
         }
         const int st = kb % kG16Stages, lap = kb / kG16Stages;
-        ok = mbar_wait(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);
+        ok = mbar_wait(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst);
         if (!ok) break;
         tc_fence_after();
         const uint64_t xd = smem_desc(smem_u32(smem + st * kG16Stage));
@@ -848,7 +882,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
     constexpr int kT0 = (S + 1) / 2;             // half 0 takes planes t < kT0, half 1 the rest
     for (int c = 0; c < NC && ok; ++c) {
       int w_ok = 0;
-      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full), (uint32_t)(c & 1), abort_flag);
+      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full), (uint32_t)(c & 1), wst);
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       __syncwarp();
       if (!ok) break;
@@ -910,7 +944,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
   }
   tc_fence_before();
   __syncthreads();
-  if (bars->abort && threadIdx.x == 0) {
+  if (bars->wait.abort && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     if (g.ctl) {
       Control* c = const_cast<Control*>(g.ctl);
@@ -1343,18 +1377,25 @@ enum { OPD_XCOLS = 0, OPD_PCOLS = 1, OPD_FCOLS = 2 };
 __global__ void zero_cmax_grouped_kernel(const GroupItem* __restrict__ items) {
   const GroupItem& it = items[blockIdx.x];
   if (it.b[0].ctl->done) return;
-  for (int j = threadIdx.x; j < it.k; j += blockDim.x) it.x_cmax[j] = it.p_cmax[j] = it.f_cmax[j] = 0ull;
+  for (int j = threadIdx.x; j < it.k; j += blockDim.x) it.x_cmax[j] = it.p_cmax[j] = 0ull;
+  for (int j = threadIdx.x; j < kfm_cols(it.k); j += blockDim.x) it.f_cmax[j] = 0ull;
 }
+
+// Columns of operand OP and the plane rows between its digit planes: the
+// [F | M] panel of the row update has kfm_cols(k) of both, X and P have k
+// columns in planes of k_pad rows.
+__device__ __forceinline__ int grouped_cols(const GroupItem& it, int op) { return op == OPD_FCOLS ? kfm_cols(it.k) : it.k; }
+__device__ __forceinline__ int grouped_kp(const GroupItem& it, int op) { return op == OPD_FCOLS ? kfm_cols(it.k) : it.k_pad; }
 
 // Operand OP of problem `it` in sweep parity `parity`: rows, row / column strides.
 __device__ __forceinline__ const double* grouped_operand(const GroupItem& it, int parity, int op, int64_t* rows,
                                                         int64_t* rs, int64_t* cs, unsigned long long** cmax,
                                                         __half** planes, int** colexp, int* K) {
   const SweepBufs& b = it.b[parity];
-  if (op == OPD_FCOLS) {   // F is k x k column-major: element (l, j) at F[l + j k]
+  if (op == OPD_FCOLS) {   // the [F | M] panel, k x kfm column-major: element (l, c) at FM[l + c k]
     *rows = it.k; *rs = 1; *cs = it.k; *cmax = it.f_cmax;
     *planes = static_cast<__half*>(it.f_planes); *colexp = it.f_colexp; *K = it.kr;
-    return b.f;
+    return b.fm;
   }
   *rows = it.n; *rs = it.k; *cs = 1;
   *K = it.n_pad;
@@ -1376,7 +1417,7 @@ __global__ void colmax_grouped_kernel(const GroupItem* __restrict__ items, int p
   int* colexp;
   int K;
   const double* Y = grouped_operand(it, parity, OP, &rows, &rs, &cs, &cmax, &planes, &colexp, &K);
-  colmax_body(Y, rows, it.k, rs, cs, cmax, blockIdx.x, gridDim.x);
+  colmax_body(Y, rows, grouped_cols(it, OP), rs, cs, cmax, blockIdx.x, gridDim.x);
 }
 
 template <int S, int OP>
@@ -1388,8 +1429,9 @@ __global__ void __launch_bounds__(256) slice_cols_grouped_kernel(const GroupItem
   int* colexp;
   int K;
   const double* Y = grouped_operand(it, parity, OP, &rows, &rs, &cs, &cmax, &planes, &colexp, &K);
-  if ((int)blockIdx.x * 64 >= K || (int)blockIdx.y * 32 >= it.k_pad || it.b[0].ctl->done) return;
-  slice_cols_body<S>(Y, rows, it.k, rs, cs, K, it.k_pad, cmax, planes, colexp, blockIdx.x, blockIdx.y);
+  const int kp = grouped_kp(it, OP);
+  if ((int)blockIdx.x * 64 >= K || (int)blockIdx.y * 32 >= kp || it.b[0].ctl->done) return;
+  slice_cols_body<S>(Y, rows, grouped_cols(it, OP), rs, cs, K, kp, cmax, planes, colexp, blockIdx.x, blockIdx.y);
 }
 
 template <int S>
@@ -1556,11 +1598,13 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __ha
 //   warp 1     tcgen05.mma.  A = the S row digit planes of the X tile stacked
 //              along K (plane s at K = 16 s .. 16 s + 15, exponent e_i per
 //              row); B = the S column digit planes of F stacked along N
-//              (plane t at N = 16 t .., exponent f_j per column).  The
-//              instruction for plane s takes B rows 0 .. 16 (S - s) - 1 and
-//              writes TMEM columns 16 s ..: column 16 w + j then holds the sum
-//              of every pair (s, t) with s + t = w, the pairs of one weight
-//              only, exact in FP32 (at most 8 pairs x 16 x 2^14 = 2^21).
+//              (plane t at N = 16 t .., exponent f_j per column), then those
+//              of M (rows 128 ..).  The instruction for plane s takes B rows
+//              0 .. 16 (S - s) - 1 and writes TMEM columns 16 s ..: column
+//              16 w + j then holds the sum of every pair (s, t) with s + t = w,
+//              the pairs of one weight only, exact in FP32 (at most 8 pairs x
+//              16 x 2^14 = 2^21); a second instruction does the same for M
+//              into columns 128 + 16 s ...
 //   warps 2-5  one thread per tile row: cut the X row into the A operand
 //              (running up to two tiles ahead of the epilogue).
 //   warps 6-13 two threads per tile row (warps w and w + 4 share a TMEM lane
@@ -1568,8 +1612,9 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __ha
 //              each (X F)_ij with integer arithmetic up to its bit pattern,
 //              form x' = x + (w - x d_j) / d_j - (X F)_ij in FP64, write it
 //              over the X tile in shared memory and store it with TMA (32 rows
-//              per lane group), keeping the column sums of x'^2 and
-//              (w - x d_j)^2.
+//              per lane group), keeping the column sums of x'^2,
+//              (w - x d_j)^2 and v^2, v = (w - x d_j) - (X M)_ij the row of
+//              V2 = R2 - X2 M (E21 = V2 D^-1, line 6 of Algorithm 4).
 // Accumulators and A operands are double-
 // buffered, the X / W tiles triple-buffered.  Every wait is bounded; on expiry
 // the CTA records a timeout.  No FP64 instruction outside the update formula
@@ -1580,7 +1625,8 @@ constexpr int kU16Tile = 128 * 128;                // 128 rows x 16 FP64: 16 KiB
 constexpr int kU16Stage = 2 * kU16Tile;           // X tile, W tile
 constexpr int kU16ABlock = kBM * kBK * 2;         // 128 rows x 64 K F16 (four planes)
 constexpr int kU16ABuf = ((kMaxS + 3) / 4) * kU16ABlock;   // planes 0..7, four per block
-constexpr int kU16BBytes = 16 * kMaxS * 128;      // 128 rows (t, j) of 128 B; K = l in the first 32 B
+constexpr int kU16BRows = 16 * kMaxS;             // rows (t, j) of one operand's planes
+constexpr int kU16BBytes = 2 * kU16BRows * 128;   // F's then M's rows of 128 B; K = l in the first 32 B
 constexpr int kU16SliceWarps = 4;                 // one thread per tile row
 constexpr int kU16EpiWarps = 8;                   // two threads per tile row
 constexpr int kU16Threads = 64 + 32 * (kU16SliceWarps + kU16EpiWarps);
@@ -1592,12 +1638,14 @@ struct Upd16Args {
   int row_begin;        // rows below it (the leading block) are left alone
   int tiles;            // ceil(n / 128); the grid is at most this
   const double* F;      // k x k column-major
+  const double* M;      // k x k column-major (V2 = R2 - X2 M)
   const double* d;
   const double* dinv;
   double* Xn;           // plain stores of the one tile that holds rows below row_begin
-  double* upart;        // [gridDim.x][2k]: column sums of x'^2, then of (w - x d)^2
+  double* upart;        // [gridDim.x][3k]: column sums of x'^2, of (w - x d)^2, of v^2
   const Control* ctl;
   int* err;
+  unsigned long long wait_ns;   // limit of every bounded wait (0: the default)
 };
 
 struct __align__(8) BarsU16 {
@@ -1605,7 +1653,7 @@ struct __align__(8) BarsU16 {
   // four: the second warp of a group can run up to two tiles ahead)
   uint64_t full[kU16Stages], empty[kU16Stages], a_full[2], a_empty[2], acc_full[2], acc_empty[2], sub[4][4], drain;
   uint32_t tmem_base;
-  int abort;
+  WaitState wait;
 };
 
 // Byte offset of 16-byte chunk c of row r in a tile of 128-byte rows with the
@@ -1628,6 +1676,39 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
                  "=r"(r[7])                                                                          \
                : "r"(taddr))
 
+// One lane's 8 columns of one accumulator set of update16 into two exact int64
+// sums (digit-pair groups w < 4 and w >= 4), the weights taken in pairs
+// (w, w + 1) within each group: C_w 2^8 + C_(w+1) stays below 2^30.
+template <int S>
+__device__ __forceinline__ void drain_u16(uint32_t tl, long long (&hi)[8], long long (&lo)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
+  int pend[8];
+#pragma unroll
+  for (int w = 0; w < S; ++w) {
+    uint32_t v[8];
+    TC_LD8(tl + 16 * w, v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int base = w < 4 ? 0 : 4;                       // first weight of its group
+    const int end = w < 4 ? (S < 4 ? S : 4) : S;           // one past its group's last
+    const bool first = ((w - base) & 1) == 0;
+    const bool paired = first ? (w + 1 < end) : true;
+    const int last_w = first ? (paired ? w + 1 : w) : w;   // weight of the pair's low digit
+    const int sh = w < 4 ? kBits * (3 - last_w) : kBits * (S - 1 - last_w);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cw = int_of_f32(v[j]);
+      if (first && paired) {
+        pend[j] = cw;
+      } else {
+        const int pr = first ? cw : pend[j] * (1 << kBits) + cw;
+        if (w < 4) hi[j] += (long long)pr << sh;
+        else lo[j] += (long long)pr << sh;
+      }
+    }
+  }
+}
+
 template <int S>
 __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_constant__ CUtensorMap tmX,
                                                                   const __grid_constant__ CUtensorMap tmW,
@@ -1640,13 +1721,13 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
   unsigned char* abuf0 = smem + kU16Stages * kU16Stage;
   unsigned char* bop = abuf0 + 2 * kU16ABuf;
   BarsU16* bars = reinterpret_cast<BarsU16*>(bop + kU16BBytes);
-  __shared__ int fexp_s[16];
+  __shared__ int fexp_s[32];                 // column exponents of F (0 .. 15), of M (16 .. 31)
   __shared__ double d_s[16], dinv_s[16];
-  __shared__ double colsum[2][4][16];
+  __shared__ double colsum[3][4][16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
   const int cnt = (g.tiles - (int)blockIdx.x + G - 1) / G;   // this CTA's tiles: blockIdx.x + i G
-  volatile int* abort_flag = &bars->abort;
+  WaitState* wst = &bars->wait;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kU16Stages; ++i) {
       mbar_init(smem_u32(&bars->full[i]), 1);
@@ -1660,7 +1741,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     }
     for (int i = 0; i < 16; ++i) mbar_init(smem_u32(&bars->sub[i >> 2][i & 3]), 2);
     mbar_init(smem_u32(&bars->drain), 1);
-    bars->abort = 0;
+    wait_state_init(&bars->wait, g.wait_ns);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -1669,21 +1750,21 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (threadIdx.x < 16) {
-    // column exponents of F, and d, 1/d (zero past k)
-    const int j = threadIdx.x;
+  if (threadIdx.x < 32) {
+    // column exponents of F and M, and d, 1/d (zero past k)
+    const int j = threadIdx.x & 15;
+    const double* Fm = threadIdx.x < 16 ? g.F : g.M;
     int fe = 0;
-    double dj = 0.0, dij = 0.0;
     if (j < g.k) {
       unsigned long long m = 0ull;
-      for (int l = 0; l < g.k; ++l) m = max(m, abs_bits(g.F[(int64_t)j * g.k + l]));
+      for (int l = 0; l < g.k; ++l) m = max(m, abs_bits(Fm[(int64_t)j * g.k + l]));
       fe = m < kInfBits ? exponent_of_bits(m) : kNonFinite;
-      dj = g.d[j];
-      dij = g.dinv[j];
     }
-    fexp_s[j] = fe;
-    d_s[j] = dj;
-    dinv_s[j] = dij;
+    fexp_s[threadIdx.x] = fe;
+    if (threadIdx.x < 16) {
+      d_s[j] = j < g.k ? g.d[j] : 0.0;
+      dinv_s[j] = j < g.k ? g.dinv[j] : 0.0;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -1699,7 +1780,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       int issued = 0;
       for (int i = 0; i < cnt && ok; ++i) {
         const int st = i % kU16Stages, lap = i / kU16Stages;
-        ok = mbar_wait_sleep(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), abort_flag);
+        ok = mbar_wait_sleep(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), wst);
         if (!ok) break;
         const int row0 = ((int)blockIdx.x + i * G) * 128;
         unsigned char* sx = stage0 + st * kU16Stage;
@@ -1719,8 +1800,8 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       const uint64_t bd = smem_desc(smem_u32(bop));
       for (int i = 0; i < cnt && ok; ++i) {
         const int a = i & 1, u = i >> 1;
-        ok = mbar_wait_sleep(smem_u32(&bars->a_full[a]), (uint32_t)(u & 1), abort_flag);
-        if (ok) ok = mbar_wait_sleep(smem_u32(&bars->acc_empty[a]), (uint32_t)((u & 1) ^ 1), abort_flag);
+        ok = mbar_wait_sleep(smem_u32(&bars->a_full[a]), (uint32_t)(u & 1), wst);
+        if (ok) ok = mbar_wait_sleep(smem_u32(&bars->acc_empty[a]), (uint32_t)((u & 1) ^ 1), wst);
         if (!ok) break;
         tc_fence_after();
         const uint32_t ab = smem_u32(abuf0 + a * kU16ABuf);
@@ -1728,6 +1809,9 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         for (int s = 0; s < S; ++s) {
           const uint64_t ad = smem_desc(ab + (uint32_t)((s >> 2) * kU16ABlock)) + (uint64_t)(2 * (s & 3));
           tc_mma(tbase + (uint32_t)(a * 256 + 16 * s), ad, bd, idesc_f16(kBM, 16 * (S - s)), s == 0 ? 0u : 1u);
+          // X M: M's planes from B row 128 on, accumulators from TMEM column 128 on
+          tc_mma(tbase + (uint32_t)(a * 256 + 128 + 16 * s), ad, bd + (uint64_t)((kU16BRows * 128) >> 4),
+                 idesc_f16(kBM, 16 * (S - s)), s == 0 ? 0u : 1u);
         }
         tc_commit(smem_u32(&bars->a_empty[a]));
         tc_commit(smem_u32(&bars->acc_full[a]));
@@ -1740,16 +1824,18 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
   } else if (warp < 2 + kU16SliceWarps) {
     // ---------------- slicers: one thread per tile row, all 16 columns ----------------
     const int r = (warp - 2) * 32 + lane;
-    // B operand first: digit t of F(l, j) at row 16 t + j, K = l (two (j, l) a thread)
-    for (int e = r; e < 256; e += 128) {
-      const int j = e >> 4, l = e & 15;
-      const int fe = fexp_s[j];
-      const double v = (j < g.k && l < g.k && fe != kNonFinite) ? g.F[(int64_t)j * g.k + l] : 0.0;
+    // B operand first: digit t of F(l, j) at row 16 t + j, K = l, and of M(l, j)
+    // at row 128 + 16 t + j (four (operand, j, l) a thread)
+    for (int e = r; e < 512; e += 128) {
+      const int op = e >> 8, j = (e >> 4) & 15, l = e & 15;
+      const int fe = fexp_s[16 * op + j];
+      const double* Fm = op ? g.M : g.F;
+      const double v = (j < g.k && l < g.k && fe != kNonFinite) ? Fm[(int64_t)j * g.k + l] : 0.0;
       int dg[S];
       digits_of<S>(v, fe == kNonFinite ? 0 : fe, dg);
 #pragma unroll
       for (int t = 0; t < S; ++t)
-        *reinterpret_cast<uint16_t*>(bop + swz128(16 * t + j, l >> 3) + (l & 7) * 2) =
+        *reinterpret_cast<uint16_t*>(bop + swz128(kU16BRows * op + 16 * t + j, l >> 3) + (l & 7) * 2) =
             __half_as_ushort(__int2half_rn(dg[t]));
     }
     bool ok = true;
@@ -1757,12 +1843,12 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       const int st = i % kU16Stages, lap = i / kU16Stages, a = i & 1;
       int w_ok = 1;
       if (lane == 0) {
-        w_ok = mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);
-        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[a]), (uint32_t)(((i >> 1) & 1) ^ 1), abort_flag);
+        w_ok = mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst);
+        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[a]), (uint32_t)(((i >> 1) & 1) ^ 1), wst);
       }
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       if (!ok) break;
-      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), abort_flag);   // complete: each lane acquires
+      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst);   // complete: each lane acquires
       const unsigned char* xt = stage0 + st * kU16Stage;
       unsigned long long b[16];
       unsigned long long am = 0ull;
@@ -1798,14 +1884,14 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     const int half = ew >> 2;                    // columns 8 half .. 8 half + 7
     const bool leader = half == 0;               // stores the lane group's 32 rows
     const int r = lg * 32 + lane;
-    double sq[8], rq[8];
+    double sq[8], rq[8], vq[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) sq[j] = rq[j] = 0.0;
+    for (int j = 0; j < 8; ++j) sq[j] = rq[j] = vq[j] = 0.0;
     bool ok = true;
     for (int i = 0; i < cnt && ok; ++i) {
       const int a = i & 1, u = i >> 1;
       int w_ok = 1;
-      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[a]), (uint32_t)(u & 1), abort_flag);
+      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[a]), (uint32_t)(u & 1), wst);
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       if (!ok) break;
       __syncwarp();
@@ -1813,7 +1899,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       // the X and W tiles of this tile: loaded (the slicers waited for them)
       // and not refilled before this warp's leader releases the stage
       const int st = i % kU16Stages;
-      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)((i / kU16Stages) & 1), abort_flag);
+      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)((i / kU16Stages) & 1), wst);
       unsigned char* xt = stage0 + st * kU16Stage;
       const unsigned char* wt = xt + kU16Tile;
       // the row's exponent (as the slicers took it) and this thread's X values
@@ -1829,37 +1915,14 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         }
         e_row = am < kInfBits ? exponent_of_bits(am) : kNonFinite;
       }
-      long long hi[8], lo[8];
       const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * 256 + 8 * half);
-      {
-        // weights in pairs (w, w + 1) within each group: C_w 2^8 + C_(w+1) stays below 2^30
+      // X M first (TMEM columns 128 ..), rounded at once, then X F
+      double xm[8];
+      long long hi[8], lo[8];
+      drain_u16<S>(tl + 128u, hi, lo);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
-        int pend[8];
-#pragma unroll
-        for (int w = 0; w < S; ++w) {
-          uint32_t v[8];
-          TC_LD8(tl + 16 * w, v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const int base = w < 4 ? 0 : 4;                       // first weight of its group
-          const int end = w < 4 ? (S < 4 ? S : 4) : S;           // one past its group's last
-          const bool first = ((w - base) & 1) == 0;
-          const bool paired = first ? (w + 1 < end) : true;
-          const int last_w = first ? (paired ? w + 1 : w) : w;   // weight of the pair's low digit
-          const int sh = w < 4 ? kBits * (3 - last_w) : kBits * (S - 1 - last_w);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int cw = int_of_f32(v[j]);
-            if (first && paired) {
-              pend[j] = cw;
-            } else {
-              const int pr = first ? cw : pend[j] * (1 << kBits) + cw;
-              if (w < 4) hi[j] += (long long)pr << sh;
-              else lo[j] += (long long)pr << sh;
-            }
-          }
-        }
-      }
+      for (int j = 0; j < 8; ++j) xm[j] = recombine<S>(hi[j], lo[j], e_row, fexp_s[16 + 8 * half + j]);
+      drain_u16<S>(tl, hi, lo);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[a]));
@@ -1876,11 +1939,14 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         const double f1 = recombine<S>(hi[2 * q + 1], lo[2 * q + 1], e_row, fexp_s[j1]);
         const double r0 = fma(-x2.x, d_s[j0], wv.x), r1 = fma(-x2.y, d_s[j1], wv.y);
         const double n0 = fma(r0, dinv_s[j0], x2.x) - f0, n1 = fma(r1, dinv_s[j1], x2.y) - f1;
+        const double v0 = r0 - xm[2 * q], v1 = r1 - xm[2 * q + 1];   // rows of V2 = R2 - X2 M
         if (live) {
           sq[2 * q] = fma(n0, n0, sq[2 * q]);
           sq[2 * q + 1] = fma(n1, n1, sq[2 * q + 1]);
           rq[2 * q] = fma(r0, r0, rq[2 * q]);
           rq[2 * q + 1] = fma(r1, r1, rq[2 * q + 1]);
+          vq[2 * q] = fma(v0, v0, vq[2 * q]);
+          vq[2 * q + 1] = fma(v1, v1, vq[2 * q + 1]);
         }
         *reinterpret_cast<double2*>(xt + swz128(r, cc)) = make_double2(n0, n1);
       }
@@ -1894,7 +1960,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       if (leader) {
         int s_ok = 1;
         if (lane == 0) {
-          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg][i & 3]), (uint32_t)((i >> 2) & 1), abort_flag);
+          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg][i & 3]), (uint32_t)((i >> 2) & 1), wst);
           if (s_ok) {
             if (!plain && row0 + 32 * lg < g.n) {
               tma_store_2d(&tmXn, smem_u32(xt + lg * 32 * 128), 0, (int)(row0 + 32 * lg));
@@ -1914,21 +1980,23 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       for (int o = 16; o > 0; o >>= 1) {
         sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], o);
         rq[j] += __shfl_xor_sync(0xffffffffu, rq[j], o);
+        vq[j] += __shfl_xor_sync(0xffffffffu, vq[j], o);
       }
       if (lane == 0) {
         colsum[0][lg][8 * half + j] = sq[j];
         colsum[1][lg][8 * half + j] = rq[j];
+        colsum[2][lg][8 * half + j] = vq[j];
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if ((int)threadIdx.x < 2 * g.k) {
+  if ((int)threadIdx.x < 3 * g.k) {
     const int which = threadIdx.x / g.k, j = threadIdx.x % g.k;
-    g.upart[(int64_t)blockIdx.x * 2 * g.k + which * g.k + j] =
+    g.upart[(int64_t)blockIdx.x * 3 * g.k + which * g.k + j] =
         colsum[which][0][j] + colsum[which][1][j] + colsum[which][2][j] + colsum[which][3][j];
   }
-  if (bars->abort && threadIdx.x == 0) {
+  if (bars->wait.abort && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     if (g.ctl) {
       Control* c = const_cast<Control*>(g.ctl);
@@ -1969,7 +2037,7 @@ struct __align__(8) Bars16F {
   uint64_t raw_full[kG16FRaw], raw_empty[kG16FRaw], pl_full[kG16FPlanes], pl_empty[kG16FPlanes], acc_full,
       acc_empty, drain;
   uint32_t tmem_base;
-  int abort;
+  WaitState wait;
 };
 
 template <int S>
@@ -2003,7 +2071,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
   const int kb_lo = (int)((int64_t)g.kb_total * split / g.ksplit);
   const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / g.ksplit);
   const int KB = kb_hi - kb_lo;
-  volatile int* abort_flag = &bars->abort;
+  WaitState* wst = &bars->wait;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kG16FRaw; ++i) {
       mbar_init(smem_u32(&bars->raw_full[i]), 1);
@@ -2016,7 +2084,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
     mbar_init(smem_u32(&bars->acc_full), 1);
     mbar_init(smem_u32(&bars->acc_empty), kEpiWarps);
     mbar_init(smem_u32(&bars->drain), 1);
-    bars->abort = 0;
+    wait_state_init(&bars->wait, g.wait_ns);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -2039,7 +2107,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       int issued = 0;
       for (int kb = 0; kb < KB && ok; ++kb) {
         const int st = kb % kG16FRaw, lap = kb / kG16FRaw;
-        ok = mbar_wait_sleep(smem_u32(&bars->raw_empty[st]), (uint32_t)((lap & 1) ^ 1), abort_flag);
+        ok = mbar_wait_sleep(smem_u32(&bars->raw_empty[st]), (uint32_t)((lap & 1) ^ 1), wst);
         if (!ok) break;
         const int row = (kb_lo + kb) * kBK;
         unsigned char* rt = raw0 + st * 2 * kG16FRawTile;
@@ -2061,12 +2129,12 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
         const bool first = (kb % kG16Chunk) == 0;
         const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
         if (first && c > 0) {   // one accumulator set: the previous chunk must be drained
-          ok = mbar_wait_sleep(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), abort_flag);
+          ok = mbar_wait_sleep(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), wst);
           if (!ok) break;
           tc_fence_after();
         }
         const int pb = kb % kG16FPlanes;
-        ok = mbar_wait_sleep(smem_u32(&bars->pl_full[pb]), (uint32_t)((kb / kG16FPlanes) & 1), abort_flag);
+        ok = mbar_wait_sleep(smem_u32(&bars->pl_full[pb]), (uint32_t)((kb / kG16FPlanes) & 1), wst);
         if (!ok) break;
         tc_fence_after();
         unsigned char* pt = pl0 + pb * kG16Stage;
@@ -2106,13 +2174,13 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       const int st = kb % kG16FRaw, pb = kb % kG16FPlanes;
       int w_ok = 1;
       if (lane == 0) {
-        w_ok = mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), abort_flag);
+        w_ok = mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), wst);
         if (w_ok)
-          w_ok = mbar_wait_sleep(smem_u32(&bars->pl_empty[pb]), (uint32_t)(((kb / kG16FPlanes) & 1) ^ 1), abort_flag);
+          w_ok = mbar_wait_sleep(smem_u32(&bars->pl_empty[pb]), (uint32_t)(((kb / kG16FPlanes) & 1) ^ 1), wst);
       }
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       if (!ok) break;
-      mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), abort_flag);   // each lane acquires
+      mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), wst);   // each lane acquires
       {
         const unsigned char* rt = raw0 + (st * 2 + op) * kG16FRawTile;
         unsigned long long b[8];
@@ -2139,7 +2207,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       if (last) {
         const int c = kb / kG16Chunk;
         int a_ok = 1;
-        if (lane == 0) a_ok = mbar_wait_sleep(smem_u32(&bars->acc_full), (uint32_t)(c & 1), abort_flag);
+        if (lane == 0) a_ok = mbar_wait_sleep(smem_u32(&bars->acc_full), (uint32_t)(c & 1), wst);
         ok = __shfl_sync(0xffffffffu, a_ok, 0) != 0;
         __syncwarp();
         if (!ok) break;
@@ -2193,7 +2261,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
   }
   tc_fence_before();
   __syncthreads();
-  if (bars->abort && threadIdx.x == 0) {
+  if (bars->wait.abort && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     if (g.ctl) {
       Control* c = const_cast<Control*>(g.ctl);
@@ -2325,9 +2393,10 @@ static SlicedLayout sliced_layout(int64_t n_pad, int k_pad, int kr, int S, int k
   L.p_cmax = take((size_t)k_pad * 8);
   L.xr_planes = take((size_t)S * n_pad * kr * 2);
   L.xr_rowexp = take((size_t)n_pad * 4);
-  L.f_planes = take((size_t)S * k_pad * kr * 2);
-  L.f_colexp = take((size_t)k_pad * 4);
-  L.f_cmax = take((size_t)k_pad * 8);
+  // the row update's B operand: the [F | M] panel (kfm_cols(k) columns)
+  L.f_planes = take((size_t)S * kfm_cols(k) * kr * 2);
+  L.f_colexp = take((size_t)kfm_cols(k) * 4);
+  L.f_cmax = take((size_t)kfm_cols(k) * 8);
   L.gpart = take((size_t)2 * ksplit * k * k * 16);
   L.ppart = take(psplit > 1 ? (size_t)psplit * n * k * 16 : 64);
   L.err = take(64);
@@ -2451,8 +2520,8 @@ int SlicedA::prepare(cudaStream_t s) {
                           sl::kBK, sl::kBN);
   ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmXR_), ws_ + L.xr_planes, (uint64_t)kr_, S * n_pad_,
                           sl::kBK, sl::kBM);
-  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmF_), ws_ + L.f_planes, (uint64_t)kr_, S * k_pad_, sl::kBK,
-                          sl::kBN);
+  ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmF_), ws_ + L.f_planes, (uint64_t)kr_, S * kfm_cols(k_),
+                          sl::kBK, sl::kBN);
   if (!ok) {
     snprintf(err_, sizeof(err_), "tensor map encoding failed");
     return EIGREF_E_CUDA;
@@ -2464,12 +2533,13 @@ int SlicedA::prepare(cudaStream_t s) {
   return EIGREF_OK;
 }
 
-static sl::MmaArgs base_args(const Control* ctl, int* err) {
+static sl::MmaArgs base_args(const Control* ctl, int* err, unsigned long long wait_ns) {
   sl::MmaArgs g;
   memset(&g, 0, sizeof(g));
   g.ctl = ctl;
   g.err = err;
   g.ksplit = 1;
+  g.wait_ns = wait_ns;
   return g;
 }
 
@@ -2518,7 +2588,7 @@ MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Co
   t.a = *reinterpret_cast<const CUtensorMap*>(tmA_);
   t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(b_from_p ? tmP_ : tmX_);
   sl::MmaArgs& g = t.g;
-  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err), wait_ns_);
   g.a_plane_rows = n_pad_;
   g.b_plane_rows = k_pad_;
   g.kb_total = n_pad_ / sl::kBK;
@@ -2554,7 +2624,7 @@ MmaTask SlicedA::gram_task(double* part, const Control* ctl) const {
   t.b = *reinterpret_cast<const CUtensorMap*>(tmX_);
   t.b2 = *reinterpret_cast<const CUtensorMap*>(tmP_);
   sl::MmaArgs& g = t.g;
-  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err), wait_ns_);
   g.a_plane_rows = k_pad_;
   g.b_plane_rows = k_pad_;
   g.kb_total = n_pad_ / sl::kBK;
@@ -2579,12 +2649,12 @@ MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, 
   t.a = *reinterpret_cast<const CUtensorMap*>(tmXR_);
   t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(tmF_);
   sl::MmaArgs& g = t.g;
-  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err));
+  g = base_args(ctl, reinterpret_cast<int*>(ws_ + L.err), wait_ns_);
   g.a_plane_rows = n_pad_;
-  g.b_plane_rows = k_pad_;
+  g.b_plane_rows = kfm_cols(k_);
   g.kb_total = kr_ / sl::kBK;
   g.rowexp = reinterpret_cast<const int*>(ws_ + L.xr_rowexp);
-  g.colexp = reinterpret_cast<const int*>(ws_ + L.f_colexp);
+  g.colexp = reinterpret_cast<const int*>(ws_ + L.f_colexp);   // by column of the [F | M] panel
   g.m_valid = n_;
   g.k = k_;
   g.row_begin = k_;
@@ -2594,7 +2664,7 @@ MmaTask SlicedA::update_task(const double* X, const double* W, const double* d, 
   g.dinv = dinv;
   g.Xn = Xn;
   g.upart = upart;
-  t.gx = k_pad_ / sl::kBN;
+  t.gx = kfm_cols(k_) / sl::kBN;   // a column block: 16 columns of X F and the same of X M
   t.gy = n_pad_ / sl::kBM;
   t.gz = 1;
   return t;
@@ -2699,7 +2769,7 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
   return 6;
 }
 
-int SlicedA::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
+int SlicedA::update(const double* X, const double* W, const double* FM, const double* d, const double* dinv,
                     double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   auto* xr = reinterpret_cast<__half*>(ws_ + L.xr_planes);
@@ -2707,10 +2777,11 @@ int SlicedA::update(const double* X, const double* W, const double* F, const dou
   int* xrexp = reinterpret_cast<int*>(ws_ + L.xr_rowexp);
   int* fexp = reinterpret_cast<int*>(ws_ + L.f_colexp);
   auto* fmax_ = reinterpret_cast<unsigned long long*>(ws_ + L.f_cmax);
-  // F is k x k column-major: element (l, j) at F[l + j k]
+  // FM is k x kfm column-major: element (l, c) at FM[l + c k]
+  const int kfm = kfm_cols(k_);
 #define EIGREF_CALL_SLICE_UPD(S_)                                                                       \
   sl::launch_slice_rows<S_>(X, n_, k_, n_pad_, kr_, xr, xrexp, ctl, s);                                 \
-  sl::launch_slice_cols<S_>(F, k_, k_, 1, k_, kr_, k_pad_, fmax_, fp, fexp, ctl, s)
+  sl::launch_slice_cols<S_>(FM, k_, kfm, 1, k_, kr_, kfm, fmax_, fp, fexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_UPD)
 #undef EIGREF_CALL_SLICE_UPD
   const MmaTask t = update_task(X, W, d, dinv, Xn, upart, ctl);
@@ -2786,7 +2857,8 @@ static void slice_grouped(int op, const GroupItem* items, const GroupDims& gd, i
     case SLICE_F_COLS: {
       const int kr = (gd.max_k + 63) / 64 * 64;
       sl::colmax_grouped_kernel<sl::OPD_FCOLS><<<dim3(1, 1, gd.count), 256, 0, s>>>(items, parity);
-      sl::slice_cols_grouped_kernel<S, sl::OPD_FCOLS><<<dim3(kr / 64, kp, gd.count), 256, 0, s>>>(items, parity);
+      sl::slice_cols_grouped_kernel<S, sl::OPD_FCOLS><<<dim3(kr / 64, kfm_cols(gd.max_k) / 32, gd.count), 256, 0, s>>>(
+          items, parity);
       break;
     }
     default:
@@ -2883,8 +2955,8 @@ int SlicedGram::configure(int64_t n, int k, int slices) {
   return EIGREF_OK;
 }
 
-int SlicedGram::update(const double* X, const double* W, const double* F, const double* d, const double* dinv,
-                       double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
+int SlicedGram::update(const double* X, const double* W, const double* F, const double* M, const double* d,
+                       const double* dinv, double* Xn, double* upart, const Control* ctl, cudaStream_t s) {
   if (!upd_ok_) return -1;
   alignas(64) CUtensorMap mx, mw, mn;
   if (!sl::make_map_f64(&mx, X, k_, n_, 128) || !sl::make_map_f64(&mw, W, k_, n_, 128) ||
@@ -2897,12 +2969,14 @@ int SlicedGram::update(const double* X, const double* W, const double* F, const 
   a.row_begin = k_;
   a.tiles = (int)((n_ + 127) / 128);
   a.F = F;
+  a.M = M;
   a.d = d;
   a.dinv = dinv;
   a.Xn = Xn;
   a.upart = upart;
   a.ctl = ctl;
   a.err = reinterpret_cast<int*>(ws_ + L.err);
+  a.wait_ns = wait_ns_;
 #define EIGREF_CALL_U16(S_) sl::update16_kernel<S_><<<upd_grid_, sl::kU16Threads, sl::kU16Smem, s>>>(mx, mw, mn, a)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_U16)
 #undef EIGREF_CALL_U16
@@ -2951,6 +3025,7 @@ int SlicedGram::gram_fused(const double* X, const double* P, double* out, const 
   fa.g.part = reinterpret_cast<longlong2*>(ws_ + L.part);
   fa.g.ctl = ctl;
   fa.g.err = reinterpret_cast<int*>(ws_ + L.err);
+  fa.g.wait_ns = wait_ns_;
   fa.xmax = x_cmax();
   fa.wmax = p_cmax();
   fa.xexp = xexp;
@@ -2989,6 +3064,7 @@ int SlicedGram::gram(const double* X, const double* P, double* out, const Contro
   g.part = reinterpret_cast<longlong2*>(ws_ + L.part);
   g.ctl = ctl;
   g.err = reinterpret_cast<int*>(ws_ + L.err);
+  g.wait_ns = wait_ns_;
   const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
   const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
   const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);
@@ -3038,6 +3114,7 @@ int SlicedGram::gram_ready(const double* X, const double* P, double* out, const 
   g.part = reinterpret_cast<longlong2*>(ws_ + L.part);
   g.ctl = ctl;
   g.err = reinterpret_cast<int*>(ws_ + L.err);
+  g.wait_ns = wait_ns_;
   const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(tmX_);
   const CUtensorMap& mp = *reinterpret_cast<const CUtensorMap*>(tmP_);
   const int rg = (int)std::min<int64_t>((2LL * k_ * k_ + 7) / 8, 152 * 8);

@@ -38,11 +38,12 @@ struct MmaArgs {
   const double* d;       // UPDATE: Rayleigh quotients [k]
   const double* dinv;    // UPDATE: 1 / d
   double* Xn;            // UPDATE: row-major n x k (overlaps none of X, W, d, dinv)
-  double* upart;         // UPDATE: [m tiles][2k] column sums of X'^2 and of (W - X D)^2
+  double* upart;         // UPDATE: [m tiles][3k] column sums of X'^2, (W - X D)^2 and V2^2 (V2 = R2 - X2 M)
   const Control* ctl;
   int* err;              // set to 1 on a timed-out wait
   int sk_ranges;         // PRODUCT: > 0: equal-work ranges of (row tile, K block) units per column block
   long long sk_units;    // PRODUCT with sk_ranges: units per column block (row tiles x K blocks)
+  unsigned long long wait_ns;   // limit of every bounded wait inside the kernel (0: the default, 2 s)
 };
 }  // namespace sl
 
@@ -91,9 +92,11 @@ class SlicedA {
   // out[0] = X^T X, out[1] = X^T P (k x k column-major, all n rows), with X the
   // operand of the last product(); part = split-K scratch (null: internal).
   int gram(const double* P, double* part, double* out, const Control* ctl, cudaStream_t s);
-  // Rows k..n-1 of X' = X + (W - X D) D^-1 - X F (F k x k column-major) and
-  // per-row-tile column sums of X'^2 and (W - X D)^2 into upart[update_grid()][2k].
-  int update(const double* X, const double* W, const double* F, const double* d, const double* dinv, double* Xn,
+  // Rows k..n-1 of X' = X + (W - X D) D^-1 - X F and per-row-tile column
+  // sums of X'^2, (W - X D)^2 and V2^2 (V2 = R2 - X2 M, the rows of E21 D)
+  // into upart[update_grid()][3k].  FM: the k x kfm_cols(k) panel of F and M
+  // interleaved by 16 columns (SweepBufs::fm).
+  int update(const double* X, const double* W, const double* FM, const double* d, const double* dinv, double* Xn,
              double* upart, const Control* ctl, cudaStream_t s);
   int update_grid() const;
   // The same three stages as launchable tasks (the batch groups them), and the
@@ -123,9 +126,12 @@ class SlicedA {
   void set_splits(int psplit, int ksplit);
   int psplit() const { return psplit_; }
   int ksplit() const { return ksplit_; }
+  // Limit of every bounded wait inside the tensor-core kernels (0: 2 s).
+  void set_wait_ns(unsigned long long ns) { wait_ns_ = ns; }
   const char* error() const { return err_; }
 
  private:
+  unsigned long long wait_ns_ = 0;
   size_t layout_total() const;
   const double* A_ = nullptr;
   int64_t n_ = 0, lda_ = 0;
@@ -160,20 +166,23 @@ class SlicedGram {
   void colmax_x(const double* X, cudaStream_t s);   // x_cmax() = column maxima of X
   int gram_fused(const double* X, const double* P, double* out, const Control* ctl, cudaStream_t s);
   // X' = X + (W - X D) D^-1 - X F for rows k .. n - 1 on the tensor cores
-  // (even k); upart gets update_grid() x 2k column sums (x'^2, (w - x d)^2).
-  // Returns the launch count, or -1 when this k has no such kernel.
+  // (even k); upart gets update_grid() x 3k column sums (x'^2, (w - x d)^2,
+  // v^2 with V2 = R2 - X2 M).  Returns the launch count, or -1 when this k
+  // has no such kernel.
   bool update_ready() const { return upd_ok_; }
   int update_grid() const { return upd_grid_; }
-  int update(const double* X, const double* W, const double* F, const double* d, const double* dinv, double* Xn,
-             double* upart, const Control* ctl, cudaStream_t s);
+  int update(const double* X, const double* W, const double* F, const double* M, const double* d,
+             const double* dinv, double* Xn, double* upart, const Control* ctl, cudaStream_t s);
   unsigned long long* x_cmax() const;
   unsigned long long* p_cmax() const;
   int timed_out(cudaStream_t s) const;
   int ksplit() const { return ksplit_; }
   int slices() const { return slices_; }
+  void set_wait_ns(unsigned long long ns) { wait_ns_ = ns; }
   const char* error() const { return err_; }
 
  private:
+  unsigned long long wait_ns_ = 0;
   int64_t n_ = 0, n_pad_ = 0;
   int k_ = 0, slices_ = 0, ksplit_ = 1;
   int upd_grid_ = 0;

@@ -79,3 +79,34 @@ def test_create_rejects_bad_arguments(L):
 def test_oracle_evaluator_builds():
     from oracle import dd
     assert os.path.exists(dd.build())
+
+
+def test_binding_refuses_mismatched_shapes_before_the_library(monkeypatch):
+    """A narrow or mismatched P (or X, G, S) is refused in the binding, so no
+    kernel can write past an output's end; the library is never reached."""
+    import numpy as np
+    import paper_2602_23778_gb300 as pkg
+
+    def no_library():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(pkg, "lib", no_library)
+    A = np.zeros((8, 8))
+    X = np.zeros((8, 3), order="F")
+    good = np.zeros((8, 3), order="F")
+    for bad in (np.zeros((8, 2), order="F"), np.zeros((7, 3), order="F"), np.zeros((9, 3), order="F")):
+        with pytest.raises(ValueError):
+            pkg.product_dense_noalloc(A, X, bad)
+        with pytest.raises(ValueError):
+            pkg.Handle.product_dense(None, A, X, bad)
+        with pytest.raises(ValueError):
+            pkg.Handle.gram(None, X, bad, np.zeros((3, 3), order="F"), np.zeros((3, 3), order="F"))
+    with pytest.raises(ValueError):
+        pkg.product_dense_noalloc(A, np.zeros((7, 3), order="F"), good)
+    with pytest.raises(ValueError):
+        pkg.Handle.gram(None, X, good, np.zeros((2, 3), order="F"), np.zeros((3, 3), order="F"))
+    rp = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8], dtype=np.int32)
+    ci = np.arange(8, dtype=np.int32)
+    val = np.ones(8)
+    with pytest.raises(ValueError):
+        pkg.Handle.product_csr(None, rp, ci, val, X, np.zeros((8, 2), order="F"))

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from oracle import dd, refine as R
-from tests.gpu_util import dev, host, rel_diff, sweep_tol, U
+from tests.gpu_util import abs_csr, abs_dense, corr_bound, dev, host, oracle_spread, record, rel_diff, sweep_tol, U
+from tests.oracle_cases import delta_tie
 from workloads import configs as C
 
 pytestmark = pytest.mark.gpu
@@ -40,29 +41,93 @@ def run_oracle(p, **kw):
     return R.refine(R.dense_operator(p.A, p.shift), p.X0, p.normA, p.shift, **kw)
 
 
+def check_norms(name, rg, p, spread):
+    """||R_t|| and ||E_t|| of every sweep against the oracle: 1e-12 relative
+    plus 8x the oracle's own rounding spread at that sweep (oracle_spread).
+    Records the achieved differences."""
+    ro = spread["base"]
+    m = len(ro["hist_corr"])
+    dc = np.abs(rg["hist_corr"][:m] - ro["hist_corr"])
+    dr = np.abs(rg["hist_residual"][:m] - ro["hist_res"])
+    bc, br = corr_bound(ro["hist_corr"], spread["hist_corr"]), corr_bound(ro["hist_res"], spread["hist_res"])
+    record(name, corr_abs=dc.max(), corr_rel=(dc / ro["hist_corr"]).max(), corr_bound_rel=(bc / ro["hist_corr"]).min(),
+           res_rel=(dr / ro["hist_res"]).max(), res_bound_rel=(br / ro["hist_res"]).min(),
+           corr_min=ro["hist_corr"].min())
+    assert np.all(dc <= bc), (dc, bc)
+    assert np.all(dr <= br), (dr, br)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
 @pytest.mark.parametrize("n,k", [(96, 1), (130, 3), (300, 8), (517, 17), (700, 64), (1000, 128), (257, 128)])
-def test_single_sweep_dense(eig, n, k):
+def test_single_sweep_dense(eig, n, k, precision):
     p = dense_case(n, k, seed=100 + n + k)
-    Xg, rg = run_gpu(eig, p, max_iters=1)
+    Xg, rg = run_gpu(eig, p, max_iters=1, precision=precision)
+    sp = oracle_spread(R.dense_operator(p.A, p.shift), p.X0, p.normA, p.shift, abs_dense(p.A, p.shift), max_iters=1)
     Xo, ro = run_oracle(p, max_iters=1)
     assert rg["status"] == 0 and rg["iterations"] == 1
     tol = sweep_tol(p.normA + abs(p.shift), p.min_gap)
-    assert rel_diff(Xg, Xo) <= tol
+    dx = rel_diff(Xg, Xo)
+    record("single_sweep_dense[%s-%d-%d]" % (precision, n, k), x_rel=dx, x_bound=tol,
+           d_rel=rel_diff(rg["eigenvalues"], ro["d"]), min_gap=p.min_gap)
+    assert dx <= tol
     assert rel_diff(rg["eigenvalues"], ro["d"]) <= 1e-12
-    assert abs(rg["hist_residual"][0] - ro["hist_res"][0]) <= 1e-10 * ro["hist_res"][0]
-    assert abs(rg["hist_corr"][0] - ro["hist_corr"][0]) <= 1e-8 * ro["hist_corr"][0]
+    check_norms("single_sweep_dense_norms[%s-%d-%d]" % (precision, n, k), rg, p, sp)
 
 
-def test_trajectory_n512(eig):
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_trajectory_n512(eig, precision):
     """The n = 512, k = 8 workload: all 10 sweeps agree with the oracle."""
     p = C.config1()
-    Xg, rg = run_gpu(eig, p, max_iters=10)
+    Xg, rg = run_gpu(eig, p, max_iters=10, precision=precision)
+    sp = oracle_spread(R.dense_operator(p.A, p.shift), p.X0, p.normA, p.shift, abs_dense(p.A, p.shift), max_iters=10)
     Xo, ro = run_oracle(p, max_iters=10)
     assert rg["iterations"] == 10
+    record("trajectory_n512[%s]" % precision, x_rel=rel_diff(Xg, Xo), x_bound=1e-12,
+           d_rel=rel_diff(rg["eigenvalues"], ro["d"]))
     assert rel_diff(Xg, Xo) <= 1e-12
-    assert np.abs(rg["hist_residual"] - ro["hist_res"]).max() <= 1e-10 * ro["hist_res"].max()
-    assert np.abs(rg["hist_corr"] - ro["hist_corr"]).max() <= 1e-8 * ro["hist_corr"].max()
+    check_norms("trajectory_n512_norms[%s]" % precision, rg, p, sp)
     assert rel_diff(rg["eigenvalues"], ro["d"]) <= 1e-14
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_correction_norm_at_converged_iterate(eig, precision):
+    """||E_t||_F at the rounding floor: the oracle's iterate after 80 sweeps
+    (||E|| near 1e-15), then one sweep on both sides from that iterate.  The
+    norm is formed from the explicit rows of E (no k x k expansion), so the
+    two sides differ by the rounding floor the oracle shows itself."""
+    p = dense_case(400, 6, seed=9)
+    Xc, rc = run_oracle(p, max_iters=80)
+    assert rc["hist_corr"][-1] < 1e-13
+    q = C.Problem({**p, "X0": np.asfortranarray(Xc)})
+    Xg, rg = run_gpu(eig, q, max_iters=1, precision=precision)
+    sp = oracle_spread(R.dense_operator(q.A, q.shift), q.X0, q.normA, q.shift, abs_dense(q.A, q.shift), max_iters=1)
+    Xo, _ = run_oracle(q, max_iters=1)
+    assert rg["iterations"] == 1
+    record("converged_iterate[%s]" % precision, x_rel=rel_diff(Xg, Xo), corr=rg["hist_corr"][0],
+           corr_oracle=sp["base"]["hist_corr"][0], corr_spread=sp["hist_corr"][0])
+    check_norms("converged_iterate_norms[%s]" % precision, rg, q, sp)
+    assert rel_diff(Xg, Xo) <= sweep_tol(q.normA + abs(q.shift), q.min_gap)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_delta_tie_on_gpu(eig, precision):
+    """The threshold of line 6 on the GPU: Rayleigh quotients exactly delta
+    apart take the beta branch (the sweep stays finite and small, as the
+    oracle's), one ulp more takes the division (|E| huge: both report
+    divergence after the first sweep)."""
+    for units, want in ((10, 0), (11, 5)):
+        B, X0, norm_b = delta_tie(units)
+        X = dev(np.asfortranarray(X0))
+        rg = eig.refine_dense(dev(B), X, norm_a=norm_b, max_iters=1, history=True, precision=precision,
+                              raise_on_error=False)
+        Xo, ro = R.refine(R.dense_operator(B), X0, norm_b, max_iters=1)
+        assert ro["status"] == want and rg["status"] == want, (units, rg["status"], ro["status"])
+        assert rg["iterations"] == ro["iterations"] == 1
+        c_g, c_o = rg["hist_corr"][0], ro["hist_corr"][0]
+        record("delta_tie[%s-%d]" % (precision, units), corr_rel=abs(c_g - c_o) / c_o, x_rel=rel_diff(host(X), Xo))
+        assert abs(c_g - c_o) <= 1e-12 * c_o
+        assert rel_diff(host(X), Xo) <= 1e-12
+        assert (c_o < 1.0) == (want == 0)
 
 
 def test_graph_and_chunking_do_not_change_results(eig):
@@ -190,14 +255,21 @@ def run_oracle_csr(p, **kw):
     return R.refine(op, p.X0, p.normA, p.shift, **kw)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
 @pytest.mark.parametrize("nx,ny,k", [(40, 30, 16), (33, 17, 5), (64, 64, 3)])
-def test_csr_sweeps(eig, nx, ny, k):
+def test_csr_sweeps(eig, nx, ny, k, precision):
     p = laplace_case(nx, ny, k, noise=1e-5, per_column=True)
-    Xg, rg = run_gpu_csr(eig, p, max_iters=3)
+    Xg, rg = run_gpu_csr(eig, p, max_iters=3, precision=precision)
     Xo, ro = run_oracle_csr(p, max_iters=3)
     assert rg["iterations"] == 3
     gaps = np.diff(np.sort(p.lam)).min()
-    assert rel_diff(Xg, Xo) <= sweep_tol(p.normA + abs(p.shift), gaps) * 3
+    tol = sweep_tol(p.normA + abs(p.shift), gaps) * 3
+    record("csr_sweeps[%s-%d-%d-%d]" % (precision, nx, ny, k), x_rel=rel_diff(Xg, Xo), x_bound=tol)
+    assert rel_diff(Xg, Xo) <= tol
+    op = R.csr_operator(p.row_ptr, p.col_idx, p.val, p.n, p.shift)
+    check_norms("csr_sweeps_norms[%s-%d-%d-%d]" % (precision, nx, ny, k), rg, p,
+                oracle_spread(op, p.X0, p.normA, p.shift, abs_csr(p.row_ptr, p.col_idx, p.val, p.n, p.shift),
+                              max_iters=3))
 
 
 def test_csr_product_vs_scipy(eig):

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import refine as R
-from tests.oracle_cases import separated
+from tests.oracle_cases import delta_tie, separated
 
 MUTATIONS = {
     "diag_sign": ("E[i, j] = (1.0 - alpha[i]) / 2.0", "E[i, j] = (alpha[i] - 1.0) / 2.0"),
@@ -21,6 +21,10 @@ MUTATIONS = {
     "rq_unscaled": ("d = np.einsum(\"ij,ij->j\", Xh, W) / alpha", "d = np.einsum(\"ij,ij->j\", Xh, W)"),
     "wy_t_untransposed": ("return B - Y @ (T.T @ (Y.T @ B))", "return B - Y @ (T @ (Y.T @ B))"),
     "alg1_sign": ("T = -np.linalg.solve(Y1.T, np.eye(k))", "T = np.linalg.solve(Y1.T, np.eye(k))"),
+    "delta_u": ("U_FP64 = 2.0 ** -53 ", "U_FP64 = 2.0 ** -52 "),
+    "delta_no_c": ("return c * norm_b * U_FP64", "return norm_b * U_FP64"),
+    "delta_no_norm": ("return c * norm_b * U_FP64", "return c * U_FP64"),
+    "tie_strict": ("elif abs(d[j] - d[i]) <= delta:", "elif abs(d[j] - d[i]) < delta:"),
 }
 
 
@@ -67,6 +71,12 @@ def battery(mod):
         Xn, _ = mod.refine_step(op, X, mod.delta_threshold(c.normA, 1e30))
         if np.abs(Xn.T @ Xn - np.eye(3)).max() > 50 * eps ** 2:
             return False
+        # the threshold: a tie at exactly delta takes beta, one ulp more divides
+        for units, beta_branch in ((10, True), (11, False)):
+            B, X, norm_b = delta_tie(units)
+            _, info = mod.refine_step(mod.dense_operator(B), X, mod.delta_threshold(norm_b))
+            if (info.E[0, 1] == 0.0) != beta_branch:
+                return False
     except (np.linalg.LinAlgError, FloatingPointError):
         return False
     return True

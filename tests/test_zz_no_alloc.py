@@ -1,9 +1,9 @@
 """eigref_product_dense_noalloc: the FP64 product for callers that cannot
-allocate device memory (for example while their stream is being captured into
-a CUDA graph, or inside a framework whose pool owns the device).  Its scratch
-is a fixed array inside the library; the test checks, through the C ABI, that
-two calls in a row give what eigref_product_dense gives, and that requests
-beyond the fixed size are refused.  Collected last on purpose."""
+allocate device memory (inside a framework whose memory pool owns the device,
+or on a path where an allocation's implicit synchronisation is not allowed).
+Its scratch is a fixed array inside the library; the test checks, through the
+C ABI, that two calls in a row give what eigref_product_dense gives, and that
+requests beyond the fixed size are refused.  Collected last on purpose."""
 import numpy as np
 import pytest
 
