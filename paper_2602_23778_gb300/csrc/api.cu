@@ -226,7 +226,7 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
     }
     launch_finalize(b, k, delta, s);
     launch_normalize(b, n, k, s, pr.fused_max ? pr.sgram->x_cmax() : nullptr);
-    return launches + 1 + 12 + 1 + 2;
+    return launches + 1 + 9 + 1 + 2;
   }
   if (pr.sliced) {
     // split form: Gram products over all rows on the tensor cores, the
@@ -241,7 +241,7 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
     launches += 4;
   }
   launch_kxk_stage(b, k, delta, beta_zero, s);
-  launches += b.mixed ? 12 : 9;
+  launches += b.mixed ? 9 : 7;
   if (pr.sliced) {
     pr.sliced->update(b.x, b.p, b.fm, b.d, b.dinv, b.xn, b.upart, b.ctl, s);
     launches += 4;
@@ -1148,7 +1148,7 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
         launch_mma_tasks(S, sl::MODE_UPDATE, upd[par].data(), count, s, side, evs);
         launch_finalize_grouped(items_dev, gd, par, s);
         launch_normalize_grouped(items_dev, gd, par, s);
-        launches += 24 + 3 * groups;
+        launches += 21 + 3 * groups;
       }
       return launches;
     };

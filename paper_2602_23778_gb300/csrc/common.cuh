@@ -30,6 +30,8 @@ struct Control {
   int nonfinite;
   int singular;       // set by the LU of Y_1
   int judge;          // columns 0..judge-1 decide the stop and divergence tests
+  int ns_twice;       // split form: this sweep's first Newton-Schulz step left ||I - Y1 Z|| above the
+                      // threshold, so a second one runs
   double tol;
   double norm_a;
   double div_factor, div_floor;

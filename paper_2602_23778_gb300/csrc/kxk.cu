@@ -7,9 +7,13 @@
 //   R1 = W1 - X1 D,  Y1 = X1 - I                       (Algorithm 1: Y = X - I_{n,k})
 //   Y^T R = (S - G D) - R1,  Z = S2 - G2 D = X2^T R2
 //   M = T^T (Y^T R) = -Y1^{-1} (Y^T R)                 (T = -Y1^{-T})
-//   V1 = R1 - Y1 M   (top rows of V = H^T R, Eq. V-def; V2 = R2 - X2 M)
+//   V1 = R1 - Y1 M = S - G D (= X^T R: top rows of V = H^T R, Eq. V-def;
+//        V2 = R2 - X2 M is formed by the row update)
 //   E11 by the four cases of line 6 (Eqs. Ediag, Eoffdiag, beta)
 //   Y^T E = Y1^T E11 + (Z - G2 M) D^-1                  (E21 = V2 D^-1)
+// V1 needs no product: R1 + Y^T R = X1^T R1 + X2^T R2 = X^T R = S - G D, and
+// R1 - Y1 M = R1 + Y^T R.  (S - G D is the difference the sweep forms for
+// Y^T R anyway, so V1 carries the same rounding as before.)
 //   N = T (Y^T E) = -Y1^{-T} (Y^T E)
 //   X1' = X1 + E11 - Y1 N,  F = M D^-1 + N             (H E = E - Y N)
 // The rows below are updated by update_rows: X2' = X2 + (W2 - X2 D) D^-1 - X2 F.
@@ -69,14 +73,17 @@ __device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j, i
     }
     const double x = b.x[(int64_t)i * k + j];
     const double r1 = b.p[(int64_t)i * k + j] - x * dj;
+    const double v1 = S - G * dj;   // V1 = X^T R
     b.r1[e] = r1;
-    b.t1[e] = (S - G * dj) - r1;
+    b.v1[e] = v1;
+    b.t1[e] = v1 - r1;
     b.z[e] = s2 - g2 * dj;
     b.y1[e] = x - (i == j ? 1.0 : 0.0);
     r1s += r1 * r1;
   }
   r1s = block_sum(r1s, sh, vb);
   if (threadIdx.x == 0) {
+    if (j == 0) b.ctl->ns_twice = 0;
     b.alpha[j] = al;
     b.d[j] = dj;
     b.dinv[j] = 1.0 / dj;
@@ -231,7 +238,7 @@ __global__ void kk_solve_kernel(const double* __restrict__ LU, const int* __rest
   for (int i = tid; i < k; i += blockDim.x) out[i + (int64_t)j * k] = -x[i];
 }
 
-enum { KG_V1 = 0, KG_W2 = 1, KG_YTE = 2, KG_X1 = 3 };
+enum { KG_YTE = 2, KG_X1 = 3 };
 
 // The TT rows of op(A) and TT columns of B a tile needs, whole (every load in
 // flight at once: these products are latency-bound), into As[r][l] = op(A)(i0
@@ -262,6 +269,9 @@ __device__ __forceinline__ void kk_load_panels(const double* __restrict__ A, boo
 
 // TT x TT output tile per CTA (TT^2 threads), one output per thread:
 // s = op(A)(i,:) . Bm(:,j), summed in the order l = 0, 1, ... for any TT.
+//   KG_YTE: Y^T E = Y1^T E11 + (Z - W2) D^-1 with W2 = G2 M formed here too
+//           (second panel pair, loaded after the first product)
+//   KG_X1:  X1' = X1 + E11 - Y1 N, F = M D^-1 + N (and the [F | M] panel)
 template <int MODE, int TT = 16>
 __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, int by, int done = 0) {
   __shared__ double As[TT][kMaxK + 1];
@@ -269,23 +279,27 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
   const int i = bx * TT + tx, j = by * TT + ty;
   const int64_t kk = (int64_t)k * k;
-  const double* A = (MODE == KG_W2) ? b.g2 : b.y1;   // G2 = b.g2[0 .. k*k)
-  const double* Bm = (MODE == KG_YTE) ? b.e11 : (MODE == KG_X1 ? b.nmat : b.m);
+  const double* Bm = (MODE == KG_YTE) ? b.e11 : b.nmat;
   const bool transA = (MODE == KG_YTE);
-  kk_load_panels<TT>(A, transA, Bm, k, bx * TT, by * TT, As, Bs);
+  kk_load_panels<TT>(b.y1, transA, Bm, k, bx * TT, by * TT, As, Bs);
   __syncthreads();
   if (done) return;
   double s = 0.0;
   for (int l = 0; l < k; ++l) s = fma(As[tx][l], Bs[l][ty], s);
+  if (MODE == KG_YTE) {
+    __syncthreads();                      // every thread is done with the first panels
+    kk_load_panels<TT>(b.g2, false, b.m, k, bx * TT, by * TT, As, Bs);   // G2 = b.g2[0 .. k*k)
+    __syncthreads();
+    double w2 = 0.0;
+    for (int l = 0; l < k; ++l) w2 = fma(As[tx][l], Bs[l][ty], w2);
+    if (i >= k || j >= k) return;
+    const int64_t e = i + (int64_t)j * k;
+    b.yte[e] = s + (b.z[e] - w2) / b.d[j];
+    return;
+  }
   if (i >= k || j >= k) return;
   const int64_t e = i + (int64_t)j * k;
-  if (MODE == KG_V1) {
-    b.v1[e] = b.r1[e] - s;
-  } else if (MODE == KG_W2) {
-    b.w2[e] = s;
-  } else if (MODE == KG_YTE) {
-    b.yte[e] = s + (b.z[e] - b.w2[e]) / b.d[j];
-  } else {
+  {
     b.xn[(int64_t)i * k + j] = b.x[(int64_t)i * k + j] + b.e11[e] - s;
     const double f = b.m[e] / b.d[j] + b.nmat[e];
     b.f[e] = f;
@@ -353,7 +367,7 @@ template <int TRANS, int TT = 16>
 __device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ A, const double* __restrict__ B,
                                                      const double* __restrict__ C0, double* __restrict__ C, int k,
                                                      double alpha, double beta, int add_i, double check, Control* ctl,
-                                                     int bx, int by, int done = 0) {
+                                                     int bx, int by, int done = 0, double twice_above = 0.0) {
   __shared__ double As[TT][kMaxK + 1];
   __shared__ double Bs[kMaxK][TT + 1];
   const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
@@ -374,6 +388,7 @@ __device__ __forceinline__ void kk_gemm_generic_body(const double* __restrict__ 
       ctl->status = EIGREF_E_SINGULAR_WY;
       ctl->done = 1;
     }
+    if (twice_above > 0.0 && !(fabs(v) <= twice_above)) atomicOr(&ctl->ns_twice, 1);
   }
 }
 
@@ -387,6 +402,13 @@ __global__ void __launch_bounds__(256) kk_gemm_generic_kernel(const double* __re
 }
 
 // Tiles of 8 for k >= 64 (a k x k product then spreads over 64+ SMs), else 16.
+__host__ __device__ __forceinline__ int kk_tile(int k) { return k >= 64 ? 8 : 16; }
+// Threads of an E11 column block where it shares a launch with a product (TT^2 threads a block).
+__host__ __device__ __forceinline__ int kk_e11_vb(int k) {
+  const int t = kk_tile(k) * kk_tile(k);
+  return kk_threads(k) < t ? kk_threads(k) : t;
+}
+
 static void kk_gemm_generic(const double* A, bool transA, const double* B, const double* C0, double* C, int k,
                             double alpha, double beta, int add_i, double check, Control* ctl, cudaStream_t s) {
   if (k >= 64) {
@@ -429,24 +451,80 @@ void launch_inverse_setup(const SweepBufs& b, int k, cudaStream_t s) {
   kk_solve_kernel<0><<<k, tpb, 0, s>>>(b.lu, b.piv, b.res, b.zinv, k, b.ctl);   // Z = -Y1^{-1}(-I)
 }
 
+// The Newton-Schulz refresh of Z ~ Y1^{-1} (split form), one step
+// Z' = Z + Z T, T = I - Y1 Z, squaring ||T||.  X changes by O(||E||) a sweep,
+// so Z kept from the last sweep starts at ||T|| ~ ||E||; a second step runs
+// only when the first T has an entry above 2^-27 (then ||T'|| would stay above
+// u), and that second T' is the one checked for Y1 turning singular (> 0.5:
+// the iteration would not contract).
+constexpr double kNsOnce = 7.450580596923828e-09;   // 2^-27
+
+// First product T = I - Y1 Z into res, asking for the second step where due;
+// blocks past the product's tiles form E11 (column blk - tiles), which needs
+// only the quotients and V1 of the prep step.
+template <int TT>
+__device__ __forceinline__ void kk_ns_first_body(const SweepBufs& b, int k, double delta, int beta_zero, int blk,
+                                                 int done) {
+  const int nt = (k + TT - 1) / TT;
+  if (blk < nt * nt) {
+    kk_gemm_generic_body<0, TT>(b.y1, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, blk % nt, blk / nt, done,
+                                kNsOnce);
+  } else if (blk - nt * nt < k && !done) {
+    kk_e11_body(b, k, delta, beta_zero, blk - nt * nt, kk_e11_vb(k));
+  }
+}
+
+template <int TT>
+__global__ void __launch_bounds__(256) kk_ns_first_kernel(SweepBufs b, int k, double delta, int beta_zero) {
+  const int done = b.ctl->done;   // acted on after the panel loads
+  kk_ns_first_body<TT>(b, k, delta, beta_zero, blockIdx.x, done);
+}
+
+// Second step, T' = I - Y1 Z' (checked) and Z = Z' + Z' T'; without it Z = Z'.
+template <int TT>
+__device__ __forceinline__ void kk_ns_second_body(const SweepBufs& b, int k, int op, int bx, int by, int done) {
+  const int twice = b.ctl->ns_twice;
+  if (op == 0) {
+    if (!twice) return;
+    kk_gemm_generic_body<0, TT>(b.y1, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, bx, by, done);
+  } else if (twice) {
+    kk_gemm_generic_body<0, TT>(b.zinv2, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, bx, by, done);
+  } else if (!done) {
+    const int i = bx * TT + (int)threadIdx.x % TT, j = by * TT + (int)threadIdx.x / TT;
+    if (i < k && j < k) b.zinv[i + (int64_t)j * k] = b.zinv2[i + (int64_t)j * k];
+  }
+}
+
+template <int TT>
+__global__ void __launch_bounds__(256) kk_ns_second_kernel(SweepBufs b, int k, int op) {
+  const int done = b.ctl->done;
+  kk_ns_second_body<TT>(b, k, op, blockIdx.x, blockIdx.y, done);
+}
+
+template <int TT>
+static void kk_ns_launches(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s) {
+  const int nt = (k + TT - 1) / TT;
+  kk_ns_first_kernel<TT><<<nt * nt + k, TT * TT, 0, s>>>(b, k, delta, beta_zero);                    // T, E11
+  kk_gemm_generic(b.zinv, false, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, s);             // Z' = Z + Z T
+  kk_ns_second_kernel<TT><<<dim3(nt, nt), TT * TT, 0, s>>>(b, k, 0);                                 // T' (if due)
+  kk_ns_second_kernel<TT><<<dim3(nt, nt), TT * TT, 0, s>>>(b, k, 1);                                 // Z
+}
+
 void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cudaStream_t s) {
   const int tpb = kk_threads(k);
   kk_prep_kernel<<<k, tpb, 0, s>>>(b, k);
   if (b.mixed) {
-    // two Newton-Schulz steps bring Z to the new Y1 (ping-pong between zinv and zinv2)
-    kk_gemm_generic(b.y1, false, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, s);      // T = I - Y1 Z
-    kk_gemm_generic(b.zinv, false, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, s);     // Z' = Z + Z T
-    kk_gemm_generic(b.y1, false, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, s);     // T' = I - Y1 Z'
-    kk_gemm_generic(b.zinv2, false, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, s);    // Z = Z' + Z' T'
+    if (k >= 64)
+      kk_ns_launches<8>(b, k, delta, beta_zero, s);
+    else
+      kk_ns_launches<16>(b, k, delta, beta_zero, s);
     kk_gemm_generic(b.zinv, false, b.t1, nullptr, b.m, k, -1.0, 0.0, 0, 0.0, b.ctl, s);        // M = -Z (Y^T R)
   } else {
+    kk_e11_kernel<<<k, tpb, 0, s>>>(b, k, delta, beta_zero);
     kk_lu_kernel<<<1, 512, sizeof(double) * (size_t)k * k, s>>>(b, k);
     kk_solve_kernel<0><<<k, tpb, 0, s>>>(b.lu, b.piv, b.t1, b.m, k, b.ctl);
   }
-  kk_gemm<KG_V1>(b, k, s);
-  kk_gemm<KG_W2>(b, k, s);
-  kk_e11_kernel<<<k, tpb, 0, s>>>(b, k, delta, beta_zero);
-  kk_gemm<KG_YTE>(b, k, s);
+  kk_gemm<KG_YTE>(b, k, s);                                                                     // Y^T E (W2 inside)
   if (b.mixed)
     kk_gemm_generic(b.zinv, true, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, s);     // N = -Z^T (Y^T E)
   else
@@ -457,20 +535,13 @@ void launch_kxk_stage(const SweepBufs& b, int k, double delta, int beta_zero, cu
 // ---------------------------------------------------------------------------
 // The same stage for a batch (split form, Newton-Schulz inverse): each launch
 // covers every problem, blockIdx.z selecting it; CTAs outside a problem's
-// k x k extent return at once.
+// k x k extent return at once.  Tiles of 16 for every problem.
 // ---------------------------------------------------------------------------
 __global__ void kk_prep_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
   const GroupItem& it = items[blockIdx.z];
   const SweepBufs& b = it.b[parity];
   if ((int)blockIdx.x >= it.k || b.ctl->done) return;
   kk_prep_body(b, it.k, blockIdx.x, kk_threads(it.k));
-}
-
-__global__ void kk_e11_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
-  const GroupItem& it = items[blockIdx.z];
-  const SweepBufs& b = it.b[parity];
-  if ((int)blockIdx.x >= it.k || b.ctl->done) return;
-  kk_e11_body(b, it.k, it.delta, it.beta_zero, blockIdx.x, kk_threads(it.k));
 }
 
 template <int MODE>
@@ -481,8 +552,32 @@ __global__ void __launch_bounds__(256) kk_gemm_grouped_kernel(const GroupItem* _
   kk_gemm_body<MODE>(b, it.k, blockIdx.x, blockIdx.y, b.ctl->done);   // the flag is acted on after the loads
 }
 
+// First Newton-Schulz product with E11 (16 x 16 tiles: blocks 0 .. nt^2 - 1 of
+// the problem's own nt = ceil(k / 16), then its k E11 columns).
+__global__ void __launch_bounds__(256) kk_ns_first_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  const int nt = (it.k + 15) / 16;
+  if ((int)blockIdx.x >= nt * nt + it.k) return;
+  const int done = b.ctl->done;
+  if ((int)blockIdx.x < nt * nt) {
+    kk_gemm_generic_body<0, 16>(b.y1, b.zinv, nullptr, b.res, it.k, -1.0, 0.0, 1, 0.0, b.ctl, blockIdx.x % nt,
+                                blockIdx.x / nt, done, kNsOnce);
+  } else if (!done) {
+    kk_e11_body(b, it.k, it.delta, it.beta_zero, blockIdx.x - nt * nt, kk_e11_vb(it.k));   // as a single problem's
+  }
+}
+
+__global__ void __launch_bounds__(256) kk_ns_second_grouped_kernel(const GroupItem* __restrict__ items, int parity,
+                                                                   int op) {
+  const GroupItem& it = items[blockIdx.z];
+  const SweepBufs& b = it.b[parity];
+  if ((int)blockIdx.x * 16 >= it.k || (int)blockIdx.y * 16 >= it.k) return;
+  kk_ns_second_body<16>(b, it.k, op, blockIdx.x, blockIdx.y, b.ctl->done);
+}
+
 // The products of the Newton-Schulz refresh and of M, N (see launch_kxk_stage).
-enum { NS_T1 = 0, NS_Z1 = 1, NS_T2 = 2, NS_Z2 = 3, NS_M = 4, NS_N = 5 };
+enum { NS_Z1 = 1, NS_M = 4, NS_N = 5 };
 
 template <int OP>
 __global__ void __launch_bounds__(256) kk_ns_grouped_kernel(const GroupItem* __restrict__ items, int parity) {
@@ -492,10 +587,7 @@ __global__ void __launch_bounds__(256) kk_ns_grouped_kernel(const GroupItem* __r
   if ((int)blockIdx.x * 16 >= k || (int)blockIdx.y * 16 >= k) return;
   const int done = b.ctl->done;   // acted on after the panel loads
   const int bx = blockIdx.x, by = blockIdx.y;
-  if (OP == NS_T1) kk_gemm_generic_body<0>(b.y1, b.zinv, nullptr, b.res, k, -1.0, 0.0, 1, 0.0, b.ctl, bx, by, done);
   if (OP == NS_Z1) kk_gemm_generic_body<0>(b.zinv, b.res, b.zinv, b.zinv2, k, 1.0, 1.0, 0, 0.0, b.ctl, bx, by, done);
-  if (OP == NS_T2) kk_gemm_generic_body<0>(b.y1, b.zinv2, nullptr, b.res, k, -1.0, 0.0, 1, 0.5, b.ctl, bx, by, done);
-  if (OP == NS_Z2) kk_gemm_generic_body<0>(b.zinv2, b.res, b.zinv2, b.zinv, k, 1.0, 1.0, 0, 0.0, b.ctl, bx, by, done);
   if (OP == NS_M) kk_gemm_generic_body<0>(b.zinv, b.t1, nullptr, b.m, k, -1.0, 0.0, 0, 0.0, b.ctl, bx, by, done);
   if (OP == NS_N) kk_gemm_generic_body<1>(b.zinv, b.yte, nullptr, b.nmat, k, -1.0, 0.0, 0, 0.0, b.ctl, bx, by, done);
 }
@@ -503,17 +595,15 @@ __global__ void __launch_bounds__(256) kk_ns_grouped_kernel(const GroupItem* __r
 void launch_kxk_stage_grouped(const GroupItem* items, const GroupDims& gd, int parity, cudaStream_t s) {
   const int k = gd.max_k;
   const int tpb = kk_threads(k);
+  const int nt = (k + 15) / 16;
   const dim3 gk(k, 1, gd.count);
-  const dim3 gt((k + 15) / 16, (k + 15) / 16, gd.count);
+  const dim3 gt(nt, nt, gd.count);
   kk_prep_grouped_kernel<<<gk, tpb, 0, s>>>(items, parity);
-  kk_ns_grouped_kernel<NS_T1><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_first_grouped_kernel<<<dim3(nt * nt + k, 1, gd.count), 256, 0, s>>>(items, parity);   // T, E11
   kk_ns_grouped_kernel<NS_Z1><<<gt, 256, 0, s>>>(items, parity);
-  kk_ns_grouped_kernel<NS_T2><<<gt, 256, 0, s>>>(items, parity);
-  kk_ns_grouped_kernel<NS_Z2><<<gt, 256, 0, s>>>(items, parity);
+  kk_ns_second_grouped_kernel<<<gt, 256, 0, s>>>(items, parity, 0);
+  kk_ns_second_grouped_kernel<<<gt, 256, 0, s>>>(items, parity, 1);
   kk_ns_grouped_kernel<NS_M><<<gt, 256, 0, s>>>(items, parity);
-  kk_gemm_grouped_kernel<KG_V1><<<gt, 256, 0, s>>>(items, parity);
-  kk_gemm_grouped_kernel<KG_W2><<<gt, 256, 0, s>>>(items, parity);
-  kk_e11_grouped_kernel<<<gk, tpb, 0, s>>>(items, parity);
   kk_gemm_grouped_kernel<KG_YTE><<<gt, 256, 0, s>>>(items, parity);
   kk_ns_grouped_kernel<NS_N><<<gt, 256, 0, s>>>(items, parity);
   kk_gemm_grouped_kernel<KG_X1><<<gt, 256, 0, s>>>(items, parity);

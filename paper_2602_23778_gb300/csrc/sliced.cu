@@ -66,7 +66,9 @@ template <int S>
 struct LoExp {
   static constexpr int value = kBits * (S - 1) + 14;    // lo carries 2^-value
 };
-constexpr int kRX = 2;             // X ring stages
+constexpr int kRX = 2;             // X ring stages (Gram products, update)
+constexpr int kRXProduct = 2;      // the product's X ring (a third stage in place of two A stages measured the same)
+constexpr int kRXMax = 2;
 constexpr int kATile = kBM * kBK * 2;                // 16 KiB
 constexpr int kXTile = kMaxS * kBN * kBK * 2;        // 32 KiB (all planes of a K block)
 constexpr int kEpiWarps = 8;       // two warps per TMEM lane group, 16 columns each
@@ -74,26 +76,28 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kNonFinite = -100000;  // exponent marking a row / column holding Inf or NaN
 constexpr uint64_t kTimeoutNs = 2000000000ull;       // 2 s: no legitimate wait comes close
 constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
-constexpr int kSmemBytesProduct = kRAProduct * kATile + kRX * kXTile + 1024 + 1024;
+constexpr int kSmemBytesProduct = kRAProduct * kATile + kRXProduct * kXTile + 1024 + 1024;
 constexpr int kTrStride = kBN / 2 + 1;               // doubles a row of a warp's 32 x 16 transpose block (no bank conflicts)
 constexpr int kTrBytes = kEpiWarps * 32 * kTrStride * 8;   // 34 KiB
 constexpr int kSmemBytesUpdate = kRAUpdate * kATile + kRX * kXTile + 1024 + kTrBytes + 1024;
 __host__ __device__ constexpr int ring_a(int mode) { return mode == 0 ? kRAProduct : (mode == 2 ? kRAUpdate : kRA); }
+__host__ __device__ constexpr int ring_x(int mode) { return mode == 0 ? kRXProduct : kRX; }
 __host__ __device__ constexpr int smem_bytes(int mode) {
   return mode == 0 ? kSmemBytesProduct : (mode == 2 ? kSmemBytesUpdate : kSmemBytes);
 }
 
-// A CTA's abort flag and the limit of each of its bounded waits (shared
-// memory).  The limit comes from the launch's arguments (0: kTimeoutNs); a
-// limit below 100 us is checked on every poll, so that a tiny one gives up at
-// the first wait that is not already complete.
+// A CTA's abort flag (shared memory).  Every bounded wait takes its limit in
+// a register (the launch's wait_ns, 0: kTimeoutNs) and reads the clock every
+// 64 polls (16 for the sleeping form); a limit under kShortWaitNs is checked
+// at every poll instead, so that a tiny one gives up at the first wait that
+// is not already complete.
 struct WaitState {
   volatile int abort;
-  unsigned long long limit_ns;
 };
+constexpr unsigned long long kShortWaitNs = 100000ull;
 
 struct __align__(8) Bars {
-  uint64_t a_full[kRAProduct], a_empty[kRAProduct], x_full[kRX], x_empty[kRX], acc_full[2], acc_empty[2], drain;
+  uint64_t a_full[kRAProduct], a_empty[kRAProduct], x_full[kRXMax], x_empty[kRXMax], acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
   WaitState wait;
 };
@@ -124,19 +128,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ void wait_state_init(WaitState* w, unsigned long long limit_ns) {
-  w->abort = 0;
-  w->limit_ns = limit_ns ? limit_ns : kTimeoutNs;
+__device__ __forceinline__ unsigned long long wait_limit(unsigned long long wait_ns) {
+  return wait_ns ? wait_ns : kTimeoutNs;
 }
 // Bounded wait: false when the CTA is aborting or the wait ran past the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, WaitState* w) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, WaitState* w, unsigned long long lim) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  const uint64_t lim = w->limit_ns;
-  const uint32_t mask = lim < 100000ull ? 0u : 63u;
+  const bool every = lim < kShortWaitNs;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & mask) == 0) {
+    if ((it & 63) == 0 || every) {
       if (w->abort) return false;
       if (globaltimer() - t0 > lim) {
         w->abort = 1;
@@ -148,15 +150,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, WaitSta
 // The same with a short sleep between polls after the first few: for waits
 // that are long against the work of the other warps on the SM (the spinning
 // lanes would take their issue slots).
-__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, WaitState* w) {
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, WaitState* w, unsigned long long lim) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  const uint64_t lim = w->limit_ns;
-  const uint32_t mask = lim < 100000ull ? 0u : 15u;
+  const bool every = lim < kShortWaitNs;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (it > 8 && mask) __nanosleep(128);
-    if ((it & mask) == 0) {
+    if (it > 8) __nanosleep(128);
+    if ((it & 15) == 0 || every) {
       if (w->abort) return false;
       if (globaltimer() - t0 > lim) {
         w->abort = 1;
@@ -303,10 +304,11 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int RA = ring_a(MODE);                   // A ring stages
   unsigned char* sa = smem;                          // RA x 16 KiB
-  unsigned char* sx = smem + RA * kATile;            // kRX x 32 KiB
-  Bars* bars = reinterpret_cast<Bars*>(sx + kRX * kXTile);
+  constexpr int RX = ring_x(MODE);                   // X ring stages
+  unsigned char* sx = smem + RA * kATile;            // RX x 32 KiB
+  Bars* bars = reinterpret_cast<Bars*>(sx + RX * kXTile);
   static_assert(sizeof(Bars) <= 1024, "barrier block");
-  double* s_tr = reinterpret_cast<double*>(sx + kRX * kXTile + 1024);   // UPDATE: 8 warps x 32 x kTrStride
+  double* s_tr = reinterpret_cast<double*>(sx + RX * kXTile + 1024);    // UPDATE: 8 warps x 32 x kTrStride
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column blocks vary fastest, so the CTAs sharing A-side rows run together
   const int job = MODE == MODE_GRAM ? (zb & 1) : 0;
@@ -350,13 +352,14 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   static_assert(2 * kMaxS * kBN <= 512, "two accumulator sets must fit in TMEM");
   const CUtensorMap* tB = job ? tmB2 : tmB;
   WaitState* wst = &bars->wait;
+  const unsigned long long wlim = wait_limit(g.wait_ns);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < RA; ++i) {
       mbar_init(smem_u32(&bars->a_full[i]), 1);
       mbar_init(smem_u32(&bars->a_empty[i]), 1);
     }
-    for (int i = 0; i < kRX; ++i) {
+    for (int i = 0; i < RX; ++i) {
       mbar_init(smem_u32(&bars->x_full[i]), 1);
       mbar_init(smem_u32(&bars->x_empty[i]), 1);
     }
@@ -365,7 +368,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       mbar_init(smem_u32(&bars->acc_empty[i]), kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bars->drain), 1);
-    wait_state_init(&bars->wait, g.wait_ns);
+    bars->wait.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -395,8 +398,8 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         const int m0 = it.mb * kBM;
         for (int kb = 0; kb < it.kb && ok; ++kb, ++gkb) {
           const int kx = (it.kb_lo + kb) * kBK;      // K coordinate (elements)
-          const int xs = gkb & 1;
-          ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb >> 1) & 1) ^ 1, wst);
+          const int xs = gkb % RX;
+          ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb / RX) & 1) ^ 1, wst, wlim);
           if (!ok) break;
           mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kBN * kBK * 2));
 #pragma unroll
@@ -406,7 +409,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           ++issued_x;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, wst);
+            ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, wst, wlim);
             if (!ok) break;
             mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
             tma_load_2d(smem_u32(sa + as * kATile), tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
@@ -422,8 +425,8 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         // let the copies this thread started land before the CTA leaves
         for (int i = (issued_a > RA ? issued_a - RA : 0); i < issued_a; ++i)
           mbar_drain(smem_u32(&bars->a_full[i % RA]), (i / RA) & 1);
-        for (int i = (issued_x > kRX ? issued_x - kRX : 0); i < issued_x; ++i)
-          mbar_drain(smem_u32(&bars->x_full[i % kRX]), (i / kRX) & 1);
+        for (int i = (issued_x > RX ? issued_x - RX : 0); i < issued_x; ++i)
+          mbar_drain(smem_u32(&bars->x_full[i % RX]), (i / RX) & 1);
       }
     }
   } else if (warp == 1) {
@@ -445,12 +448,12 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           const bool first = (kb % kChunkBlocks) == 0;
           const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
           if (first) {
-            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, wst);
+            ok = mbar_wait(smem_u32(&bars->acc_empty[buf]), ((c / NBUF) & 1) ^ 1, wst, wlim);
             if (!ok) break;
             tc_fence_after();
           }
-          const int xs = gkb & 1;
-          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb >> 1) & 1, wst);
+          const int xs = gkb % RX;
+          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb / RX) & 1, wst, wlim);
           if (!ok) break;
           tc_fence_after();
           const uint64_t xd = x_desc0 + (uint64_t)(xs * (kXTile >> 4));
@@ -458,7 +461,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           const uint32_t acc0 = first ? 0u : 1u;       // the chunk's first MMA overwrites every accumulator
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, wst);
+            ok = mbar_wait(smem_u32(&bars->a_full[as]), aph, wst, wlim);
             if (!ok) break;
             tc_fence_after();
             const uint64_t ad = a_desc0 + (uint64_t)(as * (kATile >> 4));
@@ -528,7 +531,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
         // one lane waits, the warp follows (the TMEM loads below are warp-collective);
         // it sleeps between polls, leaving issue slots to the MMA warp
         int w_ok = 0;
-        if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, wst);
+        if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[buf]), (c / NBUF) & 1, wst, wlim);
         ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
         __syncwarp();
         if (!ok) break;
@@ -789,6 +792,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
   const int KB = kb_hi - kb_lo;
   const int NC = (KB + kG16Chunk - 1) / kG16Chunk;
   WaitState* wst = &bars->wait;
+  const unsigned long long wlim = wait_limit(g.wait_ns);
   if (threadIdx.x == 0) {
     for (int i = 0; i < kG16Stages; ++i) {
       mbar_init(smem_u32(&bars->full[i]), 1);
@@ -797,7 +801,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
     mbar_init(smem_u32(&bars->acc_full), 1);
     mbar_init(smem_u32(&bars->acc_empty), kEpiWarps);
     mbar_init(smem_u32(&bars->drain), 1);
-    wait_state_init(&bars->wait, g.wait_ns);
+    bars->wait.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -820,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
       int issued = 0;
       for (int kb = 0; kb < KB && ok; ++kb) {
         const int st = kb % kG16Stages, lap = kb / kG16Stages;
-        ok = mbar_wait(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), wst);
+        ok = mbar_wait(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), wst, wlim);
         if (!ok) break;
         const int kx = (kb_lo + kb) * kBK;
         mbar_expect_tx(smem_u32(&bars->full[st]), (uint32_t)(2 * kTileBytes));
@@ -841,12 +845,12 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
         const bool first = (kb % kG16Chunk) == 0;
         const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
         if (first && c > 0) {   // one accumulator set: the previous chunk must be drained
-          ok = mbar_wait(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), wst);
+          ok = mbar_wait(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), wst, wlim);
           if (!ok) break;
           tc_fence_after();
         }
         const int st = kb % kG16Stages, lap = kb / kG16Stages;
-        ok = mbar_wait(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst);
+        ok = mbar_wait(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst, wlim);
         if (!ok) break;
         tc_fence_after();
         const uint64_t xd = smem_desc(smem_u32(smem + st * kG16Stage));
@@ -882,7 +886,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16_kernel(const __grid_const
     constexpr int kT0 = (S + 1) / 2;             // half 0 takes planes t < kT0, half 1 the rest
     for (int c = 0; c < NC && ok; ++c) {
       int w_ok = 0;
-      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full), (uint32_t)(c & 1), wst);
+      if (lane == 0) w_ok = mbar_wait(smem_u32(&bars->acc_full), (uint32_t)(c & 1), wst, wlim);
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       __syncwarp();
       if (!ok) break;
@@ -1728,6 +1732,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
   const int G = gridDim.x;
   const int cnt = (g.tiles - (int)blockIdx.x + G - 1) / G;   // this CTA's tiles: blockIdx.x + i G
   WaitState* wst = &bars->wait;
+  const unsigned long long wlim = wait_limit(g.wait_ns);
   if (threadIdx.x == 0) {
     for (int i = 0; i < kU16Stages; ++i) {
       mbar_init(smem_u32(&bars->full[i]), 1);
@@ -1741,7 +1746,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     }
     for (int i = 0; i < 16; ++i) mbar_init(smem_u32(&bars->sub[i >> 2][i & 3]), 2);
     mbar_init(smem_u32(&bars->drain), 1);
-    wait_state_init(&bars->wait, g.wait_ns);
+    bars->wait.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -1780,7 +1785,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       int issued = 0;
       for (int i = 0; i < cnt && ok; ++i) {
         const int st = i % kU16Stages, lap = i / kU16Stages;
-        ok = mbar_wait_sleep(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), wst);
+        ok = mbar_wait_sleep(smem_u32(&bars->empty[st]), (uint32_t)((lap & 1) ^ 1), wst, wlim);
         if (!ok) break;
         const int row0 = ((int)blockIdx.x + i * G) * 128;
         unsigned char* sx = stage0 + st * kU16Stage;
@@ -1800,8 +1805,8 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       const uint64_t bd = smem_desc(smem_u32(bop));
       for (int i = 0; i < cnt && ok; ++i) {
         const int a = i & 1, u = i >> 1;
-        ok = mbar_wait_sleep(smem_u32(&bars->a_full[a]), (uint32_t)(u & 1), wst);
-        if (ok) ok = mbar_wait_sleep(smem_u32(&bars->acc_empty[a]), (uint32_t)((u & 1) ^ 1), wst);
+        ok = mbar_wait_sleep(smem_u32(&bars->a_full[a]), (uint32_t)(u & 1), wst, wlim);
+        if (ok) ok = mbar_wait_sleep(smem_u32(&bars->acc_empty[a]), (uint32_t)((u & 1) ^ 1), wst, wlim);
         if (!ok) break;
         tc_fence_after();
         const uint32_t ab = smem_u32(abuf0 + a * kU16ABuf);
@@ -1843,12 +1848,12 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       const int st = i % kU16Stages, lap = i / kU16Stages, a = i & 1;
       int w_ok = 1;
       if (lane == 0) {
-        w_ok = mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst);
-        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[a]), (uint32_t)(((i >> 1) & 1) ^ 1), wst);
+        w_ok = mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst, wlim);
+        if (w_ok) w_ok = mbar_wait_sleep(smem_u32(&bars->a_empty[a]), (uint32_t)(((i >> 1) & 1) ^ 1), wst, wlim);
       }
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       if (!ok) break;
-      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst);   // complete: each lane acquires
+      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst, wlim);   // complete: each lane acquires
       const unsigned char* xt = stage0 + st * kU16Stage;
       unsigned long long b[16];
       unsigned long long am = 0ull;
@@ -1891,7 +1896,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     for (int i = 0; i < cnt && ok; ++i) {
       const int a = i & 1, u = i >> 1;
       int w_ok = 1;
-      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[a]), (uint32_t)(u & 1), wst);
+      if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->acc_full[a]), (uint32_t)(u & 1), wst, wlim);
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       if (!ok) break;
       __syncwarp();
@@ -1899,7 +1904,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       // the X and W tiles of this tile: loaded (the slicers waited for them)
       // and not refilled before this warp's leader releases the stage
       const int st = i % kU16Stages;
-      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)((i / kU16Stages) & 1), wst);
+      mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)((i / kU16Stages) & 1), wst, wlim);
       unsigned char* xt = stage0 + st * kU16Stage;
       const unsigned char* wt = xt + kU16Tile;
       // the row's exponent (as the slicers took it) and this thread's X values
@@ -1960,7 +1965,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       if (leader) {
         int s_ok = 1;
         if (lane == 0) {
-          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg][i & 3]), (uint32_t)((i >> 2) & 1), wst);
+          s_ok = mbar_wait_sleep(smem_u32(&bars->sub[lg][i & 3]), (uint32_t)((i >> 2) & 1), wst, wlim);
           if (s_ok) {
             if (!plain && row0 + 32 * lg < g.n) {
               tma_store_2d(&tmXn, smem_u32(xt + lg * 32 * 128), 0, (int)(row0 + 32 * lg));
@@ -2072,6 +2077,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
   const int kb_hi = (int)((int64_t)g.kb_total * (split + 1) / g.ksplit);
   const int KB = kb_hi - kb_lo;
   WaitState* wst = &bars->wait;
+  const unsigned long long wlim = wait_limit(g.wait_ns);
   if (threadIdx.x == 0) {
     for (int i = 0; i < kG16FRaw; ++i) {
       mbar_init(smem_u32(&bars->raw_full[i]), 1);
@@ -2084,7 +2090,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
     mbar_init(smem_u32(&bars->acc_full), 1);
     mbar_init(smem_u32(&bars->acc_empty), kEpiWarps);
     mbar_init(smem_u32(&bars->drain), 1);
-    wait_state_init(&bars->wait, g.wait_ns);
+    bars->wait.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -2107,7 +2113,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       int issued = 0;
       for (int kb = 0; kb < KB && ok; ++kb) {
         const int st = kb % kG16FRaw, lap = kb / kG16FRaw;
-        ok = mbar_wait_sleep(smem_u32(&bars->raw_empty[st]), (uint32_t)((lap & 1) ^ 1), wst);
+        ok = mbar_wait_sleep(smem_u32(&bars->raw_empty[st]), (uint32_t)((lap & 1) ^ 1), wst, wlim);
         if (!ok) break;
         const int row = (kb_lo + kb) * kBK;
         unsigned char* rt = raw0 + st * 2 * kG16FRawTile;
@@ -2129,12 +2135,12 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
         const bool first = (kb % kG16Chunk) == 0;
         const bool last = (kb % kG16Chunk) == kG16Chunk - 1 || kb == KB - 1;
         if (first && c > 0) {   // one accumulator set: the previous chunk must be drained
-          ok = mbar_wait_sleep(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), wst);
+          ok = mbar_wait_sleep(smem_u32(&bars->acc_empty), (uint32_t)((c - 1) & 1), wst, wlim);
           if (!ok) break;
           tc_fence_after();
         }
         const int pb = kb % kG16FPlanes;
-        ok = mbar_wait_sleep(smem_u32(&bars->pl_full[pb]), (uint32_t)((kb / kG16FPlanes) & 1), wst);
+        ok = mbar_wait_sleep(smem_u32(&bars->pl_full[pb]), (uint32_t)((kb / kG16FPlanes) & 1), wst, wlim);
         if (!ok) break;
         tc_fence_after();
         unsigned char* pt = pl0 + pb * kG16Stage;
@@ -2174,13 +2180,13 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       const int st = kb % kG16FRaw, pb = kb % kG16FPlanes;
       int w_ok = 1;
       if (lane == 0) {
-        w_ok = mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), wst);
+        w_ok = mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), wst, wlim);
         if (w_ok)
-          w_ok = mbar_wait_sleep(smem_u32(&bars->pl_empty[pb]), (uint32_t)(((kb / kG16FPlanes) & 1) ^ 1), wst);
+          w_ok = mbar_wait_sleep(smem_u32(&bars->pl_empty[pb]), (uint32_t)(((kb / kG16FPlanes) & 1) ^ 1), wst, wlim);
       }
       ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
       if (!ok) break;
-      mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), wst);   // each lane acquires
+      mbar_wait_sleep(smem_u32(&bars->raw_full[st]), (uint32_t)((kb / kG16FRaw) & 1), wst, wlim);   // each lane acquires
       {
         const unsigned char* rt = raw0 + (st * 2 + op) * kG16FRawTile;
         unsigned long long b[8];
@@ -2207,7 +2213,7 @@ __global__ void __launch_bounds__(kThreads, 1) sgram16f_kernel(const __grid_cons
       if (last) {
         const int c = kb / kG16Chunk;
         int a_ok = 1;
-        if (lane == 0) a_ok = mbar_wait_sleep(smem_u32(&bars->acc_full), (uint32_t)(c & 1), wst);
+        if (lane == 0) a_ok = mbar_wait_sleep(smem_u32(&bars->acc_full), (uint32_t)(c & 1), wst, wlim);
         ok = __shfl_sync(0xffffffffu, a_ok, 0) != 0;
         __syncwarp();
         if (!ok) break;
