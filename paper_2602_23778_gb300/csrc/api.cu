@@ -244,13 +244,14 @@ int launch_sweep(const Problem& pr, SweepBufs b, double shift, double delta, int
   launches += b.mixed ? 9 : 7;
   if (pr.sliced) {
     pr.sliced->update(b.x, b.p, b.fm, b.d, b.dinv, b.xn, b.upart, b.ctl, s);
-    launches += 4;
+    launches += b.fm_cmax ? 3 : 4;
   } else {
     launch_update_rows(b, n, k, s);
     launches += 1;
   }
   launch_finalize(b, k, delta, s);
-  launch_normalize(b, n, k, s);
+  // split form with fused maxima: the normalisation also forms X's column maxima
+  launch_normalize(b, n, k, s, (pr.sliced && pr.sliced->fused_maxima()) ? pr.sliced->x_cmax() : nullptr);
   return launches + 2;
 }
 
@@ -372,8 +373,15 @@ Control run_control(const Run& r) {
 }
 
 // Column maxima the first sweep's slicing reads when the producers form them:
-// those of the starting X, and none yet for P.
+// those of the starting X, and none yet for P (or the [F | M] panel).
 void run_setup_maxima(const Run& r, cudaStream_t s) {
+  if (r.pr.sliced && r.pr.sliced->fused_maxima()) {
+    SlicedA* sl = r.pr.sliced;
+    cudaMemsetAsync(sl->p_cmax(), 0, (size_t)r.pr.k * 8, s);
+    cudaMemsetAsync(sl->fm_cmax(), 0, (size_t)kfm_cols(r.pr.k) * 8, s);
+    cudaMemsetAsync(sl->x_cmax(), 0, (size_t)r.pr.k * 8, s);
+    sl::launch_colmax_rowmajor(r.xbuf[0], r.pr.n, r.pr.k, sl->x_cmax(), nullptr, s);
+  }
   if (!r.pr.fused_max) return;
   cudaMemsetAsync(r.pr.p_cmax, 0, (size_t)r.pr.k * 8, s);
   r.pr.sgram->colmax_x(r.xbuf[0], s);
@@ -599,6 +607,13 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
       !h->tuned.count(std::make_tuple(r.pr.n, r.pr.k, r.pr.sliced->slices()))) {
     st = tune_splits(h, r, s);
     if (st) return st;
+  }
+  if (r.pr.sliced && !r.pr.square) {
+    // from here on the kernels that write X, P and the [F | M] panel form the
+    // column maxima the slicing needs (the autotuner's runs above did not)
+    r.pr.sliced->set_fused_maxima(true);
+    r.b.fm_cmax = r.pr.sliced->fm_cmax();
+    run_setup_maxima(r, s);
   }
   run_setup_inverse(r, s);
 

@@ -52,6 +52,8 @@ struct SweepBufs {
   double *zinv, *zinv2;  // k x k: Y1^{-1} kept across sweeps (split form) and a scratch copy
   double* fm;         // split form, dense: k x kfm(k) column-major, F and M interleaved in blocks of 16
                       // columns (block q: F(:, 16q .. 16q+15), then M(:, 16q .. 16q+15)), or null
+  unsigned long long* fm_cmax;   // or null: fm's column maxima of |.| (bit patterns), cleared by the prep
+                                 // step and formed where fm is written
   int mixed;          // 1: Y1^{-1} by Newton-Schulz updates instead of an LU per sweep
   int* piv;           // [k]
   double *alpha, *d, *dinv, *nu, *r1sq, *e11sq, *x1sq;  // [k]

@@ -431,46 +431,49 @@ __device__ __forceinline__ void finalize_body(const SweepBufs& b, int k) {
     emin = ctl->emin;
     bad = 0;
   }
-  // column sums of the update partials [ugrid][3k]: thread (grp, c) adds
-  // partials grp, grp + groups, ... of column c (consecutive threads read
-  // consecutive addresses), then the groups are added in order; fixed order,
-  // so the result is reproducible
-  __shared__ double part_s[1024];
-  __shared__ double top_s[1024];
+  // Column sums of the update partials [ugrid][3k] and of the squares of the
+  // leading block's rows: row group rg = tid / 128 (8 of them) takes rows
+  // rg, rg + 8, ... and its 128 threads the columns c, c + 128, c + 256, so
+  // each thread has all its loads (about 50 at 3k = 384) in flight at once;
+  // the 8 row-group sums of a column are then added in order (fixed order,
+  // reproducible).
+  constexpr int kRG = 8;
+  __shared__ double part_s[kRG][3 * kMaxK];
+  __shared__ double top_s[kRG * kMaxK];
   __shared__ double v2_s[kMaxK];
   {
-    const int w2 = 3 * k, groups = (int)blockDim.x / w2;
-    if (tid < groups * w2) {
-      const int c = tid % w2, grp = tid / w2;
-      double acc = 0.0;
-#pragma unroll 8
-      for (int g = grp; g < b.ugrid; g += groups) acc += b.upart[(int64_t)g * w2 + c];
-      part_s[grp * w2 + c] = acc;
-    }
-    // the leading block's column sums of squares the same way: thread
-    // (grp, j) takes rows grp, grp + g2, ...
-    const int g2 = (int)blockDim.x / k;
-    if (tid < g2 * k) {
-      const int j = tid % k, grp = tid / k;
-      double acc = 0.0;
-#pragma unroll 4
-      for (int i = grp; i < k; i += g2) {
-        const double v = b.xn[(int64_t)i * k + j];
-        acc += v * v;
+    const int w3 = 3 * k, rg = tid >> 7, t = tid & 127;
+    if (rg < kRG) {
+      double acc[3] = {0.0, 0.0, 0.0};
+      for (int g = rg; g < b.ugrid; g += kRG) {
+        const double* row = b.upart + (int64_t)g * w3;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (t + 128 * q < w3) acc[q] += row[t + 128 * q];
       }
-      top_s[grp * k + j] = acc;
+      // the leading block's rows i = rg, rg + 8, ... of column t (X' row-major)
+      double top = 0.0;
+      if (t < k)
+        for (int i = rg; i < k; i += kRG) {
+          const double v = b.xn[(int64_t)i * k + t];
+          top = fma(v, v, top);
+        }
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (t + 128 * q < w3) part_s[rg][t + 128 * q] = acc[q];
+      if (t < k) top_s[rg * k + t] = top;
     }
     __syncthreads();
     if (tid < k) {
       const int j = tid;
-      double xsq = 0.0, r2 = 0.0, v2 = 0.0;
-      for (int grp = 0; grp < groups; ++grp) {
-        xsq += part_s[grp * w2 + j];
-        r2 += part_s[grp * w2 + k + j];
-        v2 += part_s[grp * w2 + 2 * k + j];
+      double xsq = 0.0, r2 = 0.0, v2 = 0.0, tp = 0.0;
+      for (int g = 0; g < kRG; ++g) {
+        xsq += part_s[g][j];
+        r2 += part_s[g][k + j];
+        v2 += part_s[g][2 * k + j];
+        tp += top_s[g * k + j];
       }
-      for (int grp = 0; grp < g2; ++grp) xsq += top_s[grp * k + j];
-      xsq_s[j] = xsq;
+      xsq_s[j] = xsq + tp;
       r2_s[j] = r2;
       v2_s[j] = v2;
     }

@@ -81,6 +81,8 @@ __device__ __forceinline__ void kk_prep_body(const SweepBufs& b, int k, int j, i
     b.y1[e] = x - (i == j ? 1.0 : 0.0);
     r1s += r1 * r1;
   }
+  if (b.fm_cmax && j == 0)   // read by the last update's slicing; formed again below by the X1 product
+    for (int c = threadIdx.x; c < kfm_cols(k); c += blockDim.x) b.fm_cmax[c] = 0ull;
   r1s = block_sum(r1s, sh, vb);
   if (threadIdx.x == 0) {
     if (j == 0) b.ctl->ns_twice = 0;
@@ -297,16 +299,34 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
     b.yte[e] = s + (b.z[e] - w2) / b.d[j];
     return;
   }
-  if (i >= k || j >= k) return;
+  const bool live = i < k && j < k;
   const int64_t e = i + (int64_t)j * k;
-  {
+  double f = 0.0, mv = 0.0;
+  if (live) {
     b.xn[(int64_t)i * k + j] = b.x[(int64_t)i * k + j] + b.e11[e] - s;
-    const double f = b.m[e] / b.d[j] + b.nmat[e];
+    f = b.m[e] / b.d[j] + b.nmat[e];
+    mv = b.m[e];
     b.f[e] = f;
     if (b.fm) {   // the tensor-core update's operand: F and M side by side (X2 F and X2 M in one pass)
       const int64_t c = kfm_col(j);
       b.fm[i + c * k] = f;
-      b.fm[i + (c + 16) * k] = b.m[e];
+      b.fm[i + (c + 16) * k] = mv;
+    }
+  }
+  if (b.fm_cmax) {
+    // the panel's column maxima: the TT rows of column j sit on TT consecutive
+    // lanes (tx = threadIdx % TT); their maximum, then one atomic a column and tile
+    unsigned long long mf = live ? (unsigned long long)__double_as_longlong(f) & 0x7FFFFFFFFFFFFFFFull : 0ull;
+    unsigned long long mm = live ? (unsigned long long)__double_as_longlong(mv) & 0x7FFFFFFFFFFFFFFFull : 0ull;
+#pragma unroll
+    for (int o = 1; o < TT && o < 32; o <<= 1) {
+      mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+      mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+    }
+    if (tx == 0 && j < k) {
+      const int c = kfm_col(j);
+      atomicMax(b.fm_cmax + c, mf);
+      atomicMax(b.fm_cmax + c + 16, mm);
     }
   }
   (void)kk;

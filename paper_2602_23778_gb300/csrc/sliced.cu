@@ -1292,8 +1292,13 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
                                                          int64_t cs, int K, int kp,
                                                          const unsigned long long* __restrict__ cmax,
                                                          __half* __restrict__ planes, int* __restrict__ colexp,
-                                                         const Control* ctl) {
+                                                         const Control* ctl, unsigned long long* clear = nullptr,
+                                                         int nclear = 0) {
   if (ctl && ctl->done) return;
+  // another operand's column maxima, read by an earlier kernel: cleared for
+  // the kernel that forms them next
+  if (clear && blockIdx.x == 0 && blockIdx.y == 0)
+    for (int j = threadIdx.x; j < nclear; j += blockDim.x) clear[j] = 0ull;
   slice_cols_body<S>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, blockIdx.x, blockIdx.y);
 }
 
@@ -1451,24 +1456,59 @@ __global__ void slice_rows_grouped_kernel(const GroupItem* __restrict__ items, i
 // ksplit partials an element.  Equal-work ranges (R > 0): the ranges that
 // touch the element's row tile (U units of kbt K blocks a column block).
 template <int S>
-__global__ void product_reduce_kernel(const longlong2* __restrict__ part, int ksplit, const int* __restrict__ rowexp,
-                                      const int* __restrict__ colexp, int k, const double* __restrict__ Xs,
-                                      double* __restrict__ P, int64_t total, double shift, const Control* ctl,
-                                      int64_t R, int64_t U, int64_t kbt) {
+// P = recombined sum of a tile's exact partial slots - shift Xs.  One CTA per
+// (row tile, 32-column block): the tile's slot count is worked out once, a
+// warp covers 32 consecutive columns of a row (coalesced), 8 rows a step.
+__global__ void __launch_bounds__(256) product_reduce_kernel(const longlong2* __restrict__ part, int ksplit,
+                                                             const int* __restrict__ rowexp,
+                                                             const int* __restrict__ colexp, int k,
+                                                             const double* __restrict__ Xs, double* __restrict__ P,
+                                                             int64_t n, double shift, const Control* ctl, int64_t R,
+                                                             int64_t U, int64_t kbt,
+                                                             unsigned long long* __restrict__ pmax = nullptr,
+                                                             unsigned long long* clear = nullptr, int nclear = 0) {
   if (ctl && ctl->done) return;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    long long hi = 0, lo = 0;
-    int nq = ksplit;
-    if (R > 0) {
-      const int64_t u = (e / k) / kBM * kbt;   // first unit of the row tile
-      nq = (int)(((u + kbt) * R - 1) / U - ((u + 1) * R - 1) / U) + 1;
+  if (clear && blockIdx.x == 0 && blockIdx.y == 0)   // maxima read by an earlier kernel, formed again later
+    for (int j = threadIdx.x; j < nclear; j += blockDim.x) clear[j] = 0ull;
+  __shared__ unsigned long long wmax[8][32];
+  const int64_t tile = blockIdx.x;
+  int nq = ksplit;
+  if (R > 0) {
+    const int64_t u = tile * kbt;   // first unit of the row tile
+    nq = (int)(((u + kbt) * R - 1) / U - ((u + 1) * R - 1) / U) + 1;
+  }
+  const int c = (int)blockIdx.y * 32 + (int)(threadIdx.x & 31);
+  const int64_t total = n * k;
+  const int64_t r0 = tile * kBM;
+  unsigned long long m = 0ull;   // max |P| of this thread's rows, as an ordered bit pattern
+  if (c < k) {
+    const int fc = colexp[c];
+#pragma unroll 4
+    for (int lr = (int)(threadIdx.x >> 5); lr < kBM; lr += 8) {
+      const int64_t row = r0 + lr;
+      if (row >= n) break;
+      const int64_t e = row * k + c;
+      long long hi = 0, lo = 0;
+      for (int q = 0; q < nq; ++q) {
+        const longlong2 v = part[(int64_t)q * total + e];
+        hi += v.x;
+        lo += v.y;
+      }
+      const double w = recombine<S>(hi, lo, rowexp[row], fc) - shift * Xs[e];
+      P[e] = w;
+      m = max(m, abs_bits(w));
     }
-    for (int q = 0; q < nq; ++q) {
-      const longlong2 v = part[(int64_t)q * total + e];
-      hi += v.x;
-      lo += v.y;
+  }
+  if (pmax) {
+    // the eight warps' maxima of each column, then one atomic a column and CTA
+    wmax[threadIdx.x >> 5][threadIdx.x & 31] = m;
+    __syncthreads();
+    if (threadIdx.x < 32 && c < k) {
+      unsigned long long mm = 0ull;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) mm = max(mm, wmax[w][threadIdx.x]);
+      atomicMax(pmax + c, mm);
     }
-    P[e] = recombine<S>(hi, lo, rowexp[e / k], colexp[e % k]) - shift * Xs[e];
   }
 }
 
@@ -1560,6 +1600,16 @@ template <int S>
 void launch_slice_a(const double* A, int64_t n, int64_t lda, int n_pad, __half* As, int* rowexp,
                     cudaStream_t s) {
   slice_a_kernel<S><<<152 * 8, 256, 0, s>>>(A, n, lda, n_pad, As, rowexp);
+}
+
+// Column planes of Y with its column maxima already in cmax (formed by the
+// kernel that wrote Y); `clear` (nclear entries) is zeroed on the way.
+template <int S>
+void launch_slice_cols_ready(const double* Y, int64_t rows, int k, int64_t rs, int64_t cs, int K, int kp,
+                             const unsigned long long* cmax, __half* planes, int* colexp, const Control* ctl,
+                             cudaStream_t s, unsigned long long* clear = nullptr, int nclear = 0) {
+  dim3 gx((unsigned)(K / 64), (unsigned)((kp + 31) / 32));
+  slice_cols_kernel<S><<<gx, 256, 0, s>>>(Y, rows, k, rs, cs, K, kp, cmax, planes, colexp, ctl, clear, nclear);
 }
 
 template <int S>
@@ -2559,11 +2609,14 @@ static void launch_mma(int S, dim3 grid, const CUtensorMap& a, const CUtensorMap
 }
 
 static void launch_product_reduce(int S, const MmaTask& t, int psplit, const double* Xs, double* P, int64_t total,
-                                  double shift, const Control* ctl, cudaStream_t s) {
-  const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+                                  double shift, const Control* ctl, cudaStream_t s,
+                                  unsigned long long* pmax = nullptr, unsigned long long* clear = nullptr) {
+  const int64_t n = total / t.g.k;
+  const dim3 rg((unsigned)((n + sl::kBM - 1) / sl::kBM), (unsigned)((t.g.k + 31) / 32));
 #define EIGREF_CALL_PR(S_)                                                                                   \
-  sl::product_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.ppart, psplit, t.g.rowexp, t.g.colexp, t.g.k, Xs, P, total, \
-                                                   shift, ctl, t.g.sk_ranges, t.g.sk_units, t.g.kb_total)
+  sl::product_reduce_kernel<S_><<<rg, 256, 0, s>>>(t.g.ppart, psplit, t.g.rowexp, t.g.colexp, t.g.k, Xs, P, n, shift, \
+                                                   ctl, t.g.sk_ranges, t.g.sk_units, t.g.kb_total, pmax, clear, \
+                                                   clear ? t.g.k : 0)
   EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_PR)
 #undef EIGREF_CALL_PR
 }
@@ -2701,21 +2754,42 @@ int SlicedA::product(const double* X, double* P, double shift, const Control* ct
   const SlicedLayout L = sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_);
   auto* xp = reinterpret_cast<__half*>(ws_ + L.x_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.x_cmax);
+  auto* pmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* colexp = reinterpret_cast<int*>(ws_ + L.x_colexp);
-#define EIGREF_CALL_SLICE_X(S_) \
-  sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, n_pad_, k_pad_, cmax, xp, colexp, ctl, s)
+  // fused maxima: X's came from the normalisation; P's maxima (read by the
+  // last Gram slicing) are cleared here and formed by the reduction, which
+  // clears X's once this slicing has read them
+  const bool fused = fused_max_ && psplit_ > 1;
+#define EIGREF_CALL_SLICE_X(S_)                                                                              \
+  if (fused)                                                                                                 \
+    sl::launch_slice_cols_ready<S_>(X, n_, k_, k_, 1, n_pad_, k_pad_, cmax, xp, colexp, ctl, s, pmax, k_);   \
+  else                                                                                                       \
+    sl::launch_slice_cols<S_>(X, n_, k_, k_, 1, n_pad_, k_pad_, cmax, xp, colexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_X)
 #undef EIGREF_CALL_SLICE_X
   const MmaTask t = product_task(X, P, shift, ctl);
   if (ev0) cudaEventRecordWithFlags(ev0, s, ev_flags);
   launch_task(slices_, sl::MODE_PRODUCT, t, s);
-  if (psplit_ > 1) {
-    const int64_t total = n_ * k_;
-    const int rg = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-    launch_product_reduce(slices_, t, psplit_, X, P, total, shift, ctl, s);
-  }
+  if (psplit_ > 1)
+    launch_product_reduce(slices_, t, psplit_, X, P, n_ * k_, shift, ctl, s, fused ? pmax : nullptr,
+                          fused ? cmax : nullptr);
   if (ev1) cudaEventRecordWithFlags(ev1, s, ev_flags);
-  return psplit_ > 1 ? 4 : 3;
+  return psplit_ > 1 ? (fused ? 3 : 4) : 3;
+}
+
+bool SlicedA::fused_maxima() const { return fused_max_ && psplit_ > 1; }
+
+unsigned long long* SlicedA::x_cmax() const {
+  return reinterpret_cast<unsigned long long*>(
+      ws_ + sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_).x_cmax);
+}
+unsigned long long* SlicedA::p_cmax() const {
+  return reinterpret_cast<unsigned long long*>(
+      ws_ + sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_).p_cmax);
+}
+unsigned long long* SlicedA::fm_cmax() const {
+  return reinterpret_cast<unsigned long long*>(
+      ws_ + sliced_layout(n_pad_, k_pad_, kr_, slices_, ksplit_max_, k_, pslots_, n_).f_cmax);
 }
 
 int SlicedA::product_sq(const double* X, double* T, double* P, double alpha, const Control* ctl, cudaStream_t s,
@@ -2755,8 +2829,12 @@ int SlicedA::gram(const double* P, double* part, double* out, const Control* ctl
   auto* pp = reinterpret_cast<__half*>(ws_ + L.p_planes);
   auto* cmax = reinterpret_cast<unsigned long long*>(ws_ + L.p_cmax);
   int* pexp = reinterpret_cast<int*>(ws_ + L.p_colexp);
-#define EIGREF_CALL_SLICE_P(S_) \
-  sl::launch_slice_cols<S_>(P, n_, k_, k_, 1, n_pad_, k_pad_, cmax, pp, pexp, ctl, s)
+  const bool fused = fused_maxima();   // P's maxima formed by the product's reduction
+#define EIGREF_CALL_SLICE_P(S_)                                                                   \
+  if (fused)                                                                                      \
+    sl::launch_slice_cols_ready<S_>(P, n_, k_, k_, 1, n_pad_, k_pad_, cmax, pp, pexp, ctl, s);    \
+  else                                                                                            \
+    sl::launch_slice_cols<S_>(P, n_, k_, k_, 1, n_pad_, k_pad_, cmax, pp, pexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_P)
 #undef EIGREF_CALL_SLICE_P
   const MmaTask t = gram_task(part, ctl);
@@ -2785,9 +2863,13 @@ int SlicedA::update(const double* X, const double* W, const double* FM, const do
   auto* fmax_ = reinterpret_cast<unsigned long long*>(ws_ + L.f_cmax);
   // FM is k x kfm column-major: element (l, c) at FM[l + c k]
   const int kfm = kfm_cols(k_);
+  const bool fused = fused_max_;   // the [F | M] panel's maxima formed by the k x k stage
 #define EIGREF_CALL_SLICE_UPD(S_)                                                                       \
   sl::launch_slice_rows<S_>(X, n_, k_, n_pad_, kr_, xr, xrexp, ctl, s);                                 \
-  sl::launch_slice_cols<S_>(FM, k_, kfm, 1, k_, kr_, kfm, fmax_, fp, fexp, ctl, s)
+  if (fused)                                                                                            \
+    sl::launch_slice_cols_ready<S_>(FM, k_, kfm, 1, k_, kr_, kfm, fmax_, fp, fexp, ctl, s);             \
+  else                                                                                                  \
+    sl::launch_slice_cols<S_>(FM, k_, kfm, 1, k_, kr_, kfm, fmax_, fp, fexp, ctl, s)
   EIGREF_SLICE_DISPATCH(slices_, EIGREF_CALL_SLICE_UPD)
 #undef EIGREF_CALL_SLICE_UPD
   const MmaTask t = update_task(X, W, d, dinv, Xn, upart, ctl);

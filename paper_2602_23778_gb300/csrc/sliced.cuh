@@ -68,6 +68,12 @@ void launch_slice_grouped(int S, int op, const GroupItem* items, const GroupDims
 
 cudaError_t init_sliced_attributes();
 
+namespace sl {
+// Column maxima of |Y| (row-major rows x k) as non-negative double bit patterns, atomicMax into cmax.
+void launch_colmax_rowmajor(const double* Y, int64_t rows, int k, unsigned long long* cmax, const Control* ctl,
+                            cudaStream_t s);
+}  // namespace sl
+
 class SlicedA {
  public:
   // Host-side plan for A (device, n x n, lda) and k columns; no device work.
@@ -128,10 +134,24 @@ class SlicedA {
   int ksplit() const { return ksplit_; }
   // Limit of every bounded wait inside the tensor-core kernels (0: 2 s).
   void set_wait_ns(unsigned long long ns) { wait_ns_ = ns; }
+  // Fused column maxima (single-problem sweeps, after any autotuning): the
+  // slicing of X, P and the [F | M] panel reads maxima that the kernels
+  // writing them formed -- X's by the normalisation (launch_normalize with
+  // x_cmax()), P's by the product's reduction, the panel's by the k x k stage
+  // (SweepBufs::fm_cmax) -- in place of passes of their own.  X's maxima must
+  // hold the starting X's when the first sweep begins; P's and the panel's
+  // must be zero.  fused_maxima(): the product uses them (it needs the
+  // reduction, i.e. a K decomposition other than one split).
+  void set_fused_maxima(bool on) { fused_max_ = on; }
+  bool fused_maxima() const;
+  unsigned long long* x_cmax() const;
+  unsigned long long* p_cmax() const;
+  unsigned long long* fm_cmax() const;
   const char* error() const { return err_; }
 
  private:
   unsigned long long wait_ns_ = 0;
+  bool fused_max_ = false;
   size_t layout_total() const;
   const double* A_ = nullptr;
   int64_t n_ = 0, lda_ = 0;
