@@ -444,12 +444,18 @@ def measure_dense_n8192(args, local):
     r = h.refine_dense(A, X0.clone(), max_iters=60000, tol=1e-14, stop="residual", check_every=1024,
                        history=True, **kw)
     torch.cuda.synchronize()
-    r0 = float(r["hist_residual"][0]) if r["iterations"] else float("nan")
+    hr = np.asarray(r["hist_residual"])
+    T = len(hr)
+    # the asymptotic linear rate: the residual's decay per sweep over the last
+    # fifth of the run (where the slowest non-target component dominates),
+    # beside gamma = max |lambda| off the targets / min |lambda| on them
+    t0, t1 = int(0.8 * T), T - 1
+    rate = float(np.exp((np.log(hr[t1]) - np.log(hr[t0])) / (t1 - t0))) if T > 10 else float("nan")
     out["to_tolerance"] = {
         "form": "bf16", "status": r["status_string"], "sweeps": r["iterations"],
-        "final_rel_residual": r["final_rel_residual"], "first_rel_residual": r0,
-        "predicted_sweeps": float(np.log(1e-14 / r0) / np.log(gamma)) if r0 > 1e-14 else 0.0,
-        "prediction": "log(1e-14 / ||R_0||) / log(gamma): the slowest non-target component decays by gamma a sweep",
+        "final_rel_residual": r["final_rel_residual"], "first_rel_residual": float(hr[0]) if T else None,
+        "measured_rate": rate, "gamma": gamma, "rate_over_gamma": rate / gamma,
+        "rate_note": "residual decay per sweep over the last fifth of the run; the end of Section 3.2 predicts gamma",
         "seconds": r["sweeps_ms"] * 1e-3}
     h.close()
     return out
@@ -470,13 +476,21 @@ def measure_dense_n512(args, local):
     for form in ("bf16", "fp64"):
         kw = dict(norm_a=p.normA, target="shift", shift=p.shift, precision=form)
         h.refine_dense(A, X0.clone(), max_iters=10, check_every=10, **kw)
-        ms = []
+        calls = []
         for _ in range(5):
-            r = h.refine_dense(A, X0.clone(), max_iters=10, check_every=10, **kw)
-            ms.append(r["sweeps_ms"] / r["iterations"])
-        torch.cuda.synchronize()
-        out[form] = {"us_per_sweep": 1000.0 * float(np.median(ms)), "value": 1000.0 / float(np.median(ms)),
-                     "unit": UNIT, "note": "median of 5 calls of 10 graph-replayed sweeps"}
+            X = X0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.refine_dense(A, X, max_iters=10, check_every=10, **kw)
+            torch.cuda.synchronize()
+            calls.append(time.perf_counter() - t0)
+        # steady state: one long call, chunks of 100 graph-replayed sweeps
+        r = h.refine_dense(A, X0.clone(), max_iters=1000, check_every=100, **kw)
+        us = 1000.0 * r["sweeps_ms"] / r["iterations"]
+        out[form] = {"call_ms": 1000.0 * float(np.median(calls)), "us_per_sweep": us, "value": 1e6 / us,
+                     "unit": UNIT, "note": "call_ms: one call of the 10-sweep workload, wall clock with set-up and "
+                                           "graph capture (median of 5); us_per_sweep: device time a sweep over a "
+                                           "1000-sweep call"}
     h.close()
     return out
 
