@@ -503,6 +503,10 @@ def main():
     ap.add_argument("--impl", default="eigref", choices=["eigref", "reference"])
     ap.add_argument("--precision", default=None, choices=["bf16", "fp64", "int8"])
     ap.add_argument("--slices", type=int, default=0, help="digit planes of the split form (0: library default)")
+    ap.add_argument("--product-tile", type=int, default=0, choices=[0, 32, 64],
+                    help="columns of the split product's output tile (0: the library default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in K decomposition (the product's equal-work plan) instead of timing candidates")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -568,6 +572,10 @@ def main():
     kw = dict(norm_a=p.normA, target="largest_mag", precision=precision)
     if precision != "fp64":
         kw["slices"] = args.slices
+        if args.no_autotune:
+            kw["autotune"] = False
+        if args.product_tile:
+            kw["product_tile"] = args.product_tile
 
     def refine(X, iters, **extra):
         return h.refine_dense(A, X, max_iters=iters, check_every=max(2, iters), **kw, **extra)
@@ -604,7 +612,7 @@ def main():
         kfile = "fp64.cu"
     else:
         from paper_2602_23778_gb300 import sliced_info
-        info = sliced_info(precision, n, k, slices=args.slices or 8)
+        info = sliced_info(precision, n, k, slices=args.slices or 8, product_tile=args.product_tile)
         flops = info["executed_flops"]
         # the kernel runs unthrottled at the maximum SM clock inside a sub-second
         # timed region (see "clocks"): the burst BF16 rate is its peak
@@ -623,6 +631,9 @@ def main():
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": n, "k": k, "form": precision, "seed": 3000,
                       "slices": (args.slices or 8) if precision != "fp64" else None,
+                      # columns of the split product's output tile (128 x 64 wherever k allows it)
+                      "product_tile": (args.product_tile or (64 if (k + 31) // 32 % 2 == 0 else 32))
+                      if precision != "fp64" else None,
                       "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
                       "parallelism": "replicas" if world > 1 else "single",
                       # product: 1..4 equal K splits a tile, 8 the equal-work plan (whole CTA rounds)

@@ -128,6 +128,11 @@ typedef struct eigref_params {
                           ends its kernel early and the call returns EIGREF_E_TIMEOUT with X at
                           the last completed iterate; the handle stays usable.  A tiny limit
                           (1e-9) gives up at the first wait that is not already complete. */
+  int product_tile;    /* split form, single problems: columns of the dense product's output tile.
+                          64: 128 x 64 tiles (one TMEM accumulator set drained group by group; k must
+                          lie in (64 j - 32, 64 j]); 32: 128 x 32 tiles (two accumulator sets);
+                          0 = default (64 where k allows it, else 32).  Results are identical for
+                          either; EIGREF_E_INVALID for another value or a width k cannot take. */
 } eigref_params;
 
 /* Report of one refinement call.  The three array pointers are optional,
@@ -158,7 +163,7 @@ typedef struct eigref_report {
 /* Defaults: LARGEST_MAG, norm_a computed, max_iters 100, tol 0, correction
  * criterion, FP64, beta cluster, delta_c 10, div 10 / 1e-4, check 32,
  * sign_fix 1, use_graph 1, profile 0, rayleigh_ritz 0, judge_cols 0, reorth 0, resign 0, autotune 1,
- * wait_limit_s 0 (2 s). */
+ * wait_limit_s 0 (2 s), product_tile 0. */
 void eigref_params_default(eigref_params* p);
 
 /* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t

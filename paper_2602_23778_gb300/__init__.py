@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("sign_fix", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("rayleigh_ritz", ctypes.c_int), ("judge_cols", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("resign", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("wait_limit_s", ctypes.c_double)]
+                ("wait_limit_s", ctypes.c_double), ("product_tile", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -106,14 +106,18 @@ def status_string(s):
 
 # ---- array marshalling ------------------------------------------------------
 
-def sliced_info(precision, n, k, slices=8):
+def sliced_info(precision, n, k, slices=8, product_tile=0):
     """Work of one split-precision product W = B X as the library pads it:
     S (S + 1) / 2 digit-plane pairs, each a 2 n_pad^2 k_pad-flop BF16 GEMM
-    (n_pad = n rounded up to 256, k_pad = k rounded up to 32)."""
+    (n_pad = n rounded up to 256, k_pad = k rounded up to 32), and the kernel
+    that runs it (128 x 64 tiles where k_pad is a multiple of 64, unless
+    product_tile asks for 32)."""
     n_pad = -(-n // 256) * 256
     k_pad = -(-k // 32) * 32
     pairs = slices * (slices + 1) // 2
-    return {"kernel": "sliced_mma_kernel (product mode)", "slices": slices, "pairs": pairs,
+    wide = product_tile != 32 and k_pad % 64 == 0
+    return {"kernel": "sliced_wide_kernel (128 x 64 tiles)" if wide else "sliced_mma_kernel (product mode)",
+            "slices": slices, "pairs": pairs,
             "executed_flops": 2.0 * n_pad * n_pad * k_pad * pairs,
             "a_plane_bytes": 2.0 * slices * n_pad * n_pad}
 

@@ -36,8 +36,8 @@ struct eigref_ctx {
   size_t ws_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   Control* host_ctl = nullptr;  // pinned
-  // split-K choices the autotuner measured, by (n, k, slices)
-  std::map<std::tuple<int64_t, int, int>, std::pair<int, int>> tuned;
+  // split-K choices the autotuner measured, by (n, k, slices, product tile)
+  std::map<std::tuple<int64_t, int, int, int>, std::pair<int, int>> tuned;
 };
 
 namespace {
@@ -548,7 +548,7 @@ int tune_splits(eigref_ctx* h, Run& r, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CUDA_TRY(h, cudaGetLastError());
-  h->tuned[std::make_tuple(r.pr.n, r.pr.k, sl->slices())] = std::make_pair(best_p, best_k);
+  h->tuned[std::make_tuple(r.pr.n, r.pr.k, sl->slices(), sl->product_tile())] = std::make_pair(best_p, best_k);
   return EIGREF_OK;
 }
 
@@ -604,7 +604,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   st = run_setup_device(h, r, s);
   if (st) return st;
   if (r.pr.sliced && q.autotune && q.max_iters > 0 &&
-      !h->tuned.count(std::make_tuple(r.pr.n, r.pr.k, r.pr.sliced->slices()))) {
+      !h->tuned.count(std::make_tuple(r.pr.n, r.pr.k, r.pr.sliced->slices(), r.pr.sliced->product_tile()))) {
     st = tune_splits(h, r, s);
     if (st) return st;
   }
@@ -791,6 +791,7 @@ void eigref_params_default(eigref_params* p) {
   p->reorth = 0;
   p->resign = 0;
   p->autotune = 1;
+  p->product_tile = 0;
 }
 
 const char* eigref_status_string(int s) {
@@ -889,11 +890,12 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
   SlicedA sl;
   if (pp->precision != EIGREF_FP64) {
     st = sl.configure(pr.A, n, pr.lda, k, pp->precision, pp->slices);
+    if (!st) st = sl.set_product_tile(pp->product_tile);
     if (st) {
       if (a_dev) cudaFree(a_dev);
       return set_err(h, st, "%s", sl.error());
     }
-    auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices()));
+    auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices(), sl.product_tile()));
     if (tk != h->tuned.end()) sl.set_splits(tk->second.first, tk->second.second);
     pr.sliced = &sl;
   }
@@ -1395,8 +1397,9 @@ int eigref_product_dense(eigref_handle h, const double* A, int64_t n, int64_t ld
   precision = resolve_precision(precision, false, n, k);
   if (precision != EIGREF_FP64) {
     int st = sl.configure(A, n, lda, k, precision, slices);
+    if (!st) st = sl.set_product_tile(0);
     if (st) return set_err(h, st, "%s", sl.error());
-    auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices()));
+    auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices(), sl.product_tile()));
     if (tk != h->tuned.end()) sl.set_splits(tk->second.first, tk->second.second);
     pr.sliced = &sl;
   }

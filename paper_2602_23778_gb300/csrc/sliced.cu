@@ -708,6 +708,377 @@ __global__ void __launch_bounds__(kThreads, 1)
   sliced_mma_body<S, MODE_UPDATE>(&tmA, &tmB, &tmB, g, 0, 0, 0, gx, tiles);
 }
 
+// ---------------------------------------------------------------------------
+// The product W = (A - shift I) X on 128 x 64 tiles (column blocks of 64 when
+// k is a multiple of 64).  A 64-deep K block of a tile moves the same 128 KiB
+// of A planes as a 128 x 32 tile but does twice the MMA work, so the bytes a
+// flop that TMA brings into one SM's shared memory drop by 40 % and the
+// tensor pipe, not the TMA feed, sets the pace.  The 8 weight groups of a
+// 128 x 64 tile take all 512 TMEM columns (group w at columns 64 w), so
+// there is one accumulator set, drained group by group:
+//   * every MMA accumulates (the epilogue clears a group in TMEM after
+//     reading it, and before the first chunk);
+//   * the MMA for A plane s (B = X planes 0 .. S-1-s, groups s .. S-1) is
+//     issued as pieces p1 = groups s .. s+3 and p2 = groups s+4 .. S-1, in
+//     the order s0p1, s1p1, s0p2, s1p2, s2p1, s2p2, s3p1, ... so that group
+//     w takes its last contribution of a chunk from piece "w p1" and groups
+//     finish in the order 0, 1, .., S-1;
+//   * in a chunk's last K block the MMA warp commits group w's barrier
+//     after piece "w p1"; the epilogue drains (and clears) groups in that
+//     order while the rest of the block runs;
+//   * in a chunk's first K block the MMA warp waits for a group to be
+//     drained only before the first piece that touches it: the two pieces
+//     that open a block touch groups 0 .. 4 only, and the last groups to be
+//     drained (S-3 .. S-1) are first needed about 1200 clocks of tensor work
+//     later.
+// Same exactness as the 128 x 32 kernel (a group of a 128-deep chunk stays
+// below 2^24), same items (fixed K splits or equal-work ranges) and partials.
+// ---------------------------------------------------------------------------
+constexpr int kWBN = 64;                                  // columns of W per CTA
+constexpr int kWRA = 6;                                   // A ring (one plane a stage, 16 KiB)
+constexpr int kWRX = 2;                                   // X ring (all planes of a K block, 64 KiB)
+constexpr int kWXTile = kMaxS * kWBN * kBK * 2;           // 64 KiB
+constexpr int kSmemBytesWide = kWRA * kATile + kWRX * kWXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
+static_assert(kSmemBytesWide <= 232448, "shared memory of the wide product");
+static_assert(kMaxS * kWBN <= 512, "the weight groups of a 128 x 64 tile must fit in TMEM");
+
+struct __align__(8) WideBars {
+  uint64_t a_full[kWRA], a_empty[kWRA], x_full[kWRX], x_empty[kWRX], g_full[kMaxS], g_empty[kMaxS], drain;
+  uint32_t tmem_base;
+  WaitState wait;
+};
+
+// Piece i of a K block for S planes: plane s, first and last weight group.
+struct WPiece {
+  int s, glo, ghi;
+};
+template <int S>
+__host__ __device__ constexpr WPiece wide_piece(int i) {
+  // s0p1, s1p1, s0p2, s1p2, then p1 (and p2) of s = 2 .. S-1
+  if (S >= 6 && i < 4) {
+    const int s = i & 1;
+    return (i < 2) ? WPiece{s, s, s + 3} : WPiece{s, s + 4, S - 1};
+  }
+  int j = (S >= 6) ? 4 : 0;
+  for (int s = (S >= 6) ? 2 : 0; s < S; ++s) {
+    const int hi1 = s + 3 < S - 1 ? s + 3 : S - 1;
+    if (j == i) return WPiece{s, s, hi1};
+    ++j;
+    if (s + 4 <= S - 1) {
+      if (j == i) return WPiece{s, s + 4, S - 1};
+      ++j;
+    }
+  }
+  return WPiece{-1, 0, -1};
+}
+template <int S>
+__host__ __device__ constexpr int wide_pieces() {
+  int c = 0;
+  for (int s = 0; s < S; ++s) c += (s + 4 <= S - 1) ? 2 : 1;
+  return c;
+}
+// the last piece of a K block that reads A plane s (its slot is then released)
+template <int S>
+__host__ __device__ constexpr bool wide_last_of_plane(int i) {
+  const WPiece p = wide_piece<S>(i);
+  for (int j = i + 1; j < wide_pieces<S>(); ++j)
+    if (wide_piece<S>(j).s == p.s) return false;
+  return true;
+}
+template <int S>
+__host__ __device__ constexpr bool wide_first_of_plane(int i) {
+  const WPiece p = wide_piece<S>(i);
+  for (int j = 0; j < i; ++j)
+    if (wide_piece<S>(j).s == p.s) return false;
+  return true;
+}
+
+// The MMA warp's work for piece I .. of one K block, unrolled at compile
+// time so that the piece table costs the issuing thread no instructions.
+struct WideIssue {
+  WideBars* bars;
+  uint32_t tbase;
+  uint64_t a_desc0, xd;
+  int gkb, c;
+  bool last;
+  WaitState* wst;
+  unsigned long long wlim;
+};
+template <int S, int I>
+__device__ __forceinline__ bool wide_issue(const WideIssue& q, int& ready) {
+  if constexpr (I < wide_pieces<S>()) {
+    constexpr WPiece p = wide_piece<S>(I);
+    constexpr bool first_of_plane = wide_first_of_plane<S>(I), last_of_plane = wide_last_of_plane<S>(I);
+    const int ia = q.gkb * S + p.s;                   // the plane's place in the A ring's sequence
+    const int slot = ia % kWRA;
+    if (first_of_plane) {
+      if (!mbar_wait(smem_u32(&q.bars->a_full[slot]), (ia / kWRA) & 1, q.wst, q.wlim)) return false;
+      tc_fence_after();
+    }
+    while (ready < p.ghi) {
+      ++ready;
+      if (!mbar_wait(smem_u32(&q.bars->g_empty[ready]), q.c & 1, q.wst, q.wlim)) return false;
+      tc_fence_after();
+    }
+    const uint64_t ad = q.a_desc0 + (uint64_t)(slot * (kATile >> 4));
+    // B rows: X planes t = glo - s .. ghi - s (64 rows each, 128 B a row);
+    // TMEM columns 64 glo ..; +2 in the address field steps 16 K
+    const uint64_t bd = q.xd + (uint64_t)(((p.glo - p.s) * kWBN * kBK * 2) >> 4);
+    constexpr uint32_t id = idesc_f16(kBM, kWBN * (p.ghi - p.glo + 1));
+    const uint32_t dt = q.tbase + (uint32_t)(p.glo * kWBN);
+    tc_mma(dt, ad, bd, id, 1u);
+    tc_mma(dt, ad + 2, bd + 2, id, 1u);
+    tc_mma(dt, ad + 4, bd + 4, id, 1u);
+    tc_mma(dt, ad + 6, bd + 6, id, 1u);
+    if (last_of_plane) tc_commit(smem_u32(&q.bars->a_empty[slot]));
+    if (p.glo == p.s && q.last) tc_commit(smem_u32(&q.bars->g_full[p.s]));
+    return wide_issue<S, I + 1>(q, ready);
+  } else {
+    return true;
+  }
+}
+
+#define TC_ST32_ZERO(taddr)                                                                                  \
+  asm volatile(                                                                                              \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1," \
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),                                                  \
+      "r"(0u)                                                                                                \
+      : "memory")
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+    sliced_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs g) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (g.ctl && g.ctl->done) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sa = smem;                          // kWRA x 16 KiB
+  unsigned char* sx = smem + kWRA * kATile;          // kWRX x 64 KiB
+  WideBars* bars = reinterpret_cast<WideBars*>(sx + kWRX * kWXTile);
+  static_assert(sizeof(WideBars) <= 1024, "barrier block");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = blockIdx.x, mb = blockIdx.y, split = blockIdx.z;
+  const int nsplit = g.ksplit;
+  const bool ranged = g.sk_ranges > 0;
+  // Work items of this CTA, as in the 128 x 32 kernel: one K split of one
+  // tile, or the tiles an equal-work range crosses (an item a tile).
+  struct Item {
+    int nb, mb, kb_lo, kb, slot;
+  };
+  auto item = [&](int w, Item& it) -> bool {
+    if (ranged) {
+      const int64_t U = g.sk_units, R = g.sk_ranges, KBt = g.kb_total;
+      const int64_t u0 = (int64_t)mb * U / R, u1 = ((int64_t)mb + 1) * U / R;
+      const int64_t s0 = w == 0 ? u0 : (u0 / KBt + w) * KBt;
+      if (s0 >= u1) return false;
+      const int64_t e0 = min((s0 / KBt + 1) * KBt, u1);
+      const int64_t first = (((s0 / KBt) * KBt + 1) * R - 1) / U;
+      it = Item{nb, (int)(s0 / KBt), (int)(s0 % KBt), (int)(e0 - s0), (int)(mb - first)};
+      return true;
+    }
+    if (w > 0) return false;
+    const int lo = (int)((int64_t)g.kb_total * split / nsplit);
+    it = Item{nb, mb, lo, (int)((int64_t)g.kb_total * (split + 1) / nsplit) - lo, split};
+    return true;
+  };
+  WaitState* wst = &bars->wait;
+  const unsigned long long wlim = wait_limit(g.wait_ns);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWRA; ++i) {
+      mbar_init(smem_u32(&bars->a_full[i]), 1);
+      mbar_init(smem_u32(&bars->a_empty[i]), 1);
+    }
+    for (int i = 0; i < kWRX; ++i) {
+      mbar_init(smem_u32(&bars->x_full[i]), 1);
+      mbar_init(smem_u32(&bars->x_empty[i]), 1);
+    }
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&bars->g_full[i]), 1);
+      mbar_init(smem_u32(&bars->g_empty[i]), kEpiWarps);  // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->wait.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+      int issued_a = 0, issued_x = 0;
+      bool ok = true;
+      int as = 0;
+      uint32_t aph = 0;
+      int gkb = 0;
+      Item it;
+      for (int w = 0; ok && item(w, it); ++w) {
+        const int m0 = it.mb * kBM;
+        for (int kb = 0; kb < it.kb && ok; ++kb, ++gkb) {
+          const int kx = (it.kb_lo + kb) * kBK;
+          const int xs = gkb % kWRX;
+          ok = mbar_wait(smem_u32(&bars->x_empty[xs]), ((gkb / kWRX) & 1) ^ 1, wst, wlim);
+          if (!ok) break;
+          mbar_expect_tx(smem_u32(&bars->x_full[xs]), (uint32_t)(S * kWBN * kBK * 2));
+#pragma unroll
+          for (int t = 0; t < S; ++t)
+            tma_load_2d(smem_u32(sx + xs * kWXTile + t * kWBN * kBK * 2), &tmB, smem_u32(&bars->x_full[xs]), kx,
+                        t * g.b_plane_rows + it.nb * kWBN);
+          ++issued_x;
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, wst, wlim);
+            if (!ok) break;
+            mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
+            tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
+            ++issued_a;
+            if (++as == kWRA) {
+              as = 0;
+              aph ^= 1;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        for (int i = (issued_a > kWRA ? issued_a - kWRA : 0); i < issued_a; ++i)
+          mbar_drain(smem_u32(&bars->a_full[i % kWRA]), (i / kWRA) & 1);
+        for (int i = (issued_x > kWRX ? issued_x - kWRX : 0); i < issued_x; ++i)
+          mbar_drain(smem_u32(&bars->x_full[i % kWRX]), (i / kWRX) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint64_t a_desc0 = smem_desc(smem_u32(sa));
+      const uint64_t x_desc0 = smem_desc(smem_u32(sx));
+      bool ok = true;
+      int gkb = 0, gc = 0;
+      Item it;
+      for (int w = 0; ok && item(w, it); ++w) {
+        const int KB = it.kb;
+        const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
+        for (int kb = 0; kb < KB && ok; ++kb, ++gkb) {
+          const int c = gc + kb / kChunkBlocks;
+          const bool first = (kb % kChunkBlocks) == 0;
+          const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
+          const int xs = gkb % kWRX;
+          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb / kWRX) & 1, wst, wlim);
+          if (!ok) break;
+          tc_fence_after();
+          const uint64_t xd = x_desc0 + (uint64_t)(xs * (kWXTile >> 4));
+          int ready = first ? -1 : S - 1;                // groups known drained for this chunk
+          const WideIssue q{bars, tbase, a_desc0, xd, gkb, c, last, wst, wlim};
+          ok = wide_issue<S, 0>(q, ready);
+          if (!ok) break;
+          tc_commit(smem_u32(&bars->x_empty[xs]));
+        }
+        gc += NC;
+      }
+      if (!ok) {
+        tc_commit(smem_u32(&bars->drain));
+        mbar_drain(smem_u32(&bars->drain), 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue: drain groups into exact int64 sums ----------------
+    const int lg = warp & 3;                           // TMEM lane group of this warp
+    const int half = (warp - 2) >> 2;                  // which 32 of the 64 columns
+    constexpr int kC = kWBN / 2;
+    const uint32_t tw = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(half * kC);
+    // every group starts cleared
+#pragma unroll
+    for (int w = 0; w < S; ++w) TC_ST32_ZERO(tw + (uint32_t)(w * kWBN));
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0)
+      for (int w = 0; w < S; ++w) mbar_arrive(smem_u32(&bars->g_empty[w]));
+    bool ok = true;
+    int gc = 0;
+    Item it;
+    for (int wi = 0; item(wi, it); ++wi) {
+      const int NC = (it.kb + kChunkBlocks - 1) / kChunkBlocks;
+      const int64_t row = (int64_t)it.mb * kBM + lg * 32 + lane;
+      long long hi[kC], lo[kC];
+#pragma unroll
+      for (int j = 0; j < kC; ++j) hi[j] = lo[j] = 0;
+      for (int cl = 0; cl < NC && ok; ++cl) {
+        const int c = gc + cl;
+#pragma unroll
+        for (int w = 0; w < S; ++w) {
+          int w_ok = 0;
+          if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->g_full[w]), c & 1, wst, wlim);
+          ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+          __syncwarp();
+          if (!ok) break;
+          tc_fence_after();
+          // two halves of 16 columns (the register budget holds the 64 sums
+          // and one half); the group is cleared and released after the second
+          // half is in registers
+          const int sh = w < 4 ? kBits * (3 - w) : kBits * (S - 1 - w);
+          long long* acc = w < 4 ? hi : lo;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            uint32_t r[kC / 2];
+            TC_LD16(tw + (uint32_t)(w * kWBN + hh * (kC / 2)), r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (hh == 1) {
+              TC_ST32_ZERO(tw + (uint32_t)(w * kWBN));
+              asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&bars->g_empty[w]));
+            }
+#pragma unroll
+            for (int j = 0; j < kC / 2; ++j)
+              acc[hh * (kC / 2) + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+          }
+        }
+      }
+      gc += NC;
+      const int er = (ok && row < g.m_valid) ? g.rowexp[row] : 0;
+      const bool raw = nsplit > 1 || ranged;
+#pragma unroll
+      for (int j = 0; j < kC; ++j) {
+        const int col = it.nb * kWBN + half * kC + j;
+        const bool live = ok && row < g.m_valid && col < g.k;
+        if (!live) continue;
+        if (raw)
+          g.ppart[(int64_t)it.slot * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
+        else
+          g.P[row * g.k + col] = recombine<S>(hi[j], lo[j], er, g.colexp[col]) - g.shift * g.Xs[row * g.k + col];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (bars->wait.abort && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+    if (g.ctl) {
+      Control* c = const_cast<Control*>(g.ctl);
+      c->status = EIGREF_E_TIMEOUT;
+      c->done = 1;
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+  }
+}
+
 // Many problems' tiles in one launch (a batch).  The tensor maps travel in
 // the kernel's parameter block, as for the single-problem kernel; CTA c
 // takes tile c - cta_begin[t] of task t, ordered column block fastest, then
@@ -2397,6 +2768,9 @@ cudaError_t init_sliced_attributes() {
     e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_PRODUCT>,                                        \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sl::kSmemBytesProduct);                  \
   if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(sl::sliced_wide_kernel<S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                             sl::kSmemBytesWide);                                                                  \
+  if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(sl::sliced_mma_kernel<S_, sl::MODE_GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              sl::kSmemBytes);                                                                      \
   if (e == cudaSuccess)                                                                                            \
@@ -2516,6 +2890,16 @@ int SlicedA::configure(const double* A, int64_t n, int64_t lda, int k, int preci
     sk_units_ = (long long)gy * kbt;
     sk_ranges_ = gy < q ? std::min<long long>(q, 3LL * gy) : (long long)q * ((gy + q - 1) / q);
   }
+  // The 128 x 64 product: one round of one CTA per SM, ranges of at least a
+  // row tile (a tile then meets at most two ranges), or, for few row tiles,
+  // at most 3 gy ranges (at most 4 a tile).
+  if (k_pad_ % 64 == 0) {
+    const int gx = k_pad_ / 64, gy = n_pad_ / sl::kBM;
+    const int q = std::max(1, sms / gx);
+    sk_units_w_ = (long long)gy * kbt;
+    sk_ranges_w_ = gy < q ? std::min<long long>(q, 3LL * gy) : (long long)q;
+  }
+  wide_ = false;
   pslots_ = 4;
   psplit_ = kPsplitBalanced;
   return EIGREF_OK;
@@ -2536,6 +2920,19 @@ std::vector<int> SlicedA::ksplit_candidates() const {
   return v;
 }
 
+int SlicedA::set_product_tile(int cols) {
+  if (cols != 0 && cols != 32 && cols != 64) {
+    snprintf(err_, sizeof(err_), "product_tile must be 0, 32 or 64 (%d)", cols);
+    return EIGREF_E_INVALID;
+  }
+  if (cols == 64 && k_pad_ % 64 != 0) {
+    snprintf(err_, sizeof(err_), "product_tile 64 needs k in (64 j - 32, 64 j] (k = %d)", k_);
+    return EIGREF_E_INVALID;
+  }
+  wide_ = cols != 32 && k_pad_ % 64 == 0;
+  return EIGREF_OK;
+}
+
 void SlicedA::set_splits(int psplit, int ksplit) {
   psplit_ = (psplit == kPsplitBalanced && pslots_ >= 4) ? kPsplitBalanced : std::max(1, std::min(psplit, psplit_max_));
   ksplit_ = std::max(1, std::min(ksplit, ksplit_max_));
@@ -2545,6 +2942,7 @@ size_t SlicedA::workspace_bytes() const { return layout_total(); }
 
 void SlicedA::share_gpu(int problems) {
   if (problems <= 1) return;
+  wide_ = false;
   psplit_ = psplit_max_ = pslots_ = 1;
   const int kbt = n_pad_ / sl::kBK;
   ksplit_ = ksplit_max_ = std::max(1, std::min(kbt, n_pad_ / 4096));
@@ -2576,6 +2974,12 @@ int SlicedA::prepare(cudaStream_t s) {
                           sl::kBK, sl::kBN);
   ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmXR_), ws_ + L.xr_planes, (uint64_t)kr_, S * n_pad_,
                           sl::kBK, sl::kBM);
+  if (k_pad_ % 64 == 0) {
+    ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmXw_), ws_ + L.x_planes, (uint64_t)n_pad_, S * k_pad_,
+                            sl::kBK, sl::kWBN);
+    ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmPw_), ws_ + L.p_planes, (uint64_t)n_pad_, S * k_pad_,
+                            sl::kBK, sl::kWBN);
+  }
   ok = ok && sl::make_map(reinterpret_cast<CUtensorMap*>(tmF_), ws_ + L.f_planes, (uint64_t)kr_, S * kfm_cols(k_),
                           sl::kBK, sl::kBN);
   if (!ok) {
@@ -2623,7 +3027,11 @@ static void launch_product_reduce(int S, const MmaTask& t, int psplit, const dou
 
 static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
   const dim3 grid((unsigned)t.gx, (unsigned)t.gy, (unsigned)t.gz);
-  if (mode == sl::MODE_PRODUCT) {
+  if (mode == sl::MODE_PRODUCT && t.wide) {
+#define EIGREF_CALL_WIDE(S_) sl::sliced_wide_kernel<S_><<<grid, sl::kThreads, sl::kSmemBytesWide, s>>>(t.a, t.b, t.g)
+    EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_WIDE)
+#undef EIGREF_CALL_WIDE
+  } else if (mode == sl::MODE_PRODUCT) {
     launch_mma<sl::MODE_PRODUCT>(S, grid, t.a, t.b, t.b2, t.g, s);
   } else if (mode == sl::MODE_GRAM) {
     launch_mma<sl::MODE_GRAM>(S, grid, t.a, t.b, t.b2, t.g, s);
@@ -2660,13 +3068,15 @@ MmaTask SlicedA::product_task(const double* X, double* P, double shift, const Co
   g.P = P;
   g.shift = shift;
   g.ppart = reinterpret_cast<longlong2*>(ws_ + L.ppart);
-  t.gx = k_pad_ / sl::kBN;
+  t.wide = wide_ ? 1 : 0;
+  if (wide_) t.b = t.b2 = *reinterpret_cast<const CUtensorMap*>(b_from_p ? tmPw_ : tmXw_);
+  t.gx = k_pad_ / (wide_ ? sl::kWBN : sl::kBN);
   if (psplit_ == kPsplitBalanced) {
     // grid (column blocks, ranges): range blockIdx.y of column block blockIdx.x
     g.ksplit = 1;
-    g.sk_ranges = (int)sk_ranges_;
-    g.sk_units = sk_units_;
-    t.gy = (int)sk_ranges_;
+    g.sk_ranges = (int)(wide_ ? sk_ranges_w_ : sk_ranges_);
+    g.sk_units = wide_ ? sk_units_w_ : sk_units_;
+    t.gy = g.sk_ranges;
     t.gz = 1;
   } else {
     g.ksplit = psplit_;

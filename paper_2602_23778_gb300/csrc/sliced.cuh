@@ -53,6 +53,7 @@ struct MmaTask {
   CUtensorMap a, b, b2;
   sl::MmaArgs g;
   int gx, gy, gz;
+  int wide = 0;   // PRODUCT: 128 x 64 tiles (sliced_wide_kernel); grouped launches take 128 x 32 tasks only
 };
 
 // Grouped launches of the split form over a batch (all problems share S).
@@ -132,6 +133,12 @@ class SlicedA {
   void set_splits(int psplit, int ksplit);
   int psplit() const { return psplit_; }
   int ksplit() const { return ksplit_; }
+  // Columns of the product's output tile: 64 (the 128 x 64 kernel, k a
+  // multiple of 64), 32, or 0 for the default (64 where it applies).  Single
+  // problems only (grouped launches use 32).  Returns EIGREF_E_INVALID for a
+  // width this k cannot take.  Either width gives the same results bitwise.
+  int set_product_tile(int cols);
+  int product_tile() const { return wide_ ? 64 : 32; }
   // Limit of every bounded wait inside the tensor-core kernels (0: 2 s).
   void set_wait_ns(unsigned long long ns) { wait_ns_ = ns; }
   // Fused column maxima (single-problem sweeps, after any autotuning): the
@@ -159,11 +166,15 @@ class SlicedA {
   int n_pad_ = 0, k_pad_ = 0, kr_ = 0, ksplit_ = 1, psplit_ = 1, ksplit_max_ = 1, psplit_max_ = 1;
   int pslots_ = 4;                      // product partial slots a tile in the workspace
   long long sk_ranges_ = 0, sk_units_ = 0;   // the equal-work plan (ranges and units a column block)
+  long long sk_ranges_w_ = 0, sk_units_w_ = 0;   // the same for 64-column blocks
+  bool wide_ = false;                   // product on 128 x 64 tiles
   char* ws_ = nullptr;
   alignas(64) unsigned char tmA_[128];
   alignas(64) unsigned char tmX_[128];
   alignas(64) unsigned char tmXA_[128];
   alignas(64) unsigned char tmP_[128];
+  alignas(64) unsigned char tmXw_[128];   // X / P planes in 64-row boxes (the 128 x 64 product)
+  alignas(64) unsigned char tmPw_[128];
   alignas(64) unsigned char tmXR_[128];
   alignas(64) unsigned char tmF_[128];
   char err_[256] = {0};

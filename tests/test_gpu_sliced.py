@@ -194,3 +194,33 @@ def test_autotuned_splits_do_not_change_results():
             r = h.refine_dense(dev(p.A), X, norm_a=p.normA, max_iters=3, precision="bf16", autotune=tune)
             out.append((host(X), r["psplit"], r["ksplit"]))
     assert np.array_equal(out[0][0], out[1][0]), (out[0][1:], out[1][1:])
+
+
+@pytest.mark.parametrize("n,k", [(700, 40), (1000, 64), (2000, 100), (3000, 128)])
+@pytest.mark.parametrize("tune", [0, 1])
+def test_product_tiles_agree_bitwise(n, k, tune):
+    """The 128 x 64 product (one TMEM accumulator set, drained group by group)
+    and the 128 x 32 product (two sets) add the same exact digit-pair sums:
+    sweeps through either are bitwise equal, with the built-in K
+    decomposition and with the autotuner's."""
+    import paper_2602_23778_gb300 as pkg
+    p = dense_case(n, k, seed=900 + n)
+    out = []
+    for tile in (32, 64):
+        with pkg.Handle(0) as h:
+            X = dev(np.asfortranarray(p.X0))
+            r = h.refine_dense(dev(p.A), X, norm_a=p.normA, max_iters=3, precision="bf16", autotune=tune,
+                               product_tile=tile, history=True)
+            out.append((host(X), r["hist_residual"], r["hist_corr"]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_product_tile_refused_where_k_cannot_take_it(eig):
+    p = dense_case(300, 96, seed=31)
+    for tile in (64, 48):
+        X = dev(np.asfortranarray(p.X0))
+        r = eig.refine_dense(dev(p.A), X, norm_a=p.normA, max_iters=2, precision="bf16", product_tile=tile,
+                             raise_on_error=False)
+        assert r["status"] == 1 and r["iterations"] == 0, (tile, r["status"])
+        assert np.array_equal(host(X), p.X0)

@@ -24,9 +24,12 @@ def eig():
     h.close()
 
 
-def test_dense_split_form_times_out_and_recovers(eig):
-    lam = C.separated_graded(300, 8, 41, gap=0.01, tail=0.5)
-    p = C.householder(300, 8, 8, lam, 41, target="largest_mag", x_noise=1e-6)
+@pytest.mark.parametrize("k", [8, 64])
+def test_dense_split_form_times_out_and_recovers(eig, k):
+    """k = 8: the 128 x 32 product; k = 64: the 128 x 64 product, whose
+    accumulator groups are drained one by one."""
+    lam = C.separated_graded(300, k, 41, gap=min(0.01, 0.4 / k), tail=0.5)
+    p = C.householder(300, 8, k, lam, 41, target="largest_mag", x_noise=1e-6)
     X0 = np.asfortranarray(p.X0)
     kw = dict(norm_a=p.normA, target="shift", shift=p.shift, precision="bf16", autotune=False, history=True)
     X = dev(X0)
