@@ -731,19 +731,28 @@ __global__ void __launch_bounds__(kThreads, 1)
 //     that open a block touch groups 0 .. 4 only, and the last groups to be
 //     drained (S-3 .. S-1) are first needed about 1200 clocks of tensor work
 //     later.
+// One thread issues every MMA, and each barrier operation costs it tens of
+// clocks of latency, so the pipeline is cut to keep those few: A stages of
+// two planes (one wait and one release per two planes), drain barriers per
+// pair of weight groups, and the barrier of the next A stage (and of the
+// next K block's X stage and first A stage) tested without blocking before
+// the current piece's MMAs are issued, so that its latency overlaps them.
 // Same exactness as the 128 x 32 kernel (a group of a 128-deep chunk stays
 // below 2^24), same items (fixed K splits or equal-work ranges) and partials.
 // ---------------------------------------------------------------------------
 constexpr int kWBN = 64;                                  // columns of W per CTA
-constexpr int kWRA = 6;                                   // A ring (one plane a stage, 16 KiB)
+constexpr int kWPS = 2;                                   // A planes a stage
+constexpr int kWAStage = kWPS * kATile;                   // 32 KiB
+constexpr int kWRA = 3;                                   // A ring stages
 constexpr int kWRX = 2;                                   // X ring (all planes of a K block, 64 KiB)
 constexpr int kWXTile = kMaxS * kWBN * kBK * 2;           // 64 KiB
-constexpr int kSmemBytesWide = kWRA * kATile + kWRX * kWXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kWPairs = (kMaxS + 1) / 2;                  // drain barriers: one per pair of weight groups
+constexpr int kSmemBytesWide = kWRA * kWAStage + kWRX * kWXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
 static_assert(kSmemBytesWide <= 232448, "shared memory of the wide product");
 static_assert(kMaxS * kWBN <= 512, "the weight groups of a 128 x 64 tile must fit in TMEM");
 
 struct __align__(8) WideBars {
-  uint64_t a_full[kWRA], a_empty[kWRA], x_full[kWRX], x_empty[kWRX], g_full[kMaxS], g_empty[kMaxS], drain;
+  uint64_t a_full[kWRA], a_empty[kWRA], x_full[kWRX], x_empty[kWRX], g_full[kWPairs], g_empty[kWPairs], drain;
   uint32_t tmem_base;
   WaitState wait;
 };
@@ -777,24 +786,49 @@ __host__ __device__ constexpr int wide_pieces() {
   for (int s = 0; s < S; ++s) c += (s + 4 <= S - 1) ? 2 : 1;
   return c;
 }
-// the last piece of a K block that reads A plane s (its slot is then released)
 template <int S>
-__host__ __device__ constexpr bool wide_last_of_plane(int i) {
+__host__ __device__ constexpr int wide_stages() {
+  return (S + kWPS - 1) / kWPS;
+}
+// the last piece of a K block that reads A stage s / 2 (the stage is then released)
+template <int S>
+__host__ __device__ constexpr bool wide_last_of_stage(int i) {
   const WPiece p = wide_piece<S>(i);
   for (int j = i + 1; j < wide_pieces<S>(); ++j)
-    if (wide_piece<S>(j).s == p.s) return false;
+    if (wide_piece<S>(j).s / kWPS == p.s / kWPS) return false;
   return true;
 }
 template <int S>
-__host__ __device__ constexpr bool wide_first_of_plane(int i) {
+__host__ __device__ constexpr bool wide_first_of_stage(int i) {
+  if (i >= wide_pieces<S>()) return false;
   const WPiece p = wide_piece<S>(i);
   for (int j = 0; j < i; ++j)
-    if (wide_piece<S>(j).s == p.s) return false;
+    if (wide_piece<S>(j).s / kWPS == p.s / kWPS) return false;
   return true;
+}
+// piece i finishes both groups of pair s / 2 (in a chunk's last block): it is
+// "s p1" for the pair's higher group (group S - 1 when the pair has one)
+template <int S>
+__host__ __device__ constexpr bool wide_ends_pair(int i) {
+  const WPiece p = wide_piece<S>(i);
+  return p.glo == p.s && (p.s % 2 == 1 || p.s == S - 1);
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
 
 // The MMA warp's work for piece I .. of one K block, unrolled at compile
 // time so that the piece table costs the issuing thread no instructions.
+// pre: the stage of piece I was seen complete by an earlier test.  Every
+// test names a phase whose predecessor on that slot this thread has already
+// waited for, so a true result can only mean that phase.
 struct WideIssue {
   WideBars* bars;
   uint32_t tbase;
@@ -804,23 +838,38 @@ struct WideIssue {
   WaitState* wst;
   unsigned long long wlim;
 };
+struct WideNext {
+  bool a0, x;      // the next K block's first A stage and X stage, seen complete
+};
 template <int S, int I>
-__device__ __forceinline__ bool wide_issue(const WideIssue& q, int& ready) {
+__device__ __forceinline__ bool wide_issue(const WideIssue& q, int& ready, bool pre, WideNext& nx) {
   if constexpr (I < wide_pieces<S>()) {
     constexpr WPiece p = wide_piece<S>(I);
-    constexpr bool first_of_plane = wide_first_of_plane<S>(I), last_of_plane = wide_last_of_plane<S>(I);
-    const int ia = q.gkb * S + p.s;                   // the plane's place in the A ring's sequence
+    constexpr int NST = wide_stages<S>();
+    const int ia = q.gkb * NST + p.s / kWPS;          // the stage's place in the A ring's sequence
     const int slot = ia % kWRA;
-    if (first_of_plane) {
-      if (!mbar_wait(smem_u32(&q.bars->a_full[slot]), (ia / kWRA) & 1, q.wst, q.wlim)) return false;
+    if constexpr (wide_first_of_stage<S>(I)) {
+      if (!pre && !mbar_wait(smem_u32(&q.bars->a_full[slot]), (ia / kWRA) & 1, q.wst, q.wlim)) return false;
       tc_fence_after();
     }
-    while (ready < p.ghi) {
+    while (ready < p.ghi / 2) {
       ++ready;
       if (!mbar_wait(smem_u32(&q.bars->g_empty[ready]), q.c & 1, q.wst, q.wlim)) return false;
       tc_fence_after();
     }
-    const uint64_t ad = q.a_desc0 + (uint64_t)(slot * (kATile >> 4));
+    // look ahead without blocking: the next stage of this block, or after the
+    // last piece the next K block's X stage and first A stage
+    bool nxt = false;
+    if constexpr (wide_first_of_stage<S>(I + 1)) {
+      const int ib = q.gkb * NST + wide_piece<S>(I + 1).s / kWPS;
+      nxt = mbar_test(smem_u32(&q.bars->a_full[ib % kWRA]), (ib / kWRA) & 1);
+    }
+    if constexpr (I + 1 == wide_pieces<S>()) {
+      const int ib = (q.gkb + 1) * NST, xb = q.gkb + 1;
+      nx.a0 = mbar_test(smem_u32(&q.bars->a_full[ib % kWRA]), (ib / kWRA) & 1);
+      nx.x = mbar_test(smem_u32(&q.bars->x_full[xb % kWRX]), (xb / kWRX) & 1);
+    }
+    const uint64_t ad = q.a_desc0 + (uint64_t)((slot * kWAStage + (p.s % kWPS) * kATile) >> 4);
     // B rows: X planes t = glo - s .. ghi - s (64 rows each, 128 B a row);
     // TMEM columns 64 glo ..; +2 in the address field steps 16 K
     const uint64_t bd = q.xd + (uint64_t)(((p.glo - p.s) * kWBN * kBK * 2) >> 4);
@@ -830,9 +879,10 @@ __device__ __forceinline__ bool wide_issue(const WideIssue& q, int& ready) {
     tc_mma(dt, ad + 2, bd + 2, id, 1u);
     tc_mma(dt, ad + 4, bd + 4, id, 1u);
     tc_mma(dt, ad + 6, bd + 6, id, 1u);
-    if (last_of_plane) tc_commit(smem_u32(&q.bars->a_empty[slot]));
-    if (p.glo == p.s && q.last) tc_commit(smem_u32(&q.bars->g_full[p.s]));
-    return wide_issue<S, I + 1>(q, ready);
+    if constexpr (wide_last_of_stage<S>(I)) tc_commit(smem_u32(&q.bars->a_empty[slot]));
+    if constexpr (wide_ends_pair<S>(I))
+      if (q.last) tc_commit(smem_u32(&q.bars->g_full[p.s / 2]));
+    return wide_issue<S, I + 1>(q, ready, nxt, nx);
   } else {
     return true;
   }
@@ -854,8 +904,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (s_skip) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sa = smem;                          // kWRA x 16 KiB
-  unsigned char* sx = smem + kWRA * kATile;          // kWRX x 64 KiB
+  unsigned char* sa = smem;                          // kWRA x 32 KiB
+  unsigned char* sx = smem + kWRA * kWAStage;        // kWRX x 64 KiB
   WideBars* bars = reinterpret_cast<WideBars*>(sx + kWRX * kWXTile);
   static_assert(sizeof(WideBars) <= 1024, "barrier block");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -895,9 +945,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&bars->x_full[i]), 1);
       mbar_init(smem_u32(&bars->x_empty[i]), 1);
     }
-    for (int i = 0; i < S; ++i) {
+    for (int i = 0; i < kWPairs; ++i) {
       mbar_init(smem_u32(&bars->g_full[i]), 1);
-      mbar_init(smem_u32(&bars->g_empty[i]), kEpiWarps);  // one arrival per epilogue warp
+      // one arrival per epilogue warp and group of the pair
+      mbar_init(smem_u32(&bars->g_empty[i]), kEpiWarps * (2 * i + 1 < S ? 2 : 1));
     }
     mbar_init(smem_u32(&bars->drain), 1);
     bars->wait.abort = 0;
@@ -939,11 +990,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         t * g.b_plane_rows + it.nb * kWBN);
           ++issued_x;
 #pragma unroll
-          for (int s = 0; s < S; ++s) {
+          for (int j = 0; j < wide_stages<S>(); ++j) {
+            constexpr int kLast = S - kWPS * (wide_stages<S>() - 1);   // planes of the last stage
+            const int np = j == wide_stages<S>() - 1 ? kLast : kWPS;
             ok = mbar_wait(smem_u32(&bars->a_empty[as]), aph ^ 1, wst, wlim);
             if (!ok) break;
-            mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)kATile);
-            tma_load_2d(smem_u32(sa + as * kATile), &tmA, smem_u32(&bars->a_full[as]), kx, s * g.a_plane_rows + m0);
+            mbar_expect_tx(smem_u32(&bars->a_full[as]), (uint32_t)(np * kATile));
+            for (int h = 0; h < np; ++h)
+              tma_load_2d(smem_u32(sa + as * kWAStage + h * kATile), &tmA, smem_u32(&bars->a_full[as]), kx,
+                          (kWPS * j + h) * g.a_plane_rows + m0);
             ++issued_a;
             if (++as == kWRA) {
               as = 0;
@@ -966,6 +1021,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t x_desc0 = smem_desc(smem_u32(sx));
       bool ok = true;
       int gkb = 0, gc = 0;
+      WideNext nx{false, false};
       Item it;
       for (int w = 0; ok && item(w, it); ++w) {
         const int KB = it.kb;
@@ -975,13 +1031,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool first = (kb % kChunkBlocks) == 0;
           const bool last = (kb % kChunkBlocks) == kChunkBlocks - 1 || kb == KB - 1;
           const int xs = gkb % kWRX;
-          ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb / kWRX) & 1, wst, wlim);
-          if (!ok) break;
+          if (!nx.x) {
+            ok = mbar_wait(smem_u32(&bars->x_full[xs]), (gkb / kWRX) & 1, wst, wlim);
+            if (!ok) break;
+          }
           tc_fence_after();
           const uint64_t xd = x_desc0 + (uint64_t)(xs * (kWXTile >> 4));
-          int ready = first ? -1 : S - 1;                // groups known drained for this chunk
+          int ready = first ? -1 : (S - 1) / 2;          // group pairs known drained for this chunk
           const WideIssue q{bars, tbase, a_desc0, xd, gkb, c, last, wst, wlim};
-          ok = wide_issue<S, 0>(q, ready);
+          const bool pre = nx.a0;
+          ok = wide_issue<S, 0>(q, ready, pre, nx);
           if (!ok) break;
           tc_commit(smem_u32(&bars->x_empty[xs]));
         }
@@ -1005,7 +1064,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncwarp();
     if (lane == 0)
-      for (int w = 0; w < S; ++w) mbar_arrive(smem_u32(&bars->g_empty[w]));
+      for (int w = 0; w < S; ++w) mbar_arrive(smem_u32(&bars->g_empty[w / 2]));
     bool ok = true;
     int gc = 0;
     Item it;
@@ -1019,12 +1078,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int c = gc + cl;
 #pragma unroll
         for (int w = 0; w < S; ++w) {
-          int w_ok = 0;
-          if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->g_full[w]), c & 1, wst, wlim);
-          ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
-          __syncwarp();
-          if (!ok) break;
-          tc_fence_after();
+          // one barrier a pair of groups: wait at the pair's first group; each
+          // group, once read and cleared, adds one arrival a warp to the
+          // pair's release barrier (which completes with the pair's last)
+          if (w % 2 == 0) {
+            int w_ok = 0;
+            if (lane == 0) w_ok = mbar_wait_sleep(smem_u32(&bars->g_full[w / 2]), c & 1, wst, wlim);
+            ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+            __syncwarp();
+            if (!ok) break;
+            tc_fence_after();
+          }
           // two halves of 16 columns (the register budget holds the 64 sums
           // and one half); the group is cleared and released after the second
           // half is in registers
@@ -1040,7 +1104,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(smem_u32(&bars->g_empty[w]));
+              if (lane == 0) mbar_arrive(smem_u32(&bars->g_empty[w / 2]));
             }
 #pragma unroll
             for (int j = 0; j < kC / 2; ++j)
