@@ -14,6 +14,16 @@
 
 namespace eigref {
 
+// max of two 64-bit unsigned integers as one compare and one select (PTX,
+// so that it stays two integer instructions).  The bit patterns of
+// non-negative doubles order like these integers; the column and row maxima
+// of the split form are taken this way.
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("{\n .reg .pred p;\n setp.gt.u64 p, %1, %2;\n selp.b64 %0, %1, %2, p;\n}\n" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 constexpr int kMaxK = 128;                                 // k x k stage lives in shared memory
 

@@ -91,9 +91,48 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const double* __restrict
   }
 }
 
+// The same product for problems whose 64 x 64 tiles would leave most SMs
+// idle (small n, or k far below 64): 16 x 16 output tile per CTA, one output
+// per thread, the K sum in the same order as above (a single FMA chain over
+// l = 0 .. n-1), operands read through L1 (a warp reads 2 rows of A and one
+// 128-byte row of X per step).  FP64-pipe bound with many CTAs per SM.
+__global__ void __launch_bounds__(256) gemm_fp64_small_kernel(const double* __restrict__ A, int64_t lda,
+                                                              const double* __restrict__ X,
+                                                              double* __restrict__ P, int64_t n, int k,
+                                                              double shift, const double* __restrict__ Xs,
+                                                              const Control* ctl) {
+  if (ctl && ctl->done) return;
+  const int tid = threadIdx.x;
+  const int64_t row = (int64_t)blockIdx.x * 16 + (tid >> 4);
+  const int col = blockIdx.y * 16 + (tid & 15);
+  if (row >= n || col >= k) return;
+  const double* a = A + row * lda;
+  const double* x = X + col;
+  double acc = 0.0;
+  int64_t l = 0;
+  for (; l + 4 <= n; l += 4) {
+    const double a0 = __ldg(a + l), a1 = __ldg(a + l + 1), a2 = __ldg(a + l + 2), a3 = __ldg(a + l + 3);
+    const double x0 = __ldg(x + l * k), x1 = __ldg(x + (l + 1) * k), x2 = __ldg(x + (l + 2) * k),
+                 x3 = __ldg(x + (l + 3) * k);
+    acc = fma(a0, x0, acc);
+    acc = fma(a1, x1, acc);
+    acc = fma(a2, x2, acc);
+    acc = fma(a3, x3, acc);
+  }
+  for (; l < n; ++l) acc = fma(__ldg(a + l), __ldg(x + l * k), acc);
+  P[row * k + col] = acc - shift * Xs[row * k + col];
+}
+
 void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, int64_t n, int k,
                       double shift, const Control* ctl, cudaStream_t s, const double* Xs) {
   dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((k + GB_N - 1) / GB_N));
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((int64_t)grid.x * grid.y < 2 * sms || k <= 16) {
+    const dim3 g2((unsigned)((n + 15) / 16), (unsigned)((k + 15) / 16));
+    gemm_fp64_small_kernel<<<g2, 256, 0, s>>>(A, lda, X, P, n, k, shift, Xs ? Xs : X, ctl);
+    return;
+  }
   gemm_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, X, P, n, k, shift, Xs ? Xs : X, ctl);
 }
 
@@ -610,7 +649,7 @@ __global__ void __launch_bounds__(256) normalize_max_kernel(double* __restrict__
   for (int64_t e = t; e < total; e += T) {
     const double v = X[e] * sc;
     X[e] = v;
-    m = max(m, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+    m = umax64(m, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
   }
   if (t < total) atomicMax(&colm[t % k], m);
   __syncthreads();

@@ -320,8 +320,8 @@ __device__ __forceinline__ void kk_gemm_body(const SweepBufs& b, int k, int bx, 
     unsigned long long mm = live ? (unsigned long long)__double_as_longlong(mv) & 0x7FFFFFFFFFFFFFFFull : 0ull;
 #pragma unroll
     for (int o = 1; o < TT && o < 32; o <<= 1) {
-      mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-      mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+      mf = umax64(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+      mm = umax64(mm, __shfl_xor_sync(0xffffffffu, mm, o));
     }
     if (tx == 0 && j < k) {
       const int c = kfm_col(j);

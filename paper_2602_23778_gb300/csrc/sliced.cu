@@ -1476,6 +1476,29 @@ __device__ __forceinline__ unsigned long long abs_bits(double a) {
 }
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
+// The exponent e of the largest |a| of a 128-byte FP64 row r in a swizzled
+// tile (|a| < 2^e for every value of the row), with 32-bit integer work: the
+// largest high word of |a| carries the largest exponent field; only a row
+// whose largest value is subnormal or zero needs the full bit patterns.
+// kNonFinite when the row holds Inf or NaN.
+__device__ __forceinline__ int row_exponent16(const unsigned char* tile, int r) {
+  uint32_t hw = 0u;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint4 v = *reinterpret_cast<const uint4*>(tile + (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)));
+    hw = max(hw, max(v.y & 0x7FFFFFFFu, v.w & 0x7FFFFFFFu));
+  }
+  if (hw >= 0x7FF00000u) return kNonFinite;
+  if (hw >= 0x00100000u) return (int)(hw >> 20) - 1022;
+  unsigned long long am = 0ull;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double2 v = *reinterpret_cast<const double2*>(tile + (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)));
+    am = umax64(am, umax64(abs_bits(v.x), abs_bits(v.y)));
+  }
+  return exponent_of_bits(am);
+}
+
 // An integer-valued FP32 (|x| < 2^22) as an int: one add at the 1.5 x 2^23
 // offset, no conversion instruction.
 __device__ __forceinline__ int int_of_f32(uint32_t u) {
@@ -1579,8 +1602,8 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t n, int64_t 
   for (int64_t i = wid; i < n_pad; i += nw) {
     unsigned long long amax = 0ull;
     if (i < n)
-      for (int64_t l = lane; l < n; l += 32) amax = max(amax, abs_bits(A[i * lda + l]));
-    for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      for (int64_t l = lane; l < n; l += 32) amax = umax64(amax, abs_bits(A[i * lda + l]));
+    for (int o = 16; o > 0; o >>= 1) amax = umax64(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     const bool finite = amax < kInfBits;
     const int e = exponent_of_bits(amax);
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
@@ -1614,10 +1637,10 @@ __device__ __forceinline__ void colmax_body(const double* __restrict__ Y, int64_
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t iu = i + u * stride;
-      if (iu < rows) m[u] = max(m[u], abs_bits(Y[iu * rs + j * cs]));
+      if (iu < rows) m[u] = umax64(m[u], abs_bits(Y[iu * rs + j * cs]));
     }
   }
-  const unsigned long long mm = max(max(m[0], m[1]), max(m[2], m[3]));
+  const unsigned long long mm = umax64(umax64(m[0], m[1]), umax64(m[2], m[3]));
   // one atomic per column and block
   part[threadIdx.x] = live ? mm : 0ull;
   __syncthreads();
@@ -1649,14 +1672,14 @@ __global__ void __launch_bounds__(256) colmax_flat_kernel(const double* __restri
       const int64_t qu = q + u * T;
       if (qu < pairs) {
         const double2 v = Y2[qu];
-        m0[u] = max(m0[u], abs_bits(v.x));
-        m1[u] = max(m1[u], abs_bits(v.y));
+        m0[u] = umax64(m0[u], abs_bits(v.x));
+        m1[u] = umax64(m1[u], abs_bits(v.y));
       }
     }
   }
   if (t < pairs) {
-    atomicMax(&colm[(2 * t) % k], max(m0[0], m0[1]));
-    atomicMax(&colm[(2 * t + 1) % k], max(m1[0], m1[1]));
+    atomicMax(&colm[(2 * t) % k], umax64(m0[0], m0[1]));
+    atomicMax(&colm[(2 * t + 1) % k], umax64(m1[0], m1[1]));
   }
   if (t == 0 && (total & 1))   // odd total: the last element
     atomicMax(&colm[(total - 1) % k], abs_bits(Y[total - 1]));
@@ -1787,8 +1810,8 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ Y, in
   for (int64_t i = wid; i < n_pad; i += nw) {
     unsigned long long amax = 0ull;
     if (i < n)
-      for (int l = lane; l < k; l += 32) amax = max(amax, abs_bits(Y[i * k + l]));
-    for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      for (int l = lane; l < k; l += 32) amax = umax64(amax, abs_bits(Y[i * k + l]));
+    for (int o = 16; o > 0; o >>= 1) amax = umax64(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     const bool finite = amax < kInfBits;
     const int e = exponent_of_bits(amax);
     if (lane == 0) rowexp[i] = finite ? e : kNonFinite;
@@ -1931,7 +1954,7 @@ __global__ void __launch_bounds__(256) product_reduce_kernel(const longlong2* __
       }
       const double w = recombine<S>(hi, lo, rowexp[row], fc) - shift * Xs[e];
       P[e] = w;
-      m = max(m, abs_bits(w));
+      m = umax64(m, abs_bits(w));
     }
   }
   if (pmax) {
@@ -1941,7 +1964,7 @@ __global__ void __launch_bounds__(256) product_reduce_kernel(const longlong2* __
     if (threadIdx.x < 32 && c < k) {
       unsigned long long mm = 0ull;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) mm = max(mm, wmax[w][threadIdx.x]);
+      for (int w = 0; w < 8; ++w) mm = umax64(mm, wmax[w][threadIdx.x]);
       atomicMax(pmax + c, mm);
     }
   }
@@ -2117,7 +2140,7 @@ constexpr int kU16ABuf = ((kMaxS + 3) / 4) * kU16ABlock;   // planes 0..7, four 
 constexpr int kU16BRows = 16 * kMaxS;             // rows (t, j) of one operand's planes
 constexpr int kU16BBytes = 2 * kU16BRows * 128;   // F's then M's rows of 128 B; K = l in the first 32 B
 constexpr int kU16SliceWarps = 4;                 // one thread per tile row
-constexpr int kU16EpiWarps = 8;                   // two threads per tile row
+constexpr int kU16EpiWarps = 16;                  // four threads per tile row, four columns each
 constexpr int kU16Threads = 64 + 32 * (kU16SliceWarps + kU16EpiWarps);
 constexpr int kU16Smem = kU16Stages * kU16Stage + 2 * kU16ABuf + kU16BBytes + 1024 + 1024;
 
@@ -2138,8 +2161,9 @@ struct Upd16Args {
 };
 
 struct __align__(8) BarsU16 {
-  // sub[g][i & 3]: both warps of lane group g have written tile i (a ring of
-  // four: the second warp of a group can run up to two tiles ahead)
+  // sub[g][i & 3]: the four warps of lane group g have written tile i (a ring
+  // of four: a warp can run at most two tiles ahead of its group's leader,
+  // which releases the X stage and, with the others, the accumulators)
   uint64_t full[kU16Stages], empty[kU16Stages], a_full[2], a_empty[2], acc_full[2], acc_empty[2], sub[4][4], drain;
   uint32_t tmem_base;
   WaitState wait;
@@ -2165,18 +2189,26 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
                  "=r"(r[7])                                                                          \
                : "r"(taddr))
 
-// One lane's 8 columns of one accumulator set of update16 into two exact int64
+#define TC_LD4(taddr, r)                                                                     \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"                 \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])                            \
+               : "r"(taddr))
+
+// One lane's C columns of one accumulator set of update16 into two exact int64
 // sums (digit-pair groups w < 4 and w >= 4), the weights taken in pairs
 // (w, w + 1) within each group: C_w 2^8 + C_(w+1) stays below 2^30.
-template <int S>
-__device__ __forceinline__ void drain_u16(uint32_t tl, long long (&hi)[8], long long (&lo)[8]) {
+template <int S, int C = 8>
+__device__ __forceinline__ void drain_u16(uint32_t tl, long long (&hi)[C], long long (&lo)[C]) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
-  int pend[8];
+  for (int j = 0; j < C; ++j) hi[j] = lo[j] = 0;
+  int pend[C];
 #pragma unroll
   for (int w = 0; w < S; ++w) {
-    uint32_t v[8];
-    TC_LD8(tl + 16 * w, v);
+    uint32_t v[C];
+    if constexpr (C == 8)
+      TC_LD8(tl + 16 * w, v);
+    else
+      TC_LD4(tl + 16 * w, v);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const int base = w < 4 ? 0 : 4;                       // first weight of its group
     const int end = w < 4 ? (S < 4 ? S : 4) : S;           // one past its group's last
@@ -2185,7 +2217,7 @@ __device__ __forceinline__ void drain_u16(uint32_t tl, long long (&hi)[8], long 
     const int last_w = first ? (paired ? w + 1 : w) : w;   // weight of the pair's low digit
     const int sh = w < 4 ? kBits * (3 - last_w) : kBits * (S - 1 - last_w);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < C; ++j) {
       const int cw = int_of_f32(v[j]);
       if (first && paired) {
         pend[j] = cw;
@@ -2229,7 +2261,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
       mbar_init(smem_u32(&bars->acc_empty[i]), kU16EpiWarps);
     }
-    for (int i = 0; i < 16; ++i) mbar_init(smem_u32(&bars->sub[i >> 2][i & 3]), 2);
+    for (int i = 0; i < 16; ++i) mbar_init(smem_u32(&bars->sub[i >> 2][i & 3]), kU16EpiWarps / 4);
     mbar_init(smem_u32(&bars->drain), 1);
     bars->wait.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -2247,7 +2279,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     int fe = 0;
     if (j < g.k) {
       unsigned long long m = 0ull;
-      for (int l = 0; l < g.k; ++l) m = max(m, abs_bits(Fm[(int64_t)j * g.k + l]));
+      for (int l = 0; l < g.k; ++l) m = umax64(m, abs_bits(Fm[(int64_t)j * g.k + l]));
       fe = m < kInfBits ? exponent_of_bits(m) : kNonFinite;
     }
     fexp_s[threadIdx.x] = fe;
@@ -2340,23 +2372,22 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       if (!ok) break;
       mbar_wait_sleep(smem_u32(&bars->full[st]), (uint32_t)(lap & 1), wst, wlim);   // complete: each lane acquires
       const unsigned char* xt = stage0 + st * kU16Stage;
-      unsigned long long b[16];
-      unsigned long long am = 0ull;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const double2 v = *reinterpret_cast<const double2*>(xt + swz128(r, c));
-        b[2 * c] = (unsigned long long)__double_as_longlong(v.x);
-        b[2 * c + 1] = (unsigned long long)__double_as_longlong(v.y);
-        am = max(am, max(b[2 * c] & 0x7FFFFFFFFFFFFFFFull, b[2 * c + 1] & 0x7FFFFFFFFFFFFFFFull));
-      }
-      const bool fin = am < kInfBits;
-      const int e = fin ? exponent_of_bits(am) : 0;
+      // the row's exponent first, then the planes half a row at a time (the
+      // values are read from shared memory twice, to keep registers for the
+      // sixteen epilogue warps)
+      const int er = row_exponent16(xt, r);
+      const bool fin = er != kNonFinite;
+      const int e = fin ? er : 0;
       unsigned char* ab = abuf0 + a * kU16ABuf;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {   // columns 8 h .. 8 h + 7: one 16-byte chunk per plane
         unsigned long long bh[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) bh[q] = fin ? b[8 * h + q] : 0ull;
+        for (int q = 0; q < 4; ++q) {
+          const double2 v = *reinterpret_cast<const double2*>(xt + swz128(r, 4 * h + q));
+          bh[2 * q] = fin ? (unsigned long long)__double_as_longlong(v.x) : 0ull;
+          bh[2 * q + 1] = fin ? (unsigned long long)__double_as_longlong(v.y) : 0ull;
+        }
         uint4 pl[S];
         planes_of8<S>(bh, e, pl);
 #pragma unroll
@@ -2368,15 +2399,16 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       if (lane == 0) mbar_arrive(smem_u32(&bars->a_full[a]));
     }
   } else {
-    // ---------------- epilogue: two threads per tile row, eight columns each ----------------
-    const int ew = warp - 2 - kU16SliceWarps;   // 0..7
+    // ---------------- epilogue: four threads per tile row, four columns each ----------------
+    constexpr int kC = 4;                        // columns a thread
+    const int ew = warp - 2 - kU16SliceWarps;   // 0..15
     const int lg = warp & 3;                     // TMEM lane group: tile rows 32 lg .. 32 lg + 31
-    const int half = ew >> 2;                    // columns 8 half .. 8 half + 7
-    const bool leader = half == 0;               // stores the lane group's 32 rows
+    const int qt = ew >> 2;                      // columns kC qt .. kC qt + kC - 1
+    const bool leader = qt == 0;                 // stores the lane group's 32 rows
     const int r = lg * 32 + lane;
-    double sq[8], rq[8], vq[8];
+    double sq[kC], rq[kC], vq[kC];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) sq[j] = rq[j] = vq[j] = 0.0;
+    for (int j = 0; j < kC; ++j) sq[j] = rq[j] = vq[j] = 0.0;
     bool ok = true;
     for (int i = 0; i < cnt && ok; ++i) {
       const int a = i & 1, u = i >> 1;
@@ -2393,26 +2425,18 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       unsigned char* xt = stage0 + st * kU16Stage;
       const unsigned char* wt = xt + kU16Tile;
       // the row's exponent (as the slicers took it) and this thread's X values
-      double2 xv[4];
-      int e_row;
-      {
-        unsigned long long am = 0ull;
+      double2 xv[kC / 2];
+      const int e_row = row_exponent16(xt, r);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const double2 v = *reinterpret_cast<const double2*>(xt + swz128(r, c));
-          am = max(am, max(abs_bits(v.x), abs_bits(v.y)));
-          if ((c >> 2) == half) xv[c & 3] = v;
-        }
-        e_row = am < kInfBits ? exponent_of_bits(am) : kNonFinite;
-      }
-      const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * 256 + 8 * half);
+      for (int q = 0; q < kC / 2; ++q) xv[q] = *reinterpret_cast<const double2*>(xt + swz128(r, (kC / 2) * qt + q));
+      const uint32_t tl = tbase + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * 256 + kC * qt);
       // X M first (TMEM columns 128 ..), rounded at once, then X F
-      double xm[8];
-      long long hi[8], lo[8];
-      drain_u16<S>(tl + 128u, hi, lo);
+      double xm[kC];
+      long long hi[kC], lo[kC];
+      drain_u16<S, kC>(tl + 128u, hi, lo);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) xm[j] = recombine<S>(hi[j], lo[j], e_row, fexp_s[16 + 8 * half + j]);
-      drain_u16<S>(tl, hi, lo);
+      for (int j = 0; j < kC; ++j) xm[j] = recombine<S>(hi[j], lo[j], e_row, fexp_s[16 + kC * qt + j]);
+      drain_u16<S, kC>(tl, hi, lo);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->acc_empty[a]));
@@ -2420,8 +2444,8 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       const int64_t row = row0 + r;
       const bool live = row >= g.row_begin && row < g.n;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int cc = 4 * half + q;          // 16-byte chunk: columns 2 cc, 2 cc + 1
+      for (int q = 0; q < kC / 2; ++q) {
+        const int cc = (kC / 2) * qt + q;     // 16-byte chunk: columns 2 cc, 2 cc + 1
         const double2 x2 = xv[q];
         const double2 wv = *reinterpret_cast<const double2*>(wt + swz128(r, cc));
         const int j0 = 2 * cc, j1 = 2 * cc + 1;
@@ -2442,7 +2466,7 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
       }
       const bool plain = row0 < g.row_begin;   // the tile with the leading block
       if (plain && live)
-        for (int j = 8 * half; j < 8 * half + 8 && j < g.k; ++j)
+        for (int j = kC * qt; j < kC * qt + kC && j < g.k; ++j)
           g.Xn[row * g.k + j] = reinterpret_cast<const double*>(xt + swz128(r, j >> 1))[j & 1];
       fence_async_smem();
       __syncwarp();
@@ -2466,16 +2490,16 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
     if (lane == 0) bulk_wait_all();
     // column sums over this warp's rows, in a fixed order
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kC; ++j) {
       for (int o = 16; o > 0; o >>= 1) {
         sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], o);
         rq[j] += __shfl_xor_sync(0xffffffffu, rq[j], o);
         vq[j] += __shfl_xor_sync(0xffffffffu, vq[j], o);
       }
       if (lane == 0) {
-        colsum[0][lg][8 * half + j] = sq[j];
-        colsum[1][lg][8 * half + j] = rq[j];
-        colsum[2][lg][8 * half + j] = vq[j];
+        colsum[0][lg][kC * qt + j] = sq[j];
+        colsum[1][lg][kC * qt + j] = rq[j];
+        colsum[2][lg][kC * qt + j] = vq[j];
       }
     }
   }

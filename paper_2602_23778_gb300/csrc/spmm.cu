@@ -73,11 +73,11 @@ __global__ void __launch_bounds__(256) spmm_csr_vec2_kernel(const int32_t* __res
         const unsigned long long a = (unsigned long long)__double_as_longlong(ax) & 0x7FFFFFFFFFFFFFFFull;
         const unsigned long long b = (unsigned long long)__double_as_longlong(ay) & 0x7FFFFFFFFFFFFFFFull;
         if (c2 < lane + LPR) {
-          mx[0][0] = max(mx[0][0], a);
-          mx[0][1] = max(mx[0][1], b);
+          mx[0][0] = umax64(mx[0][0], a);
+          mx[0][1] = umax64(mx[0][1], b);
         } else {
-          mx[1][0] = max(mx[1][0], a);
-          mx[1][1] = max(mx[1][1], b);
+          mx[1][0] = umax64(mx[1][0], a);
+          mx[1][1] = umax64(mx[1][1], b);
         }
       }
     }
