@@ -237,6 +237,14 @@ def cpu_oracle_rate(p, sweeps):
     return sweeps / wall, max(1, round(cpu / wall)), wall
 
 
+def dense_config(n, k, world):
+    """The dense workload as both arms name it (the workload only; how it is
+    computed goes under "method")."""
+    return {"workload": WORKLOAD, "n": n, "k": k, "seed": 3000,
+            "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -246,7 +254,8 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": p.n, "k": p.k, "form": "CPU oracle, paper-literal Algorithm 4"},
+            "config": dense_config(p.n, p.k, args.gpus),
+            "method": {"form": "CPU oracle, paper-literal Algorithm 4 (FP64)"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d oracle sweeps of the full n=16384, k=128 workload (%.1f s)" % (args.steps, wall)},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -629,13 +638,12 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision + "-slices+f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "k": k, "form": precision, "seed": 3000,
+           "config": dense_config(n, k, world),
+           "method": {"form": precision,
                       "slices": (args.slices or 8) if precision != "fp64" else None,
                       # columns of the split product's output tile (128 x 64 wherever k allows it)
                       "product_tile": (args.product_tile or (64 if (k + 31) // 32 % 2 == 0 else 32))
                       if precision != "fp64" else None,
-                      "l2": "inputs larger than L2 (A is 2.1 GB); no flush",
-                      "parallelism": "replicas" if world > 1 else "single",
                       # product: 1..4 equal K splits a tile, 8 the equal-work plan (whole CTA rounds)
                       "split_k": {"product": rep["psplit"], "gram": rep["ksplit"]} if precision != "fp64" else None},
            "setup_ms": rep["setup_ms"], "call_s": call_s, "roofline": roof,
