@@ -691,6 +691,10 @@ def main():
         # pinned host buffers (page-locked, as a serving host keeps its inputs)
         Ah = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()
         Xh = torch.from_numpy(np.ascontiguousarray(p.X0.T)).pin_memory().t()   # column-major n x k
+        # untimed warm-up call with host buffers (the handle keeps its device
+        # staging buffer for A, as a serving process would)
+        Xw = torch.from_numpy(np.ascontiguousarray(p.X0.T)).pin_memory().t()
+        h.refine_dense(Ah, Xw, max_iters=args.warmup, check_every=max(2, args.warmup), **kw)
         t0 = time.perf_counter()
         re = h.refine_dense(Ah, Xh, max_iters=args.steps, check_every=args.steps, **kw)
         e2e_s = time.perf_counter() - t0
@@ -698,8 +702,9 @@ def main():
         out["e2e"] = {"value": re["iterations"] / e2e_s, "unit": UNIT,
                       "h2d_bytes_per_step": (nb_a + nb_x) / args.steps,
                       "d2h_bytes_per_step": (nb_x + 8 * k) / args.steps,
-                      "note": "pinned host A and X through eigref_refine_dense; the H2D copies, slicing of A "
-                              "and all set-up inside the timed call"}
+                      "note": "pinned host A and X through eigref_refine_dense after one untimed warm-up call; "
+                              "the H2D copies of A and X, slicing of A, all set-up and the D2H copy of X inside "
+                              "the timed call"}
 
     if rank == 0 and world == 1 and not args.no_other_workloads and args.n == 16384 and args.k == 128:
         # the other workloads of the benchmark set, measured in the same run

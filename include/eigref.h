@@ -171,13 +171,17 @@ void eigref_params_default(eigref_params* p);
  * Errors: EIGREF_E_INVALID (h NULL, bad device), EIGREF_E_CUDA. */
 int eigref_create(eigref_handle* h, int device, void* cuda_stream);
 
-/* Release the handle and its workspace.  NULL is a no-op. */
+/* Release the handle, its workspace and its staging buffer for host A.
+ * NULL is a no-op. */
 int eigref_destroy(eigref_handle h);
 
 /* Refine the k columns of X in place against dense symmetric A (Algorithm 4
  * iterated, Section 3.1.3).  1 <= k <= 128, k < n.  On EIGREF_OK,
  * EIGREF_E_NOT_CONVERGED or EIGREF_E_DIVERGED, X holds the last iterate; on
  * EIGREF_E_NONFINITE the last finite one; on EIGREF_E_INVALID it is untouched.
+ * A and X may be device or host memory.  A host A is copied into a device
+ * buffer that the handle keeps for later calls (grown when a larger A comes,
+ * released by eigref_destroy); page-locked host memory copies fastest.
  * rep may be NULL. */
 int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda,
                         double* X, int64_t ldx, int k,

@@ -36,6 +36,10 @@ struct eigref_ctx {
   size_t ws_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   Control* host_ctl = nullptr;  // pinned
+  // device copy of a host A (refine_dense with A in host memory): kept for the
+  // next call, grown when a larger A comes, freed with the handle
+  void* a_stage = nullptr;
+  size_t a_stage_bytes = 0;
   // split-K choices the autotuner measured, by (n, k, slices, product tile)
   std::map<std::tuple<int64_t, int, int, int>, std::pair<int, int>> tuned;
 };
@@ -845,6 +849,7 @@ int eigref_destroy(eigref_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->ws) cudaFree(h->ws);
+  if (h->a_stage) cudaFree(h->a_stage);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->host_ctl) cudaFreeHost(h->host_ctl);
@@ -874,16 +879,31 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
   pr.k = k;
   pr.lda = lda;
   pr.square = pp->target == EIGREF_SMALLEST_MAG;
-  double* a_dev = nullptr;
   if (is_device_ptr(A)) {
     pr.A = A;
   } else {
-    // host A: one pitched copy into a separate device buffer for this call
-    cudaError_t e = cudaMalloc(&a_dev, (size_t)n * n * sizeof(double));
-    if (e != cudaSuccess) { cudaGetLastError(); return set_err(h, EIGREF_E_NOMEM, "device copy of A"); }
-    e = cudaMemcpy2DAsync(a_dev, n * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
-                          cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) { cudaFree(a_dev); return set_err(h, EIGREF_E_CUDA, "copy of A: %s", cudaGetErrorString(e)); }
+    // host A: one pitched copy into the handle's staging buffer (kept between
+    // calls: a serving host that refines against matrices of one size pays
+    // the allocation once)
+    const size_t bytes = (size_t)n * n * sizeof(double);
+    if (bytes > h->a_stage_bytes) {
+      if (h->a_stage) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->a_stage);
+        h->a_stage = nullptr;
+        h->a_stage_bytes = 0;
+      }
+      if (cudaMalloc(&h->a_stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h->a_stage = nullptr;
+        return set_err(h, EIGREF_E_NOMEM, "device copy of A");
+      }
+      h->a_stage_bytes = bytes;
+    }
+    double* a_dev = static_cast<double*>(h->a_stage);
+    cudaError_t e = cudaMemcpy2DAsync(a_dev, n * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
+                                      cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return set_err(h, EIGREF_E_CUDA, "copy of A: %s", cudaGetErrorString(e));
     pr.A = a_dev;
     pr.lda = n;
   }
@@ -891,20 +911,12 @@ int eigref_refine_dense(eigref_handle h, const double* A, int64_t n, int64_t lda
   if (pp->precision != EIGREF_FP64) {
     st = sl.configure(pr.A, n, pr.lda, k, pp->precision, pp->slices);
     if (!st) st = sl.set_product_tile(pp->product_tile);
-    if (st) {
-      if (a_dev) cudaFree(a_dev);
-      return set_err(h, st, "%s", sl.error());
-    }
+    if (st) return set_err(h, st, "%s", sl.error());
     auto tk = h->tuned.find(std::make_tuple(n, k, sl.slices(), sl.product_tile()));
     if (tk != h->tuned.end()) sl.set_splits(tk->second.first, tk->second.second);
     pr.sliced = &sl;
   }
-  st = refine_common(h, pr, X, ldx, pp, rep);
-  if (a_dev) {
-    cudaStreamSynchronize(h->stream);
-    cudaFree(a_dev);
-  }
-  return st;
+  return refine_common(h, pr, X, ldx, pp, rep);
 }
 
 int eigref_refine_csr(eigref_handle h, const int32_t* row_ptr, const int32_t* col_idx, const double* val, int64_t n,

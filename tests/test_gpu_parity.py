@@ -201,13 +201,20 @@ def test_invalid_arguments_leave_x_untouched(eig):
 
 
 def test_host_buffers_match_device(eig):
-    p = dense_case(300, 5, seed=13)
-    Xd, rd = run_gpu(eig, p, max_iters=4)
-    Xh = np.asfortranarray(p.X0.copy())
-    rh = eig.refine_dense(np.ascontiguousarray(p.A), Xh, norm_a=p.normA, target="shift", shift=p.shift,
-                          max_iters=4)
-    assert rh["iterations"] == 4
-    assert np.array_equal(Xh, Xd)
+    """Host A and X give the device-buffer results bit for bit; the handle's
+    staging buffer for host A is reused by a smaller A, grown for a larger
+    one and reused again (both forms)."""
+    for n, k, seed in ((300, 5, 13), (200, 3, 16), (520, 33, 17), (300, 5, 13)):
+        p = dense_case(n, k, seed=seed)
+        for prec in ("fp64", "bf16"):
+            Xd = dev(np.asfortranarray(p.X0))
+            eig.refine_dense(dev(p.A), Xd, norm_a=p.normA, target="shift", shift=p.shift, max_iters=4,
+                             precision=prec)
+            Xh = np.asfortranarray(p.X0.copy())
+            rh = eig.refine_dense(np.ascontiguousarray(p.A), Xh, norm_a=p.normA, target="shift", shift=p.shift,
+                                  max_iters=4, precision=prec)
+            assert rh["iterations"] == 4
+            assert np.array_equal(Xh, host(Xd)), (n, k, prec)
 
 
 def test_norm_inf_and_shift_targets(eig):
