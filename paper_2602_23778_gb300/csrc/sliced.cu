@@ -77,11 +77,16 @@ constexpr int kNonFinite = -100000;  // exponent marking a row / column holding 
 constexpr uint64_t kTimeoutNs = 2000000000ull;       // 2 s: no legitimate wait comes close
 constexpr int kSmemBytes = kRA * kATile + kRX * kXTile + 1024 /*barriers*/ + 1024 /*alignment*/;
 constexpr int kSmemBytesProduct = kRAProduct * kATile + kRXProduct * kXTile + 1024 + 1024;
-constexpr int kTrStride = kBN / 2 + 1;               // doubles a row of a warp's 32 x 16 transpose block (no bank conflicts)
-constexpr int kTrBytes = kEpiWarps * 32 * kTrStride * 8;   // 34 KiB
+// The row update's epilogue: 16 warps, four a TMEM lane group, 8 of the 32
+// tile columns each (the other modes keep 8 warps of 16 columns)
+constexpr int kEpiWarpsU = 16;
+constexpr int kThreadsU = 64 + 32 * kEpiWarpsU;
+constexpr int kTrStride = kBN * 4 / kEpiWarpsU + 1;   // doubles a row of a warp's 32 x 8 transpose block (no bank conflicts)
+constexpr int kTrBytes = kEpiWarpsU * 32 * kTrStride * 8;   // 36 KiB
 constexpr int kSmemBytesUpdate = kRAUpdate * kATile + kRX * kXTile + 1024 + kTrBytes + 1024;
 __host__ __device__ constexpr int ring_a(int mode) { return mode == 0 ? kRAProduct : (mode == 2 ? kRAUpdate : kRA); }
 __host__ __device__ constexpr int ring_x(int mode) { return mode == 0 ? kRXProduct : kRX; }
+__host__ __device__ constexpr int threads_of(int mode) { return mode == 2 ? kThreadsU : kThreads; }
 __host__ __device__ constexpr int smem_bytes(int mode) {
   return mode == 0 ? kSmemBytesProduct : (mode == 2 ? kSmemBytesUpdate : kSmemBytes);
 }
@@ -203,6 +208,12 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+#define TC_LD8(taddr, r)                                                                             \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"               \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+                 "=r"(r[7])                                                                          \
+               : "r"(taddr))
+
 #define TC_LD16(taddr, r)                                                                                   \
   asm volatile(                                                                                             \
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
@@ -308,7 +319,8 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   unsigned char* sx = smem + RA * kATile;            // RX x 32 KiB
   Bars* bars = reinterpret_cast<Bars*>(sx + RX * kXTile);
   static_assert(sizeof(Bars) <= 1024, "barrier block");
-  double* s_tr = reinterpret_cast<double*>(sx + RX * kXTile + 1024);    // UPDATE: 8 warps x 32 x kTrStride
+  double* s_tr = reinterpret_cast<double*>(sx + RX * kXTile + 1024);    // UPDATE: 16 warps x 32 x kTrStride
+  constexpr int EW = MODE == MODE_UPDATE ? kEpiWarpsU : kEpiWarps;       // epilogue warps
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column blocks vary fastest, so the CTAs sharing A-side rows run together
   const int job = MODE == MODE_GRAM ? (zb & 1) : 0;
@@ -365,7 +377,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
-      mbar_init(smem_u32(&bars->acc_empty[i]), kEpiWarps);  // one arrival per epilogue warp
+      mbar_init(smem_u32(&bars->acc_empty[i]), EW);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bars->drain), 1);
     bars->wait.abort = 0;
@@ -505,8 +517,8 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
   } else {
     // ---------------- epilogue: drain chunks into exact int64 sums ----------------
     const int lg = warp & 3;                           // TMEM lane group of this warp
-    const int half = (warp - 2) >> 2;                  // which 16 of the 32 columns
-    constexpr int kC = kBN / 2;
+    constexpr int kC = kBN * 4 / EW;                   // columns of a warp: 16 (8 warps) or 8 (16 warps)
+    const int half = (warp - 2) >> 2;                  // which kC of the 32 columns
     bool ok = true;
     int gc = 0;                                        // chunks over the CTA's tiles
     Item it;
@@ -521,7 +533,7 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       if (MODE == MODE_UPDATE && row < g.m_valid && row >= g.row_begin) {
         // the row's X and W values the update reads after the drain: into L1
         // while the MMAs run (128 contiguous bytes each)
-        const int64_t e0 = row * g.k + nbt * kC;
+        const int64_t e0 = row * g.k + nbt * (kBN / 2);
         asm volatile("prefetch.global.L1 [%0];" ::"l"(g.X + e0));
         asm volatile("prefetch.global.L1 [%0];" ::"l"(g.W + e0));
       }
@@ -545,7 +557,12 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
           uint32_t r[GW][kC];
 #pragma unroll
           for (int q = 0; q < GW; ++q)
-            if (w0 + q < S) TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
+            if (w0 + q < S) {
+              if constexpr (kC == 16)
+                TC_LD16(tw + (uint32_t)((w0 + q) * kBN), r[q]);
+              else
+                TC_LD8(tw + (uint32_t)((w0 + q) * kBN), r[q]);
+            }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int q = 0; q < GW; ++q) {
@@ -572,17 +589,21 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
       if constexpr (MODE == MODE_UPDATE) {
         // The B operand interleaves F and M by 16 columns, so column block nbt
         // covers the real columns c0 .. c0 + 15 with X F in the first half of
-        // the tile (warps of half 0) and X M in the second (half 1).
-        //   half 0:  X' = X + (W - X D) D^-1 - X F   (written), sums of X'^2 and R^2
-        //   half 1:  V2 = R2 - X2 M                  (the rows of E21 D), sums of V2^2
-        // Each lane recombines its row of X F or X M (16 columns); the warp's
-        // 32 x 16 block then turns through shared memory, so that a half-warp
-        // holds 16 consecutive columns of one row and every global load and
-        // store of X, W and X' moves 128-byte rows (one row per lane would
-        // touch 32 rows an access).  X, W, d and 1/d are read-only in this
+        // the tile and X M in the second; four warps share each lane group's
+        // 32 rows, 8 columns each (part = half: 0, 1 X F, 2, 3 X M):
+        //   X F:  X' = X + (W - X D) D^-1 - X F   (written), sums of X'^2 and R^2
+        //   X M:  V2 = R2 - X2 M                  (the rows of E21 D), sums of V2^2
+        // Each lane recombines its row of 8 columns; the warp's 32 x 8 block
+        // then turns through shared memory, so that 8 lanes hold 8 consecutive
+        // columns of one row and every global load and store of X, W and X'
+        // moves 64-byte row segments.  X, W, d and 1/d are read-only in this
         // launch (X' is another buffer).
-        const int c0 = nbt * kC;
-        const int cl = c0 + (lane & (kC - 1));           // this lane's column after the turn
+        constexpr int kR = kBN / 2;                      // real columns of a tile
+        constexpr int kL = 32 / kC;                      // rows a step after the turn
+        const bool isF = half < 2;
+        const int c0 = nbt * kR;
+        const int cf = c0 + (half & 1) * kC;             // this warp's first real column
+        const int cl = cf + (lane & (kC - 1));           // this lane's column after the turn
         const bool cok = cl < g.k;
         const int e_l = cok ? __ldg(cexp + nbt * kBN + half * kC + (lane & (kC - 1))) : 0;
         double* tr = s_tr + (warp - 2) * 32 * kTrStride;
@@ -590,30 +611,30 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
 #pragma unroll
         for (int j = 0; j < kC; ++j) {
           const int ej = __shfl_sync(0xffffffffu, e_l, j);
-          const bool lv = ok && row < g.m_valid && row >= g.row_begin && c0 + j < g.k;
+          const bool lv = ok && row < g.m_valid && row >= g.row_begin && cf + j < g.k;
           tr[lane * kTrStride + j] = lv ? recombine<S>(hi[j], lo[j], er, ej) : 0.0;
         }
         __syncwarp();
-        // lane L: column cl of rows r0 + 2i, i = 0 .. 15
-        const int64_t r0 = (int64_t)mbt * kBM + lg * 32 + (lane >> 4);
+        // lane L: column cl of rows r0 + kL i, i = 0 .. kC - 1
+        const int64_t r0 = (int64_t)mbt * kBM + lg * 32 + (lane / kC);
         const double dj = cok ? __ldg(g.d + cl) : 0.0, dij = cok ? __ldg(g.dinv + cl) : 0.0;
         double xv[kC], wv[kC];
 #pragma unroll
         for (int i = 0; i < kC; ++i) {
-          const int64_t r = r0 + 2 * i;
+          const int64_t r = r0 + kL * i;
           const bool lv = ok && cok && r < g.m_valid && r >= g.row_begin;
           xv[i] = lv ? __ldg(g.X + r * g.k + cl) : 0.0;
           wv[i] = lv ? __ldg(g.W + r * g.k + cl) : 0.0;
         }
-        // column sums, rows in order: half 0 of X'^2 and (W - X D)^2, half 1 of V2^2
+        // column sums, rows in order: X F warps of X'^2 and (W - X D)^2, X M warps of V2^2
         double s0 = 0.0, s1 = 0.0;
 #pragma unroll
         for (int i = 0; i < kC; ++i) {
-          const int64_t r = r0 + 2 * i;
+          const int64_t r = r0 + kL * i;
           if (ok && cok && r < g.m_valid && r >= g.row_begin) {
             const double rr = wv[i] - xv[i] * dj;
-            const double t = tr[(2 * i + (lane >> 4)) * kTrStride + (lane & (kC - 1))];
-            if (half == 0) {
+            const double t = tr[(kL * i + lane / kC) * kTrStride + (lane & (kC - 1))];
+            if (isF) {
               const double xn = xv[i] + rr * dij - t;
               g.Xn[r * g.k + cl] = xn;
               s0 = fma(xn, xn, s0);
@@ -624,25 +645,29 @@ __device__ __forceinline__ void sliced_mma_body(const CUtensorMap* tmA, const CU
             }
           }
         }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 16);     // the two half-warps share the columns
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+        // the lanes that share a column (lane % kC), in a fixed order
+#pragma unroll
+        for (int o = kC; o < 32; o <<= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
         const int tp = w & 1;                            // tile parity: the buffer of this tile's sums
         if (lane < kC) {
-          if (half == 0) {
-            s_colsum[tp][0][lg][lane] = s0;
-            s_colsum[tp][1][lg][lane] = s1;
+          const int cc = (half & 1) * kC + lane;        // real column within the tile
+          if (isF) {
+            s_colsum[tp][0][lg][cc] = s0;
+            s_colsum[tp][1][lg][cc] = s1;
           } else {
-            s_colsum[tp][2][lg][lane] = s0;
+            s_colsum[tp][2][lg][cc] = s0;
           }
         }
-        // the eight epilogue warps meet; the first two add the four lane
-        // groups' sums of the tile.  A warp writes buffer tp again two tiles
-        // later, after the next meeting, which every reader of this one has
-        // passed.
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+        // the epilogue warps meet; the first two add the four lane groups'
+        // sums of the tile.  A warp writes buffer tp again two tiles later,
+        // after the next meeting, which every reader of this one has passed.
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
         const int et = (int)threadIdx.x - 64;
-        if (et < 3 * kC) {
-          const int which = et / kC, cc = et % kC;
+        if (et < 3 * kR) {
+          const int which = et / kR, cc = et % kR;
           const int col = c0 + cc;
           if (col < g.k) {
             const double v = s_colsum[tp][which][0][cc] + s_colsum[tp][which][1][cc] + s_colsum[tp][which][2][cc] +
@@ -702,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // shares the SM; here the MMAs of a CTA's next tile overlap the epilogue of
 // its current one.
 template <int S>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsU, 1)
     sliced_update_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                                     MmaArgs g, int gx, int tiles) {
   sliced_mma_body<S, MODE_UPDATE>(&tmA, &tmB, &tmB, g, 0, 0, 0, gx, tiles);
@@ -1159,7 +1184,7 @@ struct GroupMma {
 };
 
 template <int S, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) sliced_mma_grouped_kernel(const __grid_constant__ GroupMma p) {
+__global__ void __launch_bounds__(threads_of(MODE), 1) sliced_mma_grouped_kernel(const __grid_constant__ GroupMma p) {
   const int c = blockIdx.x;
   int t = 0;
   while (t + 1 < p.count && c >= p.cta_begin[t + 1]) ++t;
@@ -2183,12 +2208,6 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-#define TC_LD8(taddr, r)                                                                             \
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"               \
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
-                 "=r"(r[7])                                                                          \
-               : "r"(taddr))
-
 #define TC_LD4(taddr, r)                                                                     \
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"                 \
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])                            \
@@ -3130,7 +3149,7 @@ static void launch_task(int S, int mode, const MmaTask& t, cudaStream_t s) {
     const int tiles = t.gx * t.gy;
     const int ctas = std::max(1, std::min(tiles, sms));
 #define EIGREF_CALL_UPD(S_)                                                                                   \
-  sl::sliced_update_persistent_kernel<S_><<<ctas, sl::kThreads, sl::kSmemBytesUpdate, s>>>(t.a, t.b, t.g, t.gx, tiles)
+  sl::sliced_update_persistent_kernel<S_><<<ctas, sl::kThreadsU, sl::kSmemBytesUpdate, s>>>(t.a, t.b, t.g, t.gx, tiles)
     EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_UPD)
 #undef EIGREF_CALL_UPD
   }
@@ -3379,7 +3398,7 @@ int SlicedA::update(const double* X, const double* W, const double* FM, const do
 template <int MODE>
 static void launch_mma_group(int S, const sl::GroupMma& p, int ctas, cudaStream_t s) {
 #define EIGREF_CALL_MMA_G(S_) \
-  sl::sliced_mma_grouped_kernel<S_, MODE><<<ctas, sl::kThreads, sl::smem_bytes(MODE), s>>>(p)
+  sl::sliced_mma_grouped_kernel<S_, MODE><<<ctas, sl::threads_of(MODE), sl::smem_bytes(MODE), s>>>(p)
   EIGREF_SLICE_DISPATCH(S, EIGREF_CALL_MMA_G)
 #undef EIGREF_CALL_MMA_G
 }
