@@ -657,8 +657,66 @@ __global__ void __launch_bounds__(256) normalize_max_kernel(double* __restrict__
     if (colm[j]) atomicMax(cmax + j, colm[j]);
 }
 
+// The same for even k with 16-byte accesses: a thread takes column pairs
+// (2 c, 2 c + 1), c fixed (the thread count is a multiple of k / 2), and keeps
+// four pairs in flight a step, so that HBM, not the latency of one load a
+// thread, sets the pace.
+__global__ void __launch_bounds__(256) normalize_max2_kernel(double* __restrict__ X, int64_t n, int k,
+                                                             const double* __restrict__ nu, const Control* ctl,
+                                                             unsigned long long* __restrict__ cmax) {
+  if (!ctl->pending_norm) return;
+  __shared__ unsigned long long colm[kMaxK];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) colm[j] = 0ull;
+  __syncthreads();
+  const int h = k / 2;
+  const int64_t total = n * h;                       // pairs
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int c = (int)(t % h);
+  const double s0 = nu[2 * c], s1 = nu[2 * c + 1];
+  double2* X2 = reinterpret_cast<double2*>(X);
+  unsigned long long m0 = 0ull, m1 = 0ull;
+  int64_t e = t;
+  for (; e + 3 * T < total; e += 4 * T) {
+    double2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = X2[e + q * T];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q].x *= s0;
+      v[q].y *= s1;
+      X2[e + q * T] = v[q];
+      m0 = umax64(m0, (unsigned long long)__double_as_longlong(v[q].x) & 0x7FFFFFFFFFFFFFFFull);
+      m1 = umax64(m1, (unsigned long long)__double_as_longlong(v[q].y) & 0x7FFFFFFFFFFFFFFFull);
+    }
+  }
+  for (; e < total; e += T) {
+    double2 v = X2[e];
+    v.x *= s0;
+    v.y *= s1;
+    X2[e] = v;
+    m0 = umax64(m0, (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull);
+    m1 = umax64(m1, (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull);
+  }
+  if (t < total) {
+    atomicMax(&colm[2 * c], m0);
+    atomicMax(&colm[2 * c + 1], m1);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    if (colm[j]) atomicMax(cmax + j, colm[j]);
+}
+
 void launch_normalize(const SweepBufs& b, int64_t n, int k, cudaStream_t s, unsigned long long* cmax) {
   int64_t total = n * k;
+  if (cmax && k % 2 == 0 && (reinterpret_cast<uintptr_t>(b.xn) & 15) == 0) {
+    // blocks: about 8 per SM, the thread count a multiple of k / 2
+    int g = 256, kk = k / 2;
+    while (kk % 2 == 0 && g % 2 == 0) { kk /= 2; g /= 2; }
+    const int blocks = ((152 * 8 + kk - 1) / kk) * kk;
+    normalize_max2_kernel<<<blocks, 256, 0, s>>>(b.xn, n, k, b.nu, b.ctl, cmax);
+    return;
+  }
   if (cmax) {
     // blocks: about 8 per SM, a multiple of k / gcd(k, 256)
     int g = 256, kk = k;
