@@ -252,7 +252,7 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 // pattern: no FP64 instruction (FP64 runs at a small fraction of the integer
 // rate on this part), and the same value as rounding the exact sum once.
 template <int S>
-__device__ __forceinline__ double recombine(long long hi, long long lo, int er, int fc) {
+__device__ __forceinline__ double recombine_wide(long long hi, long long lo, int er, int fc) {
   if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);  // Inf / NaN operand
   constexpr int m = LoExp<S>::value > kHiExp ? LoExp<S>::value : kHiExp;
   constexpr int K = m - kHiExp;                 // lo = 0 when S < 4 (no weight group >= 4)
@@ -291,6 +291,53 @@ __device__ __forceinline__ double recombine(long long hi, long long lo, int er, 
                                             (mant & 0xFFFFFFFFFFFFFull)));
   const double v = ldexp((double)mant, ex);   // outside the normal range (not met in practice)
   return neg ? -v : v;
+}
+
+// The same value by a shorter route where |hi|, |lo| < 2^61 and the exact sum
+// has at most 52 + K bits above the 2^K boundary (the case met in practice):
+// with t = hi + floor(lo / 2^K) and low = lo mod 2^K, V = t 2^K + low and
+// 0 <= low < 2^K, so the sign of V is the sign of t, and |V| = T 2^K + low'
+// with T = |t| (less one, and low' = 2^K - low, when t < 0 and low != 0).
+// The 53 bits kept are then T shifted left and the top of low', the bits
+// rounded off all lie in low' (K <= 32: 32-bit arithmetic), and the rounding
+// is to nearest, ties to even, as above.  Anything else takes the 128-bit route.
+template <int S>
+__device__ __forceinline__ double recombine(long long hi, long long lo, int er, int fc) {
+  if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);  // Inf / NaN operand
+  constexpr int m = LoExp<S>::value > kHiExp ? LoExp<S>::value : kHiExp;
+  constexpr int K = m - kHiExp;                 // 0, 8, 16, 24 or 32
+  static_assert(K >= 0 && K <= 32, "two-word recombination needs K <= 32");
+  constexpr long long kLim = 1ll << 61;
+  if (hi > -kLim && hi < kLim && lo > -kLim && lo < kLim) {
+    const long long t = hi + (lo >> K);
+    constexpr uint32_t lowm = (uint32_t)((1ull << K) - 1ull);
+    uint32_t low = (uint32_t)lo & lowm;
+    const bool neg = t < 0;
+    const unsigned long long T = neg ? (unsigned long long)(-t) - (low != 0u ? 1ull : 0ull) : (unsigned long long)t;
+    low = neg ? ((0u - low) & lowm) : low;
+    if (T < (1ull << 52)) {
+      if (T == 0ull && low == 0u) return 0.0;
+      const int nb = T ? 64 - __clzll((long long)T) + K : 32 - __clz((int)low);   // bits of |V|
+      int sh = nb - 53;
+      unsigned long long mant;
+      if (sh <= 0) {
+        mant = ((T << K) | (unsigned long long)low) << (-sh);
+      } else {                                   // 1 <= sh <= K - 1
+        mant = (T << (K - sh)) | (unsigned long long)(low >> sh);
+        const uint32_t rem = low & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        mant += (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
+        if (mant >> 53) {
+          mant >>= 1;
+          ++sh;
+        }
+      }
+      const int be = sh - m + er + fc + 52 + 1023;
+      if (be >= 1 && be <= 2046)
+        return __longlong_as_double(
+            (long long)(((unsigned long long)neg << 63) | (((unsigned long long)(be - 1) << 52) + mant)));
+    }
+  }
+  return recombine_wide<S>(hi, lo, er, fc);
 }
 
 // One CTA's tile: output column block nb, row tile mb, K split / job zb.
@@ -1148,7 +1195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (raw)
           g.ppart[(int64_t)it.slot * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
         else
-          g.P[row * g.k + col] = recombine<S>(hi[j], lo[j], er, g.colexp[col]) - g.shift * g.Xs[row * g.k + col];
+          g.P[row * g.k + col] = recombine_wide<S>(hi[j], lo[j], er, g.colexp[col]) - g.shift * g.Xs[row * g.k + col];
       }
     }
   }
@@ -2213,39 +2260,61 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])                            \
                : "r"(taddr))
 
+// One weight group of update16's accumulators (weights W0 .. W0 + NW - 1, at
+// most four) as exact int64 sums, one a column: weight w counts
+// 2^(kBits (TOP - w)).  The group's TMEM columns are loaded together and
+// waited for once.  Each accumulator C_w is an integer-valued FP32 with
+// |C_w| <= (w + 1) 2^18 (at most 16 products of two digits of at most 2^7
+// for each of the w + 1 plane pairs); adding 1.5 x 2^23 makes its bit
+// pattern C_w + 0x4B400000, and two weights w, w + 1 are joined as
+// C_w 2^kBits + C_(w+1) (below 2^30) in 32-bit arithmetic, the offsets taken
+// off modulo 2^32 in the same step; the two halves of the group are then
+// joined in 64 bits.
+template <int W0, int NW, int TOP, int C>
+__device__ __forceinline__ void drain_u16_group(uint32_t tl, long long (&out)[C]) {
+  uint32_t v[NW][C];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    if constexpr (C == 8)
+      TC_LD8(tl + 16 * (W0 + w), v[w]);
+    else
+      TC_LD4(tl + 16 * (W0 + w), v[w]);
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  constexpr uint32_t kOff = 0x4B400000u;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    long long acc = 0;
+#pragma unroll
+    for (int a = 0; a < NW; a += 2) {
+      const uint32_t ua = __float_as_uint(__uint_as_float(v[a][j]) + 12582912.0f);
+      int h;
+      int last;
+      if (a + 1 < NW) {
+        const uint32_t ub = __float_as_uint(__uint_as_float(v[a + 1][j]) + 12582912.0f);
+        h = (int)(ua * (1u << kBits) + ub - ((1u << kBits) + 1u) * kOff);
+        last = a + 1;
+      } else {
+        h = (int)(ua - kOff);
+        last = a;
+      }
+      acc += (long long)h * (1ll << (kBits * (TOP - (W0 + last))));
+    }
+    out[j] = acc;
+  }
+}
+
 // One lane's C columns of one accumulator set of update16 into two exact int64
-// sums (digit-pair groups w < 4 and w >= 4), the weights taken in pairs
-// (w, w + 1) within each group: C_w 2^8 + C_(w+1) stays below 2^30.
+// sums: digit-pair groups w < 4 (hi, weight w counting 2^(kBits (3 - w))) and
+// w >= 4 (lo, 2^(kBits (S - 1 - w))).
 template <int S, int C = 8>
 __device__ __forceinline__ void drain_u16(uint32_t tl, long long (&hi)[C], long long (&lo)[C]) {
+  drain_u16_group<0, (S < 4 ? S : 4), 3, C>(tl, hi);
+  if constexpr (S > 4) {
+    drain_u16_group<4, S - 4, S - 1, C>(tl, lo);
+  } else {
 #pragma unroll
-  for (int j = 0; j < C; ++j) hi[j] = lo[j] = 0;
-  int pend[C];
-#pragma unroll
-  for (int w = 0; w < S; ++w) {
-    uint32_t v[C];
-    if constexpr (C == 8)
-      TC_LD8(tl + 16 * w, v);
-    else
-      TC_LD4(tl + 16 * w, v);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int base = w < 4 ? 0 : 4;                       // first weight of its group
-    const int end = w < 4 ? (S < 4 ? S : 4) : S;           // one past its group's last
-    const bool first = ((w - base) & 1) == 0;
-    const bool paired = first ? (w + 1 < end) : true;
-    const int last_w = first ? (paired ? w + 1 : w) : w;   // weight of the pair's low digit
-    const int sh = w < 4 ? kBits * (3 - last_w) : kBits * (S - 1 - last_w);
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const int cw = int_of_f32(v[j]);
-      if (first && paired) {
-        pend[j] = cw;
-      } else {
-        const int pr = first ? cw : pend[j] * (1 << kBits) + cw;
-        if (w < 4) hi[j] += (long long)pr << sh;
-        else lo[j] += (long long)pr << sh;
-      }
-    }
+    for (int j = 0; j < C; ++j) lo[j] = 0;
   }
 }
 
