@@ -111,14 +111,14 @@ def refine_step(apply_b, Xh, delta, beta="cluster"):
     beta = "zero":    beta_ij = 0 (after a Rayleigh--Ritz preprocessing).
     """
     n, k = Xh.shape
-    W = apply_b(Xh)                                     # line 1: W = A X-hat
-    Y, T = compact_wy(Xh)                               # line 2: Algorithm 1
-    alpha = np.einsum("ij,ij->j", Xh, Xh)               # line 3: alpha_j = x_j^T x_j
-    d = np.einsum("ij,ij->j", Xh, W) / alpha            # line 4: Rayleigh quotients, Eq. (Rayleigh)
+    W = apply_b(Xh)                                     # W = A X-hat
+    Y, T = compact_wy(Xh)                               # compact WY factors, Algorithm 1
+    alpha = np.einsum("ij,ij->j", Xh, Xh)               # alpha_j = x_j^T x_j
+    d = np.einsum("ij,ij->j", Xh, W) / alpha            # Rayleigh quotients, Eq. (Rayleigh)
     R = W - Xh * d[None, :]                             # W - X-hat D-tilde_1
-    V = apply_ht(Y, T, R)                               # line 5: V = H-hat^T (W - X-hat D-tilde_1), Eq. (V-def)
+    V = apply_ht(Y, T, R)                               # V = H-hat^T (W - X-hat D-tilde_1), Eq. (V-def)
     E = np.empty((n, k))
-    for i in range(k):                                  # line 6: the four cases, Eqs. (Ediag), (Eoffdiag)
+    for i in range(k):                                  # E-tilde_L by its four cases, Eqs. (Ediag), (Eoffdiag)
         for j in range(k):
             if i == j:
                 E[i, j] = (1.0 - alpha[i]) / 2.0
@@ -127,7 +127,7 @@ def refine_step(apply_b, Xh, delta, beta="cluster"):
             else:
                 E[i, j] = V[i, j] / (d[j] - d[i])
     E[k:, :] = V[k:, :] / d[None, :]
-    Xt = Xh + apply_h(Y, T, E)                          # line 7: X-hat + H-hat E-tilde_L, Eq. (update-X)
+    Xt = Xh + apply_h(Y, T, E)                          # X-hat + H-hat E-tilde_L, Eq. (update-X)
     return Xt, StepInfo(d=d, alpha=alpha, R=R, V=V, E=E, Y=Y, T=T, W=W,
                         res_fro=float(np.linalg.norm(R)), e_fro=float(np.linalg.norm(E)))
 

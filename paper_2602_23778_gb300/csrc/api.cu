@@ -1288,8 +1288,9 @@ int eigref_refine_batched(eigref_handle h, int count, const eigref_problem* prob
   return status;
 }
 
-// G = X^T X, S = X^T P over all n rows (lines 3-4 of Algorithm 4 on their
-// own) through the kernels the sweeps use.
+// G = X^T X, S = X^T P over all n rows (the Gram sums behind the Rayleigh
+// quotients of Algorithm 4, Eq. Rayleigh, on their own) through the kernels
+// the sweeps use.
 int eigref_gram(eigref_handle h, const double* X, int64_t ldx, const double* P, int64_t ldp, int64_t n, int k,
                 int precision, int slices, double* G, double* S) {
   if (!h) return EIGREF_E_INVALID;

@@ -1,7 +1,7 @@
-// FP64 kernels of one refinement sweep: the product W = B X (plain FP64
-// form, line 1 of Algorithm 4), the Gram reductions X^T X and X^T W
-// (lines 3-4), the row update of the rows below the leading k x k block
-// (line 7 in the folded form), the per-sweep statistics and stopping test
+// FP64 kernels of one refinement sweep of Algorithm 4: the product W = B X
+// (plain FP64 form), the Gram reductions X^T X and X^T W (Rayleigh quotients,
+// Eq. Rayleigh), the row update of the rows below the leading k x k block
+// (Eq. update-X in the folded form), the per-sweep statistics and stopping test
 // (Section 3.1.3), and column normalisation.
 //
 // GB300 runs FP64 at about 2 DFMA per clock per SM (1.1 TFLOP/s measured for
@@ -305,11 +305,12 @@ void launch_gram(const double* X, const double* P, int k, int64_t r0, int64_t r1
 }
 
 // ---------------------------------------------------------------------------
-// Row update below the leading block (rows k..n-1), folded form of line 7:
+// Row update below the leading block (rows k..n-1), folded form of the update
+// X-tilde = X-hat + H-hat E-tilde_L (Algorithm 4, Eq. update-X):
 //   x' = x + (w - x o d) / d - x F,   F = M D^-1 + N
 // with per-CTA partial column sums of x'^2, of the residual r = w - x o d and
 // of the rows of V2 = R2 - X2 M (E21 = V2 D^-1, the lower block of E-tilde_L
-// in line 6): ||E21||_F is formed from explicit rows, as the stopping test of
+// in Algorithm 4): ||E21||_F is formed from explicit rows, as the stopping test of
 // Section 3.1.3 reads it, not from k x k Gram quantities (whose difference
 // cancels once the correction falls below sqrt(u)).
 // ---------------------------------------------------------------------------

@@ -1,15 +1,16 @@
-// The k x k stage of one sweep (Algorithm 4, lines 2-6 and the top block of
-// line 7), in the folded form the GPU uses.  With B the refined operator,
+// The k x k stage of one sweep of Algorithm 4 (everything between the product
+// and the row update, and the top block of the update), in the folded form the
+// GPU uses.  With B the refined operator,
 // W = B X, subscript 1 = rows 0..k-1 and 2 = rows k..n-1:
 //
 //   G = X^T X, S = X^T W (split into the top block G1, S1 and the rest G2, S2)
-//   alpha_j = G_jj, d_j = S_jj / G_jj                  (lines 3-4, Eq. Rayleigh)
+//   alpha_j = G_jj, d_j = S_jj / G_jj                  (Eq. Rayleigh)
 //   R1 = W1 - X1 D,  Y1 = X1 - I                       (Algorithm 1: Y = X - I_{n,k})
 //   Y^T R = (S - G D) - R1,  Z = S2 - G2 D = X2^T R2
 //   M = T^T (Y^T R) = -Y1^{-1} (Y^T R)                 (T = -Y1^{-T})
 //   V1 = R1 - Y1 M = S - G D (= X^T R: top rows of V = H^T R, Eq. V-def;
 //        V2 = R2 - X2 M is formed by the row update)
-//   E11 by the four cases of line 6 (Eqs. Ediag, Eoffdiag, beta)
+//   E11 by the four cases of Algorithm 4 (Eqs. Ediag, Eoffdiag, beta)
 //   Y^T E = Y1^T E11 + (Z - G2 M) D^-1                  (E21 = V2 D^-1)
 // V1 needs no product: R1 + Y^T R = X1^T R1 + X2^T R2 = X^T R = S - G D, and
 // R1 - Y1 M = R1 + Y^T R.  (S - G D is the difference the sweep forms for
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256) kk_gemm_kernel(SweepBufs b, int k) {
   kk_gemm_body<MODE, TT>(b, k, blockIdx.x, blockIdx.y, done);
 }
 
-// E11 by the cases of line 6 of Algorithm 4, one block per column j, plus the
+// E11 by the cases of Algorithm 4 (Eqs. Ediag, Eoffdiag), one block per column j, plus the
 // column sum the finalize step needs: ||E11(:,j)||^2.
 __device__ __forceinline__ void kk_e11_body(const SweepBufs& b, int k, double delta, int beta_zero, int j, int vb) {
   __shared__ double sh[32];

@@ -1,4 +1,4 @@
-// CSR SpMM over k right-hand columns: P = A X - shift X (line 1 of
+// CSR SpMM over k right-hand columns: P = A X - shift X (the product of
 // Algorithm 4 for sparse A; Table tab:cost prices it at O(nnz(A) k)).
 //
 // X and P are row-major n x k, so the k values a nonzero a_il multiplies sit

@@ -111,7 +111,7 @@ def test_correction_norm_at_converged_iterate(eig, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "bf16"])
 def test_delta_tie_on_gpu(eig, precision):
-    """The threshold of line 6 on the GPU: Rayleigh quotients exactly delta
+    """The cluster threshold of Algorithm 4 on the GPU: Rayleigh quotients exactly delta
     apart take the beta branch (the sweep stays finite and small, as the
     oracle's), one ulp more takes the division (|E| huge: both report
     divergence after the first sweep)."""

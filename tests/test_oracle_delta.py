@@ -1,7 +1,8 @@
-"""Pins of the cluster threshold of Algorithm 4 (line 6) against what Section
+"""Pins of the cluster threshold of Algorithm 4 (the choice between beta and
+the gap division in E-tilde_L) against what Section
 3.1.3 fixes: delta = c ||A|| u with c = 10 and u the unit roundoff of binary64
-(2^-53), and the tie |d_j - d_i| = delta taking the beta branch (the test of
-line 6 is "<= delta").  The Rayleigh quotients of the crafted cases are exact
+(2^-53), and the tie |d_j - d_i| = delta taking the beta branch (the test in
+Algorithm 4 is "<= delta").  The Rayleigh quotients of the crafted cases are exact
 binary64 numbers, so the two branches are decided exactly, one ulp apart."""
 import numpy as np
 import pytest
