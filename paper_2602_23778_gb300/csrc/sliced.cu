@@ -2191,14 +2191,17 @@ void launch_slice_rows(const double* Y, int64_t n, int k, int n_pad, int K, __ha
 //              into columns 128 + 16 s ...
 //   warps 2-5  one thread per tile row: cut the X row into the A operand
 //              (running up to two tiles ahead of the epilogue).
-//   warps 6-13 two threads per tile row (warps w and w + 4 share a TMEM lane
-//              group), eight columns each: drain the accumulators, rebuild
-//              each (X F)_ij with integer arithmetic up to its bit pattern,
-//              form x' = x + (w - x d_j) / d_j - (X F)_ij in FP64, write it
+//   warps 6-21 four threads per tile row (warps w, w + 4, w + 8, w + 12 share
+//              a TMEM lane group), four columns each: drain the accumulators,
+//              rebuild each (X F)_ij with integer arithmetic up to its bit
+//              pattern, form x' = x + (w - x d_j) / d_j - (X F)_ij in FP64 as
+//              the one fused multiply-add w (1 / d_j) - (X F)_ij (the same
+//              value in exact arithmetic; the rounding of 1 / d_j scales
+//              column j as a whole, which the normalisation takes out), write it
 //              over the X tile in shared memory and store it with TMA (32 rows
 //              per lane group), keeping the column sums of x'^2,
 //              (w - x d_j)^2 and v^2, v = (w - x d_j) - (X M)_ij the row of
-//              V2 = R2 - X2 M (E21 = V2 D^-1, line 6 of Algorithm 4).
+//              V2 = R2 - X2 M (E21 = V2 D^-1, the lower block of E-tilde_L in Algorithm 4).
 // Accumulators and A operands are double-
 // buffered, the X / W tiles triple-buffered.  Every wait is bounded; on expiry
 // the CTA records a timeout.  No FP64 instruction outside the update formula
@@ -2540,7 +2543,8 @@ __global__ void __launch_bounds__(kU16Threads, 1) update16_kernel(const __grid_c
         const double f0 = recombine<S>(hi[2 * q], lo[2 * q], e_row, fexp_s[j0]);
         const double f1 = recombine<S>(hi[2 * q + 1], lo[2 * q + 1], e_row, fexp_s[j1]);
         const double r0 = fma(-x2.x, d_s[j0], wv.x), r1 = fma(-x2.y, d_s[j1], wv.y);
-        const double n0 = fma(r0, dinv_s[j0], x2.x) - f0, n1 = fma(r1, dinv_s[j1], x2.y) - f1;
+        // x' = x + r / d - f = w / d - f, one fused multiply-add
+        const double n0 = fma(wv.x, dinv_s[j0], -f0), n1 = fma(wv.y, dinv_s[j1], -f1);
         const double v0 = r0 - xm[2 * q], v1 = r1 - xm[2 * q + 1];   // rows of V2 = R2 - X2 M
         if (live) {
           sq[2 * q] = fma(n0, n0, sq[2 * q]);
