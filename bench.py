@@ -45,8 +45,19 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# nominal dense rates per GPU (TFLOP/s): used only as ratios to the measured BF16 peak
-NOMINAL = {"bf16": 2250.0, "fp64": 1.25, "int8": 4500.0}
+# FP64 pipe: 2 DFMA a clock and SM, the nominal 1.25 TFLOP/s over 152 SMs at
+# the 2070 MHz maximum clock (1.25e12 / (152 x 2.07e9 x 2) = 1.99)
+SMS, DFMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
+
+
+def fp64_peak(clocks):
+    """FP64 arithmetic peak (TFLOP/s) from the unit count and the SM clock
+    sampled during the timed region (the maximum clock when unsampled)."""
+    mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+    return SMS * DFMA_PER_CLK * 2 * mhz * 1e6 / 1e12
+
+
+FP64_NOTE = "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock (nominal 1.25 TFLOP/s at 2070 MHz)"
 
 
 class ClockSampler:
@@ -309,7 +320,8 @@ def measure_laplacian(args, world, rank, local, steps=None):
     pk, pk_kind = peaks()
     gbs = bytes_launch / (launch_ms * 1e-3) / 1e9
     tfs = flops_launch / (launch_ms * 1e-3) / 1e12
-    fp64_peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+    clocks = clk.summary()
+    peak64 = fp64_peak(clocks)
     out = {"metric": METRIC, "value": world * 1000.0 / ms_step, "unit": UNIT, "n_gpus": world,
            "steps": rep["iterations"], "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f64+bf16-slices",
@@ -319,14 +331,13 @@ def measure_laplacian(args, world, rank, local, steps=None):
                                                "Gram products and row update as digit planes on the tensor cores"),
                       "split_k_gram": rep["ksplit"] or None,
                       "l2": "inputs larger than L2 (CSR 65 MB + X 131 MB + P 131 MB per SpMM); no flush"},
-           "roofline": {"bound": "alu", "kernel": "spmm_csr_vec2_kernel", "achieved": tfs, "peak": fp64_peak,
-                        "unit": "TFLOP/s", "frac": tfs / fp64_peak, "traffic": traffic_for("spmm.cu", "csr"),
+           "roofline": {"bound": "alu", "kernel": "spmm_csr_vec2_kernel", "achieved": tfs, "peak": peak64,
+                        "unit": "TFLOP/s", "frac": tfs / peak64, "traffic": traffic_for("spmm.cu", "csr"),
                         "launch_ms": launch_ms, "algorithmic_flops_per_launch": flops_launch,
-                        "peak_note": "FP64 pipe: measured BF16 burst x nominal FP64/BF16 ratio (1.25/2250), of "
-                                     + pk_kind,
+                        "peak_note": FP64_NOTE,
                         "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
                                 "algorithmic_bytes_per_launch": bytes_launch}},
-           "gpu_launches": int(rep["kernel_launches"]), "clocks": clk.summary(),
+           "gpu_launches": int(rep["kernel_launches"]), "clocks": clocks,
            "status": rep["status_string"]}
     if rank == 0 and precision != "fp64" and not args.no_fp64_compare:
         r64 = timed(dict(kw, precision="fp64"), steps)
@@ -382,8 +393,8 @@ def measure_batched(args, world, rank, local, steps=None):
     pk, pk_kind = peaks()
     if prec == "fp64":
         flops = sum(2.0 * p.n * p.n * p.k for p in ps)
-        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-        roof = {"bound": "alu", "peak_note": "FP64 pipe: measured BF16 burst x nominal FP64/BF16, of %s" % pk_kind}
+        peak = fp64_peak(clk.summary())
+        roof = {"bound": "alu", "peak_note": FP64_NOTE}
     else:
         flops = sum(sliced_info(prec, p.n, p.k)["executed_flops"] for p in ps)
         peak = pk["bf16_tflops_sustained"]
@@ -615,9 +626,8 @@ def main():
     prod_ms = rep["product_ms"] / max(1, rep["product_launches"])
     if precision == "fp64":
         flops = 2.0 * n * n * k
-        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-        roof = {"bound": "alu", "kernel": "gemm_fp64_kernel", "peak_note":
-                "FP64 peak = measured BF16 burst x nominal FP64/BF16 ratio (1.25/2250), of %s" % pk_kind}
+        peak = fp64_peak(clk.summary())
+        roof = {"bound": "alu", "kernel": "gemm_fp64_kernel", "peak_note": FP64_NOTE}
         kfile = "fp64.cu"
     else:
         from paper_2602_23778_gb300 import sliced_info

@@ -20,87 +20,19 @@ namespace eigref {
 // ---------------------------------------------------------------------------
 // P = A X - shift Xs (Xs = X unless given).  A n x n row-major (lda), X, Xs
 // and P n x k row-major.
-// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread.
+// 16 x 16 output tile per CTA, one output per thread: the K sum is a single
+// FMA chain over l = 0 .. n-1, operands read through L1 (a warp reads two
+// elements of A, one per row, and one 128-byte row of X a step).  GB300 issues
+// about 2 DFMA a clock and SM, so the kernel is bound by the FP64 pipe, not by
+// its loads; n k / 256 CTAs (8192 at n = 16384, k = 128) leave no tail
+// worth the name, where 64 x 64 tiles with a shared-memory K panel ran 1.68
+// waves and reached 0.83 of this kernel's rate.
 // ---------------------------------------------------------------------------
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
-
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(const double* __restrict__ A, int64_t lda,
                                                         const double* __restrict__ X,
                                                         double* __restrict__ P, int64_t n, int k,
                                                         double shift, const double* __restrict__ Xs,
                                                         const Control* ctl) {
-  if (ctl && ctl->done) return;
-  __shared__ double As[GB_K][GB_M + 1];
-  __shared__ double Bs[GB_K][GB_N];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * GB_M;
-  const int n0 = blockIdx.y * GB_N;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-
-  double ra[4], rb[4];
-  auto load = [&](int64_t k0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      int r = e >> 4, c = e & 15;
-      int64_t gr = m0 + r, gc = k0 + c;
-      ra[q] = (gr < n && gc < n) ? A[gr * lda + gc] : 0.0;
-      int rr = e >> 6, cc = e & 63;
-      int64_t gk = k0 + rr;
-      int gn = n0 + cc;
-      rb[q] = (gk < n && gn < k) ? X[gk * k + gn] : 0.0;
-    }
-  };
-  load(0);
-  for (int64_t k0 = 0; k0 < n; k0 += GB_K) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      As[e & 15][e >> 4] = ra[q];
-      Bs[e >> 6][e & 63] = rb[q];
-    }
-    __syncthreads();
-    if (k0 + GB_K < n) load(k0 + GB_K);
-#pragma unroll
-    for (int kk = 0; kk < GB_K; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t row = m0 + ty * 4 + i;
-    if (row >= n) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int col = n0 + tx * 4 + j;
-      if (col < k) P[row * k + col] = acc[i][j] - shift * Xs[row * k + col];
-    }
-  }
-}
-
-// The same product for problems whose 64 x 64 tiles would leave most SMs
-// idle (small n, or k far below 64): 16 x 16 output tile per CTA, one output
-// per thread, the K sum in the same order as above (a single FMA chain over
-// l = 0 .. n-1), operands read through L1 (a warp reads 2 rows of A and one
-// 128-byte row of X per step).  FP64-pipe bound with many CTAs per SM.
-__global__ void __launch_bounds__(256) gemm_fp64_small_kernel(const double* __restrict__ A, int64_t lda,
-                                                              const double* __restrict__ X,
-                                                              double* __restrict__ P, int64_t n, int k,
-                                                              double shift, const double* __restrict__ Xs,
-                                                              const Control* ctl) {
   if (ctl && ctl->done) return;
   const int tid = threadIdx.x;
   const int64_t row = (int64_t)blockIdx.x * 16 + (tid >> 4);
@@ -125,14 +57,7 @@ __global__ void __launch_bounds__(256) gemm_fp64_small_kernel(const double* __re
 
 void launch_gemm_fp64(const double* A, int64_t lda, const double* X, double* P, int64_t n, int k,
                       double shift, const Control* ctl, cudaStream_t s, const double* Xs) {
-  dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((k + GB_N - 1) / GB_N));
-  int sms = 152, dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if ((int64_t)grid.x * grid.y < 2 * sms || k <= 16) {
-    const dim3 g2((unsigned)((n + 15) / 16), (unsigned)((k + 15) / 16));
-    gemm_fp64_small_kernel<<<g2, 256, 0, s>>>(A, lda, X, P, n, k, shift, Xs ? Xs : X, ctl);
-    return;
-  }
+  const dim3 grid((unsigned)((n + 15) / 16), (unsigned)((k + 15) / 16));
   gemm_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, X, P, n, k, shift, Xs ? Xs : X, ctl);
 }
 
