@@ -252,7 +252,7 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 // pattern: no FP64 instruction (FP64 runs at a small fraction of the integer
 // rate on this part), and the same value as rounding the exact sum once.
 template <int S>
-__device__ __forceinline__ double recombine_wide(long long hi, long long lo, int er, int fc) {
+__device__ __forceinline__ double recombine128(long long hi, long long lo, int er, int fc) {
   if (er == kNonFinite || fc == kNonFinite) return __longlong_as_double(0x7FF8000000000000ll);  // Inf / NaN operand
   constexpr int m = LoExp<S>::value > kHiExp ? LoExp<S>::value : kHiExp;
   constexpr int K = m - kHiExp;                 // lo = 0 when S < 4 (no weight group >= 4)
@@ -291,6 +291,13 @@ __device__ __forceinline__ double recombine_wide(long long hi, long long lo, int
                                             (mant & 0xFFFFFFFFFFFFFull)));
   const double v = ldexp((double)mant, ex);   // outside the normal range (not met in practice)
   return neg ? -v : v;
+}
+
+// The same, out of line: the rare case of the two-word route below, kept out
+// of its callers' instruction stream.
+template <int S>
+__device__ __noinline__ double recombine_wide(long long hi, long long lo, int er, int fc) {
+  return recombine128<S>(hi, lo, er, fc);
 }
 
 // The same value by a shorter route where |hi|, |lo| < 2^61 and the exact sum
@@ -1195,7 +1202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (raw)
           g.ppart[(int64_t)it.slot * g.m_valid * g.k + row * g.k + col] = make_longlong2(hi[j], lo[j]);
         else
-          g.P[row * g.k + col] = recombine_wide<S>(hi[j], lo[j], er, g.colexp[col]) - g.shift * g.Xs[row * g.k + col];
+          g.P[row * g.k + col] = recombine128<S>(hi[j], lo[j], er, g.colexp[col]) - g.shift * g.Xs[row * g.k + col];
       }
     }
   }
