@@ -49,7 +49,7 @@ enum eigref_status {
   EIGREF_E_NOT_CONVERGED = 6,  /* max_iters sweeps without meeting tol (tol > 0) */
   EIGREF_E_NONFINITE = 7,      /* a sweep produced Inf/NaN; X keeps the last finite iterate */
   EIGREF_E_TIMEOUT = 8,        /* a bounded device wait gave up */
-  EIGREF_E_UNSUPPORTED = 9     /* valid request this build does not implement */
+  EIGREF_E_UNSUPPORTED = 9     /* valid request the library does not implement */
 };
 
 /* Which eigenvectors the refinement converges to (Section 3.1 and Section 5.1).

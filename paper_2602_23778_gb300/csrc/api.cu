@@ -751,7 +751,7 @@ int refine_common(eigref_ctx* h, Problem& pr, double* X, int64_t ldx, const eigr
   return status;
 }
 
-// EIGREF_AUTO: the split form where this build has one that pays off.
+// EIGREF_AUTO: the split form where the library has one that pays off.
 int resolve_precision(int precision, bool csr, int64_t n, int k) {
   if (precision != EIGREF_AUTO) return precision;
   if (csr) return k <= 16 ? EIGREF_BF16_SLICES : EIGREF_FP64;
